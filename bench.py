@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Throughput of the whole Lagrangian step of the IP + MLS-IBM method on GB300.
+
+One step = internal forces of the four potentials, MLS interpolation at every
+face centroid with the direct-forcing marker force, probe gradient and
+traction, node update, and spreading onto the staggered grid (with the
+previous step's footprint cleared), as three kernel launches of ibm_step.
+
+Metric: Lagrangian node-steps/s (vertices x steps / device time).  Default
+workload: 1000 icosphere level-3 drops (642 nodes, 1280 faces each), radii
+U[0.015, 0.03], Poisson-disk placed in the unit periodic box, 512^3 MAC grid,
+frozen velocity = 32 random divergence-free Fourier modes (amplitude 1,
+wavenumbers 1-8), k_s ~ U[0.5, 2], k_b ~ U[0.005, 0.02] per body.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun every rank runs its own independent replica (bodies do not
+interact), so the job scales weakly with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+from paper_1612_03399_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Lagrangian node-steps/s (force+MLS interp+advance+spread), % HBM roofline"
+UNIT = "node-steps/s"
+
+WORKLOADS = {
+    "drops1000": (lambda seed: W.batched_drops(1000, 3, 512, seed=seed),
+                  "1000 icosphere-L3 drops (642 nodes, 1280 faces each), radii U[0.015,0.03], "
+                  "Poisson-disk placed, 512^3 MAC grid, 32-mode divergence-free Fourier velocity "
+                  "(amplitude 1, |k| 1-8), k_s~U[0.5,2], k_b~U[0.005,0.02]"),
+    "uneven4096": (lambda seed: W.uneven_bodies(4096, 768, seed=seed),
+                   "4096 closed bodies, icosphere levels 2/3/4/5 w.p. 0.4/0.3/0.2/0.1, radius "
+                   "0.005*2^(L-2), ellipsoid stretch U[1,1.5], 768^3 MAC grid, Fourier velocity"),
+    "drop64": (lambda seed: W.single_drop(3, 64),
+               "one icosphere-L3 drop r=0.25 in frozen shear u=y-0.5, 64^3 grid"),
+    "membranes": (lambda seed: W.membranes(8, 512, seed=seed),
+                  "closed ellipsoidal membrane (655362 nodes) + two clamped leaflet sheets "
+                  "(~100k faces each), 512^3 grid, Fourier velocity amplitude 2"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="drops1000", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--patch", type=int, default=0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (independent replicas; barrier + max over ranks)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(ws, val, device):
+    if ws == 1:
+        return val
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(ws, val, device):
+    if ws == 1:
+        return val
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# algorithmic byte model of the two main kernels
+# ---------------------------------------------------------------------------
+
+def touched_nodes(wl, x, ctx, device):
+    """Unique grid nodes per velocity component touched by the centroid
+    stencils and by the centroid-or-probe stencils (3x3x3 nearest-node
+    supports on the MAC lattices)."""
+    n = wl.grid.n
+    h = torch.tensor(wl.grid.h, dtype=torch.float64, device=device)
+    origins = torch.tensor(np.concatenate([np.repeat(b.origin[None], len(b.tri), 0)
+                                           for b in wl.bodies]), device=device)
+    tri = torch.tensor(np.concatenate([b.tri + int(ctx.v_off[i]) for i, b in enumerate(wl.bodies)]),
+                       dtype=torch.long, device=device)
+    closed = torch.tensor(np.concatenate([np.full(len(b.tri), b.closed) for b in wl.bodies]),
+                          device=device)
+    X = x.double().T
+    xa, xb, xc = X[tri[:, 0]], X[tri[:, 1]], X[tri[:, 2]]
+    c = (xa + xb + xc) / 3 + origins
+    N = torch.cross(xb - xa, xc - xa, dim=1)
+    nrm = N / N.norm(dim=1, keepdim=True)
+    ph = float(h.mean())
+    s = torch.tensor([-1, 0, 1], device=device)
+    offs = ((0.0, 0.5, 0.5), (0.5, 0.0, 0.5), (0.5, 0.5, 0.0))
+    res_c, res_all = [], []
+    for comp in range(3):
+        mark_c = torch.zeros(n[0] * n[1] * n[2], dtype=torch.bool, device=device)
+        mark_a = torch.zeros_like(mark_c)
+        for which, P in enumerate([c, c + ph * nrm, (c - ph * nrm)[~closed]]):
+            for chunk in torch.split(P, 1 << 18):
+                t = chunk / h - torch.tensor(offs[comp], dtype=torch.float64, device=device)
+                ic = torch.floor(t + 0.5).long()
+                ix = torch.remainder(ic[:, 0:1] + s, n[0])
+                iy = torch.remainder(ic[:, 1:2] + s, n[1])
+                iz = torch.remainder(ic[:, 2:3] + s, n[2])
+                flat = ((iz[:, :, None, None] * n[1] + iy[:, None, :, None]) * n[0]
+                        + ix[:, None, None, :]).reshape(-1)
+                mark_a[flat] = True
+                if which == 0:
+                    mark_c[flat] = True
+        res_c.append(int(mark_c.sum()))
+        res_all.append(int(mark_a.sum()))
+    return res_c, res_all
+
+
+def byte_model(wl, ctx, x, device):
+    nv = sum(len(b.rest) for b in wl.bodies)
+    nf = sum(len(b.tri) for b in wl.bodies)
+    ne = ctx.E
+    centre_nodes, all_nodes = touched_nodes(wl, x, ctx, device)
+    marker = (nv * 24            # x, v gathered (each vertex once)
+              + nf * 12          # F_ext written
+              + 4 * sum(all_nodes)          # velocity nodes read (centroid + probe stencils)
+              + 8 * sum(centre_nodes))      # force nodes read-modify-written by the spread
+    force = (nv * (12 + 12 + 24 + 1)        # x, v read; x', v' written; clamp flag
+             + ne * 12                      # l0, (cos, sin) theta0
+             + nf * (4 + 12))               # A0_f, F_ext read
+    return {"marker": marker, "force": force, "nodes_centre": centre_nodes, "nodes_all": all_nodes}
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch of `kernel_key` from the committed ncu summary,
+    or None when the kernels changed since those counters were taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        from paper_1612_03399_gb300 import build as B
+        d = json.load(open(p))
+        if d.get("source_digest") != B._digest():
+            return None
+        return d.get("kernels", {}).get(kernel_key)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(wl, n_bodies, steps, fields_cpu=None):
+    """Time the FP64 oracle, as it stands, on the first n_bodies bodies of the
+    workload (same grid and field) for `steps` steps; node-steps/s."""
+    from oracle import ibm_oracle as O
+    sub = wl.bodies[:n_bodies]
+    ob = [O.Body(b.rest, b.tri, b.origin, closed=b.closed, clamped=b.clamped, ks=b.ks, kb=b.kb,
+                 ka=b.ka, kA=b.kA, kv=b.kv, mass=b.mass) for b in sub]
+    prm = O.Params(wl.grid.n, wl.grid.L, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    if fields_cpu is None:
+        fields_cpu = W.sample_field(wl.field, wl.grid, device="cpu", dtype=torch.float64)
+    xs = [torch.tensor(b.rest) for b in sub]
+    vs = [torch.zeros_like(x) for x in xs]
+    nodes = sum(len(b.rest) for b in sub)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        out = O.step(ob, xs, vs, fields_cpu, prm)
+        xs = [t.detach() for t in out["x_next"]]
+        vs = [t.detach() for t in out["v_next"]]
+    dt = time.perf_counter() - t0
+    return nodes * steps / dt, dt, nodes
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    make, descr = WORKLOADS[args.workload]
+    wl = make(1)
+    nb = min(len(wl.bodies), 8)
+    fields = W.sample_field(wl.field, wl.grid, device="cpu", dtype=torch.float64)
+    oracle_sample_rate(wl, 1, 1, fields)          # warm-up (allocator, threads)
+    rate, secs, nodes = oracle_sample_rate(wl, nb, max(1, args.steps), fields)
+    cores = torch.get_num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": descr, "sample_bodies": nb},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{nb} bodies ({nodes} nodes) of the workload, {args.steps} steps"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GB300 arm
+# ---------------------------------------------------------------------------
+
+def run_gb300(args, ws, rank, local):
+    from paper_1612_03399_gb300 import _lib
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    make, descr = WORKLOADS[args.workload]
+    wl = make(1 + rank)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
+                       patch_size=args.patch, device=local)
+    stream = torch.cuda.current_stream(device)
+    fields = W.sample_field(wl.field, wl.grid, device=device, dtype=torch.float32)
+    nx, ny, nz = wl.grid.n
+    f = tuple(torch.zeros((nz, ny, nx), dtype=torch.float32, device=device) for _ in range(3))
+    xa, va = ctx.init_state()
+    xb, vb = torch.empty_like(xa), torch.empty_like(va)
+    bytes_model = byte_model(wl, ctx, xa, device) if rank == 0 else None
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)   # > L2 (129 MB)
+    ctx.set_phase_timing(True)
+    for _ in range(max(args.warmup, 3)):
+        ctx.step(xa, va, fields, xb, vb, f)
+        xa, va, xb, vb = xb, vb, xa, va
+    ctx.check_device_error()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    phases = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        ctx.step(xa, va, fields, xb, vb, f)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        phases.append(ctx.phase_times())
+        xa, va, xb, vb = xb, vb, xa, va
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ctx.check_device_error()
+    barrier(ws)
+    t_max = reduce_max(ws, total_ms, device)
+    nodes_all = reduce_sum(ws, float(ctx.V), device)
+    value = nodes_all * args.steps / (t_max * 1e-3)
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        xh = xa.cpu().pin_memory()
+        vh = va.cpu().pin_memory()
+        xo = torch.empty_like(xh).pin_memory()
+        vo = torch.empty_like(vh).pin_memory()
+        barrier(ws)
+        e2e_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            xa.copy_(xh, non_blocking=True)
+            va.copy_(vh, non_blocking=True)
+            ctx.step(xa, va, fields, xb, vb, f)
+            xo.copy_(xb, non_blocking=True)
+            vo.copy_(vb, non_blocking=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            e2e_ms += ev0.elapsed_time(ev1)
+            xh, xo = xo, xh
+            vh, vo = vo, vh
+        e2e_max = reduce_max(ws, e2e_ms, device)
+        nbytes = 2 * 3 * ctx.V * 4
+        e2e = {"value": nodes_all * args.steps / (e2e_max * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    if rank != 0:
+        return
+    ph = np.array(phases)
+    mean_ph = ph.mean(0)
+    names = ["clear", "marker", "force"]
+    dom = int(np.argmax(mean_ph[1:])) + 1
+    peak, peak_kind = hbm_peak()
+    algo = bytes_model[names[dom]]
+    achieved = algo / (mean_ph[dom] * 1e-3) / 1e9
+    traffic = ncu_traffic(names[dom])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": descr, "bodies": ctx.B, "vertices": ctx.V, "faces": ctx.F,
+                   "grid": list(wl.grid.n), "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"{ws} independent replica(s)"},
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes": algo},
+        "phases_ms": {n: float(m) for n, m in zip(names, mean_ph)},
+        "kernel_frac": {n: float(m / mean_ph.sum()) for n, m in zip(names, mean_ph)},
+        "other_kernel": {n: {"algorithmic_bytes": bytes_model[n],
+                             "achieved_gbs": bytes_model[n] / (mean_ph[k] * 1e-3) / 1e9}
+                         for k, n in enumerate(names) if n != "clear"},
+        "gpu_launches": 3 * args.steps,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        fields_cpu = tuple(t.double().cpu() for t in fields)
+        oracle_sample_rate(wl, 1, 1, fields_cpu)
+        nb = 16
+        rate, secs, nodes = oracle_sample_rate(wl, nb, 2, fields_cpu)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": torch.get_num_threads(),
+                                "kind": "oracle",
+                                "sample": f"{nb} of the {ctx.B} bodies ({nodes} nodes) on the full "
+                                          f"grid and field, 2 steps, {secs:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_gb300(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

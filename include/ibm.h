@@ -1,0 +1,190 @@
+/*
+ * ibm.h -- C ABI of the GB300 Lagrangian hot path of the interaction-potential
+ * + moving-least-squares immersed-boundary method (Spandan et al., "A parallel
+ * interaction potential approach coupled with the immersed boundary method for
+ * fully resolved simulations of deformable interfaces and membranes").
+ *
+ * One step, for many triangulated deformable bodies at once, with the Eulerian
+ * velocity frozen:
+ *   (a) internal nodal forces from the four interaction potentials (Sec. 2.3),
+ *   (b) MLS interpolation of the staggered-grid velocity to the face-centroid
+ *       markers, direct-forcing marker force and probe traction (Sec. 2.2),
+ *   (c) node update m x'' = F_ext + F_int (Sec. 2.3; Sec. 5, step 4),
+ *   (d) spreading of the marker forces back onto the grid (Sec. 2.2, Eq. mls_cl).
+ *
+ * Conventions (all entry points):
+ *  - Every float* / double* argument except those marked "host" is a DEVICE
+ *    pointer on the context's device, owned by the caller.  The context owns
+ *    only topology, rest data and scratch.
+ *  - Vertex arrays are float32 SoA [3][V]: x components first, then y, then z,
+ *    vertices of body b at [v_off(b), v_off(b) + n_vert(b)) in body order.
+ *    Positions are BODY-FRAME coordinates x - origin(b) (origin given per body
+ *    at creation), which keeps edge vectors accurate in float32.
+ *  - Per-face (per-marker) arrays are float32 SoA [3][F], faces in body order.
+ *  - Eulerian fields are float32 [nz][ny][nx] (x fastest) on the MAC staggered
+ *    lattice of the triply periodic box [0,L)^3: u at (i, j+1/2, k+1/2) h,
+ *    v at (i+1/2, j, k+1/2) h, w at (i+1/2, j+1/2, k) h; force fields fx, fy,
+ *    fz live on the u, v, w lattices respectively.
+ *  - All calls are asynchronous and ordered on the context's stream (set with
+ *    ibm_set_stream; default: the legacy default stream).  Only
+ *    ibm_create_bodies and ibm_check_device_error synchronise.
+ *  - Errors: a call returns an ibm_status; ibm_last_error() gives the message.
+ *    No C++ exception crosses this interface.  Sizes are validated on the host.
+ *  - The library never falls back to the CPU: without a usable CUDA device
+ *    ibm_create_bodies returns IBM_ERR_CUDA.
+ */
+#ifndef IBM_GB300_H
+#define IBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibm_ctx ibm_ctx;
+
+typedef enum {
+  IBM_OK = 0,
+  IBM_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad parameter          */
+  IBM_ERR_MESH = 2,         /* non-manifold / mis-oriented / degenerate mesh  */
+  IBM_ERR_CUDA = 3,         /* CUDA runtime error (message has the details)   */
+  IBM_ERR_DEVICE = 4,       /* device error word set by a kernel              */
+  IBM_ERR_OOM = 5,          /* device allocation failed                       */
+  IBM_ERR_UNSUPPORTED = 6   /* request outside the supported limits           */
+} ibm_status;
+
+/* One triangulated body (Sec. 2.2, Fig. lagmesh; the GTS-style vertex/face
+ * lists of Sec. 5).  All pointers are HOST pointers, read during
+ * ibm_create_bodies only.  Bodies whose (n_vert, tri) are identical share one
+ * device copy of the topology tables. */
+typedef struct {
+  int32_t n_vert;
+  int32_t n_face;
+  const double* rest;      /* host [n_vert][3], absolute rest positions; the rest
+                              state of every potential (l0, theta0, A0_f, A0, V0)  */
+  const int32_t* tri;      /* host [n_face][3], counter-clockwise seen from the
+                              outside (outward normals), 0-based vertex ids        */
+  const uint8_t* clamped;  /* host [n_vert] or NULL; nonzero = node held fixed     */
+  double origin[3];        /* body-frame origin (absolute), a point near the body  */
+  double ks;               /* in-plane spring constant k_e (Eq. elaspot)           */
+  double kb;               /* bending constant k_b                                 */
+  double ka;               /* local area constant (per face, Eq. areapot)          */
+  double kA;               /* global area constant (per body)                      */
+  double kv;               /* volume constant (closed bodies; ignored if open)     */
+  double mass;             /* node mass m (Sec. 2.3; 1 for drops)                  */
+  int32_t closed;          /* 1 closed surface (one outward probe), 0 open sheet
+                              (two probes, Sec. 2.2)                               */
+  int32_t reserved;
+} ibm_body_desc;
+
+typedef struct {
+  int32_t n[3];            /* cells per direction (nx, ny, nz), each >= 4 */
+  int32_t reserved;
+  double L[3];             /* box lengths; h_d = L_d / n_d                */
+} ibm_grid_desc;
+
+typedef struct {
+  double dt;               /* structural and forcing time step                   */
+  double mu;               /* fluid viscosity in tau = mu (grad u + grad u^T)    */
+  double alpha;            /* MLS weight shape parameter (Eq. mls_w); 0 -> 0.3   */
+  double probe_h;          /* probe length; <= 0 -> mean grid spacing (Sec. 2.2) */
+  int32_t theta0_zero;     /* 1: W_b = k_b(1 - cos theta) literally; 0: rest angle */
+  int32_t forward_euler;   /* 1: forward Euler node update; 0: symplectic Euler  */
+  int32_t patch_size;      /* vertices per force-kernel block; 0 -> default (128) */
+  int32_t reserved;
+} ibm_params;
+
+/* Create a context for n_bodies bodies on CUDA device `device`: validates the
+ * meshes (Sec. 5 auxiliary arrays are built here: edges, faces of each edge,
+ * the four vertices of each hinge, vertex->face incidence), computes the rest
+ * state in float64 and uploads everything.  Synchronous.  On failure *out is
+ * NULL and the status says why (IBM_ERR_MESH for bad meshes). */
+ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodies, int32_t n_bodies,
+                             const ibm_grid_desc* grid, const ibm_params* params,
+                             int32_t device);
+
+/* Free everything the context owns.  NULL is ignored. */
+void ibm_destroy(ibm_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing
+ * ibm_create_bodies when ctx is NULL).  Valid until the next call. */
+const char* ibm_last_error(const ibm_ctx* ctx);
+
+/* Stream (a cudaStream_t) on which all later calls are ordered. */
+ibm_status ibm_set_stream(ibm_ctx* ctx, void* stream);
+
+/* host out[6]: total vertices V, faces F, edges E, bodies B, distinct
+ * topologies, force-kernel work items. */
+ibm_status ibm_get_sizes(const ibm_ctx* ctx, int64_t* out);
+
+/* host out[3*B]: vertex, face, edge offset of every body. */
+ibm_status ibm_get_offsets(const ibm_ctx* ctx, int64_t* out);
+
+/* Initial state: x = rest - origin (float32, body frame), v = 0. */
+ibm_status ibm_init_state(ibm_ctx* ctx, float* x, float* v);
+
+/* Replace the elastic constants and masses: host consts[B][6] =
+ * (ks, kb, ka, kA, kv, mass) per body.  Stream-ordered. */
+ibm_status ibm_set_body_constants(ibm_ctx* ctx, const double* consts);
+
+/* Per-body surface area A and enclosed volume V (Sec. 2.3: the global area
+ * and volume of the potentials), summed in float64 in a fixed order:
+ * out[B][2] = (A, V); V is 0 for open bodies. */
+ibm_status ibm_body_measures(ibm_ctx* ctx, const float* x, double* out);
+
+/* (a) Internal forces F_int = -grad(W_e + W_b + W_a + W_A + W_v) at x
+ * (Sec. 2.3, Eqs. elaspot..areapot): F_int [3][V].  Deterministic: every
+ * element's contribution is summed per vertex in a fixed order.  energy, if
+ * not NULL: [B][5] float64 = (W_e, W_b, W_a local, W_A global, W_v). */
+ibm_status ibm_compute_forces(ibm_ctx* ctx, const float* x, float* F_int, double* energy);
+
+/* (b) MLS interpolation at the face centroids of the staggered velocity
+ * (u, v, w) (Sec. 2.2, Eqs. mls..mls_Q), direct-forcing marker force
+ * F = (V^b - U)/dt with V^b the mean velocity of the face's three nodes, and
+ * probe traction F_ext = (tau . n) A (p = 0, frozen flow; two probes on open
+ * sheets).  Outputs [3][F], each may be NULL. */
+ibm_status ibm_interpolate(ibm_ctx* ctx, const float* x, const float* v, const float* u,
+                           const float* vv, const float* w, float* U, float* F_marker,
+                           float* F_ext);
+
+/* (c) Node update with F_ext^v = sum over faces of F_ext/3 (Sec. 2.3) and the
+ * given F_int: symplectic (default) or forward Euler; clamped nodes keep x and
+ * get v = 0.  x_out/v_out may alias x/v. */
+ibm_status ibm_advance(ibm_ctx* ctx, const float* x, const float* v, const float* F_int,
+                       const float* F_ext, float* x_out, float* v_out);
+
+/* (d) Spread marker forces F_marker [3][F] at the centroids of x onto the
+ * force fields: f_i^k += c_l phi_k^l F_i^l (Eq. mls_cl).  ACCUMULATES into the
+ * caller's fields (atomic adds: summation order is not fixed). */
+ibm_status ibm_spread(ibm_ctx* ctx, const float* x, const float* F_marker, float* fx, float* fy,
+                      float* fz);
+
+#define IBM_STEP_CLEAR_PREV 1u  /* zero the grid nodes the previous ibm_step of this
+                                   context spread to, before spreading this step   */
+
+/* One whole step (a)-(d) in three launches: x, v -> x_out, v_out (must not
+ * alias x, v), spreading this step's marker forces into fx, fy, fz.  With
+ * IBM_STEP_CLEAR_PREV the fields hold exactly this step's forces afterwards,
+ * provided they held only the previous ibm_step's forces (or zeros) before. */
+ibm_status ibm_step(ibm_ctx* ctx, const float* x, const float* v, const float* u,
+                    const float* vv, const float* w, float* x_out, float* v_out, float* fx,
+                    float* fy, float* fz, uint32_t flags);
+
+/* Synchronise the stream and report the device error word (IBM_ERR_DEVICE if
+ * a kernel flagged an out-of-range or non-finite value). */
+ibm_status ibm_check_device_error(ibm_ctx* ctx);
+
+/* Phase timing of ibm_step (profiling aid, no counterpart in the paper): when
+ * on (nonzero), every ibm_step records CUDA events on the context's stream
+ * around its three kernels.  ibm_get_phase_times waits for the last recorded
+ * step and writes host ms[3] = (footprint clear, marker kernel, force+update
+ * kernel) of that step. */
+ibm_status ibm_set_phase_timing(ibm_ctx* ctx, int32_t on);
+ibm_status ibm_get_phase_times(ibm_ctx* ctx, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBM_GB300_H */

@@ -1,0 +1,243 @@
+"""ctypes binding of the C ABI in include/ibm.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Tensors are passed by data_ptr(); the library never falls back to the CPU and
+this module raises if the library or a CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+IBM_STEP_CLEAR_PREV = 1
+
+_STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID_ARG", 2: "IBM_ERR_MESH", 3: "IBM_ERR_CUDA",
+           4: "IBM_ERR_DEVICE", 5: "IBM_ERR_OOM", 6: "IBM_ERR_UNSUPPORTED"}
+
+
+class IBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BodyDesc(C.Structure):
+    _fields_ = [("n_vert", C.c_int32), ("n_face", C.c_int32),
+                ("rest", C.POINTER(C.c_double)), ("tri", C.POINTER(C.c_int32)),
+                ("clamped", C.POINTER(C.c_uint8)), ("origin", C.c_double * 3),
+                ("ks", C.c_double), ("kb", C.c_double), ("ka", C.c_double), ("kA", C.c_double),
+                ("kv", C.c_double), ("mass", C.c_double), ("closed", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("reserved", C.c_int32), ("L", C.c_double * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
+                ("probe_h", C.c_double), ("theta0_zero", C.c_int32), ("forward_euler", C.c_int32),
+                ("patch_size", C.c_int32), ("reserved", C.c_int32)]
+
+
+# exported symbols and their signatures (ctypes types), in header order
+P = C.c_void_p
+SIGNATURES = {
+    "ibm_create_bodies": (C.c_int, [C.POINTER(P), C.POINTER(BodyDesc), C.c_int32,
+                                    C.POINTER(GridDesc), C.POINTER(Params), C.c_int32]),
+    "ibm_destroy": (None, [P]),
+    "ibm_last_error": (C.c_char_p, [P]),
+    "ibm_set_stream": (C.c_int, [P, P]),
+    "ibm_get_sizes": (C.c_int, [P, C.POINTER(C.c_int64)]),
+    "ibm_get_offsets": (C.c_int, [P, C.POINTER(C.c_int64)]),
+    "ibm_init_state": (C.c_int, [P, P, P]),
+    "ibm_set_body_constants": (C.c_int, [P, C.POINTER(C.c_double)]),
+    "ibm_body_measures": (C.c_int, [P, P, P]),
+    "ibm_compute_forces": (C.c_int, [P, P, P, P]),
+    "ibm_interpolate": (C.c_int, [P, P, P, P, P, P, P, P, P]),
+    "ibm_advance": (C.c_int, [P, P, P, P, P, P, P]),
+    "ibm_spread": (C.c_int, [P, P, P, P, P, P]),
+    "ibm_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
+    "ibm_check_device_error": (C.c_int, [P]),
+    "ibm_set_phase_timing": (C.c_int, [P, C.c_int32]),
+    "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
+}
+
+_lib = None
+
+
+def library(build_if_missing: bool = True):
+    """Load libibm_gb300.so (building it in-tree first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"{path} not built")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One set of bodies on one Eulerian grid (ibm_create_bodies).
+
+    bodies: list of workloads.Body; grid: workloads.Grid.  State tensors are
+    float32 [3, V] in the body frame (x - origin); per-marker arrays [3, F];
+    fields [nz, ny, nx].
+    """
+
+    def __init__(self, bodies, grid, dt=1e-3, mu=1.0, alpha=0.3, probe_h=0.0, theta0_zero=False,
+                 forward_euler=False, patch_size=0, device=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the IBM library needs a CUDA device; there is no CPU fallback")
+        self.lib = library()
+        self.device = torch.device("cuda", device)
+        self._keep = []
+        descs = (BodyDesc * len(bodies))()
+        for i, b in enumerate(bodies):
+            rest = np.ascontiguousarray(b.rest, dtype=np.float64)
+            tri = np.ascontiguousarray(b.tri, dtype=np.int32)
+            d = descs[i]
+            d.n_vert, d.n_face = len(rest), len(tri)
+            d.rest = rest.ctypes.data_as(C.POINTER(C.c_double))
+            d.tri = tri.ctypes.data_as(C.POINTER(C.c_int32))
+            self._keep += [rest, tri]
+            if b.clamped is not None:
+                cl = np.ascontiguousarray(b.clamped, dtype=np.uint8)
+                d.clamped = cl.ctypes.data_as(C.POINTER(C.c_uint8))
+                self._keep.append(cl)
+            for k in range(3):
+                d.origin[k] = float(b.origin[k])
+            d.ks, d.kb, d.ka, d.kA, d.kv, d.mass = (float(b.ks), float(b.kb), float(b.ka),
+                                                    float(b.kA), float(b.kv), float(b.mass))
+            d.closed = 1 if b.closed else 0
+        g = GridDesc()
+        for k in range(3):
+            g.n[k] = int(grid.n[k])
+            g.L[k] = float(grid.L[k])
+        p = Params(dt=dt, mu=mu, alpha=alpha, probe_h=probe_h, theta0_zero=int(theta0_zero),
+                   forward_euler=int(forward_euler), patch_size=int(patch_size))
+        h = C.c_void_p()
+        st = self.lib.ibm_create_bodies(C.byref(h), descs, len(bodies), C.byref(g), C.byref(p),
+                                        device)
+        self._keep = []
+        if st != 0:
+            raise IBMError(st, self.lib.ibm_last_error(None).decode())
+        self.h = h
+        sizes = (C.c_int64 * 6)()
+        self._check(self.lib.ibm_get_sizes(self.h, sizes))
+        self.V, self.F, self.E, self.B, self.n_topo, self.n_work = [int(s) for s in sizes]
+        offs = (C.c_int64 * (3 * self.B))()
+        self._check(self.lib.ibm_get_offsets(self.h, offs))
+        o = np.array(offs, dtype=np.int64).reshape(self.B, 3)
+        self.v_off, self.f_off, self.e_off = o[:, 0], o[:, 1], o[:, 2]
+        self.grid = grid
+        self.set_stream(torch.cuda.current_stream(self.device))
+
+    # -- plumbing ------------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            raise IBMError(st, self.lib.ibm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ibm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self.lib.ibm_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def _vec(self, n):
+        import torch
+        return torch.empty((3, n), dtype=torch.float32, device=self.device)
+
+    # -- entry points ----------------------------------------------------------
+    def init_state(self):
+        x, v = self._vec(self.V), self._vec(self.V)
+        self._check(self.lib.ibm_init_state(self.h, _ptr(x), _ptr(v)))
+        return x, v
+
+    def set_constants(self, consts):
+        k = np.ascontiguousarray(consts, dtype=np.float64).reshape(self.B, 6)
+        self._check(self.lib.ibm_set_body_constants(self.h, k.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def body_measures(self, x):
+        import torch
+        out = torch.empty((self.B, 2), dtype=torch.float64, device=self.device)
+        self._check(self.lib.ibm_body_measures(self.h, _ptr(x), _ptr(out)))
+        return out
+
+    def compute_forces(self, x, energy=False, out=None):
+        import torch
+        F = out if out is not None else self._vec(self.V)
+        E = torch.empty((self.B, 5), dtype=torch.float64, device=self.device) if energy else None
+        self._check(self.lib.ibm_compute_forces(self.h, _ptr(x), _ptr(F), _ptr(E)))
+        return (F, E) if energy else F
+
+    def interpolate(self, x, v, fields, U=True, F_marker=True, F_ext=True):
+        u, vv, w = fields
+        Uo = self._vec(self.F) if U else None
+        Fm = self._vec(self.F) if F_marker else None
+        Fe = self._vec(self.F) if F_ext else None
+        self._check(self.lib.ibm_interpolate(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
+                                             _ptr(Uo), _ptr(Fm), _ptr(Fe)))
+        return Uo, Fm, Fe
+
+    def advance(self, x, v, F_int, F_ext, x_out=None, v_out=None):
+        xo = x_out if x_out is not None else self._vec(self.V)
+        vo = v_out if v_out is not None else self._vec(self.V)
+        self._check(self.lib.ibm_advance(self.h, _ptr(x), _ptr(v), _ptr(F_int), _ptr(F_ext),
+                                         _ptr(xo), _ptr(vo)))
+        return xo, vo
+
+    def spread(self, x, F_marker, f):
+        fx, fy, fz = f
+        self._check(self.lib.ibm_spread(self.h, _ptr(x), _ptr(F_marker), _ptr(fx), _ptr(fy), _ptr(fz)))
+        return f
+
+    def step(self, x, v, fields, x_out, v_out, f, clear=True):
+        u, vv, w = fields
+        fx, fy, fz = f
+        self._check(self.lib.ibm_step(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
+                                      _ptr(x_out), _ptr(v_out), _ptr(fx), _ptr(fy), _ptr(fz),
+                                      IBM_STEP_CLEAR_PREV if clear else 0))
+
+    def check_device_error(self):
+        self._check(self.lib.ibm_check_device_error(self.h))
+
+    def set_phase_timing(self, on=True):
+        self._check(self.lib.ibm_set_phase_timing(self.h, 1 if on else 0))
+
+    def phase_times(self):
+        """(clear, marker, force+update) milliseconds of the last timed step."""
+        ms = (C.c_float * 3)()
+        self._check(self.lib.ibm_get_phase_times(self.h, ms))
+        return tuple(float(m) for m in ms)

@@ -1,0 +1,790 @@
+// Host side of the C ABI: input validation, the mesh auxiliary arrays of
+// Sec. 5 (edges, faces of each edge, the four vertices of each hinge, vertex
+// incidence), per-patch tables of the force kernel, the rest state in float64,
+// device upload and the entry points declared in include/ibm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "ibm_internal.cuh"
+
+using namespace ibm;
+
+namespace {
+
+std::mutex g_mu;
+std::string g_err;
+
+struct Failure {
+  ibm_status s;
+  std::string msg;
+};
+
+[[noreturn]] void fail(ibm_status s, const std::string& m) { throw Failure{s, m}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    fail(e == cudaErrorMemoryAllocation ? IBM_ERR_OOM : IBM_ERR_CUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+struct HostTopo {
+  int nv = 0, nf = 0, ne = 0;
+  bool has_boundary = false;
+  std::vector<int32_t> tri;
+  std::vector<int4> edge;  // a, b, c, d
+  std::vector<int32_t> v2f_ptr, v2f_idx;
+  std::vector<PatchHdr> patch;
+  std::vector<int32_t> loc_vert;
+  std::vector<PEdge> pedge;
+  std::vector<PFace> pface;
+  std::vector<int32_t> csr_ptr;
+  std::vector<uint16_t> csr_slot;
+  int max_loc = 0, max_slot = 0, max_own = 0;
+};
+
+inline uint64_t key2(int32_t p, int32_t q) {
+  return ((uint64_t)(uint32_t)p << 32) | (uint32_t)q;
+}
+
+// Edges, hinges and incidence of one oriented triangle mesh, plus the patch
+// tables.  Throws IBM_ERR_MESH on index errors, repeated vertices in a face,
+// a directed edge used twice (an edge shared by more than two faces or two
+// faces of opposite orientation).
+void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
+  T.nv = nv;
+  T.nf = nf;
+  T.tri.assign(tri, tri + 3 * (size_t)nf);
+  std::unordered_map<uint64_t, int32_t> half;
+  half.reserve((size_t)nf * 6);
+  for (int f = 0; f < nf; ++f) {
+    const int a = tri[3 * f], b = tri[3 * f + 1], c = tri[3 * f + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv)
+      fail(IBM_ERR_MESH, "face " + std::to_string(f) + " has a vertex index out of range");
+    if (a == b || b == c || c == a)
+      fail(IBM_ERR_MESH, "face " + std::to_string(f) + " repeats a vertex");
+    const int hp[3][3] = {{a, b, c}, {b, c, a}, {c, a, b}};
+    for (auto& h : hp) {
+      if (!half.emplace(key2(h[0], h[1]), h[2]).second)
+        fail(IBM_ERR_MESH, "edge (" + std::to_string(h[0]) + "," + std::to_string(h[1]) +
+                               ") is used twice in the same direction: non-manifold or "
+                               "inconsistently oriented mesh");
+    }
+  }
+  std::unordered_map<uint64_t, int32_t> und;
+  und.reserve((size_t)nf * 3);
+  for (int f = 0; f < nf; ++f) {
+    const int a = tri[3 * f], b = tri[3 * f + 1], c = tri[3 * f + 2];
+    const int hp[3][3] = {{a, b, c}, {b, c, a}, {c, a, b}};
+    for (auto& h : hp) {
+      const uint64_t k = key2(std::min(h[0], h[1]), std::max(h[0], h[1]));
+      if (und.count(k)) continue;
+      auto it = half.find(key2(h[1], h[0]));
+      const int s = it == half.end() ? -1 : it->second;
+      if (s < 0) T.has_boundary = true;
+      und.emplace(k, (int32_t)T.edge.size());
+      T.edge.push_back(make_int4(h[0], h[1], h[2], s));
+    }
+  }
+  T.ne = (int)T.edge.size();
+  // vertex -> face
+  T.v2f_ptr.assign(nv + 1, 0);
+  for (int f = 0; f < nf; ++f)
+    for (int k = 0; k < 3; ++k) T.v2f_ptr[tri[3 * f + k] + 1]++;
+  for (int v = 0; v < nv; ++v) T.v2f_ptr[v + 1] += T.v2f_ptr[v];
+  T.v2f_idx.assign(T.v2f_ptr[nv], 0);
+  std::vector<int32_t> fill(T.v2f_ptr.begin(), T.v2f_ptr.end() - 1);
+  std::vector<int32_t> v2fc(T.v2f_ptr[nv]);  // face*3 + corner
+  for (int f = 0; f < nf; ++f)
+    for (int k = 0; k < 3; ++k) {
+      const int v = tri[3 * f + k];
+      v2fc[fill[v]] = 3 * f + k;
+      T.v2f_idx[fill[v]++] = f;
+    }
+  // vertex -> (edge, role) with role 0..3 = a, b, c, d
+  std::vector<int32_t> v2e_ptr(nv + 1, 0);
+  for (const int4& e : T.edge) {
+    v2e_ptr[e.x + 1]++;
+    v2e_ptr[e.y + 1]++;
+    v2e_ptr[e.z + 1]++;
+    if (e.w >= 0) v2e_ptr[e.w + 1]++;
+  }
+  for (int v = 0; v < nv; ++v) v2e_ptr[v + 1] += v2e_ptr[v];
+  std::vector<int32_t> v2e(v2e_ptr[nv]);
+  fill.assign(v2e_ptr.begin(), v2e_ptr.end() - 1);
+  for (int e = 0; e < T.ne; ++e) {
+    const int4 E = T.edge[e];
+    v2e[fill[E.x]++] = 4 * e + 0;
+    v2e[fill[E.y]++] = 4 * e + 1;
+    v2e[fill[E.z]++] = 4 * e + 2;
+    if (E.w >= 0) v2e[fill[E.w]++] = 4 * e + 3;
+  }
+  // patches
+  const int npatch = (nv + P - 1) / P;
+  std::vector<int32_t> e_stamp(T.ne, -1), e_loc(T.ne), f_stamp(nf, -1), f_loc(nf),
+      v_stamp(nv, -1), v_loc(nv);
+  std::vector<int32_t> es, fs;
+  for (int p = 0; p < npatch; ++p) {
+    PatchHdr H{};
+    const int o0 = p * P, o1 = std::min(nv, o0 + P);
+    H.own0 = o0;
+    H.n_own = o1 - o0;
+    H.loc_off = (int32_t)T.loc_vert.size();
+    for (int v = o0; v < o1; ++v) {
+      v_stamp[v] = p;
+      v_loc[v] = v - o0;
+      T.loc_vert.push_back(v);
+    }
+    auto local = [&](int v) -> uint16_t {
+      if (v < 0) return kNone;
+      if (v_stamp[v] != p) {
+        v_stamp[v] = p;
+        v_loc[v] = (int32_t)T.loc_vert.size() - H.loc_off;
+        T.loc_vert.push_back(v);
+      }
+      return (uint16_t)v_loc[v];
+    };
+    es.clear();
+    fs.clear();
+    for (int v = o0; v < o1; ++v) {
+      for (int k = v2e_ptr[v]; k < v2e_ptr[v + 1]; ++k) {
+        const int e = v2e[k] >> 2;
+        if (e_stamp[e] != p) {
+          e_stamp[e] = p;
+          es.push_back(e);
+        }
+      }
+      for (int k = T.v2f_ptr[v]; k < T.v2f_ptr[v + 1]; ++k) {
+        const int f = T.v2f_idx[k];
+        if (f_stamp[f] != p) {
+          f_stamp[f] = p;
+          fs.push_back(f);
+        }
+      }
+    }
+    std::sort(es.begin(), es.end());
+    std::sort(fs.begin(), fs.end());
+    H.edge_off = (int32_t)T.pedge.size();
+    H.n_edge = (int32_t)es.size();
+    for (size_t i = 0; i < es.size(); ++i) {
+      const int e = es[i];
+      e_loc[e] = (int32_t)i;
+      const int4 E = T.edge[e];
+      PEdge r;
+      r.l[0] = local(E.x);
+      r.l[1] = local(E.y);
+      r.l[2] = local(E.z);
+      r.l[3] = local(E.w);
+      r.eid = e | ((E.x >= o0 && E.x < o1) ? (int32_t)0x80000000 : 0);
+      T.pedge.push_back(r);
+    }
+    H.face_off = (int32_t)T.pface.size();
+    H.n_face = (int32_t)fs.size();
+    for (size_t i = 0; i < fs.size(); ++i) {
+      const int f = fs[i];
+      f_loc[f] = (int32_t)i;
+      PFace r;
+      r.l[0] = local(tri[3 * f]);
+      r.l[1] = local(tri[3 * f + 1]);
+      r.l[2] = local(tri[3 * f + 2]);
+      r.owned = (tri[3 * f] >= o0 && tri[3 * f] < o1) ? 1 : 0;
+      r.fid = f;
+      T.pface.push_back(r);
+    }
+    H.n_loc = (int32_t)T.loc_vert.size() - H.loc_off;
+    H.n_slot = 4 * H.n_edge + 3 * H.n_face;
+    if (H.n_loc >= (int)kNone || H.n_slot > 65535)
+      fail(IBM_ERR_UNSUPPORTED, "patch too large for 16-bit local indices; lower patch_size");
+    H.csr_off = (int32_t)T.csr_ptr.size();
+    H.slot_off = (int32_t)T.csr_slot.size();
+    for (int v = o0; v < o1; ++v) {
+      T.csr_ptr.push_back((int32_t)T.csr_slot.size() - H.slot_off);
+      for (int k = v2e_ptr[v]; k < v2e_ptr[v + 1]; ++k) {
+        const int e = v2e[k] >> 2, role = v2e[k] & 3;
+        T.csr_slot.push_back((uint16_t)(4 * e_loc[e] + role));
+      }
+      for (int k = T.v2f_ptr[v]; k < T.v2f_ptr[v + 1]; ++k) {
+        const int f = v2fc[k] / 3, corner = v2fc[k] % 3;
+        T.csr_slot.push_back((uint16_t)(4 * H.n_edge + 3 * f_loc[f] + corner));
+      }
+    }
+    T.csr_ptr.push_back((int32_t)T.csr_slot.size() - H.slot_off);
+    T.max_loc = std::max(T.max_loc, H.n_loc);
+    T.max_slot = std::max(T.max_slot, H.n_slot);
+    T.max_own = std::max(T.max_own, H.n_own);
+    T.patch.push_back(H);
+  }
+}
+
+uint64_t hash_mesh(const int32_t* t, int nf, int nv) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)nv;
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(t);
+  for (size_t i = 0; i < (size_t)nf * 3 * sizeof(int32_t); ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+struct D3 {
+  double x, y, z;
+};
+inline D3 dsub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline D3 dcross(D3 a, D3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline double dnorm(D3 a) { return std::sqrt(ddot(a, a)); }
+
+template <class T>
+T* upload(ibm_ctx* c, const std::vector<T>& h) {
+  if (h.empty()) return nullptr;
+  void* p = nullptr;
+  check_cuda(cudaMalloc(&p, h.size() * sizeof(T)), "cudaMalloc");
+  c->allocations.push_back(p);
+  check_cuda(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+  return static_cast<T*>(p);
+}
+
+template <class T>
+T* zeros(ibm_ctx* c, size_t n) {
+  if (n == 0) return nullptr;
+  void* p = nullptr;
+  check_cuda(cudaMalloc(&p, n * sizeof(T)), "cudaMalloc");
+  c->allocations.push_back(p);
+  check_cuda(cudaMemset(p, 0, n * sizeof(T)), "cudaMemset");
+  return static_cast<T*>(p);
+}
+
+void free_all(ibm_ctx* c) {
+  for (void* p : c->allocations) cudaFree(p);
+  c->allocations.clear();
+}
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+ibm_status set_err(ibm_ctx* c, ibm_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+ibm_status cuda_status(ibm_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return IBM_OK;
+  return set_err(c, IBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void make_consts(ibm_ctx* c) {
+  const ibm_params& p = c->prm;
+  ibm::Grid& g = c->grid;
+  double h[3];
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = c->gdesc.n[d];
+    h[d] = c->gdesc.L[d] / c->gdesc.n[d];
+    g.h[d] = (float)h[d];
+    g.invh[d] = (float)(1.0 / h[d]);
+  }
+  const double alpha = p.alpha > 0 ? p.alpha : 0.3;
+  c->sc.dt = (float)p.dt;
+  c->sc.inv_dt = (float)(1.0 / p.dt);
+  c->sc.mu = (float)p.mu;
+  c->sc.probe_h = (float)(p.probe_h > 0 ? p.probe_h : (h[0] + h[1] + h[2]) / 3.0);
+  c->sc.kappa = (float)(1.0 / ((1.5 * alpha) * (1.5 * alpha)));
+  c->sc.cl_scale = (float)(((h[0] + h[1] + h[2]) / 3.0) / (h[0] * h[1] * h[2]));
+  c->sc.forward_euler = p.forward_euler ? 1 : 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+
+extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodies,
+                                        int32_t n_bodies, const ibm_grid_desc* grid,
+                                        const ibm_params* params, int32_t device) {
+  if (out) *out = nullptr;
+  ibm_ctx* c = nullptr;
+  try {
+    if (!out || !bodies || !grid || !params || n_bodies <= 0)
+      fail(IBM_ERR_INVALID_ARG, "null argument or n_bodies <= 0");
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0)
+      fail(IBM_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(ce));
+    if (device < 0 || device >= ndev) fail(IBM_ERR_INVALID_ARG, "device index out of range");
+    check_cuda(cudaSetDevice(device), "cudaSetDevice");
+    // grid and parameters
+    long long nodes = 1;
+    for (int d = 0; d < 3; ++d) {
+      if (grid->n[d] < 4 || grid->n[d] > (1 << 16))
+        fail(IBM_ERR_INVALID_ARG, "grid n must be in [4, 65536] per direction");
+      if (!is_fin(grid->L[d]) || grid->L[d] <= 0) fail(IBM_ERR_INVALID_ARG, "grid L must be > 0");
+      nodes *= grid->n[d];
+    }
+    if (nodes >= (1ll << 31)) fail(IBM_ERR_UNSUPPORTED, "grid has 2^31 or more nodes");
+    const ibm_params& p = *params;
+    if (!is_fin(p.dt) || p.dt <= 0) fail(IBM_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!is_fin(p.mu) || p.mu < 0) fail(IBM_ERR_INVALID_ARG, "mu must be finite and >= 0");
+    if (!is_fin(p.alpha) || p.alpha < 0) fail(IBM_ERR_INVALID_ARG, "alpha must be >= 0");
+    if (!is_fin(p.probe_h)) fail(IBM_ERR_INVALID_ARG, "probe_h must be finite");
+    const int P = p.patch_size > 0 ? p.patch_size : 128;
+    if (P < 32 || P > 2048) fail(IBM_ERR_INVALID_ARG, "patch_size must be in [32, 2048]");
+
+    c = new ibm_ctx();
+    c->device = device;
+    c->prm = p;
+    c->prm.patch_size = P;
+    c->gdesc = *grid;
+    make_consts(c);
+    double h[3];
+    for (int d = 0; d < 3; ++d) h[d] = grid->L[d] / grid->n[d];
+
+    // topologies, shared between bodies with identical faces
+    std::vector<HostTopo> topos;
+    std::unordered_map<uint64_t, std::vector<int>> by_hash;
+    std::vector<int> body_topo(n_bodies);
+    for (int b = 0; b < n_bodies; ++b) {
+      const ibm_body_desc& B = bodies[b];
+      if (B.n_vert < 3 || B.n_face < 1 || !B.rest || !B.tri)
+        fail(IBM_ERR_INVALID_ARG, "body " + std::to_string(b) + ": needs >= 3 vertices, >= 1 face");
+      const uint64_t hsh = hash_mesh(B.tri, B.n_face, B.n_vert);
+      int found = -1;
+      for (int t : by_hash[hsh]) {
+        const HostTopo& T = topos[t];
+        if (T.nv == B.n_vert && T.nf == B.n_face &&
+            std::memcmp(T.tri.data(), B.tri, sizeof(int32_t) * 3 * (size_t)B.n_face) == 0) {
+          found = t;
+          break;
+        }
+      }
+      if (found < 0) {
+        topos.emplace_back();
+        try {
+          build_topology(topos.back(), B.tri, B.n_vert, B.n_face, P);
+        } catch (Failure& f) {
+          f.msg = "body " + std::to_string(b) + ": " + f.msg;
+          throw;
+        }
+        found = (int)topos.size() - 1;
+        by_hash[hsh].push_back(found);
+      }
+      body_topo[b] = found;
+      if (B.closed && topos[found].has_boundary)
+        fail(IBM_ERR_MESH, "body " + std::to_string(b) + " is marked closed but has boundary edges");
+    }
+    // body records and rest state (float64)
+    long long V = 0, F = 0, E = 0;
+    for (int b = 0; b < n_bodies; ++b) {
+      V += bodies[b].n_vert;
+      F += bodies[b].n_face;
+      E += topos[body_topo[b]].ne;
+    }
+    if (V >= (1ll << 31) / 3 || F >= (1ll << 31) / 3 || E >= (1ll << 31))
+      fail(IBM_ERR_UNSUPPORTED, "too many vertices/faces for 32-bit indexing");
+    c->V = V;
+    c->F = F;
+    c->E = E;
+    c->B = n_bodies;
+    c->n_topo = (int)topos.size();
+    std::vector<float> rest(3 * V), l0(E), A0f(F);
+    std::vector<float2> cs0(E);
+    std::vector<uint8_t> clamp(V, 0);
+    std::vector<int4> chunks;
+    std::vector<int2> work;
+    c->h_body.resize(n_bodies);
+    long long vo = 0, fo = 0, eo = 0;
+    for (int b = 0; b < n_bodies; ++b) {
+      const ibm_body_desc& Bd = bodies[b];
+      const HostTopo& T = topos[body_topo[b]];
+      const std::string tag = "body " + std::to_string(b) + ": ";
+      const double kk[6] = {Bd.ks, Bd.kb, Bd.ka, Bd.kA, Bd.kv, Bd.mass};
+      for (double k : kk)
+        if (!is_fin(k)) fail(IBM_ERR_INVALID_ARG, tag + "non-finite elastic constant or mass");
+      if (Bd.mass <= 0) fail(IBM_ERR_INVALID_ARG, tag + "mass must be > 0");
+      for (int d = 0; d < 3; ++d)
+        if (!is_fin(Bd.origin[d])) fail(IBM_ERR_INVALID_ARG, tag + "non-finite origin");
+      std::vector<D3> x(Bd.n_vert);
+      for (int v = 0; v < Bd.n_vert; ++v) {
+        x[v] = {Bd.rest[3 * v] - Bd.origin[0], Bd.rest[3 * v + 1] - Bd.origin[1],
+                Bd.rest[3 * v + 2] - Bd.origin[2]};
+        if (!is_fin(x[v].x) || !is_fin(x[v].y) || !is_fin(x[v].z))
+          fail(IBM_ERR_INVALID_ARG, tag + "non-finite rest position");
+        rest[vo + v] = (float)x[v].x;
+        rest[V + vo + v] = (float)x[v].y;
+        rest[2 * V + vo + v] = (float)x[v].z;
+        if (Bd.clamped) clamp[vo + v] = Bd.clamped[v] ? 1 : 0;
+      }
+      for (int e = 0; e < T.ne; ++e) {
+        const int4 Ed = T.edge[e];
+        const D3 ev = dsub(x[Ed.y], x[Ed.x]);
+        const double l = dnorm(ev);
+        if (!(l > 0)) fail(IBM_ERR_MESH, tag + "zero-length rest edge");
+        l0[eo + e] = (float)l;
+        float2 cs = make_float2(1.f, 0.f);
+        if (Ed.w >= 0 && !p.theta0_zero) {
+          const D3 N1 = dcross(ev, dsub(x[Ed.z], x[Ed.x]));
+          const D3 N2 = dcross(dsub(x[Ed.w], x[Ed.y]), ev);
+          const double n1 = dnorm(N1), n2 = dnorm(N2);
+          const D3 a = {N1.x / n1, N1.y / n1, N1.z / n1}, bb = {N2.x / n2, N2.y / n2, N2.z / n2};
+          const double ct = ddot(a, bb);
+          const double st = ddot(dcross(a, bb), ev) / l;
+          cs = make_float2((float)ct, (float)st);
+        }
+        cs0[eo + e] = cs;
+      }
+      double A0 = 0.0, V0 = 0.0;
+      for (int f = 0; f < T.nf; ++f) {
+        const D3 xa = x[T.tri[3 * f]], xb = x[T.tri[3 * f + 1]], xc = x[T.tri[3 * f + 2]];
+        const double a = 0.5 * dnorm(dcross(dsub(xb, xa), dsub(xc, xa)));
+        if (!(a > 0)) fail(IBM_ERR_MESH, tag + "degenerate (zero-area) rest face");
+        A0f[fo + f] = (float)a;
+        A0 += a;
+        V0 += ddot(xa, dcross(xb, xc)) / 6.0;
+      }
+      if (Bd.closed && !(V0 > 0))
+        fail(IBM_ERR_MESH, tag + "closed body with non-positive rest volume (faces oriented inward?)");
+      BodyDev& R = c->h_body[b];
+      std::memset(&R, 0, sizeof(R));
+      R.v_off = (int32_t)vo;
+      R.f_off = (int32_t)fo;
+      R.e_off = (int32_t)eo;
+      R.topo = body_topo[b];
+      R.nv = Bd.n_vert;
+      R.nf = Bd.n_face;
+      R.ne = T.ne;
+      R.closed = Bd.closed ? 1 : 0;
+      for (int d = 0; d < 3; ++d) {
+        const double o = Bd.origin[d] / h[d];
+        const double Gd = std::floor(o);
+        R.frac[d] = (float)(o - Gd);
+        long long Gi = (long long)Gd % grid->n[d];
+        if (Gi < 0) Gi += grid->n[d];
+        R.G[d] = (int32_t)Gi;
+      }
+      R.ks = (float)Bd.ks;
+      R.kb = (float)Bd.kb;
+      R.ka = (float)Bd.ka;
+      R.kA = (float)Bd.kA;
+      R.kv = Bd.closed ? (float)Bd.kv : 0.f;
+      R.inv_mass = (float)(1.0 / Bd.mass);
+      R.A0 = A0;
+      R.V0 = Bd.closed ? V0 : 1.0;
+      R.chunk_off = (int32_t)chunks.size();
+      const int nch = (Bd.n_face + kChunk - 1) / kChunk;
+      R.n_chunk = nch;
+      for (int k = 0; k < nch; ++k)
+        chunks.push_back(make_int4(b, k * kChunk, std::min(kChunk, Bd.n_face - k * kChunk), k));
+      for (int q = 0; q < (int)T.patch.size(); ++q) work.push_back(make_int2(b, q));
+      vo += Bd.n_vert;
+      fo += Bd.n_face;
+      eo += T.ne;
+    }
+    c->n_chunks = (int32_t)chunks.size();
+    c->n_work = (int32_t)work.size();
+
+    // concatenate the topology tables
+    std::vector<TopoDev> td(topos.size());
+    std::vector<int32_t> tri_all, v2f_ptr_all, v2f_idx_all, loc_all, csr_all;
+    std::vector<int4> edge_all;
+    std::vector<PatchHdr> patch_all;
+    std::vector<PEdge> pedge_all;
+    std::vector<PFace> pface_all;
+    std::vector<uint16_t> slot_all;
+    int max_loc = 0, max_slot = 0, max_own = 0;
+    for (size_t t = 0; t < topos.size(); ++t) {
+      const HostTopo& T = topos[t];
+      TopoDev& D = td[t];
+      std::memset(&D, 0, sizeof(D));
+      D.nv = T.nv;
+      D.nf = T.nf;
+      D.ne = T.ne;
+      D.n_patch = (int32_t)T.patch.size();
+      D.tri_off = (int32_t)tri_all.size();
+      tri_all.insert(tri_all.end(), T.tri.begin(), T.tri.end());
+      D.edge_off = (int32_t)edge_all.size();
+      edge_all.insert(edge_all.end(), T.edge.begin(), T.edge.end());
+      D.v2f_ptr_off = (int32_t)v2f_ptr_all.size();
+      v2f_ptr_all.insert(v2f_ptr_all.end(), T.v2f_ptr.begin(), T.v2f_ptr.end());
+      D.v2f_idx_off = (int32_t)v2f_idx_all.size();
+      v2f_idx_all.insert(v2f_idx_all.end(), T.v2f_idx.begin(), T.v2f_idx.end());
+      D.patch_off = (int32_t)patch_all.size();
+      const int32_t lo = (int32_t)loc_all.size(), eo2 = (int32_t)pedge_all.size(),
+                    fo2 = (int32_t)pface_all.size(), co = (int32_t)csr_all.size(),
+                    so = (int32_t)slot_all.size();
+      for (PatchHdr H : T.patch) {
+        H.loc_off += lo;
+        H.edge_off += eo2;
+        H.face_off += fo2;
+        H.csr_off += co;
+        H.slot_off += so;
+        patch_all.push_back(H);
+      }
+      loc_all.insert(loc_all.end(), T.loc_vert.begin(), T.loc_vert.end());
+      pedge_all.insert(pedge_all.end(), T.pedge.begin(), T.pedge.end());
+      pface_all.insert(pface_all.end(), T.pface.begin(), T.pface.end());
+      csr_all.insert(csr_all.end(), T.csr_ptr.begin(), T.csr_ptr.end());
+      slot_all.insert(slot_all.end(), T.csr_slot.begin(), T.csr_slot.end());
+      max_loc = std::max(max_loc, T.max_loc);
+      max_slot = std::max(max_slot, T.max_slot);
+      max_own = std::max(max_own, T.max_own);
+    }
+    c->force_smem = sizeof(float) * 3 * ((size_t)max_loc + (size_t)max_slot);
+    c->max_own = max_own;
+    if (c->force_smem > 227 * 1024)
+      fail(IBM_ERR_UNSUPPORTED, "force-kernel shared memory above 227 KB; lower patch_size");
+    check_cuda(set_force_smem_limit(c->force_smem), "cudaFuncSetAttribute");
+
+    DeviceTables& d = c->d;
+    d.body = upload(c, c->h_body);
+    d.topo = upload(c, td);
+    d.tri = upload(c, tri_all);
+    d.edge = upload(c, edge_all);
+    d.v2f_ptr = upload(c, v2f_ptr_all);
+    d.v2f_idx = upload(c, v2f_idx_all);
+    d.patch = upload(c, patch_all);
+    d.loc_vert = upload(c, loc_all);
+    d.pedge = upload(c, pedge_all);
+    d.pface = upload(c, pface_all);
+    d.csr_ptr = upload(c, csr_all);
+    d.csr_slot = upload(c, slot_all);
+    d.l0 = upload(c, l0);
+    d.cs0 = upload(c, cs0);
+    d.A0f = upload(c, A0f);
+    d.clamp = upload(c, clamp);
+    d.rest = upload(c, rest);
+    d.chunks = upload(c, chunks);
+    d.work = upload(c, work);
+    d.partial = zeros<double>(c, 2 * (size_t)c->n_chunks);
+    d.counter = zeros<int32_t>(c, (size_t)n_bodies);
+    d.meas = zeros<double>(c, 2 * (size_t)n_bodies);
+    d.fext = zeros<float>(c, 3 * (size_t)F);
+    d.err = zeros<int32_t>(c, 1);
+    const size_t nbr = (size_t)((grid->n[0] + 7) / 8) * ((grid->n[1] + 7) / 8) * ((grid->n[2] + 7) / 8);
+    c->d_bricks = zeros<uint8_t>(c, nbr);
+    check_cuda(cudaDeviceSynchronize(), "create");
+    *out = c;
+    return IBM_OK;
+  } catch (Failure& f) {
+    if (c) {
+      free_all(c);
+      delete c;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err = f.msg;
+    return f.s;
+  } catch (std::exception& e) {
+    if (c) {
+      free_all(c);
+      delete c;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err = std::string("host error: ") + e.what();
+    return IBM_ERR_OOM;
+  }
+}
+
+extern "C" void ibm_destroy(ibm_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
+  free_all(c);
+  delete c;
+}
+
+extern "C" const char* ibm_last_error(const ibm_ctx* c) {
+  if (c) return c->err.c_str();
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_err.c_str();
+}
+
+extern "C" ibm_status ibm_set_stream(ibm_ctx* c, void* stream) {
+  if (!c) return IBM_ERR_INVALID_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_get_sizes(const ibm_ctx* c, int64_t* out) {
+  if (!c || !out) return IBM_ERR_INVALID_ARG;
+  out[0] = c->V;
+  out[1] = c->F;
+  out[2] = c->E;
+  out[3] = c->B;
+  out[4] = c->n_topo;
+  out[5] = c->n_work;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_get_offsets(const ibm_ctx* c, int64_t* out) {
+  if (!c || !out) return IBM_ERR_INVALID_ARG;
+  for (size_t b = 0; b < c->h_body.size(); ++b) {
+    out[3 * b] = c->h_body[b].v_off;
+    out[3 * b + 1] = c->h_body[b].f_off;
+    out[3 * b + 2] = c->h_body[b].e_off;
+  }
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_init_state(ibm_ctx* c, float* x, float* v) {
+  if (!c || !x || !v) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaMemcpyAsync(x, c->d.rest, sizeof(float) * 3 * c->V,
+                                  cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(float) * 3 * c->V, c->stream);
+  return cuda_status(c, e, "ibm_init_state");
+}
+
+extern "C" ibm_status ibm_set_body_constants(ibm_ctx* c, const double* k) {
+  if (!c || !k) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  for (int64_t b = 0; b < c->B; ++b) {
+    for (int j = 0; j < 6; ++j)
+      if (!is_fin(k[6 * b + j])) return set_err(c, IBM_ERR_INVALID_ARG, "non-finite constant");
+    if (k[6 * b + 5] <= 0) return set_err(c, IBM_ERR_INVALID_ARG, "mass must be > 0");
+    BodyDev& R = c->h_body[b];
+    R.ks = (float)k[6 * b];
+    R.kb = (float)k[6 * b + 1];
+    R.ka = (float)k[6 * b + 2];
+    R.kA = (float)k[6 * b + 3];
+    R.kv = R.closed ? (float)k[6 * b + 4] : 0.f;
+    R.inv_mass = (float)(1.0 / k[6 * b + 5]);
+  }
+  cudaSetDevice(c->device);
+  // synchronous with respect to the host buffer (pageable source)
+  cudaError_t e = cudaMemcpyAsync(c->d.body, c->h_body.data(), sizeof(BodyDev) * c->B,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(c, e, "ibm_set_body_constants");
+}
+
+extern "C" ibm_status ibm_body_measures(ibm_ctx* c, const float* x, double* out) {
+  if (!c || !x || !out) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  cudaSetDevice(c->device);
+  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, c->d.meas, sizeof(double) * 2 * c->B, cudaMemcpyDeviceToDevice,
+                        c->stream);
+  return cuda_status(c, e, "ibm_body_measures");
+}
+
+extern "C" ibm_status ibm_compute_forces(ibm_ctx* c, const float* x, float* F_int,
+                                         double* energy) {
+  if (!c || !x || !F_int) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  cudaSetDevice(c->device);
+  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
+  if (e == cudaSuccess && energy)
+    e = cudaMemsetAsync(energy, 0, sizeof(double) * 5 * c->B, c->stream);
+  if (e == cudaSuccess)
+    e = launch_force(c, x, nullptr, nullptr, F_int, nullptr, nullptr, energy, false);
+  return cuda_status(c, e, "ibm_compute_forces");
+}
+
+extern "C" ibm_status ibm_interpolate(ibm_ctx* c, const float* x, const float* v, const float* u,
+                                      const float* vv, const float* w, float* U, float* Fm,
+                                      float* Fext) {
+  if (!c || !x || !u || !vv || !w) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (Fm && !v) return set_err(c, IBM_ERR_INVALID_ARG, "F_marker needs the vertex velocities");
+  const bool interp = U || Fm;
+  const bool probe = Fext != nullptr;
+  if (!interp && !probe) return IBM_OK;
+  cudaSetDevice(c->device);
+  cudaError_t e = launch_mls(c, x, v, u, vv, w, U, Fm, nullptr, Fext, nullptr, nullptr, nullptr,
+                             false, interp, probe, false, false);
+  return cuda_status(c, e, "ibm_interpolate");
+}
+
+extern "C" ibm_status ibm_advance(ibm_ctx* c, const float* x, const float* v, const float* F_int,
+                                  const float* F_ext, float* x_out, float* v_out) {
+  if (!c || !x || !v || !F_int || !F_ext || !x_out || !v_out)
+    return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  cudaSetDevice(c->device);
+  return cuda_status(c, launch_advance(c, x, v, F_int, F_ext, x_out, v_out), "ibm_advance");
+}
+
+extern "C" ibm_status ibm_spread(ibm_ctx* c, const float* x, const float* Fm, float* fx, float* fy,
+                                 float* fz) {
+  if (!c || !x || !Fm || !fx || !fy || !fz) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  cudaSetDevice(c->device);
+  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Fm,
+                             nullptr, fx, fy, fz, false, false, false, true, false);
+  return cuda_status(c, e, "ibm_spread");
+}
+
+extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const float* u,
+                               const float* vv, const float* w, float* x_out, float* v_out,
+                               float* fx, float* fy, float* fz, uint32_t flags) {
+  if (!c || !x || !v || !u || !vv || !w || !x_out || !v_out || !fx || !fy || !fz)
+    return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (x_out == x || v_out == v || x_out == v || v_out == x)
+    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_step: outputs must not alias the inputs");
+  cudaSetDevice(c->device);
+  const bool clear = (flags & IBM_STEP_CLEAR_PREV) != 0;
+  cudaError_t e = cudaSuccess;
+  auto mark = [&](int k) {
+    if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[k], c->stream);
+  };
+  mark(0);
+  if (clear && c->have_prev) e = launch_clear(c, fx, fy, fz);
+  mark(1);
+  if (e == cudaSuccess)
+    e = launch_mls(c, x, v, u, vv, w, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz, true, true,
+                   true, true, clear);
+  mark(2);
+  if (e == cudaSuccess)
+    e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true);
+  mark(3);
+  if (e == cudaSuccess) {
+    c->have_prev = clear;
+    c->timed = c->timing;
+  }
+  return cuda_status(c, e, "ibm_step");
+}
+
+extern "C" ibm_status ibm_set_phase_timing(ibm_ctx* c, int32_t on) {
+  if (!c) return IBM_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (on && !c->ev[0]) {
+    for (auto& ev : c->ev) {
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_status(c, e, "cudaEventCreate");
+    }
+  }
+  c->timing = on != 0;
+  c->timed = false;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_get_phase_times(ibm_ctx* c, float* ms) {
+  if (!c || !ms) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (!c->timed) return set_err(c, IBM_ERR_INVALID_ARG, "no timed ibm_step recorded");
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaEventSynchronize(c->ev[3]);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(ms + k, c->ev[k], c->ev[k + 1]);
+  return cuda_status(c, e, "ibm_get_phase_times");
+}
+
+extern "C" ibm_status ibm_check_device_error(ibm_ctx* c) {
+  if (!c) return IBM_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  int32_t w = 0;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&w, c->d.err, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(c, e, "ibm_check_device_error");
+  if (w) {
+    cudaMemset(c->d.err, 0, sizeof(w));
+    return set_err(c, IBM_ERR_DEVICE,
+                   std::string("device error word ") + std::to_string(w) +
+                       ((w & ERR_NONFINITE) ? " (non-finite or out-of-range marker position)" : ""));
+  }
+  return IBM_OK;
+}

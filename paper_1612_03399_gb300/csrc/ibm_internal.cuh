@@ -1,0 +1,145 @@
+// Internal device-side layout shared by the host builder and the kernels of
+// the GB300 IP + MLS-IBM library.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ibm.h"
+
+namespace ibm {
+
+// ---------------------------------------------------------------------------
+// per-body record (one per body, read by every kernel through the work lists)
+// ---------------------------------------------------------------------------
+struct BodyDev {
+  int32_t v_off, f_off, e_off, topo;   // global offsets, topology id
+  int32_t nv, nf, ne, closed;
+  int32_t G[3];                        // floor(origin_d / h_d)
+  int32_t chunk_off;                   // first marker chunk of this body
+  float frac[3];                       // origin_d / h_d - G_d, in [0, 1)
+  int32_t n_chunk;
+  float ks, kb, ka, kA, kv, inv_mass;  // elastic constants, 1/m
+  float pad0, pad1;
+  double A0, V0;                       // rest area and volume (float64)
+};
+
+// per distinct mesh topology (shared by every body with the same faces)
+struct TopoDev {
+  int32_t nv, nf, ne, n_patch;
+  int32_t tri_off;      // into tri   (3 int32 per face, body-local vertex ids)
+  int32_t edge_off;     // into edge  (int4 a, b, c, d per edge; d = -1 on a boundary edge)
+  int32_t v2f_ptr_off;  // into v2f_ptr (nv + 1 entries, relative to v2f_idx_off)
+  int32_t v2f_idx_off;  // into v2f_idx (body-local face ids)
+  int32_t patch_off;    // into patch headers
+  int32_t pad[3];
+};
+
+// One force-kernel block works on a "patch": a contiguous range of a
+// topology's vertices (own vertices) plus the halo vertices that the
+// elements touching them reference.
+struct PatchHdr {
+  int32_t own0, n_own, n_loc, loc_off;       // own range, local vertex count, loc_vert offset
+  int32_t n_edge, edge_off, n_face, face_off;
+  int32_t csr_off, slot_off, n_slot, pad;    // csr_ptr offset (n_own + 1), csr_slot offset
+};
+
+// element records local to a patch: local vertex indices (0xFFFF = none)
+struct PEdge {
+  uint16_t l[4];       // a, b (edge), c, d (wings)
+  int32_t eid;         // body-local edge id; bit 31 set when this patch owns the edge
+};
+struct PFace {
+  uint16_t l[3];
+  uint16_t owned;      // 1 when this patch owns the face (energy bookkeeping)
+  int32_t fid;         // body-local face id
+};
+
+struct Grid {
+  int32_t n[3];
+  float h[3], invh[3];
+};
+
+// scalars of one call
+struct StepConsts {
+  float dt, inv_dt, mu, probe_h;
+  float kappa;           // 1 / (1.5 alpha)^2: W = exp(-kappa * (delta in cells)^2) per direction
+  float cl_scale;        // (hx + hy + hz) / 3 / (hx hy hz): c_l = A_l * cl_scale
+  int32_t forward_euler;
+  int32_t pad;
+};
+
+constexpr int kChunk = 128;          // markers (faces) per block of the MLS kernel
+constexpr int kForceThreads = 256;   // threads per force-kernel block
+constexpr uint16_t kNone = 0xFFFF;
+
+// error word bits (device)
+enum : int32_t { ERR_NONFINITE = 1, ERR_BAD_INDEX = 2 };
+
+struct DeviceTables {
+  BodyDev* body = nullptr;
+  TopoDev* topo = nullptr;
+  int32_t* tri = nullptr;
+  int4* edge = nullptr;
+  int32_t* v2f_ptr = nullptr;
+  int32_t* v2f_idx = nullptr;
+  PatchHdr* patch = nullptr;
+  int32_t* loc_vert = nullptr;
+  PEdge* pedge = nullptr;
+  PFace* pface = nullptr;
+  int32_t* csr_ptr = nullptr;
+  uint16_t* csr_slot = nullptr;
+  float* l0 = nullptr;          // [E] rest edge lengths
+  float2* cs0 = nullptr;        // [E] (cos theta0, sin theta0) per hinge edge
+  float* A0f = nullptr;         // [F] rest face areas
+  uint8_t* clamp = nullptr;     // [V]
+  float* rest = nullptr;        // [3][V] body-frame rest positions
+  int4* chunks = nullptr;       // (body, first local face, count, chunk index in body)
+  int2* work = nullptr;         // (body, patch index within topology)
+  double* partial = nullptr;    // [n_chunks][2] per-chunk (A, V)
+  int32_t* counter = nullptr;   // [B] chunk arrival counters
+  double* meas = nullptr;       // [B][2] (A, V)
+  float* fext = nullptr;        // [3][F] scratch marker traction (ibm_step)
+  int32_t* err = nullptr;       // device error word
+};
+
+}  // namespace ibm
+
+struct ibm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t V = 0, F = 0, E = 0, B = 0;
+  int32_t n_topo = 0, n_chunks = 0, n_work = 0;
+  ibm_params prm{};
+  ibm_grid_desc gdesc{};
+  ibm::Grid grid{};
+  ibm::StepConsts sc{};
+  size_t force_smem = 0;
+  int32_t max_own = 0;
+  bool have_prev = false;
+  uint8_t* d_bricks = nullptr;  // one flag per 8^3-cell brick touched by the last ibm_step spread
+  bool timing = false;          // record phase events in ibm_step
+  bool timed = false;           // a timed step has been recorded
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<ibm::BodyDev> h_body;
+  std::vector<void*> allocations;
+  ibm::DeviceTables d;
+};
+
+namespace ibm {
+// kernel launchers (defined in the kernel translation units)
+cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* u,
+                       const float* vv, const float* w, float* U, float* Fm, const float* Fm_in,
+                       float* Fext, float* fx, float* fy, float* fz, bool measure, bool interp,
+                       bool probe, bool spread, bool record_cells);
+cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz);
+cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float* Fext,
+                         float* Fint, float* x_out, float* v_out, double* energy, bool advance);
+cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,
+                           const float* Fext, float* x_out, float* v_out);
+cudaError_t set_force_smem_limit(size_t bytes);
+}  // namespace ibm

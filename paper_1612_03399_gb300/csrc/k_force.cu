@@ -1,0 +1,311 @@
+// Internal forces of the interaction potentials (Sec. 2.3, Eqs.
+// elaspot..areapot) and the node update (Sec. 2.3; Sec. 5 step 4).
+//
+// One block per patch (a contiguous range of a topology's vertices).  The
+// block stages the positions of its own and halo vertices in shared memory,
+// evaluates every element touching an own vertex exactly once into
+// shared-memory contribution slots (4 per edge: a, b and the wings c, d; 3 per
+// face), and each own vertex then sums its slots through a CSR list fixed at
+// build time.  The summation order never changes, so F_int is bitwise
+// deterministic; nothing is written to global memory but the result.
+//
+// Edge e = (a, b) with wings c (face (a, b, c)) and d (face (b, a, d)):
+//   spring   W = k_s/2 (l - l0)^2      F_a = k_s (l - l0) e/l, F_b = -F_a
+//   bending  W = k_b (1 - cos(theta - theta0)),  F = -k_b sin(theta - theta0) grad theta,
+//            cos theta = n1.n2, sin theta = (n1 x n2).e/|e|, and with
+//            N1 = e x (c - a), N2 = (d - b) x e, s_c = (c - a).e/|e|^2, s_d likewise,
+//            grad_c theta = -|e| N1/|N1|^2, grad_d theta = -|e| N2/|N2|^2,
+//            grad_a theta = -(1 - s_c) grad_c - (1 - s_d) grad_d,
+//            grad_b theta = -s_c grad_c - s_d grad_d
+//            (the unique gradient that is invariant under translations and
+//            rotations and moves the wings about the hinge).
+// Face (a, b, c), A_f = |N|/2, n = N/|N|:
+//   grad_a A_f = n x (c - b)/2 (cyclic), grad_a V = b x c / 6 (cyclic, body frame),
+//   F = -(k_A (A - A0)/A0 + k_a (A_f - A0_f)/A0_f) grad A_f - k_v (V - V0)/V0 grad V.
+#include <cuda_runtime.h>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+namespace {
+
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 scale(V3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+
+struct Smem {
+  float *px, *py, *pz, *cx, *cy, *cz;
+  __device__ V3 pos(int i) const { return {px[i], py[i], pz[i]}; }
+  __device__ void put(int s, V3 f) const {
+    cx[s] = f.x;
+    cy[s] = f.y;
+    cz[s] = f.z;
+  }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <bool ADVANCE>
+__global__ void __launch_bounds__(kForceThreads) force_kernel(
+    DeviceTables T, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
+    const float* __restrict__ v, const float* __restrict__ Fext, float* __restrict__ Fint,
+    float* __restrict__ x_out, float* __restrict__ v_out, double* __restrict__ energy) {
+  extern __shared__ float sm[];
+  const int2 wk = T.work[blockIdx.x];
+  const BodyDev B = T.body[wk.x];
+  const TopoDev topo = T.topo[B.topo];
+  const PatchHdr P = T.patch[topo.patch_off + wk.y];
+  Smem S;
+  S.px = sm;
+  S.py = S.px + P.n_loc;
+  S.pz = S.py + P.n_loc;
+  S.cx = S.pz + P.n_loc;
+  S.cy = S.cx + P.n_slot;
+  S.cz = S.cy + P.n_slot;
+
+  for (int i = threadIdx.x; i < P.n_loc; i += blockDim.x) {
+    const int gv = B.v_off + __ldg(T.loc_vert + P.loc_off + i);
+    S.px[i] = __ldg(x + gv);
+    S.py[i] = __ldg(x + V + gv);
+    S.pz[i] = __ldg(x + 2 * V + gv);
+  }
+  // per-body global terms from the float64 area / volume sums
+  const double Ab = T.meas[2 * wk.x], Vb = T.meas[2 * wk.x + 1];
+  const float cA = (float)(B.kA * ((Ab - B.A0) / B.A0));
+  const float cV = B.closed ? (float)(B.kv * ((Vb - B.V0) / B.V0)) : 0.f;
+  const bool want_e = energy != nullptr;
+  double eS = 0.0, eB = 0.0, eA = 0.0;
+  __syncthreads();
+
+  // edges: spring + bending
+  for (int k = threadIdx.x; k < P.n_edge; k += blockDim.x) {
+    const PEdge r = T.pedge[P.edge_off + k];
+    const int ge = B.e_off + (r.eid & 0x7fffffff);
+    const V3 pa = S.pos(r.l[0]), pb = S.pos(r.l[1]);
+    const V3 e = sub(pb, pa);
+    const float l2 = dot(e, e);
+    const float inv_l = rsqrtf(l2);
+    const float l = l2 * inv_l;
+    const float l0 = __ldg(T.l0 + ge);
+    const float s = B.ks * (l - l0) * inv_l;
+    V3 fa = scale(e, s), fb = scale(e, -s), fc = {0.f, 0.f, 0.f}, fd = {0.f, 0.f, 0.f};
+    if (want_e && (r.eid < 0)) eS += 0.5 * (double)B.ks * (double)(l - l0) * (double)(l - l0);
+    if (r.l[3] != kNone) {
+      const V3 pc = S.pos(r.l[2]), pd = S.pos(r.l[3]);
+      const V3 ac = sub(pc, pa), ad = sub(pd, pa);
+      const V3 N1 = cross(e, ac);
+      const V3 N2 = cross(sub(pd, pb), e);
+      const float q1 = dot(N1, N1), q2 = dot(N2, N2);
+      const float r1 = rsqrtf(q1), r2 = rsqrtf(q2);
+      const V3 n1 = scale(N1, r1), n2 = scale(N2, r2);
+      const float cth = dot(n1, n2);
+      const float sth = dot(cross(n1, n2), e) * inv_l;
+      const float2 cs0 = __ldg(T.cs0 + ge);
+      const float sdiff = sth * cs0.x - cth * cs0.y;  // sin(theta - theta0)
+      const float coef = -B.kb * sdiff;               // F = coef * grad theta
+      const V3 gc = scale(N1, -l * r1 * r1);
+      const V3 gd = scale(N2, -l * r2 * r2);
+      const float inv_l2 = inv_l * inv_l;
+      const float sc_ = dot(ac, e) * inv_l2, sd_ = dot(ad, e) * inv_l2;
+      const V3 ga = {-(1.f - sc_) * gc.x - (1.f - sd_) * gd.x, -(1.f - sc_) * gc.y - (1.f - sd_) * gd.y,
+                     -(1.f - sc_) * gc.z - (1.f - sd_) * gd.z};
+      const V3 gb = {-sc_ * gc.x - sd_ * gd.x, -sc_ * gc.y - sd_ * gd.y, -sc_ * gc.z - sd_ * gd.z};
+      fa = {fa.x + coef * ga.x, fa.y + coef * ga.y, fa.z + coef * ga.z};
+      fb = {fb.x + coef * gb.x, fb.y + coef * gb.y, fb.z + coef * gb.z};
+      fc = scale(gc, coef);
+      fd = scale(gd, coef);
+      if (want_e && (r.eid < 0))
+        eB += (double)B.kb * (1.0 - ((double)cth * cs0.x + (double)sth * cs0.y));
+    }
+    S.put(4 * k + 0, fa);
+    S.put(4 * k + 1, fb);
+    S.put(4 * k + 2, fc);
+    S.put(4 * k + 3, fd);
+  }
+  // faces: local area, global area, volume
+  const int fbase = 4 * P.n_edge;
+  for (int k = threadIdx.x; k < P.n_face; k += blockDim.x) {
+    const PFace r = T.pface[P.face_off + k];
+    const V3 pa = S.pos(r.l[0]), pb = S.pos(r.l[1]), pc = S.pos(r.l[2]);
+    const V3 N = cross(sub(pb, pa), sub(pc, pa));
+    const float q = dot(N, N);
+    const float rn = rsqrtf(q);
+    const float Af = 0.5f * q * rn;
+    const float A0f = __ldg(T.A0f + B.f_off + r.fid);
+    const float gA = cA + B.ka * (Af - A0f) / A0f;
+    const V3 n = scale(N, rn);
+    const float hA = -0.5f * gA, hV = -cV * (1.f / 6.f);
+    const V3 ga = cross(n, sub(pc, pb)), gb = cross(n, sub(pa, pc)), gcc = cross(n, sub(pb, pa));
+    const V3 va = cross(pb, pc), vb = cross(pc, pa), vc = cross(pa, pb);
+    S.put(fbase + 3 * k + 0, {hA * ga.x + hV * va.x, hA * ga.y + hV * va.y, hA * ga.z + hV * va.z});
+    S.put(fbase + 3 * k + 1, {hA * gb.x + hV * vb.x, hA * gb.y + hV * vb.y, hA * gb.z + hV * vb.z});
+    S.put(fbase + 3 * k + 2, {hA * gcc.x + hV * vc.x, hA * gcc.y + hV * vc.y, hA * gcc.z + hV * vc.z});
+    if (want_e && r.owned) eA += 0.5 * (double)B.ka * (double)(Af - A0f) * (double)(Af - A0f) / A0f;
+  }
+  __syncthreads();
+
+  // own vertices: fixed-order gather of the slots
+  for (int i = threadIdx.x; i < P.n_own; i += blockDim.x) {
+    const int s0 = __ldg(T.csr_ptr + P.csr_off + i), s1 = __ldg(T.csr_ptr + P.csr_off + i + 1);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int k = s0; k < s1; ++k) {
+      const int s = T.csr_slot[P.slot_off + k];
+      fx += S.cx[s];
+      fy += S.cy[s];
+      fz += S.cz[s];
+    }
+    const int lv = P.own0 + i;
+    const int gv = B.v_off + lv;
+    if (!ADVANCE) {
+      Fint[gv] = fx;
+      Fint[V + gv] = fy;
+      Fint[2 * V + gv] = fz;
+    } else {
+      // F_ext^v = sum over the vertex's faces of F_ext / 3
+      const int* vp = T.v2f_ptr + topo.v2f_ptr_off;
+      const int q0 = __ldg(vp + lv), q1 = __ldg(vp + lv + 1);
+      float ex = 0.f, ey = 0.f, ez = 0.f;
+      for (int q = q0; q < q1; ++q) {
+        const int gf = B.f_off + __ldg(T.v2f_idx + topo.v2f_idx_off + q);
+        ex += __ldg(Fext + gf);
+        ey += __ldg(Fext + F + gf);
+        ez += __ldg(Fext + 2 * F + gf);
+      }
+      const float third = 1.f / 3.f;
+      const float ax = (fx + ex * third) * B.inv_mass, ay = (fy + ey * third) * B.inv_mass,
+                  az = (fz + ez * third) * B.inv_mass;
+      const float x0 = S.px[i], y0 = S.py[i], z0 = S.pz[i];
+      float vx = __ldg(v + gv), vy = __ldg(v + V + gv), vz = __ldg(v + 2 * V + gv);
+      float nx, ny, nz;
+      if (sc.forward_euler) {
+        nx = x0 + sc.dt * vx; ny = y0 + sc.dt * vy; nz = z0 + sc.dt * vz;
+        vx += sc.dt * ax; vy += sc.dt * ay; vz += sc.dt * az;
+      } else {
+        vx += sc.dt * ax; vy += sc.dt * ay; vz += sc.dt * az;
+        nx = x0 + sc.dt * vx; ny = y0 + sc.dt * vy; nz = z0 + sc.dt * vz;
+      }
+      if (T.clamp[gv]) {
+        nx = x0; ny = y0; nz = z0;
+        vx = vy = vz = 0.f;
+      }
+      x_out[gv] = nx; x_out[V + gv] = ny; x_out[2 * V + gv] = nz;
+      v_out[gv] = vx; v_out[V + gv] = vy; v_out[2 * V + gv] = vz;
+    }
+  }
+
+  if (want_e) {
+    __shared__ double red[3][kForceThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    eS = warp_sum(eS);
+    eB = warp_sum(eB);
+    eA = warp_sum(eA);
+    if (lane == 0) {
+      red[0][wid] = eS;
+      red[1][wid] = eB;
+      red[2][wid] = eA;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0, c = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        a += red[0][k];
+        b += red[1][k];
+        c += red[2][k];
+      }
+      atomicAdd(energy + 5 * wk.x + 0, a);
+      atomicAdd(energy + 5 * wk.x + 1, b);
+      atomicAdd(energy + 5 * wk.x + 2, c);
+      if (wk.y == 0) {
+        energy[5 * wk.x + 3] = 0.5 * B.kA * (Ab - B.A0) * (Ab - B.A0) / B.A0;
+        energy[5 * wk.x + 4] = B.closed ? 0.5 * B.kv * (Vb - B.V0) * (Vb - B.V0) / B.V0 : 0.0;
+      }
+    }
+  }
+}
+
+// node update with a given F_int (the stand-alone advance entry point)
+__global__ void __launch_bounds__(kForceThreads) advance_kernel(
+    DeviceTables T, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
+    const float* __restrict__ v, const float* __restrict__ Fint, const float* __restrict__ Fext,
+    float* __restrict__ x_out, float* __restrict__ v_out) {
+  const int2 wk = T.work[blockIdx.x];
+  const BodyDev B = T.body[wk.x];
+  const TopoDev topo = T.topo[B.topo];
+  const PatchHdr P = T.patch[topo.patch_off + wk.y];
+  for (int i = threadIdx.x; i < P.n_own; i += blockDim.x) {
+    const int lv = P.own0 + i;
+    const int gv = B.v_off + lv;
+    const int* vp = T.v2f_ptr + topo.v2f_ptr_off;
+    const int q0 = __ldg(vp + lv), q1 = __ldg(vp + lv + 1);
+    float ex = 0.f, ey = 0.f, ez = 0.f;
+    for (int q = q0; q < q1; ++q) {
+      const int gf = B.f_off + __ldg(T.v2f_idx + topo.v2f_idx_off + q);
+      ex += __ldg(Fext + gf);
+      ey += __ldg(Fext + F + gf);
+      ez += __ldg(Fext + 2 * F + gf);
+    }
+    const float third = 1.f / 3.f;
+    const float ax = (__ldg(Fint + gv) + ex * third) * B.inv_mass;
+    const float ay = (__ldg(Fint + V + gv) + ey * third) * B.inv_mass;
+    const float az = (__ldg(Fint + 2 * V + gv) + ez * third) * B.inv_mass;
+    const float x0 = __ldg(x + gv), y0 = __ldg(x + V + gv), z0 = __ldg(x + 2 * V + gv);
+    float vx = __ldg(v + gv), vy = __ldg(v + V + gv), vz = __ldg(v + 2 * V + gv);
+    float nx, ny, nz;
+    if (sc.forward_euler) {
+      nx = x0 + sc.dt * vx; ny = y0 + sc.dt * vy; nz = z0 + sc.dt * vz;
+      vx += sc.dt * ax; vy += sc.dt * ay; vz += sc.dt * az;
+    } else {
+      vx += sc.dt * ax; vy += sc.dt * ay; vz += sc.dt * az;
+      nx = x0 + sc.dt * vx; ny = y0 + sc.dt * vy; nz = z0 + sc.dt * vz;
+    }
+    if (T.clamp[gv]) {
+      nx = x0; ny = y0; nz = z0;
+      vx = vy = vz = 0.f;
+    }
+    x_out[gv] = nx; x_out[V + gv] = ny; x_out[2 * V + gv] = nz;
+    v_out[gv] = vx; v_out[V + gv] = vy; v_out[2 * V + gv] = vz;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float* Fext,
+                         float* Fint, float* x_out, float* v_out, double* energy, bool advance) {
+  if (c->n_work == 0) return cudaSuccess;
+  if (advance)
+    force_kernel<true><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
+        c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, Fext, Fint, x_out, v_out, energy);
+  else
+    force_kernel<false><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
+        c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, Fext, Fint, x_out, v_out, energy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,
+                           const float* Fext, float* x_out, float* v_out) {
+  if (c->n_work == 0) return cudaSuccess;
+  advance_kernel<<<c->n_work, kForceThreads, 0, c->stream>>>(c->d, c->sc, (int32_t)c->V,
+                                                              (int32_t)c->F, x, v, Fint, Fext,
+                                                              x_out, v_out);
+  return cudaGetLastError();
+}
+
+cudaError_t set_force_smem_limit(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(force_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(force_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes);
+}
+
+}  // namespace ibm

@@ -15,6 +15,7 @@ drops (Sec. 3.1), 2562-node drops (Sec. 3.2), and closed/open membranes
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -61,6 +62,12 @@ def icosphere(level: int):
     V = 10*4^level + 2, F = 20*4^level, faces oriented counter-clockwise seen
     from outside (outward normals).
     """
+    v, t = _icosphere_cached(int(level))
+    return v.copy(), t.copy()
+
+
+@functools.lru_cache(maxsize=None)
+def _icosphere_cached(level: int):
     t = (1.0 + 5.0 ** 0.5) / 2.0
     v = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
                   [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
