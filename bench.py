@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--patch", type=int, default=0)
+    ap.add_argument("--bodies", type=int, default=0,
+                    help="profiling only: fewer drops on the same grid (drops1000 workload)")
     return ap.parse_args()
 
 
@@ -304,6 +306,9 @@ def run_gb300(args, ws, rank, local):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     make, descr = WORKLOADS[args.workload]
+    if args.bodies and args.workload == "drops1000":
+        make = lambda seed: W.batched_drops(args.bodies, 3, 512, seed=seed)  # noqa: E731
+        descr = descr.replace("1000 icosphere", f"{args.bodies} icosphere")
     wl = make(1 + rank)
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
                        patch_size=args.patch, device=local)
@@ -397,6 +402,7 @@ def run_gb300(args, ws, rank, local):
                              "achieved_gbs": bytes_model[n] / (mean_ph[k] * 1e-3) / 1e9}
                          for k, n in enumerate(names) if n != "clear"},
         "gpu_launches": 3 * args.steps,
+        "counters": ctx.counters(),
         "e2e": e2e,
         "clocks": clk,
     }

@@ -184,6 +184,11 @@ ibm_status ibm_check_device_error(ibm_ctx* ctx);
 ibm_status ibm_set_phase_timing(ibm_ctx* ctx, int32_t on);
 ibm_status ibm_get_phase_times(ibm_ctx* ctx, float* ms);
 
+/* Diagnostic counters since creation (synchronises): host out[4] =
+ * (marker blocks whose stencil box did not fit shared memory and took the
+ * direct global path, 0, 0, 0). */
+ibm_status ibm_get_counters(ibm_ctx* ctx, int64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

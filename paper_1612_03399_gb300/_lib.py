@@ -65,6 +65,7 @@ SIGNATURES = {
     "ibm_check_device_error": (C.c_int, [P]),
     "ibm_set_phase_timing": (C.c_int, [P, C.c_int32]),
     "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
+    "ibm_get_counters": (C.c_int, [P, C.POINTER(C.c_int64)]),
 }
 
 _lib = None
@@ -235,6 +236,11 @@ class Context:
 
     def set_phase_timing(self, on=True):
         self._check(self.lib.ibm_set_phase_timing(self.h, 1 if on else 0))
+
+    def counters(self):
+        out = (C.c_int64 * 4)()
+        self._check(self.lib.ibm_get_counters(self.h, out))
+        return {"marker_box_fallbacks": int(out[0])}
 
     def phase_times(self):
         """(clear, marker, force+update) milliseconds of the last timed step."""

@@ -207,13 +207,14 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
     H.slot_off = (int32_t)T.csr_slot.size();
     for (int v = o0; v < o1; ++v) {
       T.csr_ptr.push_back((int32_t)T.csr_slot.size() - H.slot_off);
+      // contribution slots are laid out [role][element] (edges, then faces)
       for (int k = v2e_ptr[v]; k < v2e_ptr[v + 1]; ++k) {
         const int e = v2e[k] >> 2, role = v2e[k] & 3;
-        T.csr_slot.push_back((uint16_t)(4 * e_loc[e] + role));
+        T.csr_slot.push_back((uint16_t)(role * H.n_edge + e_loc[e]));
       }
       for (int k = T.v2f_ptr[v]; k < T.v2f_ptr[v + 1]; ++k) {
         const int f = v2fc[k] / 3, corner = v2fc[k] % 3;
-        T.csr_slot.push_back((uint16_t)(4 * H.n_edge + 3 * f_loc[f] + corner));
+        T.csr_slot.push_back((uint16_t)(4 * H.n_edge + corner * H.n_face + f_loc[f]));
       }
     }
     T.csr_ptr.push_back((int32_t)T.csr_slot.size() - H.slot_off);
@@ -567,8 +568,9 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.meas = zeros<double>(c, 2 * (size_t)n_bodies);
     d.fext = zeros<float>(c, 3 * (size_t)F);
     d.err = zeros<int32_t>(c, 1);
-    const size_t nbr = (size_t)((grid->n[0] + 7) / 8) * ((grid->n[1] + 7) / 8) * ((grid->n[2] + 7) / 8);
-    c->d_bricks = zeros<uint8_t>(c, nbr);
+    d.coef = zeros<float2>(c, (size_t)n_bodies);
+    d.boxes = zeros<int4>(c, 2 * (size_t)c->n_chunks);
+    d.stats = zeros<int32_t>(c, 4);
     check_cuda(cudaDeviceSynchronize(), "create");
     *out = c;
     return IBM_OK;
@@ -762,6 +764,16 @@ extern "C" ibm_status ibm_set_phase_timing(ibm_ctx* c, int32_t on) {
   c->timing = on != 0;
   c->timed = false;
   return IBM_OK;
+}
+
+extern "C" ibm_status ibm_get_counters(ibm_ctx* c, int64_t* out) {
+  if (!c || !out) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  cudaSetDevice(c->device);
+  int32_t s[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(s, c->d.stats, sizeof(s), cudaMemcpyDeviceToHost);
+  for (int k = 0; k < 4; ++k) out[k] = s[k];
+  return cuda_status(c, e, "ibm_get_counters");
 }
 
 extern "C" ibm_status ibm_get_phase_times(ibm_ctx* c, float* ms) {

@@ -102,9 +102,14 @@ struct DeviceTables {
   double* partial = nullptr;    // [n_chunks][2] per-chunk (A, V)
   int32_t* counter = nullptr;   // [B] chunk arrival counters
   double* meas = nullptr;       // [B][2] (A, V)
+  float2* coef = nullptr;       // [B] (k_A (A - A0)/A0, k_v (V - V0)/V0) for the force kernel
   float* fext = nullptr;        // [3][F] scratch marker traction (ibm_step)
+  int4* boxes = nullptr;        // [n_chunks][2] grid box (lo, size) each marker block spread into
+  int32_t* stats = nullptr;     // [4] counters: marker blocks that did not fit shared memory
   int32_t* err = nullptr;       // device error word
 };
+
+constexpr int kMarkerSmemBytes = 48 * 1024;   // stencil box staging per marker block
 
 }  // namespace ibm
 
@@ -121,7 +126,6 @@ struct ibm_ctx {
   size_t force_smem = 0;
   int32_t max_own = 0;
   bool have_prev = false;
-  uint8_t* d_bricks = nullptr;  // one flag per 8^3-cell brick touched by the last ibm_step spread
   bool timing = false;          // record phase events in ibm_step
   bool timed = false;           // a timed step has been recorded
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

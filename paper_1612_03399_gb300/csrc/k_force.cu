@@ -80,9 +80,10 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     S.pz[i] = __ldg(x + 2 * V + gv);
   }
   // per-body global terms from the float64 area / volume sums
-  const double Ab = T.meas[2 * wk.x], Vb = T.meas[2 * wk.x + 1];
-  const float cA = (float)(B.kA * ((Ab - B.A0) / B.A0));
-  const float cV = B.closed ? (float)(B.kv * ((Vb - B.V0) / B.V0)) : 0.f;
+  // per-body global-term coefficients, formed once per body from the float64
+  // area / volume sums by the marker kernel
+  const float2 cf = T.coef[wk.x];
+  const float cA = cf.x, cV = cf.y;
   const bool want_e = energy != nullptr;
   double eS = 0.0, eB = 0.0, eA = 0.0;
   __syncthreads();
@@ -127,10 +128,11 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
       if (want_e && (r.eid < 0))
         eB += (double)B.kb * (1.0 - ((double)cth * cs0.x + (double)sth * cs0.y));
     }
-    S.put(4 * k + 0, fa);
-    S.put(4 * k + 1, fb);
-    S.put(4 * k + 2, fc);
-    S.put(4 * k + 3, fd);
+    // slot layout [role][element]: consecutive threads hit consecutive banks
+    S.put(k, fa);
+    S.put(P.n_edge + k, fb);
+    S.put(2 * P.n_edge + k, fc);
+    S.put(3 * P.n_edge + k, fd);
   }
   // faces: local area, global area, volume
   const int fbase = 4 * P.n_edge;
@@ -147,9 +149,10 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     const float hA = -0.5f * gA, hV = -cV * (1.f / 6.f);
     const V3 ga = cross(n, sub(pc, pb)), gb = cross(n, sub(pa, pc)), gcc = cross(n, sub(pb, pa));
     const V3 va = cross(pb, pc), vb = cross(pc, pa), vc = cross(pa, pb);
-    S.put(fbase + 3 * k + 0, {hA * ga.x + hV * va.x, hA * ga.y + hV * va.y, hA * ga.z + hV * va.z});
-    S.put(fbase + 3 * k + 1, {hA * gb.x + hV * vb.x, hA * gb.y + hV * vb.y, hA * gb.z + hV * vb.z});
-    S.put(fbase + 3 * k + 2, {hA * gcc.x + hV * vc.x, hA * gcc.y + hV * vc.y, hA * gcc.z + hV * vc.z});
+    S.put(fbase + k, {hA * ga.x + hV * va.x, hA * ga.y + hV * va.y, hA * ga.z + hV * va.z});
+    S.put(fbase + P.n_face + k, {hA * gb.x + hV * vb.x, hA * gb.y + hV * vb.y, hA * gb.z + hV * vb.z});
+    S.put(fbase + 2 * P.n_face + k,
+          {hA * gcc.x + hV * vc.x, hA * gcc.y + hV * vc.y, hA * gcc.z + hV * vc.z});
     if (want_e && r.owned) eA += 0.5 * (double)B.ka * (double)(Af - A0f) * (double)(Af - A0f) / A0f;
   }
   __syncthreads();
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
       atomicAdd(energy + 5 * wk.x + 1, b);
       atomicAdd(energy + 5 * wk.x + 2, c);
       if (wk.y == 0) {
+        const double Ab = T.meas[2 * wk.x], Vb = T.meas[2 * wk.x + 1];
         energy[5 * wk.x + 3] = 0.5 * B.kA * (Ab - B.A0) * (Ab - B.A0) / B.A0;
         energy[5 * wk.x + 4] = B.closed ? 0.5 * B.kv * (Vb - B.V0) * (Vb - B.V0) / B.V0 : 0.0;
       }

@@ -1,9 +1,16 @@
-// Marker kernels: face geometry, per-body area/volume reductions, MLS
+// Marker kernel: face geometry, per-body area/volume reductions, MLS
 // interpolation at the centroid, direct-forcing marker force, probe gradient
 // and traction, and spreading (Sec. 2.2, Eqs. mls..mls_cl; Sec. 5 steps 1-3).
 //
-// One thread per face (marker).  A block holds up to kChunk faces of ONE body,
-// so every body scalar is uniform across the block.
+// One block = up to kChunk faces (markers) of ONE body, one thread per face.
+// Faces are ordered along a space-filling curve, so a block's markers form a
+// compact surface patch.  The block first finds the grid box that holds every
+// 3x3x3 support of its centroids and probe ends, stages u, v, w on that box in
+// shared memory with coalesced row loads, interpolates from shared memory,
+// accumulates its spread contributions in a shared force box with shared
+// atomics, and flushes the box to the global force fields once (one global
+// atomic per non-zero node instead of 81 per marker).  A block whose box does
+// not fit falls back to direct global loads and atomics.
 //
 // MLS with the linear basis and a weight that factorises over directions
 // (W = prod_d exp(-kappa delta_d^2), delta in cells) has an exact closed-form
@@ -16,6 +23,7 @@
 // the 27 node values.  Partition of unity holds exactly, so c_l reduces to
 // A_l (hx+hy+hz)/3 / (hx hy hz) on the uniform grid.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 
 #include "ibm_internal.cuh"
@@ -88,38 +96,58 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-// three wrapped node indices ic-1, ic, ic+1 of one direction
-__device__ __forceinline__ void node3(int c, int n, int (&o)[3]) {
-  const int m = wrap(c - 1, n);
-  o[0] = m;
-  o[1] = (m + 1 == n) ? 0 : m + 1;
-  o[2] = (o[1] + 1 == n) ? 0 : o[1] + 1;
+// Centre node (unwrapped global lattice index) and fractional offset of a
+// point, in every direction, on the lattice of velocity component `comp`
+// (node offset 0 along the component's own direction, 1/2 across it).
+__device__ __forceinline__ void locate(const float (&tau)[3], int comp, const int (&G)[3],
+                                       int (&c)[3], float (&tp)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float u = tau[d] - (d == comp ? 0.f : 0.5f);
+    const float cc = floorf(u + 0.5f);
+    tp[d] = u - cc;
+    c[d] = G[d] + (int)cc;
+  }
 }
 
-// Location of a point in one direction for a lattice with node offset `off`
-// (0 or 1/2 cell): tau = position / h in cells relative to the body's
-// integer origin G; returns the centre node (global, unwrapped) and the
-// fractional offset.
-__device__ __forceinline__ int locate(float tau, float off, int G, float& tp) {
-  const float u = tau - off;
-  const float c = floorf(u + 0.5f);
-  tp = u - c;
-  return G + (int)c;
-}
+// addressing of the 3x3x3 support: rows (sy, sz) and columns sx
+struct GlobalAcc {   // wrapped indices into a full [nz][ny][nx] field
+  int ix[3], iy[3], iz[3];
+  int nx, ny;
+  __device__ void init(const int (&c)[3], const Grid& g) {
+    nx = g.n[0];
+    ny = g.n[1];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      ix[s] = wrap(c[0] - 1 + s, g.n[0]);
+      iy[s] = wrap(c[1] - 1 + s, g.n[1]);
+      iz[s] = wrap(c[2] - 1 + s, g.n[2]);
+    }
+  }
+  __device__ int row(int sy, int sz) const { return (iz[sz] * ny + iy[sy]) * nx; }
+  __device__ int col(int sx) const { return ix[sx]; }
+};
+struct BoxAcc {      // indices into a box staged in shared memory
+  int base, sx, sxy;
+  __device__ void init(const int (&c)[3], const int (&lo)[3], const int (&s)[3]) {
+    sx = s[0];
+    sxy = s[0] * s[1];
+    base = (c[0] - 1 - lo[0]) + sx * (c[1] - 1 - lo[1]) + sxy * (c[2] - 1 - lo[2]);
+  }
+  __device__ int row(int sy, int sz) const { return base + sz * sxy + sy * sx; }
+  __device__ int col(int s) const { return s; }
+};
 
-// value of the MLS interpolant of `f` (one component) at the point
-__device__ __forceinline__ float mls_value(const float* __restrict__ f, const int (&ix)[3],
-                                           const int (&iy)[3], const int (&iz)[3], int nx,
-                                           int ny, const DirW& X, const DirW& Y,
-                                           const DirW& Z) {
+template <class Acc>
+__device__ __forceinline__ float mls_value(const float* __restrict__ f, const Acc& A, const DirW& X,
+                                           const DirW& Y, const DirW& Z) {
   float q = 0.f;
 #pragma unroll
   for (int sz = 0; sz < 3; ++sz) {
 #pragma unroll
     for (int sy = 0; sy < 3; ++sy) {
-      const int base = (iz[sz] * ny + iy[sy]) * nx;
-      const float u0 = __ldg(f + base + ix[0]), u1 = __ldg(f + base + ix[1]),
-                  u2 = __ldg(f + base + ix[2]);
+      const float* r = f + A.row(sy, sz);
+      const float u0 = r[A.col(0)], u1 = r[A.col(1)], u2 = r[A.col(2)];
       const float xa = X.a[0] * u0 + X.a[1] * u1 + X.a[2] * u2;
       const float xb = X.b[0] * u0 + X.b[1] * u1 + X.b[2] * u2;
       const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
@@ -129,19 +157,16 @@ __device__ __forceinline__ float mls_value(const float* __restrict__ f, const in
   return q;
 }
 
-// full derivative (in cells) of the MLS interpolant at the point
-__device__ __forceinline__ void mls_grad(const float* __restrict__ f, const int (&ix)[3],
-                                         const int (&iy)[3], const int (&iz)[3], int nx, int ny,
-                                         const DirWD& X, const DirWD& Y, const DirWD& Z,
-                                         float (&g)[3]) {
+template <class Acc>
+__device__ __forceinline__ void mls_grad(const float* __restrict__ f, const Acc& A, const DirWD& X,
+                                         const DirWD& Y, const DirWD& Z, float (&g)[3]) {
   float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
   for (int sz = 0; sz < 3; ++sz) {
 #pragma unroll
     for (int sy = 0; sy < 3; ++sy) {
-      const int base = (iz[sz] * ny + iy[sy]) * nx;
-      const float u0 = __ldg(f + base + ix[0]), u1 = __ldg(f + base + ix[1]),
-                  u2 = __ldg(f + base + ix[2]);
+      const float* r = f + A.row(sy, sz);
+      const float u0 = r[A.col(0)], u1 = r[A.col(1)], u2 = r[A.col(2)];
       const float xa = X.a[0] * u0 + X.a[1] * u1 + X.a[2] * u2;
       const float xb = X.b[0] * u0 + X.b[1] * u1 + X.b[2] * u2;
       const float xda = X.da[0] * u0 + X.da[1] * u1 + X.da[2] * u2;
@@ -156,79 +181,102 @@ __device__ __forceinline__ void mls_grad(const float* __restrict__ f, const int 
   g[0] = gx; g[1] = gy; g[2] = gz;
 }
 
-__device__ __forceinline__ void mls_spread(float* __restrict__ f, const int (&ix)[3],
-                                           const int (&iy)[3], const int (&iz)[3], int nx,
-                                           int ny, const DirW& X, const DirW& Y, const DirW& Z,
-                                           float coef) {
+template <class Acc>
+__device__ __forceinline__ void mls_spread(float* f, const Acc& A, const DirW& X, const DirW& Y,
+                                           const DirW& Z, float coef) {
 #pragma unroll
   for (int sz = 0; sz < 3; ++sz) {
 #pragma unroll
     for (int sy = 0; sy < 3; ++sy) {
-      const int base = (iz[sz] * ny + iy[sy]) * nx;
+      float* r = f + A.row(sy, sz);
       const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
       const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
 #pragma unroll
-      for (int sx = 0; sx < 3; ++sx) {
-        const float phi_c = (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1;
-        atomicAdd(f + base + ix[sx], phi_c);
-      }
+      for (int sx = 0; sx < 3; ++sx) atomicAdd(r + A.col(sx), (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1);
     }
   }
 }
 
-// gradient tensor G[i][j] = d u_i / d x_j of the three staggered components
-// at body-frame point p
-__device__ __forceinline__ void velocity_gradient(const float* __restrict__ u,
-                                                  const float* __restrict__ vv,
-                                                  const float* __restrict__ w, const Grid& g,
-                                                  const BodyDev& B, float kappa, const float (&p)[3],
-                                                  float (&G)[3][3]) {
-  float tau[3];
+__device__ __forceinline__ void dir3(const float (&tp)[3], float kappa, DirW& X, DirW& Y, DirW& Z) {
+  dir_weights(tp[0], kappa, X);
+  dir_weights(tp[1], kappa, Y);
+  dir_weights(tp[2], kappa, Z);
+}
+
+// grad u at a point: G[i][j] += sign * d u_i / d x_j
+template <bool BOX>
+__device__ __forceinline__ void add_gradient(const float* f0, const float* f1, const float* f2,
+                                             const float (&tau)[3], const BodyDev& B,
+                                             const Grid& g, float kappa, const int (&lo)[3],
+                                             const int (&sz)[3], float sign, float (&G)[3][3]) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) tau[d] = fmaf(p[d], g.invh[d], B.frac[d]);
-  // direction factors for node offset 0 (index 0) and 1/2 (index 1)
-  DirWD W0[3], W1[3];
-  int I0[3][3], I1[3][3];
+  for (int comp = 0; comp < 3; ++comp) {
+    const float* fc = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
+    int c[3];
+    float tp[3];
+    locate(tau, comp, B.G, c, tp);
+    DirWD X, Y, Z;
+    dir_weights_d(tp[0], kappa, X);
+    dir_weights_d(tp[1], kappa, Y);
+    dir_weights_d(tp[2], kappa, Z);
+    float gr[3];
+    if (BOX) {
+      BoxAcc A;
+      A.init(c, lo, sz);
+      mls_grad(fc, A, X, Y, Z, gr);
+    } else {
+      GlobalAcc A;
+      A.init(c, g);
+      mls_grad(fc, A, X, Y, Z, gr);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) G[comp][j] += sign * gr[j] * g.invh[j];
+  }
+}
+
+__device__ __forceinline__ void minmax_loc(const float (&tau)[3], const int (&G)[3], int (&lo)[3],
+                                           int (&hi)[3]) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    float tp;
-    int c = locate(tau[d], 0.f, B.G[d], tp);
-    dir_weights_d(tp, kappa, W0[d]);
-    node3(c, g.n[d], I0[d]);
-    c = locate(tau[d], 0.5f, B.G[d], tp);
-    dir_weights_d(tp, kappa, W1[d]);
-    node3(c, g.n[d], I1[d]);
+    const int c0 = G[d] + (int)floorf(tau[d]);   // every component's support lies in c0-1 .. c0+2
+    lo[d] = min(lo[d], c0 - 1);
+    hi[d] = max(hi[d], c0 + 2);
   }
-  float gr[3];
-  mls_grad(u, I0[0], I1[1], I1[2], g.n[0], g.n[1], W0[0], W1[1], W1[2], gr);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) G[0][j] = gr[j] * g.invh[j];
-  mls_grad(vv, I1[0], I0[1], I1[2], g.n[0], g.n[1], W1[0], W0[1], W1[2], gr);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) G[1][j] = gr[j] * g.invh[j];
-  mls_grad(w, I1[0], I1[1], I0[2], g.n[0], g.n[1], W1[0], W1[1], W0[2], gr);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) G[2][j] = gr[j] * g.invh[j];
 }
 
 template <bool MEASURE, bool INTERP, bool PROBE, bool SPREAD>
-__global__ void __launch_bounds__(kChunk) marker_kernel(
+__global__ void __launch_bounds__(kChunk, 4) marker_kernel(
     DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ v, const float* __restrict__ u, const float* __restrict__ vv,
     const float* __restrict__ w, float* __restrict__ U, float* __restrict__ Fm,
     const float* __restrict__ Fm_in, float* __restrict__ Fext, float* __restrict__ fx,
-    float* __restrict__ fy, float* __restrict__ fz, uint8_t* __restrict__ bricks,
-    int3 nbrick) {
-  const int4 ch = T.chunks[blockIdx.x];  // body, first local face, count, chunk index
+    float* __restrict__ fy, float* __restrict__ fz, int record_box) {
+  constexpr bool FIELD = INTERP || PROBE || SPREAD;
+  constexpr bool VEL = INTERP || PROBE;
+  extern __shared__ float sbox[];
+  __shared__ int s_lo[3], s_hi[3];
+  __shared__ double s_red[2][kChunk / 32];
+  __shared__ int s_last;
+  const int4 ch = T.chunks[blockIdx.x];  // body, first local face, count, chunk index in body
   const BodyDev B = T.body[ch.x];
-  const TopoDev topo = T.topo[B.topo];
+  const int tri_off = T.topo[B.topo].tri_off;
   const int lf = ch.y + threadIdx.x;
   const bool active = threadIdx.x < ch.z;
-  double Af = 0.0, Vf = 0.0;
+  if (FIELD && threadIdx.x < 3) {
+    s_lo[threadIdx.x] = INT_MAX;
+    s_hi[threadIdx.x] = INT_MIN;
+  }
+  float Af = 0.f, Vf = 0.f;
+  float c[3] = {0.f, 0.f, 0.f}, nrm[3] = {0.f, 0.f, 0.f}, area = 0.f;
+  float tc[3], tp[3], tm[3];
+  bool ok = false;
+  int ia = 0, ib = 0, ic = 0, gf = 0;
   if (active) {
-    const int gf = B.f_off + lf;
-    const int* tr = T.tri + topo.tri_off + 3 * lf;
-    const int ia = B.v_off + __ldg(tr), ib = B.v_off + __ldg(tr + 1), ic = B.v_off + __ldg(tr + 2);
+    gf = B.f_off + lf;
+    const int* tr = T.tri + tri_off + 3 * lf;
+    ia = B.v_off + __ldg(tr);
+    ib = B.v_off + __ldg(tr + 1);
+    ic = B.v_off + __ldg(tr + 2);
     float xa[3], xb[3], xc[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -241,234 +289,291 @@ __global__ void __launch_bounds__(kChunk) marker_kernel(
     const float N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
                         e1[0] * e2[1] - e1[1] * e2[0]};
     const float nn = sqrtf(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-    const float area = 0.5f * nn;
+    area = 0.5f * nn;
     if (MEASURE) {
-      Af = (double)area;
+      Af = area;
       if (B.closed) {
-        const float cbc[3] = {xb[1] * xc[2] - xb[2] * xc[1], xb[2] * xc[0] - xb[0] * xc[2],
-                              xb[0] * xc[1] - xb[1] * xc[0]};
-        Vf = (double)(xa[0] * cbc[0] + xa[1] * cbc[1] + xa[2] * cbc[2]) * (1.0 / 6.0);
+        Vf = (xa[0] * (xb[1] * xc[2] - xb[2] * xc[1]) + xa[1] * (xb[2] * xc[0] - xb[0] * xc[2]) +
+              xa[2] * (xb[0] * xc[1] - xb[1] * xc[0])) * (1.f / 6.f);
       }
     }
-    if (INTERP || PROBE || SPREAD) {
+    if (FIELD) {
       const float third = 1.f / 3.f;
-      const float c[3] = {(xa[0] + xb[0] + xc[0]) * third, (xa[1] + xb[1] + xc[1]) * third,
-                          (xa[2] + xb[2] + xc[2]) * third};
-      float tau[3];
-      bool ok = nn > 0.f;
+      const float inv = 1.f / nn;
+      ok = nn > 0.f;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        tau[d] = fmaf(c[d], g.invh[d], B.frac[d]);
-        ok = ok && fabsf(tau[d]) < 1.0e7f;   // also false for NaN
+        c[d] = (xa[d] + xb[d] + xc[d]) * third;
+        nrm[d] = N[d] * inv;
+        tc[d] = fmaf(c[d], g.invh[d], B.frac[d]);
+        tp[d] = fmaf(c[d] + sc.probe_h * nrm[d], g.invh[d], B.frac[d]);
+        tm[d] = fmaf(c[d] - sc.probe_h * nrm[d], g.invh[d], B.frac[d]);
+        ok = ok && fabsf(tc[d]) < 1.0e7f && fabsf(tp[d]) < 1.0e7f && fabsf(tm[d]) < 1.0e7f;
       }
-      if (!ok) {
-        atomicOr(T.err, ERR_NONFINITE);
-      } else {
-        if (INTERP || SPREAD) {
-          DirW W0[3], W1[3];
-          int I0[3][3], I1[3][3];
+      if (!ok) atomicOr(T.err, ERR_NONFINITE);
+    }
+  }
+
+  // ---- the block's grid box --------------------------------------------
+  int lo[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
+  bool fit = false;
+  float* vbox = sbox;
+  float* fbox = sbox;
+  if (FIELD) {
+    int mlo[3] = {INT_MAX, INT_MAX, INT_MAX}, mhi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    if (active && ok) {
+      minmax_loc(tc, B.G, mlo, mhi);
+      if (PROBE) {
+        minmax_loc(tp, B.G, mlo, mhi);
+        if (!B.closed) minmax_loc(tm, B.G, mlo, mhi);
+      }
+    }
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            float tp;
-            int cc = locate(tau[d], 0.f, B.G[d], tp);
-            dir_weights(tp, sc.kappa, W0[d]);
-            node3(cc, g.n[d], I0[d]);
-            cc = locate(tau[d], 0.5f, B.G[d], tp);
-            dir_weights(tp, sc.kappa, W1[d]);
-            node3(cc, g.n[d], I1[d]);
-          }
-          float Fl[3];
-          if (INTERP) {
-            float Ul[3];
-            Ul[0] = mls_value(u, I0[0], I1[1], I1[2], g.n[0], g.n[1], W0[0], W1[1], W1[2]);
-            Ul[1] = mls_value(vv, I1[0], I0[1], I1[2], g.n[0], g.n[1], W1[0], W0[1], W1[2]);
-            Ul[2] = mls_value(w, I1[0], I1[1], I0[2], g.n[0], g.n[1], W1[0], W1[1], W0[2]);
+    for (int d = 0; d < 3; ++d) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              const float vb = (__ldg(v + d * V + ia) + __ldg(v + d * V + ib) +
-                                __ldg(v + d * V + ic)) * third;
-              Fl[d] = (vb - Ul[d]) * sc.inv_dt;
-            }
-            if (U) {
+      for (int o = 16; o > 0; o >>= 1) {
+        mlo[d] = min(mlo[d], __shfl_xor_sync(0xffffffffu, mlo[d], o));
+        mhi[d] = max(mhi[d], __shfl_xor_sync(0xffffffffu, mhi[d], o));
+      }
+    }
+    __syncthreads();   // s_lo / s_hi initialised
+    if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-              for (int d = 0; d < 3; ++d) U[d * F + gf] = Ul[d];
-            }
-            if (Fm) {
+      for (int d = 0; d < 3; ++d) {
+        atomicMin(&s_lo[d], mlo[d]);
+        atomicMax(&s_hi[d], mhi[d]);
+      }
+    }
+    __syncthreads();
+    long long nbox = 1;
 #pragma unroll
-              for (int d = 0; d < 3; ++d) Fm[d * F + gf] = Fl[d];
-            }
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = s_lo[d];
+      sz[d] = s_hi[d] >= s_lo[d] ? s_hi[d] - s_lo[d] + 1 : 0;
+      nbox *= sz[d];
+    }
+    const int nfield = (VEL ? 3 : 0) + (SPREAD ? 3 : 0);
+    fit = nbox > 0 && nbox * nfield * (long long)sizeof(float) <= kMarkerSmemBytes;
+    const int N = fit ? (int)nbox : 0;
+    fbox = sbox + (VEL ? 3 * N : 0);
+    if (fit) {
+      const int sxy = sz[0] * sz[1];
+      if (VEL) {
+        for (int r = threadIdx.x; r < N; r += blockDim.x) {
+          const int k = r / sxy, rem = r - k * sxy, j = rem / sz[0], i = rem - j * sz[0];
+          const size_t o = ((size_t)wrap(lo[2] + k, g.n[2]) * g.n[1] + wrap(lo[1] + j, g.n[1])) *
+                               g.n[0] + wrap(lo[0] + i, g.n[0]);
+          vbox[r] = __ldg(u + o);
+          vbox[N + r] = __ldg(vv + o);
+          vbox[2 * N + r] = __ldg(w + o);
+        }
+      }
+      if (SPREAD)
+        for (int idx = threadIdx.x; idx < 3 * N; idx += blockDim.x) fbox[idx] = 0.f;
+    } else if (nbox > 0 && threadIdx.x == 0) {
+      atomicAdd(T.stats, 1);
+    }
+    __syncthreads();
+  }
+
+  // ---- per marker: interpolation, marker force, spreading, traction -------
+  if (FIELD && active && ok) {
+    const int N = fit ? sz[0] * sz[1] * sz[2] : 0;
+    if (INTERP || SPREAD) {
+      const float third = 1.f / 3.f;
+      const float cl = area * sc.cl_scale;
+#pragma unroll 1
+      for (int comp = 0; comp < 3; ++comp) {
+        const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
+        float* frcc = comp == 0 ? fx : (comp == 1 ? fy : fz);
+        int cc[3];
+        float t3[3];
+        locate(tc, comp, B.G, cc, t3);
+        DirW X, Y, Z;
+        dir3(t3, sc.kappa, X, Y, Z);
+        float Fl;
+        if (INTERP) {
+          float Ul;
+          if (fit) {
+            BoxAcc A;
+            A.init(cc, lo, sz);
+            Ul = mls_value(vbox + comp * N, A, X, Y, Z);
           } else {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) Fl[d] = __ldg(Fm_in + d * F + gf);
+            GlobalAcc A;
+            A.init(cc, g);
+            Ul = mls_value(velc, A, X, Y, Z);
           }
-          if (SPREAD) {
-            const float cl = area * sc.cl_scale;
-            mls_spread(fx, I0[0], I1[1], I1[2], g.n[0], g.n[1], W0[0], W1[1], W1[2], cl * Fl[0]);
-            mls_spread(fy, I1[0], I0[1], I1[2], g.n[0], g.n[1], W1[0], W0[1], W1[2], cl * Fl[1]);
-            mls_spread(fz, I1[0], I1[1], I0[2], g.n[0], g.n[1], W1[0], W1[1], W0[2], cl * Fl[2]);
-            if (bricks) {
-              // mark the 8^3-cell bricks overlapped by the footprint (cells
-              // floor(tau)-1 .. floor(tau)+2 hold every component's stencil)
-              int lo[3], hi[3];
-#pragma unroll
-              for (int d = 0; d < 3; ++d) {
-                const int c0 = B.G[d] + (int)floorf(tau[d]);
-                lo[d] = wrap(c0 - 1, g.n[d]) >> 3;
-                hi[d] = wrap(c0 + 2, g.n[d]) >> 3;
-              }
-              const int bx[2] = {lo[0], hi[0]}, by[2] = {lo[1], hi[1]}, bz[2] = {lo[2], hi[2]};
-#pragma unroll
-              for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-#pragma unroll
-                  for (int i = 0; i < 2; ++i)
-                    bricks[(bz[k] * nbrick.y + by[j]) * nbrick.x + bx[i]] = 1;
-            }
+          const float vb = (__ldg(v + comp * V + ia) + __ldg(v + comp * V + ib) +
+                            __ldg(v + comp * V + ic)) * third;
+          Fl = (vb - Ul) * sc.inv_dt;
+          if (U) U[comp * F + gf] = Ul;
+          if (Fm) Fm[comp * F + gf] = Fl;
+        } else {
+          Fl = __ldg(Fm_in + comp * F + gf);
+        }
+        if (SPREAD) {
+          if (fit) {
+            BoxAcc A;
+            A.init(cc, lo, sz);
+            mls_spread(fbox + comp * N, A, X, Y, Z, cl * Fl);
+          } else {
+            GlobalAcc A;
+            A.init(cc, g);
+            mls_spread(frcc, A, X, Y, Z, cl * Fl);
           }
         }
-        if (PROBE) {
-          const float inv = 1.f / nn;
-          const float n[3] = {N[0] * inv, N[1] * inv, N[2] * inv};
-          const float p[3] = {c[0] + sc.probe_h * n[0], c[1] + sc.probe_h * n[1],
-                              c[2] + sc.probe_h * n[2]};
-          float G[3][3];
-          velocity_gradient(u, vv, w, g, B, sc.kappa, p, G);
-          if (!B.closed) {
-            // open sheet: second probe on the other side, (tau+ - tau-) . n+
-            const float pm[3] = {c[0] - sc.probe_h * n[0], c[1] - sc.probe_h * n[1],
-                                 c[2] - sc.probe_h * n[2]};
-            float Gm[3][3];
-            velocity_gradient(u, vv, w, g, B, sc.kappa, pm, Gm);
+      }
+    }
+    if (PROBE) {
+      float G[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      if (fit) {
+        add_gradient<true>(vbox, vbox + N, vbox + 2 * N, tp, B, g, sc.kappa, lo, sz, 1.f, G);
+        // open sheet: second probe on the other side, (tau+ - tau-) . n+
+        if (!B.closed)
+          add_gradient<true>(vbox, vbox + N, vbox + 2 * N, tm, B, g, sc.kappa, lo, sz, -1.f, G);
+      } else {
+        add_gradient<false>(u, vv, w, tp, B, g, sc.kappa, lo, sz, 1.f, G);
+        if (!B.closed) add_gradient<false>(u, vv, w, tm, B, g, sc.kappa, lo, sz, -1.f, G);
+      }
+      const float s = sc.mu * area;
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int j = 0; j < 3; ++j) G[i][j] -= Gm[i][j];
-          }
-          const float s = sc.mu * area;
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const float t = (G[i][0] + G[0][i]) * n[0] + (G[i][1] + G[1][i]) * n[1] +
-                            (G[i][2] + G[2][i]) * n[2];
-            Fext[i * F + gf] = s * t;
-          }
-        }
+      for (int i = 0; i < 3; ++i) {
+        const float t = (G[i][0] + G[0][i]) * nrm[0] + (G[i][1] + G[1][i]) * nrm[1] +
+                        (G[i][2] + G[2][i]) * nrm[2];
+        Fext[i * F + gf] = s * t;
       }
     }
   }
-  if (MEASURE) {
-    // deterministic per-body float64 sums: fixed-order block reduction, one
-    // partial per chunk, and the last chunk of the body to arrive adds the
-    // partials in chunk order
-    __shared__ double sA[kChunk], sV[kChunk];
-    __shared__ int last;
-    sA[threadIdx.x] = Af;
-    sV[threadIdx.x] = Vf;
+
+  // ---- flush the shared force box ------------------------------------------
+  if (SPREAD) {
     __syncthreads();
-#pragma unroll
-    for (int s = kChunk / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        sA[threadIdx.x] += sA[threadIdx.x + s];
-        sV[threadIdx.x] += sV[threadIdx.x + s];
+    if (fit) {
+      const int N = sz[0] * sz[1] * sz[2], sxy = sz[0] * sz[1];
+      for (int r = threadIdx.x; r < N; r += blockDim.x) {
+        const float a = fbox[r], b = fbox[N + r], cz = fbox[2 * N + r];
+        if (a != 0.f || b != 0.f || cz != 0.f) {
+          const int k = r / sxy, rem = r - k * sxy, j = rem / sz[0], i = rem - j * sz[0];
+          const size_t o = ((size_t)wrap(lo[2] + k, g.n[2]) * g.n[1] + wrap(lo[1] + j, g.n[1])) *
+                               g.n[0] + wrap(lo[0] + i, g.n[0]);
+          if (a != 0.f) atomicAdd(fx + o, a);
+          if (b != 0.f) atomicAdd(fy + o, b);
+          if (cz != 0.f) atomicAdd(fz + o, cz);
+        }
       }
-      __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (record_box && threadIdx.x == 0) {
       const int gc = B.chunk_off + ch.w;
-      T.partial[2 * gc] = sA[0];
-      T.partial[2 * gc + 1] = sV[0];
+      T.boxes[2 * gc] = make_int4(lo[0], lo[1], lo[2], 0);
+      T.boxes[2 * gc + 1] = make_int4(sz[0], sz[1], sz[2], 0);
+    }
+  }
+
+  // ---- per-body float64 area and volume ------------------------------------
+  if (MEASURE) {
+    // fixed-order reduction: warp shuffles, warps in order, one partial per
+    // chunk; the last chunk of the body to arrive sums the partials in order
+    double a = (double)Af, vol = (double)Vf;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      vol += __shfl_down_sync(0xffffffffu, vol, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_red[0][threadIdx.x >> 5] = a;
+      s_red[1][threadIdx.x >> 5] = vol;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sa = 0.0, sv = 0.0;
+      for (int k = 0; k < kChunk / 32; ++k) {
+        sa += s_red[0][k];
+        sv += s_red[1][k];
+      }
+      const int gc = B.chunk_off + ch.w;
+      T.partial[2 * gc] = sa;
+      T.partial[2 * gc + 1] = sv;
       __threadfence();
       const int arrived = atomicAdd(T.counter + ch.x, 1);
-      last = (arrived == B.n_chunk - 1);
+      s_last = (arrived == B.n_chunk - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (s_last && threadIdx.x == 0) {
       __threadfence();
-      double a = 0.0, vol = 0.0;
+      double ta = 0.0, tv = 0.0;
       const volatile double* P = T.partial;
       for (int k = 0; k < B.n_chunk; ++k) {
-        a += P[2 * (B.chunk_off + k)];
-        vol += P[2 * (B.chunk_off + k) + 1];
+        ta += P[2 * (B.chunk_off + k)];
+        tv += P[2 * (B.chunk_off + k) + 1];
       }
-      T.meas[2 * ch.x] = a;
-      T.meas[2 * ch.x + 1] = vol;
+      T.meas[2 * ch.x] = ta;
+      T.meas[2 * ch.x + 1] = tv;
+      const float cA = (float)(B.kA * ((ta - B.A0) / B.A0));
+      const float cV = B.closed ? (float)(B.kv * ((tv - B.V0) / B.V0)) : 0.f;
+      T.coef[ch.x] = make_float2(cA, cV);
       T.counter[ch.x] = 0;
     }
   }
 }
 
-// zero the three force fields on every marked 8^3 brick and clear its mark
-__global__ void clear_kernel(float* __restrict__ fx, float* __restrict__ fy,
-                             float* __restrict__ fz, uint8_t* __restrict__ bricks, int3 nb,
-                             int nx, int ny, int nz) {
-  const int lane = threadIdx.x & 31;
-  const long nbt = (long)nb.x * nb.y * nb.z;
-  const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-  for (long bidx = wid; bidx < nbt; bidx += nw) {
-    if (bricks[bidx] == 0) continue;
-    const int bx = (int)(bidx % nb.x);
-    const int by = (int)((bidx / nb.x) % nb.y);
-    const int bz = (int)(bidx / ((long)nb.x * nb.y));
-    // 512 cells per brick, 16 per lane: each warp store covers four whole
-    // 8-float rows (four 32-byte sectors)
-    for (int k = 0; k < 16; ++k) {
-      const int idx = lane + 32 * k;
-      const int xx = bx * 8 + (idx & 7), y = by * 8 + ((idx >> 3) & 7), z = bz * 8 + (idx >> 6);
-      if (xx < nx && y < ny && z < nz) {
-        const long o = ((long)z * ny + y) * nx + xx;
-        fx[o] = 0.f;
-        fy[o] = 0.f;
-        fz[o] = 0.f;
-      }
-    }
-    __syncwarp();
-    if (lane == 0) bricks[bidx] = 0;
+// zero the three force fields on every box recorded by the previous spread
+__global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, float* __restrict__ fx,
+                                                    float* __restrict__ fy, float* __restrict__ fz) {
+  const int4 lo = T.boxes[2 * blockIdx.x];
+  const int4 sz = T.boxes[2 * blockIdx.x + 1];
+  const long long N = (long long)sz.x * sz.y * sz.z;
+  if (N <= 0) return;
+  const int sxy = sz.x * sz.y;
+  for (long long idx = threadIdx.x; idx < N; idx += blockDim.x) {
+    const int k = (int)(idx / sxy), rem = (int)(idx - (long long)k * sxy), j = rem / sz.x,
+              i = rem - j * sz.x;
+    const size_t o = ((size_t)wrap(lo.z + k, g.n[2]) * g.n[1] + wrap(lo.y + j, g.n[1])) * g.n[0] +
+                     wrap(lo.x + i, g.n[0]);
+    fx[o] = 0.f;
+    fy[o] = 0.f;
+    fz[o] = 0.f;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) T.boxes[2 * blockIdx.x + 1] = make_int4(0, 0, 0, 0);
 }
 
 template <bool M, bool I, bool P, bool S>
 cudaError_t launch_t(ibm_ctx* c, const float* x, const float* v, const float* u, const float* vv,
                      const float* w, float* U, float* Fm, const float* Fm_in, float* Fext,
-                     float* fx, float* fy, float* fz, uint8_t* bricks, int3 nb) {
+                     float* fx, float* fy, float* fz, int record_box) {
   if (c->n_chunks == 0) return cudaSuccess;
-  marker_kernel<M, I, P, S><<<c->n_chunks, kChunk, 0, c->stream>>>(
+  const size_t smem = (I || P || S) ? kMarkerSmemBytes : 0;
+  marker_kernel<M, I, P, S><<<c->n_chunks, kChunk, smem, c->stream>>>(
       c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, U, Fm, Fm_in, Fext,
-      fx, fy, fz, bricks, nb);
+      fx, fy, fz, record_box);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-static int3 brick_dims(const ibm_ctx* c) {
-  return make_int3((c->grid.n[0] + 7) / 8, (c->grid.n[1] + 7) / 8, (c->grid.n[2] + 7) / 8);
-}
-
 cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* u,
                        const float* vv, const float* w, float* U, float* Fm, const float* Fm_in,
                        float* Fext, float* fx, float* fy, float* fz, bool measure, bool interp,
-                       bool probe, bool spread, bool record_cells) {
-  const int3 nb = brick_dims(c);
-  uint8_t* br = record_cells ? c->d_bricks : nullptr;
+                       bool probe, bool spread, bool record_box) {
+  const int rb = record_box ? 1 : 0;
   if (measure && interp && probe && spread)
-    return launch_t<true, true, true, true>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, br, nb);
+    return launch_t<true, true, true, true>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
   if (measure && !interp && !probe && !spread)
-    return launch_t<true, false, false, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, br, nb);
+    return launch_t<true, false, false, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
   if (!measure && interp && probe && !spread)
-    return launch_t<false, true, true, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, br, nb);
+    return launch_t<false, true, true, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
   if (!measure && interp && !probe && !spread)
-    return launch_t<false, true, false, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, br, nb);
+    return launch_t<false, true, false, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
   if (!measure && !interp && probe && !spread)
-    return launch_t<false, false, true, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, br, nb);
+    return launch_t<false, false, true, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
   if (!measure && !interp && !probe && spread)
-    return launch_t<false, false, false, true>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, br, nb);
+    return launch_t<false, false, false, true>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz) {
-  const int3 nb = brick_dims(c);
-  clear_kernel<<<4 * 152, 256, 0, c->stream>>>(fx, fy, fz, c->d_bricks, nb, c->grid.n[0],
-                                               c->grid.n[1], c->grid.n[2]);
+  if (c->n_chunks == 0) return cudaSuccess;
+  clear_kernel<<<c->n_chunks, 256, 0, c->stream>>>(c->d, c->grid, fx, fy, fz);
   return cudaGetLastError();
 }
 

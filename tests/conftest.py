@@ -21,3 +21,22 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+_ERRORS = {}
+
+
+@pytest.fixture
+def record_error(request):
+    """Record a measured parity error; written to $PARITY_LOG (JSON) at exit."""
+    def rec(name, value):
+        _ERRORS[f"{request.node.name}:{name}"] = float(value)
+    return rec
+
+
+def pytest_sessionfinish(session, exitstatus):
+    import json
+    path = os.environ.get("PARITY_LOG")
+    if path and _ERRORS:
+        with open(path, "w") as f:
+            json.dump(_ERRORS, f, indent=1, sort_keys=True)

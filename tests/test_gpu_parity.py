@@ -57,7 +57,7 @@ def mixed():
 
 
 @pytest.mark.parametrize("patch", [0, 32])
-def test_internal_forces_parity(mixed, patch):
+def test_internal_forces_parity(mixed, patch, record_error):
     wl, ob = mixed
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, patch_size=patch)
     rel = deformed_state(wl, 1)
@@ -67,6 +67,7 @@ def test_internal_forces_parity(mixed, patch):
     xs = H.to_abs(wl, H.split_state(ctx, wl, x))
     for i, b in enumerate(ob):
         Fo = b.internal_forces(xs[i]).numpy()
+        record_error(f"F_int[{i}]", H.rel_l2(Fg[i], Fo))
         assert H.rel_l2(Fg[i], Fo) <= 1e-5, (i, H.rel_l2(Fg[i], Fo))
         terms = b.energy_terms(xs[i])
         for k, name in enumerate(["We", "Wb", "Wa", "WA", "Wv"]):
@@ -106,7 +107,7 @@ def test_body_measures_parity(mixed):
             assert m[i, 1] == 0.0
 
 
-def test_interpolation_and_traction_parity(mixed):
+def test_interpolation_and_traction_parity(mixed, record_error):
     wl, ob = mixed
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
     rng = np.random.default_rng(3)
@@ -123,10 +124,11 @@ def test_interpolation_and_traction_parity(mixed):
     for name, g in (("U", U), ("F_marker", Fm), ("F_ext_face", Fe)):
         gg = g.double().cpu().numpy().T[keep]
         oo = out[name].numpy()[keep]
+        record_error(name, H.rel_l2(gg, oo))
         assert H.rel_l2(gg, oo) <= 1e-5, (name, H.rel_l2(gg, oo))
 
 
-def test_spread_parity_and_conservation(mixed):
+def test_spread_parity_and_conservation(mixed, record_error):
     wl, ob = mixed
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, alpha=wl.alpha)
     rng = np.random.default_rng(4)
@@ -147,6 +149,7 @@ def test_spread_parity_and_conservation(mixed):
     ref = O.spread(torch.tensor(Fm_t.double().cpu().numpy().T), torch.cat(P), torch.cat(A),
                    wl.grid.n, wl.grid.h, wl.alpha)
     got = torch.stack(f).double().cpu()
+    record_error("f", H.rel_l2(got.numpy(), ref.numpy()))
     assert H.rel_l2(got.numpy(), ref.numpy()) <= 1e-5
     # no net gain or loss (Eq. mls_cl), summed in float64
     dV = np.prod(wl.grid.h)
@@ -165,12 +168,12 @@ def tie_free_state(wl, seed0, **kw):
 
 
 @pytest.mark.parametrize("forward_euler", [False, True])
-def test_step_parity(mixed, forward_euler):
+def test_step_parity(mixed, forward_euler, record_error):
     wl, ob = mixed
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
                        forward_euler=forward_euler)
     rng = np.random.default_rng(5)
-    rel = tie_free_state(wl, 10, scale=0.02, stretch=0.03)
+    rel = tie_free_state(wl, 10, scale=0.05, stretch=0.05)
     x = H.state_tensor(wl, rel)
     # float32-exact round trip: the oracle sees exactly the GPU's inputs
     xs = H.to_abs(wl, H.split_state(ctx, wl, x))
@@ -194,14 +197,20 @@ def test_step_parity(mixed, forward_euler):
     for i, b in enumerate(wl.bodies):
         xo = out["x_next"][i].numpy() - b.origin
         assert H.rel_l2(xg[i], xo) <= 1e-6, i
-        # velocity increments carry the force error
+        # velocity increments carry the force error; the new velocity is stored
+        # in float32, so each component also carries half an ulp of |v|
         dv_g = vg[i] - vs[i].numpy()
-        dv_o = out["v_next"][i].numpy() - vs[i].numpy()
-        assert H.rel_l2(dv_g, dv_o) <= 1e-5, (i, H.rel_l2(dv_g, dv_o))
+        vo = out["v_next"][i].numpy()
+        dv_o = vo - vs[i].numpy()
+        store = np.linalg.norm(0.5 * np.spacing(np.abs(vo).astype(np.float32)).astype(np.float64))
+        excess = max(0.0, np.linalg.norm(dv_g - dv_o) - store) / np.linalg.norm(dv_o)
+        record_error(f"dv[{i}]", excess)
+        assert excess <= 1e-5, (i, excess, H.rel_l2(dv_g, dv_o))
         if b.clamped is not None:
             assert np.array_equal(xg[i][b.clamped], rel[i][b.clamped].astype(np.float32).astype(np.float64))
             assert np.all(vg[i][b.clamped] == 0)
     got = torch.stack(f).double().cpu().numpy()
+    record_error("f", H.rel_l2(got, out["f"].numpy()))
     assert H.rel_l2(got, out["f"].numpy()) <= 1e-5
 
 
@@ -226,7 +235,7 @@ def test_step_is_deterministic_and_clears_previous_spread(mixed):
         assert torch.allclose(a, b, rtol=1e-6, atol=1e-6 * float(b.abs().max()))
 
 
-def test_single_drop_100_steps():
+def test_single_drop_100_steps(record_error):
     """The paper's drop in frozen linear shear (Sec. 3.1 set-up): 642-node
     icosphere, 64^3 grid, 100 steps; body-frame positions within 1e-5."""
     wl = W.single_drop(level=3, n=64, steps=100)
@@ -251,6 +260,7 @@ def test_single_drop_100_steps():
     xg = H.split_state(ctx, wl, xa)[0]
     xo = xs[0].numpy() - wl.bodies[0].origin
     err = np.linalg.norm(xg - xo) / (wl.bodies[0].radius * math.sqrt(len(xo)))
+    record_error("x100", err)
     assert err <= 1e-5, err
     disp = np.abs(xo - (wl.bodies[0].rest - wl.bodies[0].origin)).max()
     assert disp > 0.0
