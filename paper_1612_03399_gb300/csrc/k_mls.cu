@@ -234,13 +234,20 @@ __device__ __forceinline__ void add_gradient(const float* f0, const float* f1, c
   }
 }
 
+// extend [lo, hi] by the supports of all three components at a point, with
+// exactly the centre nodes the evaluation will use
 __device__ __forceinline__ void minmax_loc(const float (&tau)[3], const int (&G)[3], int (&lo)[3],
                                            int (&hi)[3]) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int c0 = G[d] + (int)floorf(tau[d]);   // every component's support lies in c0-1 .. c0+2
-    lo[d] = min(lo[d], c0 - 1);
-    hi[d] = max(hi[d], c0 + 2);
+  for (int comp = 0; comp < 3; ++comp) {
+    int c[3];
+    float tp[3];
+    locate(tau, comp, G, c, tp);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = min(lo[d], c[d] - 1);
+      hi[d] = max(hi[d], c[d] + 1);
+    }
   }
 }
 
@@ -463,9 +470,11 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
       }
     }
     if (record_box && threadIdx.x == 0) {
+      // a box wider than the grid covers that whole direction
       const int gc = B.chunk_off + ch.w;
       T.boxes[2 * gc] = make_int4(lo[0], lo[1], lo[2], 0);
-      T.boxes[2 * gc + 1] = make_int4(sz[0], sz[1], sz[2], 0);
+      T.boxes[2 * gc + 1] =
+          make_int4(min(sz[0], g.n[0]), min(sz[1], g.n[1]), min(sz[2], g.n[2]), 0);
     }
   }
 
