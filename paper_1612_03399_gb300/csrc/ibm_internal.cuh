@@ -109,7 +109,10 @@ struct DeviceTables {
   int32_t* err = nullptr;       // device error word
 };
 
-constexpr int kMarkerSmemBytes = 48 * 1024;   // stencil box staging per marker block
+// stencil box staging per marker block: dynamic shared memory kept under the
+// 48 KB a block may use without opting in (the kernel's static shared
+// variables take the rest)
+constexpr int kMarkerSmemBytes = 47 * 1024;
 
 }  // namespace ibm
 
