@@ -570,6 +570,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.err = zeros<int32_t>(c, 1);
     d.coef = zeros<float2>(c, (size_t)n_bodies);
     d.boxes = zeros<int4>(c, 2 * (size_t)c->n_chunks);
+    d.mask = zeros<uint32_t>(c, (size_t)kMaskWords * c->n_chunks);
     d.stats = zeros<int32_t>(c, 4);
     check_cuda(cudaDeviceSynchronize(), "create");
     *out = c;

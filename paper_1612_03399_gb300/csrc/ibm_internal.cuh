@@ -104,7 +104,9 @@ struct DeviceTables {
   double* meas = nullptr;       // [B][2] (A, V)
   float2* coef = nullptr;       // [B] (k_A (A - A0)/A0, k_v (V - V0)/V0) for the force kernel
   float* fext = nullptr;        // [3][F] scratch marker traction (ibm_step)
-  int4* boxes = nullptr;        // [n_chunks][2] grid box (lo, size) each marker block spread into
+  int4* boxes = nullptr;        // [n_chunks][2] grid box (lo, whole-box flag; size) of each
+                                // marker block's last spread
+  uint32_t* mask = nullptr;     // [n_chunks][kMaskWords] nodes of that box actually written
   int32_t* stats = nullptr;     // [4] counters: marker blocks that did not fit shared memory
   int32_t* err = nullptr;       // device error word
 };
@@ -112,7 +114,9 @@ struct DeviceTables {
 // stencil box staging per marker block: dynamic shared memory kept under the
 // 48 KB a block may use without opting in (the kernel's static shared
 // variables take the rest)
-constexpr int kMarkerSmemBytes = 47 * 1024;
+constexpr int kMarkerSmemBytes = 46 * 1024;
+constexpr int kMaxBoxNodes = kMarkerSmemBytes / 8;        // one velocity + one force component
+constexpr int kMaskWords = (kMaxBoxNodes + 31) / 32;      // footprint bits per marker block
 
 }  // namespace ibm
 

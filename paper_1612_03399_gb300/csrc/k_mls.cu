@@ -203,35 +203,36 @@ __device__ __forceinline__ void dir3(const float (&tp)[3], float kappa, DirW& X,
   dir_weights(tp[2], kappa, Z);
 }
 
-// grad u at a point: G[i][j] += sign * d u_i / d x_j
-template <bool BOX>
-__device__ __forceinline__ void add_gradient(const float* f0, const float* f1, const float* f2,
-                                             const float (&tau)[3], const BodyDev& B,
-                                             const Grid& g, float kappa, const int (&lo)[3],
-                                             const int (&sz)[3], float sign, float (&G)[3][3]) {
-#pragma unroll
-  for (int comp = 0; comp < 3; ++comp) {
-    const float* fc = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
-    int c[3];
-    float tp[3];
-    locate(tau, comp, B.G, c, tp);
-    DirWD X, Y, Z;
-    dir_weights_d(tp[0], kappa, X);
-    dir_weights_d(tp[1], kappa, Y);
-    dir_weights_d(tp[2], kappa, Z);
-    float gr[3];
-    if (BOX) {
-      BoxAcc A;
-      A.init(c, lo, sz);
-      mls_grad(fc, A, X, Y, Z, gr);
-    } else {
-      GlobalAcc A;
-      A.init(c, g);
-      mls_grad(fc, A, X, Y, Z, gr);
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) G[comp][j] += sign * gr[j] * g.invh[j];
+// full-derivative MLS gradient (in cells) of component `comp` at a point,
+// from the staged box (box = true) or the global field
+__device__ __forceinline__ void probe_gradient(const float* f, bool box, const float (&tau)[3],
+                                               int comp, const BodyDev& B, const Grid& g,
+                                               float kappa, const int (&lo)[3], const int (&sz)[3],
+                                               float (&gr)[3]) {
+  int c[3];
+  float tp[3];
+  locate(tau, comp, B.G, c, tp);
+  DirWD X, Y, Z;
+  dir_weights_d(tp[0], kappa, X);
+  dir_weights_d(tp[1], kappa, Y);
+  dir_weights_d(tp[2], kappa, Z);
+  if (box) {
+    BoxAcc A;
+    A.init(c, lo, sz);
+    mls_grad(f, A, X, Y, Z, gr);
+  } else {
+    GlobalAcc A;
+    A.init(c, g);
+    mls_grad(f, A, X, Y, Z, gr);
   }
+}
+
+// global offset of node r (x fastest) of the box with corner lo and size sz
+__device__ __forceinline__ size_t box_node(int r, const int (&lo)[3], const int (&sz)[3], int sxy,
+                                           const Grid& g) {
+  const int k = r / sxy, rem = r - k * sxy, j = rem / sz[0], i = rem - j * sz[0];
+  return ((size_t)wrap(lo[2] + k, g.n[2]) * g.n[1] + wrap(lo[1] + j, g.n[1])) * g.n[0] +
+         wrap(lo[0] + i, g.n[0]);
 }
 
 // extend [lo, hi] by the supports of all three components at a point, with
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
   __shared__ int s_lo[3], s_hi[3];
   __shared__ double s_red[2][kChunk / 32];
   __shared__ int s_last;
+  __shared__ uint32_t s_mask[SPREAD ? kMaskWords : 1];
   const int4 ch = T.chunks[blockIdx.x];  // body, first local face, count, chunk index in body
   const BodyDev B = T.body[ch.x];
   const int tri_off = T.topo[B.topo].tri_off;
@@ -324,8 +326,7 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
   // ---- the block's grid box --------------------------------------------
   int lo[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
   bool fit = false;
-  float* vbox = sbox;
-  float* fbox = sbox;
+  int N = 0;
   if (FIELD) {
     int mlo[3] = {INT_MAX, INT_MAX, INT_MAX}, mhi[3] = {INT_MIN, INT_MIN, INT_MIN};
     if (active && ok) {
@@ -343,6 +344,8 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
         mhi[d] = max(mhi[d], __shfl_xor_sync(0xffffffffu, mhi[d], o));
       }
     }
+    if (SPREAD && record_box)
+      for (int k = threadIdx.x; k < kMaskWords; k += blockDim.x) s_mask[k] = 0u;
     __syncthreads();   // s_lo / s_hi initialised
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
@@ -359,89 +362,103 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
       sz[d] = s_hi[d] >= s_lo[d] ? s_hi[d] - s_lo[d] + 1 : 0;
       nbox *= sz[d];
     }
-    const int nfield = (VEL ? 3 : 0) + (SPREAD ? 3 : 0);
-    fit = nbox > 0 && nbox * nfield * (long long)sizeof(float) <= kMarkerSmemBytes;
-    const int N = fit ? (int)nbox : 0;
-    fbox = sbox + (VEL ? 3 * N : 0);
-    if (fit) {
-      const int sxy = sz[0] * sz[1];
-      if (VEL) {
-        for (int r = threadIdx.x; r < N; r += blockDim.x) {
-          const int k = r / sxy, rem = r - k * sxy, j = rem / sz[0], i = rem - j * sz[0];
-          const size_t o = ((size_t)wrap(lo[2] + k, g.n[2]) * g.n[1] + wrap(lo[1] + j, g.n[1])) *
-                               g.n[0] + wrap(lo[0] + i, g.n[0]);
-          vbox[r] = __ldg(u + o);
-          vbox[N + r] = __ldg(vv + o);
-          vbox[2 * N + r] = __ldg(w + o);
-        }
-      }
-      if (SPREAD)
-        for (int idx = threadIdx.x; idx < 3 * N; idx += blockDim.x) fbox[idx] = 0.f;
-    } else if (nbox > 0 && threadIdx.x == 0) {
-      atomicAdd(T.stats, 1);
-    }
-    __syncthreads();
+    // one velocity component (and its force component) is staged at a time
+    const int nfield = (VEL ? 1 : 0) + (SPREAD ? 1 : 0);
+    fit = nbox > 0 && nbox <= kMaxBoxNodes &&
+          nbox * nfield * (long long)sizeof(float) <= kMarkerSmemBytes;
+    N = fit ? (int)nbox : 0;
+    if (!fit && nbox > 0 && threadIdx.x == 0) atomicAdd(T.stats, 1);
   }
+  float* vbox = sbox;
+  float* fbox = sbox + (VEL ? N : 0);
+  const bool mine = FIELD && active && ok;
 
-  // ---- per marker: interpolation, marker force, spreading, traction -------
-  if (FIELD && active && ok) {
-    const int N = fit ? sz[0] * sz[1] * sz[2] : 0;
-    if (INTERP || SPREAD) {
-      const float third = 1.f / 3.f;
-      const float cl = area * sc.cl_scale;
-#pragma unroll 1
-      for (int comp = 0; comp < 3; ++comp) {
-        const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
-        float* frcc = comp == 0 ? fx : (comp == 1 ? fy : fz);
-        int cc[3];
-        float t3[3];
-        locate(tc, comp, B.G, cc, t3);
-        DirW X, Y, Z;
-        dir3(t3, sc.kappa, X, Y, Z);
-        float Fl;
-        if (INTERP) {
-          float Ul;
-          if (fit) {
-            BoxAcc A;
-            A.init(cc, lo, sz);
-            Ul = mls_value(vbox + comp * N, A, X, Y, Z);
-          } else {
-            GlobalAcc A;
-            A.init(cc, g);
-            Ul = mls_value(velc, A, X, Y, Z);
-          }
-          const float vb = (__ldg(v + comp * V + ia) + __ldg(v + comp * V + ib) +
-                            __ldg(v + comp * V + ic)) * third;
-          Fl = (vb - Ul) * sc.inv_dt;
-          if (U) U[comp * F + gf] = Ul;
-          if (Fm) Fm[comp * F + gf] = Fl;
-        } else {
-          Fl = __ldg(Fm_in + comp * F + gf);
+  // ---- per component: stage, interpolate, spread, differentiate, flush ----
+  // Each component's interpolation, spreading and gradient use only that
+  // component's field, so the shared box holds one component at a time.
+  float G[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  if (FIELD) {
+    const int sxy = sz[0] * sz[1];
+    const float third = 1.f / 3.f;
+    const float cl = area * sc.cl_scale;
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
+      float* frcc = comp == 0 ? fx : (comp == 1 ? fy : fz);
+      if (fit) {
+        __syncthreads();   // the previous component is done with the boxes
+        for (int r = threadIdx.x; r < N; r += blockDim.x) {
+          if (VEL) vbox[r] = __ldg(velc + box_node(r, lo, sz, sxy, g));
+          if (SPREAD) fbox[r] = 0.f;
         }
-        if (SPREAD) {
-          if (fit) {
-            BoxAcc A;
-            A.init(cc, lo, sz);
-            mls_spread(fbox + comp * N, A, X, Y, Z, cl * Fl);
+        __syncthreads();
+      }
+      if (mine) {
+        if (INTERP || SPREAD) {
+          int cc[3];
+          float t3[3];
+          locate(tc, comp, B.G, cc, t3);
+          DirW X, Y, Z;
+          dir3(t3, sc.kappa, X, Y, Z);
+          float Fl;
+          if (INTERP) {
+            float Ul;
+            if (fit) {
+              BoxAcc A;
+              A.init(cc, lo, sz);
+              Ul = mls_value(vbox, A, X, Y, Z);
+            } else {
+              GlobalAcc A;
+              A.init(cc, g);
+              Ul = mls_value(velc, A, X, Y, Z);
+            }
+            const float vb = (__ldg(v + comp * V + ia) + __ldg(v + comp * V + ib) +
+                              __ldg(v + comp * V + ic)) * third;
+            Fl = (vb - Ul) * sc.inv_dt;
+            if (U) U[comp * F + gf] = Ul;
+            if (Fm) Fm[comp * F + gf] = Fl;
           } else {
-            GlobalAcc A;
-            A.init(cc, g);
-            mls_spread(frcc, A, X, Y, Z, cl * Fl);
+            Fl = __ldg(Fm_in + comp * F + gf);
+          }
+          if (SPREAD) {
+            if (fit) {
+              BoxAcc A;
+              A.init(cc, lo, sz);
+              mls_spread(fbox, A, X, Y, Z, cl * Fl);
+            } else {
+              GlobalAcc A;
+              A.init(cc, g);
+              mls_spread(frcc, A, X, Y, Z, cl * Fl);
+            }
+          }
+        }
+        if (PROBE) {
+          float gr[3];
+          probe_gradient(fit ? (const float*)vbox : velc, fit, tp, comp, B, g, sc.kappa, lo, sz, gr);
+          if (!B.closed) {
+            // open sheet: second probe on the other side, (tau+ - tau-) . n+
+            float gm[3];
+            probe_gradient(fit ? (const float*)vbox : velc, fit, tm, comp, B, g, sc.kappa, lo, sz,
+                           gm);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gr[j] -= gm[j];
+          }
+#pragma unroll
+          for (int j = 0; j < 3; ++j) G[comp][j] = gr[j] * g.invh[j];
+        }
+      }
+      if (SPREAD && fit) {
+        __syncthreads();
+        for (int r = threadIdx.x; r < N; r += blockDim.x) {
+          const float val = fbox[r];
+          if (val != 0.f) {
+            atomicAdd(frcc + box_node(r, lo, sz, sxy, g), val);
+            if (record_box) atomicOr(&s_mask[r >> 5], 1u << (r & 31));
           }
         }
       }
     }
-    if (PROBE) {
-      float G[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-      if (fit) {
-        add_gradient<true>(vbox, vbox + N, vbox + 2 * N, tp, B, g, sc.kappa, lo, sz, 1.f, G);
-        // open sheet: second probe on the other side, (tau+ - tau-) . n+
-        if (!B.closed)
-          add_gradient<true>(vbox, vbox + N, vbox + 2 * N, tm, B, g, sc.kappa, lo, sz, -1.f, G);
-      } else {
-        add_gradient<false>(u, vv, w, tp, B, g, sc.kappa, lo, sz, 1.f, G);
-        if (!B.closed) add_gradient<false>(u, vv, w, tm, B, g, sc.kappa, lo, sz, -1.f, G);
-      }
+    if (PROBE && mine) {
       const float s = sc.mu * area;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -450,31 +467,20 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
         Fext[i * F + gf] = s * t;
       }
     }
-  }
-
-  // ---- flush the shared force box ------------------------------------------
-  if (SPREAD) {
-    __syncthreads();
-    if (fit) {
-      const int N = sz[0] * sz[1] * sz[2], sxy = sz[0] * sz[1];
-      for (int r = threadIdx.x; r < N; r += blockDim.x) {
-        const float a = fbox[r], b = fbox[N + r], cz = fbox[2 * N + r];
-        if (a != 0.f || b != 0.f || cz != 0.f) {
-          const int k = r / sxy, rem = r - k * sxy, j = rem / sz[0], i = rem - j * sz[0];
-          const size_t o = ((size_t)wrap(lo[2] + k, g.n[2]) * g.n[1] + wrap(lo[1] + j, g.n[1])) *
-                               g.n[0] + wrap(lo[0] + i, g.n[0]);
-          if (a != 0.f) atomicAdd(fx + o, a);
-          if (b != 0.f) atomicAdd(fy + o, b);
-          if (cz != 0.f) atomicAdd(fz + o, cz);
-        }
-      }
-    }
-    if (record_box && threadIdx.x == 0) {
-      // a box wider than the grid covers that whole direction
+    if (SPREAD && record_box) {
+      // footprint for the next step's clear: exact node mask when the box was
+      // staged, the whole box (flag 1) otherwise; a box wider than the grid
+      // covers that whole direction
+      __syncthreads();
       const int gc = B.chunk_off + ch.w;
-      T.boxes[2 * gc] = make_int4(lo[0], lo[1], lo[2], 0);
-      T.boxes[2 * gc + 1] =
-          make_int4(min(sz[0], g.n[0]), min(sz[1], g.n[1]), min(sz[2], g.n[2]), 0);
+      if (fit)
+        for (int k = threadIdx.x; k < (N + 31) / 32; k += blockDim.x)
+          T.mask[(size_t)gc * kMaskWords + k] = s_mask[k];
+      if (threadIdx.x == 0) {
+        T.boxes[2 * gc] = make_int4(lo[0], lo[1], lo[2], fit ? 0 : 1);
+        T.boxes[2 * gc + 1] =
+            make_int4(min(sz[0], g.n[0]), min(sz[1], g.n[1]), min(sz[2], g.n[2]), 0);
+      }
     }
   }
 
@@ -533,7 +539,10 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
   const long long N = (long long)sz.x * sz.y * sz.z;
   if (N <= 0) return;
   const int sxy = sz.x * sz.y;
+  const bool whole = lo.w != 0;
+  const uint32_t* mask = T.mask + (size_t)blockIdx.x * kMaskWords;
   for (long long idx = threadIdx.x; idx < N; idx += blockDim.x) {
+    if (!whole && !((__ldg(mask + (idx >> 5)) >> (idx & 31)) & 1u)) continue;
     const int k = (int)(idx / sxy), rem = (int)(idx - (long long)k * sxy), j = rem / sz.x,
               i = rem - j * sz.x;
     const size_t o = ((size_t)wrap(lo.z + k, g.n[2]) * g.n[1] + wrap(lo.y + j, g.n[1])) * g.n[0] +
