@@ -49,6 +49,7 @@ struct HostTopo {
   std::vector<int32_t> csr_ptr;
   std::vector<uint16_t> csr_slot;
   int max_loc = 0, max_slot = 0, max_own = 0;
+  std::vector<int32_t> mface, mbound;   // faces in marker-patch order, patch boundaries
 };
 
 inline uint64_t key2(int32_t p, int32_t q) {
@@ -225,6 +226,54 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
   }
 }
 
+// Marker patches: the faces split by recursive coordinate bisection of their
+// rest centroids into ceil(nf / kMT) compact parts of at most kMT faces (each
+// split along the longest extent, at the quantile that keeps part counts
+// balanced).  Writes the faces in patch order to `order` and the patch
+// boundaries to `bounds` (size parts + 1).
+void marker_patches(const int32_t* tri, int nf, const double* rest, std::vector<int32_t>& order,
+                    std::vector<int32_t>& bounds) {
+  std::vector<double> c(3 * (size_t)nf);
+  for (int f = 0; f < nf; ++f)
+    for (int d = 0; d < 3; ++d)
+      c[3 * f + d] = (rest[3 * tri[3 * f] + d] + rest[3 * tri[3 * f + 1] + d] +
+                      rest[3 * tri[3 * f + 2] + d]) / 3.0;
+  order.resize(nf);
+  for (int f = 0; f < nf; ++f) order[f] = f;
+  bounds.assign(1, 0);
+  struct Part {
+    int lo, hi, parts;
+  };
+  std::vector<Part> stack{{0, nf, (nf + kMT - 1) / kMT}};
+  std::vector<std::pair<int, int>> leaves;
+  while (!stack.empty()) {
+    Part p = stack.back();
+    stack.pop_back();
+    if (p.hi - p.lo <= kMT) {
+      leaves.push_back({p.lo, p.hi});
+      continue;
+    }
+    p.parts = std::max(p.parts, (p.hi - p.lo + kMT - 1) / kMT);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int k = p.lo; k < p.hi; ++k)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], c[3 * order[k] + d]);
+        hi[d] = std::max(hi[d], c[3 * order[k] + d]);
+      }
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+      if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+    const int p1 = p.parts / 2;
+    const int mid = p.lo + (int)((long long)(p.hi - p.lo) * p1 / p.parts);
+    std::stable_sort(order.begin() + p.lo, order.begin() + p.hi,
+                     [&](int a, int b) { return c[3 * a + ax] < c[3 * b + ax]; });
+    stack.push_back({mid, p.hi, p.parts - p1});
+    stack.push_back({p.lo, mid, p1});
+  }
+  std::sort(leaves.begin(), leaves.end());
+  for (auto& l : leaves) bounds.push_back(l.second);
+}
+
 uint64_t hash_mesh(const int32_t* t, int nf, int nv) {
   uint64_t h = 1469598103934665603ull ^ (uint64_t)nv;
   const unsigned char* p = reinterpret_cast<const unsigned char*>(t);
@@ -370,6 +419,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
         topos.emplace_back();
         try {
           build_topology(topos.back(), B.tri, B.n_vert, B.n_face, P);
+          marker_patches(B.tri, B.n_face, B.rest, topos.back().mface, topos.back().mbound);
         } catch (Failure& f) {
           f.msg = "body " + std::to_string(b) + ": " + f.msg;
           throw;
@@ -479,10 +529,10 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       R.A0 = A0;
       R.V0 = Bd.closed ? V0 : 1.0;
       R.chunk_off = (int32_t)chunks.size();
-      const int nch = (Bd.n_face + kChunk - 1) / kChunk;
+      const int nch = (int)T.mbound.size() - 1;
       R.n_chunk = nch;
       for (int k = 0; k < nch; ++k)
-        chunks.push_back(make_int4(b, k * kChunk, std::min(kChunk, Bd.n_face - k * kChunk), k));
+        chunks.push_back(make_int4(b, T.mbound[k], T.mbound[k + 1] - T.mbound[k], k));
       for (int q = 0; q < (int)T.patch.size(); ++q) work.push_back(make_int2(b, q));
       vo += Bd.n_vert;
       fo += Bd.n_face;
@@ -493,7 +543,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
 
     // concatenate the topology tables
     std::vector<TopoDev> td(topos.size());
-    std::vector<int32_t> tri_all, v2f_ptr_all, v2f_idx_all, loc_all, csr_all;
+    std::vector<int32_t> tri_all, v2f_ptr_all, v2f_idx_all, loc_all, csr_all, mface_all;
     std::vector<int4> edge_all;
     std::vector<PatchHdr> patch_all;
     std::vector<PEdge> pedge_all;
@@ -516,6 +566,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       v2f_ptr_all.insert(v2f_ptr_all.end(), T.v2f_ptr.begin(), T.v2f_ptr.end());
       D.v2f_idx_off = (int32_t)v2f_idx_all.size();
       v2f_idx_all.insert(v2f_idx_all.end(), T.v2f_idx.begin(), T.v2f_idx.end());
+      D.mface_off = (int32_t)mface_all.size();
+      mface_all.insert(mface_all.end(), T.mface.begin(), T.mface.end());
       D.patch_off = (int32_t)patch_all.size();
       const int32_t lo = (int32_t)loc_all.size(), eo2 = (int32_t)pedge_all.size(),
                     fo2 = (int32_t)pface_all.size(), co = (int32_t)csr_all.size(),
@@ -542,6 +594,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     if (c->force_smem > 227 * 1024)
       fail(IBM_ERR_UNSUPPORTED, "force-kernel shared memory above 227 KB; lower patch_size");
     check_cuda(set_force_smem_limit(c->force_smem), "cudaFuncSetAttribute");
+    check_cuda(set_marker_smem_limit(), "cudaFuncSetAttribute");
+    c->vec4 = (grid->n[0] % 4 == 0) ? 1 : 0;
 
     DeviceTables& d = c->d;
     d.body = upload(c, c->h_body);
@@ -570,7 +624,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.err = zeros<int32_t>(c, 1);
     d.coef = zeros<float2>(c, (size_t)n_bodies);
     d.boxes = zeros<int4>(c, 2 * (size_t)c->n_chunks);
-    d.mask = zeros<uint32_t>(c, (size_t)kMaskWords * c->n_chunks);
+    d.rowmap = zeros<int2>(c, (size_t)kMaxRows * c->n_chunks);
+    d.mface = upload(c, mface_all);
     d.stats = zeros<int32_t>(c, 4);
     check_cuda(cudaDeviceSynchronize(), "create");
     *out = c;

@@ -35,7 +35,8 @@ struct TopoDev {
   int32_t v2f_ptr_off;  // into v2f_ptr (nv + 1 entries, relative to v2f_idx_off)
   int32_t v2f_idx_off;  // into v2f_idx (body-local face ids)
   int32_t patch_off;    // into patch headers
-  int32_t pad[3];
+  int32_t mface_off;    // into mface (faces in marker-patch order)
+  int32_t pad[2];
 };
 
 // One force-kernel block works on a "patch": a contiguous range of a
@@ -72,7 +73,7 @@ struct StepConsts {
   int32_t pad;
 };
 
-constexpr int kChunk = 128;          // markers (faces) per block of the MLS kernel
+constexpr int kMT = 256;             // markers (faces) per block of the marker kernel (a patch)
 constexpr int kForceThreads = 256;   // threads per force-kernel block
 constexpr uint16_t kNone = 0xFFFF;
 
@@ -97,26 +98,29 @@ struct DeviceTables {
   float* A0f = nullptr;         // [F] rest face areas
   uint8_t* clamp = nullptr;     // [V]
   float* rest = nullptr;        // [3][V] body-frame rest positions
-  int4* chunks = nullptr;       // (body, first local face, count, chunk index in body)
+  int4* chunks = nullptr;       // (body, offset in the topology's mface list, count,
+                                //  chunk index in body): one marker patch each
   int2* work = nullptr;         // (body, patch index within topology)
   double* partial = nullptr;    // [n_chunks][2] per-chunk (A, V)
   int32_t* counter = nullptr;   // [B] chunk arrival counters
   double* meas = nullptr;       // [B][2] (A, V)
   float2* coef = nullptr;       // [B] (k_A (A - A0)/A0, k_v (V - V0)/V0) for the force kernel
   float* fext = nullptr;        // [3][F] scratch marker traction (ibm_step)
-  int4* boxes = nullptr;        // [n_chunks][2] grid box (lo, whole-box flag; size) of each
-                                // marker block's last spread
-  uint32_t* mask = nullptr;     // [n_chunks][kMaskWords] nodes of that box actually written
+  int32_t* mface = nullptr;     // faces of every topology in marker-patch order (body-local)
+  int4* boxes = nullptr;        // [n_chunks][2] footprint of each marker block's last spread:
+                                // (x, y, z lo, kind: 0 rows, 1 whole box, 2 rows in float4
+                                // groups), (x, y, z size, rows)
+  int2* rowmap = nullptr;       // [n_chunks][kMaxRows] (first x, length) of each footprint row
   int32_t* stats = nullptr;     // [4] counters: marker blocks that did not fit shared memory
   int32_t* err = nullptr;       // device error word
 };
 
-// stencil box staging per marker block: dynamic shared memory kept under the
-// 48 KB a block may use without opting in (the kernel's static shared
-// variables take the rest)
-constexpr int kMarkerSmemBytes = 46 * 1024;
-constexpr int kMaxBoxNodes = kMarkerSmemBytes / 8;        // one velocity + one force component
-constexpr int kMaskWords = (kMaxBoxNodes + 31) / 32;      // footprint bits per marker block
+// marker-kernel dynamic shared memory: row tables, then the staged rows of
+// one velocity and one force component
+constexpr int kMaxRows = 1024;                                     // (y, z) rows per patch
+constexpr int kMaxNodes = 8960;                                    // staged nodes per component
+constexpr int kRowTableBytes = ((4 * (3 * kMaxRows + 1) + 2 * kMaxNodes) + 15) / 16 * 16;
+constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes + 16;
 
 }  // namespace ibm
 
@@ -126,6 +130,7 @@ struct ibm_ctx {
   std::string err;
   int64_t V = 0, F = 0, E = 0, B = 0;
   int32_t n_topo = 0, n_chunks = 0, n_work = 0;
+  int vec4 = 0;                 // nx % 4 == 0: float4 row access allowed
   ibm_params prm{};
   ibm_grid_desc gdesc{};
   ibm::Grid grid{};
@@ -153,4 +158,5 @@ cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float
 cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,
                            const float* Fext, float* x_out, float* v_out);
 cudaError_t set_force_smem_limit(size_t bytes);
+cudaError_t set_marker_smem_limit();
 }  // namespace ibm

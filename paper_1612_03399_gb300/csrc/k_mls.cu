@@ -2,15 +2,17 @@
 // interpolation at the centroid, direct-forcing marker force, probe gradient
 // and traction, and spreading (Sec. 2.2, Eqs. mls..mls_cl; Sec. 5 steps 1-3).
 //
-// One block = up to kChunk faces (markers) of ONE body, one thread per face.
-// Faces are ordered along a space-filling curve, so a block's markers form a
-// compact surface patch.  The block first finds the grid box that holds every
-// 3x3x3 support of its centroids and probe ends, stages u, v, w on that box in
-// shared memory with coalesced row loads, interpolates from shared memory,
-// accumulates its spread contributions in a shared force box with shared
-// atomics, and flushes the box to the global force fields once (one global
-// atomic per non-zero node instead of 81 per marker).  A block whose box does
-// not fit falls back to direct global loads and atomics.
+// One block = one surface patch of ONE body (up to kMT faces, built by
+// recursive coordinate bisection of the rest mesh), one thread per face.
+// The block builds a ROW MAP of its grid footprint: for every (y, z) row of
+// the nodes its 3x3x3 supports (centroids and probe ends) touch, the x-range
+// touched, padded to whole float4 groups.  One velocity component at a time,
+// the block stages those rows in shared memory (float4 loads), interpolates
+// and differentiates from shared memory, accumulates its spread
+// contributions on the same rows with shared atomics and flushes them with
+// float4 global atomics; the row map is recorded so the next step's clear
+// zeroes exactly those rows.  A patch whose footprint does not fit takes the
+// direct global path (scalar loads and atomics) and records its bounding box.
 //
 // MLS with the linear basis and a weight that factorises over directions
 // (W = prod_d exp(-kappa delta_d^2), delta in cells) has an exact closed-form
@@ -110,7 +112,7 @@ __device__ __forceinline__ void locate(const float (&tau)[3], int comp, const in
   }
 }
 
-// addressing of the 3x3x3 support: rows (sy, sz) and columns sx
+// addressing of a 3x3x3 support: rows (sy, sz), columns sx
 struct GlobalAcc {   // wrapped indices into a full [nz][ny][nx] field
   int ix[3], iy[3], iz[3];
   int nx, ny;
@@ -127,14 +129,20 @@ struct GlobalAcc {   // wrapped indices into a full [nz][ny][nx] field
   __device__ int row(int sy, int sz) const { return (iz[sz] * ny + iy[sy]) * nx; }
   __device__ int col(int sx) const { return ix[sx]; }
 };
-struct BoxAcc {      // indices into a box staged in shared memory
-  int base, sx, sxy;
-  __device__ void init(const int (&c)[3], const int (&lo)[3], const int (&s)[3]) {
-    sx = s[0];
-    sxy = s[0] * s[1];
-    base = (c[0] - 1 - lo[0]) + sx * (c[1] - 1 - lo[1]) + sxy * (c[2] - 1 - lo[2]);
+struct RowAcc {      // indices into the rows staged in shared memory
+  const int* off;    // staged offset of row r, minus its first x
+  int ylo, zlo, sy;
+  int cx, cy, cz;    // support corner (centre - 1)
+  __device__ void init(const int (&c)[3], const int* off_minus_x0, int ylo_, int zlo_, int sy_) {
+    off = off_minus_x0;
+    ylo = ylo_;
+    zlo = zlo_;
+    sy = sy_;
+    cx = c[0] - 1;
+    cy = c[1] - 1;
+    cz = c[2] - 1;
   }
-  __device__ int row(int sy, int sz) const { return base + sz * sxy + sy * sx; }
+  __device__ int row(int a, int b) const { return off[(cy + a - ylo) + sy * (cz + b - zlo)] + cx; }
   __device__ int col(int s) const { return s; }
 };
 
@@ -181,19 +189,25 @@ __device__ __forceinline__ void mls_grad(const float* __restrict__ f, const Acc&
   g[0] = gx; g[1] = gy; g[2] = gz;
 }
 
+// spread coef * phi onto the 27 nodes; each thread walks the rows starting at
+// a lane-dependent row so that neighbouring markers rarely hit the same node
+// in the same instruction
 template <class Acc>
 __device__ __forceinline__ void mls_spread(float* f, const Acc& A, const DirW& X, const DirW& Y,
-                                           const DirW& Z, float coef) {
+                                           const DirW& Z, float coef, int rot) {
+#pragma unroll 1
+  for (int q = 0; q < 9; ++q) {
+    int k = q + rot;
+    k = k >= 9 ? k - 9 : k;
+    const int sy = k % 3, sz = k / 3;
+    float* r = f + A.row(sy, sz);
+    const float ay = sy == 0 ? Y.a[0] : (sy == 1 ? Y.a[1] : Y.a[2]);
+    const float by = sy == 0 ? Y.b[0] : (sy == 1 ? Y.b[1] : Y.b[2]);
+    const float az = sz == 0 ? Z.a[0] : (sz == 1 ? Z.a[1] : Z.a[2]);
+    const float bz = sz == 0 ? Z.b[0] : (sz == 1 ? Z.b[1] : Z.b[2]);
+    const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
 #pragma unroll
-  for (int sz = 0; sz < 3; ++sz) {
-#pragma unroll
-    for (int sy = 0; sy < 3; ++sy) {
-      float* r = f + A.row(sy, sz);
-      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
-      const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
-#pragma unroll
-      for (int sx = 0; sx < 3; ++sx) atomicAdd(r + A.col(sx), (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1);
-    }
+    for (int sx = 0; sx < 3; ++sx) atomicAdd(r + A.col(sx), (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1);
   }
 }
 
@@ -203,86 +217,93 @@ __device__ __forceinline__ void dir3(const float (&tp)[3], float kappa, DirW& X,
   dir_weights(tp[2], kappa, Z);
 }
 
-// full-derivative MLS gradient (in cells) of component `comp` at a point,
-// from the staged box (box = true) or the global field
-__device__ __forceinline__ void probe_gradient(const float* f, bool box, const float (&tau)[3],
-                                               int comp, const BodyDev& B, const Grid& g,
-                                               float kappa, const int (&lo)[3], const int (&sz)[3],
-                                               float (&gr)[3]) {
-  int c[3];
-  float tp[3];
-  locate(tau, comp, B.G, c, tp);
+// full-derivative MLS gradient (in cells) of component `comp` at a point
+template <class Acc>
+__device__ __forceinline__ void grad_at(const float* f, const Acc& A, const float (&tp)[3],
+                                        float kappa, float (&gr)[3]) {
   DirWD X, Y, Z;
   dir_weights_d(tp[0], kappa, X);
   dir_weights_d(tp[1], kappa, Y);
   dir_weights_d(tp[2], kappa, Z);
-  if (box) {
-    BoxAcc A;
-    A.init(c, lo, sz);
-    mls_grad(f, A, X, Y, Z, gr);
-  } else {
-    GlobalAcc A;
-    A.init(c, g);
-    mls_grad(f, A, X, Y, Z, gr);
-  }
+  mls_grad(f, A, X, Y, Z, gr);
 }
 
-// global offset of node r (x fastest) of the box with corner lo and size sz
-__device__ __forceinline__ size_t box_node(int r, const int (&lo)[3], const int (&sz)[3], int sxy,
-                                           const Grid& g) {
-  const int k = r / sxy, rem = r - k * sxy, j = rem / sz[0], i = rem - j * sz[0];
-  return ((size_t)wrap(lo[2] + k, g.n[2]) * g.n[1] + wrap(lo[1] + j, g.n[1])) * g.n[0] +
-         wrap(lo[0] + i, g.n[0]);
-}
-
-// extend [lo, hi] by the supports of all three components at a point, with
-// exactly the centre nodes the evaluation will use
-__device__ __forceinline__ void minmax_loc(const float (&tau)[3], const int (&G)[3], int (&lo)[3],
-                                           int (&hi)[3]) {
+// the 3x3x3 supports of all three components at a point: their union over
+// the rows (y, z) of a 4x4 window starting at w0 = (y0, z0), with per-row
+// x-range [xl, xh] (xl > xh: row untouched)
+struct Window {
+  int y0, z0;
+  int xl[4][4], xh[4][4];
+};
+__device__ __forceinline__ void support_window(const float (&tau)[3], const int (&G)[3], Window& W) {
+  int c[3][3];
+  float tp[3];
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) locate(tau, comp, G, c[comp], tp);
+  W.y0 = min(c[0][1], min(c[1][1], c[2][1])) - 1;
+  W.z0 = min(c[0][2], min(c[1][2], c[2][2])) - 1;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      W.xl[j][k] = INT_MAX;
+      W.xh[j][k] = INT_MIN;
+    }
 #pragma unroll
   for (int comp = 0; comp < 3; ++comp) {
-    int c[3];
-    float tp[3];
-    locate(tau, comp, G, c, tp);
+    const int dy = c[comp][1] - 1 - W.y0, dz = c[comp][2] - 1 - W.z0;   // 0 or 1
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      lo[d] = min(lo[d], c[d] - 1);
-      hi[d] = max(hi[d], c[d] + 1);
-    }
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool in = (j - dy) >= 0 && (j - dy) < 3 && (k - dz) >= 0 && (k - dz) < 3;
+        if (in) {
+          W.xl[j][k] = min(W.xl[j][k], c[comp][0] - 1);
+          W.xh[j][k] = max(W.xh[j][k], c[comp][0] + 1);
+        }
+      }
   }
 }
 
 template <bool MEASURE, bool INTERP, bool PROBE, bool SPREAD>
-__global__ void __launch_bounds__(kChunk, 4) marker_kernel(
+__global__ void __launch_bounds__(kMT, 2) marker_kernel(
     DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ v, const float* __restrict__ u, const float* __restrict__ vv,
     const float* __restrict__ w, float* __restrict__ U, float* __restrict__ Fm,
     const float* __restrict__ Fm_in, float* __restrict__ Fext, float* __restrict__ fx,
-    float* __restrict__ fy, float* __restrict__ fz, int record_box) {
+    float* __restrict__ fy, float* __restrict__ fz, int record, int vec4) {
   constexpr bool FIELD = INTERP || PROBE || SPREAD;
   constexpr bool VEL = INTERP || PROBE;
-  extern __shared__ float sbox[];
+  extern __shared__ __align__(16) unsigned char dyn[];
+  // dynamic shared memory: row tables, then staged rows (one velocity and one
+  // force component)
+  int* s_xmin = reinterpret_cast<int*>(dyn);              // [kMaxRows]  then: staged offset - x0
+  int* s_xmax = s_xmin + kMaxRows;                        // [kMaxRows]  then: row length
+  int* s_off = s_xmax + kMaxRows;                         // [kMaxRows + 1] staged row start
+  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_off + kMaxRows + 1);  // [kMaxNodes/4]
+  float* vbox = reinterpret_cast<float*>(dyn + kRowTableBytes);
   __shared__ int s_lo[3], s_hi[3];
-  __shared__ double s_red[2][kChunk / 32];
-  __shared__ int s_last;
-  __shared__ uint32_t s_mask[SPREAD ? kMaskWords : 1];
-  const int4 ch = T.chunks[blockIdx.x];  // body, first local face, count, chunk index in body
+  __shared__ double s_red[2][kMT / 32];
+  __shared__ int s_last, s_fit, s_N;
+  __shared__ int s_warp[kMT / 32];
+
+  const int4 ch = T.chunks[blockIdx.x];  // body, face-list offset, count, chunk index in body
   const BodyDev B = T.body[ch.x];
-  const int tri_off = T.topo[B.topo].tri_off;
-  const int lf = ch.y + threadIdx.x;
+  const TopoDev topo = T.topo[B.topo];
   const bool active = threadIdx.x < ch.z;
   if (FIELD && threadIdx.x < 3) {
     s_lo[threadIdx.x] = INT_MAX;
     s_hi[threadIdx.x] = INT_MIN;
   }
   float Af = 0.f, Vf = 0.f;
-  float c[3] = {0.f, 0.f, 0.f}, nrm[3] = {0.f, 0.f, 0.f}, area = 0.f;
-  float tc[3], tp[3], tm[3];
+  float nrm[3] = {0.f, 0.f, 0.f}, area = 0.f;
+  float tc[3] = {0.f, 0.f, 0.f}, tp[3] = {0.f, 0.f, 0.f}, tm[3] = {0.f, 0.f, 0.f};
   bool ok = false;
   int ia = 0, ib = 0, ic = 0, gf = 0;
   if (active) {
+    const int lf = __ldg(T.mface + topo.mface_off + ch.y + threadIdx.x);
     gf = B.f_off + lf;
-    const int* tr = T.tri + tri_off + 3 * lf;
+    const int* tr = T.tri + topo.tri_off + 3 * lf;
     ia = B.v_off + __ldg(tr);
     ib = B.v_off + __ldg(tr + 1);
     ic = B.v_off + __ldg(tr + 2);
@@ -312,28 +333,36 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
       ok = nn > 0.f;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        c[d] = (xa[d] + xb[d] + xc[d]) * third;
+        const float c = (xa[d] + xb[d] + xc[d]) * third;
         nrm[d] = N[d] * inv;
-        tc[d] = fmaf(c[d], g.invh[d], B.frac[d]);
-        tp[d] = fmaf(c[d] + sc.probe_h * nrm[d], g.invh[d], B.frac[d]);
-        tm[d] = fmaf(c[d] - sc.probe_h * nrm[d], g.invh[d], B.frac[d]);
+        tc[d] = fmaf(c, g.invh[d], B.frac[d]);
+        tp[d] = fmaf(c + sc.probe_h * nrm[d], g.invh[d], B.frac[d]);
+        tm[d] = fmaf(c - sc.probe_h * nrm[d], g.invh[d], B.frac[d]);
         ok = ok && fabsf(tc[d]) < 1.0e7f && fabsf(tp[d]) < 1.0e7f && fabsf(tm[d]) < 1.0e7f;
       }
       if (!ok) atomicOr(T.err, ERR_NONFINITE);
     }
   }
+  const bool mine = FIELD && active && ok;
+  const bool two = PROBE && !B.closed;     // open sheet: probes on both sides
 
-  // ---- the block's grid box --------------------------------------------
-  int lo[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
+  // ---- row map of the block's footprint -----------------------------------
+  int ylo = 0, zlo = 0, sy = 0, sz = 0, xlo = 0, sx = 0;
   bool fit = false;
   int N = 0;
   if (FIELD) {
     int mlo[3] = {INT_MAX, INT_MAX, INT_MAX}, mhi[3] = {INT_MIN, INT_MIN, INT_MIN};
-    if (active && ok) {
-      minmax_loc(tc, B.G, mlo, mhi);
-      if (PROBE) {
-        minmax_loc(tp, B.G, mlo, mhi);
-        if (!B.closed) minmax_loc(tm, B.G, mlo, mhi);
+    if (mine) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        if ((l == 1 && !PROBE) || (l == 2 && !two)) continue;
+        const float(&t)[3] = l == 0 ? tc : (l == 1 ? tp : tm);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int f0 = B.G[d] + (int)floorf(t[d]);
+          mlo[d] = min(mlo[d], f0 - 2);    // generous: every support lies in f0-1 .. f0+2
+          mhi[d] = max(mhi[d], f0 + 3);
+        }
       }
     }
 #pragma unroll
@@ -344,9 +373,7 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
         mhi[d] = max(mhi[d], __shfl_xor_sync(0xffffffffu, mhi[d], o));
       }
     }
-    if (SPREAD && record_box)
-      for (int k = threadIdx.x; k < kMaskWords; k += blockDim.x) s_mask[k] = 0u;
-    __syncthreads();   // s_lo / s_hi initialised
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -355,41 +382,132 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
       }
     }
     __syncthreads();
-    long long nbox = 1;
+    xlo = s_lo[0];
+    ylo = s_lo[1];
+    zlo = s_lo[2];
+    sx = s_hi[0] >= s_lo[0] ? s_hi[0] - s_lo[0] + 1 : 0;
+    sy = s_hi[1] >= s_lo[1] ? s_hi[1] - s_lo[1] + 1 : 0;
+    sz = s_hi[2] >= s_lo[2] ? s_hi[2] - s_lo[2] + 1 : 0;
+    const long long nrows = (long long)sy * sz;
+    const bool rows_ok = nrows > 0 && nrows <= kMaxRows && sx <= 30000;
+    if (rows_ok) {
+      for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
+        s_xmin[r] = INT_MAX;
+        s_xmax[r] = INT_MIN;
+      }
+      __syncthreads();
+      if (mine) {
+#pragma unroll 1
+        for (int l = 0; l < 3; ++l) {
+          if ((l == 1 && !PROBE) || (l == 2 && !two)) continue;
+          Window Wn;
+          support_window(l == 0 ? tc : (l == 1 ? tp : tm), B.G, Wn);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      lo[d] = s_lo[d];
-      sz[d] = s_hi[d] >= s_lo[d] ? s_hi[d] - s_lo[d] + 1 : 0;
-      nbox *= sz[d];
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (Wn.xl[j][k] <= Wn.xh[j][k]) {
+                const int r = (Wn.y0 + j - ylo) + sy * (Wn.z0 + k - zlo);
+                atomicMin(&s_xmin[r], Wn.xl[j][k]);
+                atomicMax(&s_xmax[r], Wn.xh[j][k]);
+              }
+        }
+      }
+      __syncthreads();
+      // row lengths (whole float4 groups when the grid allows vector access)
+      // and their exclusive scan: thread t owns rows 4t .. 4t + 3
+      int len[4], run = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = 4 * threadIdx.x + q;
+        int L = 0;
+        if (r < (int)nrows && s_xmin[r] <= s_xmax[r]) {
+          int a = s_xmin[r], b = s_xmax[r] + 1;
+          if (vec4) {
+            a = a - (((a % 4) + 4) % 4);
+            b = b + ((4 - ((b % 4) + 4) % 4) % 4);
+          }
+          s_xmin[r] = a;
+          L = b - a;
+        }
+        len[q] = L;
+        run += L;
+      }
+      // block exclusive scan of run
+      int incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((threadIdx.x & 31) >= o) incl += t;
+      }
+      if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = incl;
+      __syncthreads();
+      int base = 0;
+      for (int k = 0; k < (int)(threadIdx.x >> 5); ++k) base += s_warp[k];
+      int pos = base + incl - run;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = 4 * threadIdx.x + q;
+        if (r < kMaxRows) {
+          s_off[r] = pos;
+          s_xmax[r] = len[q];
+        }
+        pos += len[q];
+      }
+      if (threadIdx.x == blockDim.x - 1) {
+        s_N = pos;
+        s_off[kMaxRows] = pos;
+      }
+      __syncthreads();
+      N = s_N;
+      fit = N <= kMaxNodes;
+      if (fit) {
+        // row id of every float4 group (vector path) or node (scalar path),
+        // then fold x0 into the row offset: s_xmin[r] = offset - x0
+        const int gsz = vec4 ? 4 : 1;
+        for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
+          const int o = s_off[r], L = s_xmax[r];
+          for (int q = o / gsz; q < (o + L) / gsz; ++q) s_grow[q] = (unsigned short)r;
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x)
+          if (s_xmax[r] > 0) s_xmin[r] = s_off[r] - s_xmin[r];
+      }
     }
-    // one velocity component (and its force component) is staged at a time
-    const int nfield = (VEL ? 1 : 0) + (SPREAD ? 1 : 0);
-    fit = nbox > 0 && nbox <= kMaxBoxNodes &&
-          nbox * nfield * (long long)sizeof(float) <= kMarkerSmemBytes;
-    N = fit ? (int)nbox : 0;
-    if (!fit && nbox > 0 && threadIdx.x == 0) atomicAdd(T.stats, 1);
+    if (!fit && threadIdx.x == 0) atomicAdd(T.stats, 1);
+    __syncthreads();
   }
-  float* vbox = sbox;
-  float* fbox = sbox + (VEL ? N : 0);
-  const bool mine = FIELD && active && ok;
+  float* fbox = vbox + (VEL ? (N + 3) / 4 * 4 : 0);
 
   // ---- per component: stage, interpolate, spread, differentiate, flush ----
   // Each component's interpolation, spreading and gradient use only that
-  // component's field, so the shared box holds one component at a time.
-  float G[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  // component's field, so the staged rows hold one component at a time.
+  // Traction t = (G + G^T) n: pass i yields (G n)_i and adds n_i G_i. to G^T n.
+  float tGn[3] = {0.f, 0.f, 0.f}, tGTn[3] = {0.f, 0.f, 0.f};
+  const int rot = threadIdx.x % 9;
   if (FIELD) {
-    const int sxy = sz[0] * sz[1];
     const float third = 1.f / 3.f;
     const float cl = area * sc.cl_scale;
+    const int gsz = vec4 ? 4 : 1;
+    const int ngroups = fit ? N / gsz : 0;
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
       float* frcc = comp == 0 ? fx : (comp == 1 ? fy : fz);
       if (fit) {
-        __syncthreads();   // the previous component is done with the boxes
-        for (int r = threadIdx.x; r < N; r += blockDim.x) {
-          if (VEL) vbox[r] = __ldg(velc + box_node(r, lo, sz, sxy, g));
-          if (SPREAD) fbox[r] = 0.f;
+        __syncthreads();   // the previous component is done with the rows
+        for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
+          const int r = s_grow[q];
+          const int yy = wrap(ylo + r % sy, g.n[1]), zz = wrap(zlo + r / sy, g.n[2]);
+          const int xg = wrap(gsz * q - s_xmin[r], g.n[0]);
+          const size_t o = ((size_t)zz * g.n[1] + yy) * g.n[0] + xg;
+          if (vec4) {
+            if (VEL) reinterpret_cast<float4*>(vbox)[q] = __ldg(reinterpret_cast<const float4*>(velc + o));
+            if (SPREAD) reinterpret_cast<float4*>(fbox)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          } else {
+            if (VEL) vbox[q] = __ldg(velc + o);
+            if (SPREAD) fbox[q] = 0.f;
+          }
         }
         __syncthreads();
       }
@@ -404,8 +522,8 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
           if (INTERP) {
             float Ul;
             if (fit) {
-              BoxAcc A;
-              A.init(cc, lo, sz);
+              RowAcc A;
+              A.init(cc, s_xmin, ylo, zlo, sy);
               Ul = mls_value(vbox, A, X, Y, Z);
             } else {
               GlobalAcc A;
@@ -422,38 +540,61 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
           }
           if (SPREAD) {
             if (fit) {
-              BoxAcc A;
-              A.init(cc, lo, sz);
-              mls_spread(fbox, A, X, Y, Z, cl * Fl);
+              RowAcc A;
+              A.init(cc, s_xmin, ylo, zlo, sy);
+              mls_spread(fbox, A, X, Y, Z, cl * Fl, rot);
             } else {
               GlobalAcc A;
               A.init(cc, g);
-              mls_spread(frcc, A, X, Y, Z, cl * Fl);
+              mls_spread(frcc, A, X, Y, Z, cl * Fl, rot);
             }
           }
         }
         if (PROBE) {
-          float gr[3];
-          probe_gradient(fit ? (const float*)vbox : velc, fit, tp, comp, B, g, sc.kappa, lo, sz, gr);
-          if (!B.closed) {
-            // open sheet: second probe on the other side, (tau+ - tau-) . n+
-            float gm[3];
-            probe_gradient(fit ? (const float*)vbox : velc, fit, tm, comp, B, g, sc.kappa, lo, sz,
-                           gm);
+          float gr[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+          for (int l = 0; l < (two ? 2 : 1); ++l) {
+            int cc[3];
+            float t3[3];
+            locate(l == 0 ? tp : tm, comp, B.G, cc, t3);
+            float gl[3];
+            if (fit) {
+              RowAcc A;
+              A.init(cc, s_xmin, ylo, zlo, sy);
+              grad_at(vbox, A, t3, sc.kappa, gl);
+            } else {
+              GlobalAcc A;
+              A.init(cc, g);
+              grad_at(velc, A, t3, sc.kappa, gl);
+            }
+            // open sheet: (tau+ - tau-) . n+
+            const float sgn = l == 0 ? 1.f : -1.f;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) gr[j] -= gm[j];
+            for (int j = 0; j < 3; ++j) gr[j] += sgn * gl[j] * g.invh[j];
           }
+          const float gn = gr[0] * nrm[0] + gr[1] * nrm[1] + gr[2] * nrm[2];
+          const float ni = comp == 0 ? nrm[0] : (comp == 1 ? nrm[1] : nrm[2]);
+          if (comp == 0) tGn[0] = gn;
+          if (comp == 1) tGn[1] = gn;
+          if (comp == 2) tGn[2] = gn;
 #pragma unroll
-          for (int j = 0; j < 3; ++j) G[comp][j] = gr[j] * g.invh[j];
+          for (int j = 0; j < 3; ++j) tGTn[j] += ni * gr[j];
         }
       }
       if (SPREAD && fit) {
         __syncthreads();
-        for (int r = threadIdx.x; r < N; r += blockDim.x) {
-          const float val = fbox[r];
-          if (val != 0.f) {
-            atomicAdd(frcc + box_node(r, lo, sz, sxy, g), val);
-            if (record_box) atomicOr(&s_mask[r >> 5], 1u << (r & 31));
+        for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
+          const int r = s_grow[q];
+          const int yy = wrap(ylo + r % sy, g.n[1]), zz = wrap(zlo + r / sy, g.n[2]);
+          const int xg = wrap(gsz * q - s_xmin[r], g.n[0]);
+          const size_t o = ((size_t)zz * g.n[1] + yy) * g.n[0] + xg;
+          if (vec4) {
+            const float4 val = reinterpret_cast<const float4*>(fbox)[q];
+            if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f)
+              atomicAdd(reinterpret_cast<float4*>(frcc + o), val);
+          } else {
+            const float val = fbox[q];
+            if (val != 0.f) atomicAdd(frcc + o, val);
           }
         }
       }
@@ -461,25 +602,23 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
     if (PROBE && mine) {
       const float s = sc.mu * area;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const float t = (G[i][0] + G[0][i]) * nrm[0] + (G[i][1] + G[1][i]) * nrm[1] +
-                        (G[i][2] + G[2][i]) * nrm[2];
-        Fext[i * F + gf] = s * t;
-      }
+      for (int i = 0; i < 3; ++i) Fext[i * F + gf] = s * (tGn[i] + tGTn[i]);
     }
-    if (SPREAD && record_box) {
-      // footprint for the next step's clear: exact node mask when the box was
-      // staged, the whole box (flag 1) otherwise; a box wider than the grid
-      // covers that whole direction
-      __syncthreads();
+    if (SPREAD && record) {
+      // footprint for the next step's clear: the row map (x0, length per
+      // row) when staged, the bounding box (flag 1) otherwise
       const int gc = B.chunk_off + ch.w;
-      if (fit)
-        for (int k = threadIdx.x; k < (N + 31) / 32; k += blockDim.x)
-          T.mask[(size_t)gc * kMaskWords + k] = s_mask[k];
+      if (fit) {
+        for (int r = threadIdx.x; r < sy * sz; r += blockDim.x) {
+          const int L = s_xmax[r];
+          const int x0 = L > 0 ? s_off[r] - s_xmin[r] : 0;
+          T.rowmap[(size_t)gc * kMaxRows + r] = make_int2(x0, L);
+        }
+      }
       if (threadIdx.x == 0) {
-        T.boxes[2 * gc] = make_int4(lo[0], lo[1], lo[2], fit ? 0 : 1);
-        T.boxes[2 * gc + 1] =
-            make_int4(min(sz[0], g.n[0]), min(sz[1], g.n[1]), min(sz[2], g.n[2]), 0);
+        T.boxes[2 * gc] = make_int4(xlo, ylo, zlo, fit ? (vec4 ? 2 : 0) : 1);
+        T.boxes[2 * gc + 1] = make_int4(min(sx, g.n[0]), min(sy, g.n[1]), min(sz, g.n[2]),
+                                        fit ? sy * sz : 0);
       }
     }
   }
@@ -501,7 +640,7 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
     __syncthreads();
     if (threadIdx.x == 0) {
       double sa = 0.0, sv = 0.0;
-      for (int k = 0; k < kChunk / 32; ++k) {
+      for (int k = 0; k < kMT / 32; ++k) {
         sa += s_red[0][k];
         sv += s_red[1][k];
       }
@@ -531,43 +670,93 @@ __global__ void __launch_bounds__(kChunk, 4) marker_kernel(
   }
 }
 
-// zero the three force fields on every box recorded by the previous spread
+// zero the force fields on the footprint each marker block recorded in its
+// last spread: its row map, or its bounding box when it took the global path
 __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, float* __restrict__ fx,
-                                                    float* __restrict__ fy, float* __restrict__ fz) {
+                                                    float* __restrict__ fy, float* __restrict__ fz,
+                                                    int vec4) {
   const int4 lo = T.boxes[2 * blockIdx.x];
   const int4 sz = T.boxes[2 * blockIdx.x + 1];
-  const long long N = (long long)sz.x * sz.y * sz.z;
-  if (N <= 0) return;
-  const int sxy = sz.x * sz.y;
-  const bool whole = lo.w != 0;
-  const uint32_t* mask = T.mask + (size_t)blockIdx.x * kMaskWords;
-  for (long long idx = threadIdx.x; idx < N; idx += blockDim.x) {
-    if (!whole && !((__ldg(mask + (idx >> 5)) >> (idx & 31)) & 1u)) continue;
-    const int k = (int)(idx / sxy), rem = (int)(idx - (long long)k * sxy), j = rem / sz.x,
-              i = rem - j * sz.x;
-    const size_t o = ((size_t)wrap(lo.z + k, g.n[2]) * g.n[1] + wrap(lo.y + j, g.n[1])) * g.n[0] +
-                     wrap(lo.x + i, g.n[0]);
-    fx[o] = 0.f;
-    fy[o] = 0.f;
-    fz[o] = 0.f;
+  if (sz.x <= 0 || sz.y <= 0 || sz.z <= 0) return;
+  // float4 stores only for rows recorded in whole float4 groups
+  vec4 = vec4 && lo.w == 2;
+  if (lo.w == 1) {
+    const long long N = (long long)sz.x * sz.y * sz.z;
+    const int sxy = sz.x * sz.y;
+    for (long long idx = threadIdx.x; idx < N; idx += blockDim.x) {
+      const int k = (int)(idx / sxy), rem = (int)(idx - (long long)k * sxy), j = rem / sz.x,
+                i = rem - j * sz.x;
+      const size_t o = ((size_t)wrap(lo.z + k, g.n[2]) * g.n[1] + wrap(lo.y + j, g.n[1])) * g.n[0] +
+                       wrap(lo.x + i, g.n[0]);
+      fx[o] = 0.f;
+      fy[o] = 0.f;
+      fz[o] = 0.f;
+    }
+  } else {
+    const int nrows = sz.w;
+    const int2* rm = T.rowmap + (size_t)blockIdx.x * kMaxRows;
+    // a warp per row, a lane per float4 group (vector grids) or node
+    const int lane = threadIdx.x & 31;
+    for (int r = threadIdx.x >> 5; r < nrows; r += blockDim.x >> 5) {
+      const int2 e = rm[r];
+      if (e.y <= 0) continue;
+      const size_t rowb = ((size_t)wrap(lo.z + r / sz.y, g.n[2]) * g.n[1] + wrap(lo.y + r % sz.y, g.n[1])) *
+                          g.n[0];
+      if (vec4) {
+        for (int q = lane; q < e.y / 4; q += 32) {
+          const size_t o = rowb + wrap(e.x + 4 * q, g.n[0]);
+          const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(fx + o) = z4;
+          *reinterpret_cast<float4*>(fy + o) = z4;
+          *reinterpret_cast<float4*>(fz + o) = z4;
+        }
+      } else {
+        for (int q = lane; q < e.y; q += 32) {
+          const size_t o = rowb + wrap(e.x + q, g.n[0]);
+          fx[o] = 0.f;
+          fy[o] = 0.f;
+          fz[o] = 0.f;
+        }
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) T.boxes[2 * blockIdx.x + 1] = make_int4(0, 0, 0, 0);
 }
 
+// null (unused) pointers count as aligned
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 template <bool M, bool I, bool P, bool S>
 cudaError_t launch_t(ibm_ctx* c, const float* x, const float* v, const float* u, const float* vv,
                      const float* w, float* U, float* Fm, const float* Fm_in, float* Fext,
-                     float* fx, float* fy, float* fz, int record_box) {
+                     float* fx, float* fy, float* fz, int record) {
   if (c->n_chunks == 0) return cudaSuccess;
   const size_t smem = (I || P || S) ? kMarkerSmemBytes : 0;
-  marker_kernel<M, I, P, S><<<c->n_chunks, kChunk, smem, c->stream>>>(
+  const int vec4 = c->vec4 && aligned16(u) && aligned16(vv) && aligned16(w) && aligned16(fx) &&
+                   aligned16(fy) && aligned16(fz);
+  marker_kernel<M, I, P, S><<<c->n_chunks, kMT, smem, c->stream>>>(
       c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, U, Fm, Fm_in, Fext,
-      fx, fy, fz, record_box);
+      fx, fy, fz, record, vec4);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t set_marker_smem_limit() {
+  cudaError_t e = cudaSuccess;
+#define SET(M, I, P, S)                                                                      \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(marker_kernel<M, I, P, S>,                                      \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMarkerSmemBytes);
+  SET(true, true, true, true)
+  SET(false, true, true, false)
+  SET(false, true, false, false)
+  SET(false, false, true, false)
+  SET(false, false, false, true)
+#undef SET
+  return e;
+}
 
 cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* u,
                        const float* vv, const float* w, float* U, float* Fm, const float* Fm_in,
@@ -591,7 +780,8 @@ cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* 
 
 cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz) {
   if (c->n_chunks == 0) return cudaSuccess;
-  clear_kernel<<<c->n_chunks, 256, 0, c->stream>>>(c->d, c->grid, fx, fy, fz);
+  const int vec4 = c->vec4 && aligned16(fx) && aligned16(fy) && aligned16(fz);
+  clear_kernel<<<c->n_chunks, 256, 0, c->stream>>>(c->d, c->grid, fx, fy, fz, vec4);
   return cudaGetLastError();
 }
 
