@@ -110,7 +110,8 @@ struct DeviceTables {
   int4* boxes = nullptr;        // [n_chunks][2] footprint of each marker block's last spread:
                                 // (x, y, z lo, kind: 0 rows, 1 whole box, 2 rows in float4
                                 // groups), (x, y, z size, rows)
-  int2* rowmap = nullptr;       // [n_chunks][kMaxRows] (first x, length) of each footprint row
+  int2* rowmap = nullptr;       // [n_chunks][kMaxRows] (global offset of the (y, z) row,
+                                //  first x wrapped | length << 16) of each footprint row
   int32_t* stats = nullptr;     // [4] counters: marker blocks that did not fit shared memory
   int32_t* err = nullptr;       // device error word
 };
@@ -119,7 +120,7 @@ struct DeviceTables {
 // one velocity and one force component
 constexpr int kMaxRows = 1024;                                     // (y, z) rows per patch
 constexpr int kMaxNodes = 8960;                                    // staged nodes per component
-constexpr int kRowTableBytes = ((4 * (3 * kMaxRows + 1) + 2 * kMaxNodes) + 15) / 16 * 16;
+constexpr int kRowTableBytes = ((4 * (5 * kMaxRows + 1) + 2 * kMaxNodes) + 15) / 16 * 16;
 constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes + 16;
 
 }  // namespace ibm

@@ -94,6 +94,9 @@ __device__ __forceinline__ void dir_weights_d(float tp, float kappa, DirWD& o) {
 }
 
 __device__ __forceinline__ int wrap(int i, int n) {
+  if (i >= 0 && i < n) return i;
+  if (i < 0 && i >= -n) return i + n;
+  if (i >= n && i < 2 * n) return i - n;
   i %= n;
   return i < 0 ? i + n : i;
 }
@@ -228,6 +231,16 @@ __device__ __forceinline__ void grad_at(const float* f, const Acc& A, const floa
   mls_grad(f, A, X, Y, Z, gr);
 }
 
+// global offset of staged group (or node) q: its row's base plus the wrapped x
+__device__ __forceinline__ size_t row_node(int q, int gsz, const unsigned short* grow,
+                                           const int* off, const int* base, const int* x0w,
+                                           int nx) {
+  const int r = grow[q];
+  int xg = x0w[r] + (gsz * q - off[r]);
+  if (xg >= nx) xg -= nx;
+  return (size_t)base[r] + xg;
+}
+
 // the 3x3x3 supports of all three components at a point: their union over
 // the rows (y, z) of a 4x4 window starting at w0 = (y0, z0), with per-row
 // x-range [xl, xh] (xl > xh: row untouched)
@@ -280,7 +293,9 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   int* s_xmin = reinterpret_cast<int*>(dyn);              // [kMaxRows]  then: staged offset - x0
   int* s_xmax = s_xmin + kMaxRows;                        // [kMaxRows]  then: row length
   int* s_off = s_xmax + kMaxRows;                         // [kMaxRows + 1] staged row start
-  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_off + kMaxRows + 1);  // [kMaxNodes/4]
+  int* s_base = s_off + kMaxRows + 1;                     // [kMaxRows] global offset of row (y, z)
+  int* s_x0w = s_base + kMaxRows;                         // [kMaxRows] first x, wrapped
+  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_x0w + kMaxRows);  // [kMaxNodes]
   float* vbox = reinterpret_cast<float*>(dyn + kRowTableBytes);
   __shared__ int s_lo[3], s_hi[3];
   __shared__ double s_red[2][kMT / 32];
@@ -470,8 +485,14 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
           for (int q = o / gsz; q < (o + L) / gsz; ++q) s_grow[q] = (unsigned short)r;
         }
         __syncthreads();
-        for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x)
-          if (s_xmax[r] > 0) s_xmin[r] = s_off[r] - s_xmin[r];
+        for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
+          if (s_xmax[r] > 0) {
+            const int yy = wrap(ylo + r % sy, g.n[1]), zz = wrap(zlo + r / sy, g.n[2]);
+            s_base[r] = (zz * g.n[1] + yy) * g.n[0];
+            s_x0w[r] = wrap(s_xmin[r], g.n[0]);
+            s_xmin[r] = s_off[r] - s_xmin[r];
+          }
+        }
       }
     }
     if (!fit && threadIdx.x == 0) atomicAdd(T.stats, 1);
@@ -497,10 +518,7 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       if (fit) {
         __syncthreads();   // the previous component is done with the rows
         for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
-          const int r = s_grow[q];
-          const int yy = wrap(ylo + r % sy, g.n[1]), zz = wrap(zlo + r / sy, g.n[2]);
-          const int xg = wrap(gsz * q - s_xmin[r], g.n[0]);
-          const size_t o = ((size_t)zz * g.n[1] + yy) * g.n[0] + xg;
+          const size_t o = row_node(q, gsz, s_grow, s_off, s_base, s_x0w, g.n[0]);
           if (vec4) {
             if (VEL) reinterpret_cast<float4*>(vbox)[q] = __ldg(reinterpret_cast<const float4*>(velc + o));
             if (SPREAD) reinterpret_cast<float4*>(fbox)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -584,10 +602,7 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       if (SPREAD && fit) {
         __syncthreads();
         for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
-          const int r = s_grow[q];
-          const int yy = wrap(ylo + r % sy, g.n[1]), zz = wrap(zlo + r / sy, g.n[2]);
-          const int xg = wrap(gsz * q - s_xmin[r], g.n[0]);
-          const size_t o = ((size_t)zz * g.n[1] + yy) * g.n[0] + xg;
+          const size_t o = row_node(q, gsz, s_grow, s_off, s_base, s_x0w, g.n[0]);
           if (vec4) {
             const float4 val = reinterpret_cast<const float4*>(fbox)[q];
             if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f)
@@ -611,8 +626,8 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       if (fit) {
         for (int r = threadIdx.x; r < sy * sz; r += blockDim.x) {
           const int L = s_xmax[r];
-          const int x0 = L > 0 ? s_off[r] - s_xmin[r] : 0;
-          T.rowmap[(size_t)gc * kMaxRows + r] = make_int2(x0, L);
+          T.rowmap[(size_t)gc * kMaxRows + r] =
+              L > 0 ? make_int2(s_base[r], s_x0w[r] | (L << 16)) : make_int2(0, 0);
         }
       }
       if (threadIdx.x == 0) {
@@ -698,21 +713,24 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
     // a warp per row, a lane per float4 group (vector grids) or node
     const int lane = threadIdx.x & 31;
     for (int r = threadIdx.x >> 5; r < nrows; r += blockDim.x >> 5) {
-      const int2 e = rm[r];
-      if (e.y <= 0) continue;
-      const size_t rowb = ((size_t)wrap(lo.z + r / sz.y, g.n[2]) * g.n[1] + wrap(lo.y + r % sz.y, g.n[1])) *
-                          g.n[0];
+      const int2 e = rm[r];                  // (row base, first x wrapped | length << 16)
+      const int L = e.y >> 16, x0 = e.y & 0xFFFF;
+      if (L <= 0) continue;
       if (vec4) {
-        for (int q = lane; q < e.y / 4; q += 32) {
-          const size_t o = rowb + wrap(e.x + 4 * q, g.n[0]);
+        for (int q = lane; q < L / 4; q += 32) {
+          int xg = x0 + 4 * q;
+          if (xg >= g.n[0]) xg -= g.n[0];
+          const size_t o = (size_t)e.x + xg;
           const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
           *reinterpret_cast<float4*>(fx + o) = z4;
           *reinterpret_cast<float4*>(fy + o) = z4;
           *reinterpret_cast<float4*>(fz + o) = z4;
         }
       } else {
-        for (int q = lane; q < e.y; q += 32) {
-          const size_t o = rowb + wrap(e.x + q, g.n[0]);
+        for (int q = lane; q < L; q += 32) {
+          int xg = x0 + q;
+          if (xg >= g.n[0]) xg -= g.n[0];
+          const size_t o = (size_t)e.x + xg;
           fx[o] = 0.f;
           fy[o] = 0.f;
           fz[o] = 0.f;
