@@ -192,25 +192,21 @@ __device__ __forceinline__ void mls_grad(const float* __restrict__ f, const Acc&
   g[0] = gx; g[1] = gy; g[2] = gz;
 }
 
-// spread coef * phi onto the 27 nodes; each thread walks the rows starting at
-// a lane-dependent row so that neighbouring markers rarely hit the same node
-// in the same instruction
+// spread coef * phi onto the 27 nodes
 template <class Acc>
 __device__ __forceinline__ void mls_spread(float* f, const Acc& A, const DirW& X, const DirW& Y,
-                                           const DirW& Z, float coef, int rot) {
-#pragma unroll 1
-  for (int q = 0; q < 9; ++q) {
-    int k = q + rot;
-    k = k >= 9 ? k - 9 : k;
-    const int sy = k % 3, sz = k / 3;
-    float* r = f + A.row(sy, sz);
-    const float ay = sy == 0 ? Y.a[0] : (sy == 1 ? Y.a[1] : Y.a[2]);
-    const float by = sy == 0 ? Y.b[0] : (sy == 1 ? Y.b[1] : Y.b[2]);
-    const float az = sz == 0 ? Z.a[0] : (sz == 1 ? Z.a[1] : Z.a[2]);
-    const float bz = sz == 0 ? Z.b[0] : (sz == 1 ? Z.b[1] : Z.b[2]);
-    const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
+                                           const DirW& Z, float coef) {
 #pragma unroll
-    for (int sx = 0; sx < 3; ++sx) atomicAdd(r + A.col(sx), (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1);
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      float* r = f + A.row(sy, sz);
+      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
+      const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
+#pragma unroll
+      for (int sx = 0; sx < 3; ++sx)
+        atomicAdd(r + A.col(sx), (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1);
+    }
   }
 }
 
@@ -239,43 +235,6 @@ __device__ __forceinline__ size_t row_node(int q, int gsz, const unsigned short*
   int xg = x0w[r] + (gsz * q - off[r]);
   if (xg >= nx) xg -= nx;
   return (size_t)base[r] + xg;
-}
-
-// the 3x3x3 supports of all three components at a point: their union over
-// the rows (y, z) of a 4x4 window starting at w0 = (y0, z0), with per-row
-// x-range [xl, xh] (xl > xh: row untouched)
-struct Window {
-  int y0, z0;
-  int xl[4][4], xh[4][4];
-};
-__device__ __forceinline__ void support_window(const float (&tau)[3], const int (&G)[3], Window& W) {
-  int c[3][3];
-  float tp[3];
-#pragma unroll
-  for (int comp = 0; comp < 3; ++comp) locate(tau, comp, G, c[comp], tp);
-  W.y0 = min(c[0][1], min(c[1][1], c[2][1])) - 1;
-  W.z0 = min(c[0][2], min(c[1][2], c[2][2])) - 1;
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      W.xl[j][k] = INT_MAX;
-      W.xh[j][k] = INT_MIN;
-    }
-#pragma unroll
-  for (int comp = 0; comp < 3; ++comp) {
-    const int dy = c[comp][1] - 1 - W.y0, dz = c[comp][2] - 1 - W.z0;   // 0 or 1
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool in = (j - dy) >= 0 && (j - dy) < 3 && (k - dz) >= 0 && (k - dz) < 3;
-        if (in) {
-          W.xl[j][k] = min(W.xl[j][k], c[comp][0] - 1);
-          W.xh[j][k] = max(W.xh[j][k], c[comp][0] + 1);
-        }
-      }
-  }
 }
 
 template <bool MEASURE, bool INTERP, bool PROBE, bool SPREAD>
@@ -316,7 +275,11 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   bool ok = false;
   int ia = 0, ib = 0, ic = 0, gf = 0;
   if (active) {
-    const int lf = __ldg(T.mface + topo.mface_off + ch.y + threadIdx.x);
+    // threads of a warp take faces spread over the patch (t -> 8 (t % 32) + t / 32
+    // for full patches), so that one warp's simultaneous shared atomics of the
+    // spread rarely meet on a node
+    const int slot = (ch.z == kMT) ? 8 * (threadIdx.x & 31) + (threadIdx.x >> 5) : threadIdx.x;
+    const int lf = __ldg(T.mface + topo.mface_off + ch.y + slot);
     gf = B.f_off + lf;
     const int* tr = T.tri + topo.tri_off + 3 * lf;
     ia = B.v_off + __ldg(tr);
@@ -353,7 +316,7 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
         tc[d] = fmaf(c, g.invh[d], B.frac[d]);
         tp[d] = fmaf(c + sc.probe_h * nrm[d], g.invh[d], B.frac[d]);
         tm[d] = fmaf(c - sc.probe_h * nrm[d], g.invh[d], B.frac[d]);
-        ok = ok && fabsf(tc[d]) < 1.0e7f && fabsf(tp[d]) < 1.0e7f && fabsf(tm[d]) < 1.0e7f;
+        ok = ok && fabsf(tc[d]) < 4.0e6f && fabsf(tp[d]) < 4.0e6f && fabsf(tm[d]) < 4.0e6f;
       }
       if (!ok) atomicOr(T.err, ERR_NONFINITE);
     }
@@ -412,20 +375,23 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       }
       __syncthreads();
       if (mine) {
+        // every component's support at a point with f = floor(tau) lies in
+        // the 4x4x4 window f - 1 .. f + 2 (the nearest-node choice is exact
+        // for |tau| < 2^22, which the position check guarantees)
 #pragma unroll 1
         for (int l = 0; l < 3; ++l) {
           if ((l == 1 && !PROBE) || (l == 2 && !two)) continue;
-          Window Wn;
-          support_window(l == 0 ? tc : (l == 1 ? tp : tm), B.G, Wn);
+          const float(&t)[3] = l == 0 ? tc : (l == 1 ? tp : tm);
+          const int fx0 = B.G[0] + (int)floorf(t[0]) - 1;
+          const int r0 = (B.G[1] + (int)floorf(t[1]) - 1 - ylo) +
+                         sy * (B.G[2] + (int)floorf(t[2]) - 1 - zlo);
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
+          for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (Wn.xl[j][k] <= Wn.xh[j][k]) {
-                const int r = (Wn.y0 + j - ylo) + sy * (Wn.z0 + k - zlo);
-                atomicMin(&s_xmin[r], Wn.xl[j][k]);
-                atomicMax(&s_xmax[r], Wn.xh[j][k]);
-              }
+            for (int j = 0; j < 4; ++j) {
+              atomicMin(&s_xmin[r0 + j + sy * k], fx0);
+              atomicMax(&s_xmax[r0 + j + sy * k], fx0 + 3);
+            }
         }
       }
       __syncthreads();
@@ -505,7 +471,6 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   // component's field, so the staged rows hold one component at a time.
   // Traction t = (G + G^T) n: pass i yields (G n)_i and adds n_i G_i. to G^T n.
   float tGn[3] = {0.f, 0.f, 0.f}, tGTn[3] = {0.f, 0.f, 0.f};
-  const int rot = threadIdx.x % 9;
   if (FIELD) {
     const float third = 1.f / 3.f;
     const float cl = area * sc.cl_scale;
@@ -560,11 +525,11 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
             if (fit) {
               RowAcc A;
               A.init(cc, s_xmin, ylo, zlo, sy);
-              mls_spread(fbox, A, X, Y, Z, cl * Fl, rot);
+              mls_spread(fbox, A, X, Y, Z, cl * Fl);
             } else {
               GlobalAcc A;
               A.init(cc, g);
-              mls_spread(frcc, A, X, Y, Z, cl * Fl, rot);
+              mls_spread(frcc, A, X, Y, Z, cl * Fl);
             }
           }
         }
