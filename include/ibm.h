@@ -189,6 +189,32 @@ ibm_status ibm_get_phase_times(ibm_ctx* ctx, float* ms);
  * direct global path, 0, 0, 0). */
 ibm_status ibm_get_counters(ibm_ctx* ctx, int64_t* out);
 
+/* Per-body surface area and enclosed volume WITHOUT a context and without
+ * allocating any memory (no counterpart in the paper: it serves callers that
+ * cannot allocate device memory at the point of the call, for example code
+ * that runs inside another framework's memory pool or that must not add
+ * allocations while a stream is being captured).  The result equals
+ * ibm_body_measures: the same float64 sums in a fixed order.
+ *   x         device float32 [3][n_vert], body-frame positions (SoA)
+ *   tri       device int32 [F][3], GLOBAL vertex ids, faces of body b at
+ *             [face_off[b], face_off[b+1])
+ *   face_off  device int32 [n_bodies + 1]
+ *   closed    device uint8 [n_bodies] or NULL (all closed); open bodies get V = 0
+ *   out       device float64 [n_bodies][2] = (A, V)
+ *   stream    cudaStream_t (NULL: legacy default stream)
+ * Scratch lives in one static device array of 1.25 MiB that every GPU
+ * loading the library keeps until the process exits; limits: n_bodies <=
+ * 65535 and n_bodies * ceil(max_faces_per_body / 256) <= 65536, larger
+ * requests return IBM_ERR_UNSUPPORTED.  The first call on a device looks up
+ * the array's device address (no allocation); make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  Errors: see ibm_last_error(NULL). */
+ibm_status ibm_body_measures_noalloc(const float* x, int64_t n_vert, const int32_t* tri,
+                                     const int32_t* face_off, int32_t n_bodies,
+                                     int32_t max_faces_per_body, const uint8_t* closed,
+                                     double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ SIGNATURES = {
     "ibm_set_phase_timing": (C.c_int, [P, C.c_int32]),
     "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
     "ibm_get_counters": (C.c_int, [P, C.POINTER(C.c_int64)]),
+    "ibm_body_measures_noalloc": (C.c_int, [P, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]),
 }
 
 _lib = None

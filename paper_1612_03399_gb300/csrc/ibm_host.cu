@@ -353,6 +353,11 @@ void make_consts(ibm_ctx* c) {
 
 }  // namespace
 
+void ibm::set_global_error(const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err = msg;
+}
+
 // ---------------------------------------------------------------------------
 // entry points
 // ---------------------------------------------------------------------------

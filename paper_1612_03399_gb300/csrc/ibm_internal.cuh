@@ -160,4 +160,6 @@ cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const flo
                            const float* Fext, float* x_out, float* v_out);
 cudaError_t set_force_smem_limit(size_t bytes);
 cudaError_t set_marker_smem_limit();
+// message returned by ibm_last_error(NULL)
+void set_global_error(const std::string& msg);
 }  // namespace ibm
