@@ -172,6 +172,23 @@ ibm_status ibm_step(ibm_ctx* ctx, const float* x, const float* v, const float* u
                     const float* vv, const float* w, float* x_out, float* v_out, float* fx,
                     float* fy, float* fz, uint32_t flags);
 
+/* Adjoint of one step (a vector-Jacobian product, loose coupling with the
+ * flow frozen; Sec. 2.3 node update, Sec. 2.2 traction, Sec. 2.3 potentials):
+ * given cotangents gx_next, gv_next [3][V] of the positions and velocities
+ * an ibm_step from x produced, writes the cotangents gx, gv [3][V] of x and v
+ * and gparams [B][5] float64 = cotangents of (k_s, k_b, k_a, k_A, k_v) per
+ * body.  The velocity field (u, v, w) is the one the step used.  The step's
+ * dependence on x through the internal forces (exact Hessian-vector products
+ * of the four potentials, including the per-body global area and volume
+ * terms) and through the probe traction (area, normal and the MLS velocity
+ * gradient at the probe end, with its second derivatives) is included; the
+ * spread force field is not differentiated (it does not feed the state).
+ * Outputs must not alias the cotangents.  Per-body sums are in a fixed order;
+ * the result is deterministic. */
+ibm_status ibm_backward(ibm_ctx* ctx, const float* x, const float* u, const float* vv,
+                        const float* w, const float* gx_next, const float* gv_next, float* gx,
+                        float* gv, double* gparams);
+
 /* Synchronise the stream and report the device error word (IBM_ERR_DEVICE if
  * a kernel flagged an out-of-range or non-finite value). */
 ibm_status ibm_check_device_error(ibm_ctx* ctx);

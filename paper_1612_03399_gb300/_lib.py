@@ -66,6 +66,7 @@ SIGNATURES = {
     "ibm_set_phase_timing": (C.c_int, [P, C.c_int32]),
     "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
     "ibm_get_counters": (C.c_int, [P, C.POINTER(C.c_int64)]),
+    "ibm_backward": (C.c_int, [P, P, P, P, P, P, P, P, P, P]),
     "ibm_body_measures_noalloc": (C.c_int, [P, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]),
 }
 
@@ -231,6 +232,17 @@ class Context:
         self._check(self.lib.ibm_step(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
                                       _ptr(x_out), _ptr(v_out), _ptr(fx), _ptr(fy), _ptr(fz),
                                       IBM_STEP_CLEAR_PREV if clear else 0))
+
+    def backward(self, x, fields, gx_next, gv_next):
+        """Cotangents (gx, gv, gparams [B, 5]) of one step from x (ibm_backward)."""
+        import torch
+        u, vv, w = fields
+        gx, gv = self._vec(self.V), self._vec(self.V)
+        gp = torch.empty((self.B, 5), dtype=torch.float64, device=self.device)
+        self._check(self.lib.ibm_backward(self.h, _ptr(x), _ptr(u), _ptr(vv), _ptr(w),
+                                          _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv),
+                                          _ptr(gp)))
+        return gx, gv, gp
 
     def check_device_error(self):
         self._check(self.lib.ibm_check_device_error(self.h))

@@ -538,6 +538,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       R.n_chunk = nch;
       for (int k = 0; k < nch; ++k)
         chunks.push_back(make_int4(b, T.mbound[k], T.mbound[k + 1] - T.mbound[k], k));
+      R.work_off = (int32_t)work.size();
       for (int q = 0; q < (int)T.patch.size(); ++q) work.push_back(make_int2(b, q));
       vo += Bd.n_vert;
       fo += Bd.n_face;
@@ -595,10 +596,12 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       max_own = std::max(max_own, T.max_own);
     }
     c->force_smem = sizeof(float) * 3 * ((size_t)max_loc + (size_t)max_slot);
+    c->adjoint_smem = sizeof(float) * (6 * (size_t)max_loc + 3 * (size_t)max_slot);
     c->max_own = max_own;
-    if (c->force_smem > 227 * 1024)
+    if (c->adjoint_smem > 227 * 1024)
       fail(IBM_ERR_UNSUPPORTED, "force-kernel shared memory above 227 KB; lower patch_size");
     check_cuda(set_force_smem_limit(c->force_smem), "cudaFuncSetAttribute");
+    check_cuda(set_adjoint_smem_limit(c->adjoint_smem), "cudaFuncSetAttribute");
     check_cuda(set_marker_smem_limit(), "cudaFuncSetAttribute");
     c->vec4 = (grid->n[0] % 4 == 0) ? 1 : 0;
 
@@ -632,6 +635,12 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.rowmap = zeros<int2>(c, (size_t)kMaxRows * c->n_chunks);
     d.mface = upload(c, mface_all);
     d.stats = zeros<int32_t>(c, 4);
+    d.partial2 = zeros<double>(c, 2 * (size_t)c->n_chunks);
+    d.counter2 = zeros<int32_t>(c, (size_t)n_bodies);
+    d.dmeas = zeros<double>(c, 2 * (size_t)n_bodies);
+    d.gxe = zeros<float>(c, 9 * (size_t)F);
+    d.wpart = zeros<double>(c, 3 * (size_t)c->n_work);
+    d.wcounter = zeros<int32_t>(c, (size_t)n_bodies);
     check_cuda(cudaDeviceSynchronize(), "create");
     *out = c;
     return IBM_OK;
@@ -844,6 +853,18 @@ extern "C" ibm_status ibm_get_phase_times(ibm_ctx* c, float* ms) {
   cudaError_t e = cudaEventSynchronize(c->ev[3]);
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(ms + k, c->ev[k], c->ev[k + 1]);
   return cuda_status(c, e, "ibm_get_phase_times");
+}
+
+extern "C" ibm_status ibm_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
+                                   const float* w, const float* gx_next, const float* gv_next,
+                                   float* gx, float* gv, double* gparams) {
+  if (!c || !x || !u || !vv || !w || !gx_next || !gv_next || !gx || !gv || !gparams)
+    return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (gx == gx_next || gv == gv_next || gx == gv_next || gv == gx_next)
+    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_backward: outputs must not alias the cotangents");
+  cudaSetDevice(c->device);
+  return cuda_status(c, launch_backward(c, x, u, vv, w, gx_next, gv_next, gx, gv, gparams),
+                     "ibm_backward");
 }
 
 extern "C" ibm_status ibm_check_device_error(ibm_ctx* c) {

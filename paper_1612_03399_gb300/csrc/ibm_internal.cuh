@@ -23,7 +23,8 @@ struct BodyDev {
   float frac[3];                       // origin_d / h_d - G_d, in [0, 1)
   int32_t n_chunk;
   float ks, kb, ka, kA, kv, inv_mass;  // elastic constants, 1/m
-  float pad0, pad1;
+  int32_t work_off;                    // first force-kernel work item (patch) of this body
+  int32_t pad1;
   double A0, V0;                       // rest area and volume (float64)
 };
 
@@ -113,6 +114,13 @@ struct DeviceTables {
   int2* rowmap = nullptr;       // [n_chunks][kMaxRows] (global offset of the (y, z) row,
                                 //  first x wrapped | length << 16) of each footprint row
   int32_t* stats = nullptr;     // [4] counters: marker blocks that did not fit shared memory
+  // adjoint scratch
+  double* partial2 = nullptr;   // [n_chunks][2] per-chunk (grad A . g, grad V . g)
+  int32_t* counter2 = nullptr;  // [B]
+  double* dmeas = nullptr;      // [B][2] per-body (grad A . g, grad V . g)
+  float* gxe = nullptr;         // [9][F] per-face position cotangents (3 corners x 3)
+  double* wpart = nullptr;      // [n_work][3] per-patch (g k_s, g k_b, g k_a)
+  int32_t* wcounter = nullptr;  // [B]
   int32_t* err = nullptr;       // device error word
 };
 
@@ -137,6 +145,7 @@ struct ibm_ctx {
   ibm::Grid grid{};
   ibm::StepConsts sc{};
   size_t force_smem = 0;
+  size_t adjoint_smem = 0;
   int32_t max_own = 0;
   bool have_prev = false;
   bool timing = false;          // record phase events in ibm_step
@@ -158,7 +167,11 @@ cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float
                          float* Fint, float* x_out, float* v_out, double* energy, bool advance);
 cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,
                            const float* Fext, float* x_out, float* v_out);
+cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
+                            const float* w, const float* gx_next, const float* gv_next, float* gx,
+                            float* gv, double* gparams);
 cudaError_t set_force_smem_limit(size_t bytes);
+cudaError_t set_adjoint_smem_limit(size_t bytes);
 cudaError_t set_marker_smem_limit();
 // message returned by ibm_last_error(NULL)
 void set_global_error(const std::string& msg);

@@ -1,0 +1,564 @@
+// Adjoint of one step (a vector-Jacobian product): given the cotangents
+// (gx', gv') of the new positions and velocities, the cotangents (gx, gv) of
+// the old ones and of the per-body elastic constants.
+//
+// The step (Sec. 2.3, Sec. 5 step 4) is v' = v + dt F(x)/m, x' = x + dt v'
+// (symplectic) or x' = x + dt v (forward Euler), F = F_int + F_ext^v; clamped
+// nodes keep x and get v' = 0.  So gv = gv' + dt gx', the force cotangent is
+// gF = dt (gv' + dt gx')/m (symplectic) or dt gv'/m (forward Euler), zero on
+// clamped nodes, and gx = gx' + (dF_int/dx)^T gF + (dF_ext^v/dx)^T gF.
+//
+// ext_adjoint_kernel (per face): the traction F_ext = mu A (G + G^T) n at the
+// probe end p = c + h n (two probes on open sheets) depends on x through A,
+// n, c and the MLS velocity gradient G(p); its reverse sweep needs the
+// second derivatives of the MLS interpolant at p.  It also sums, per body,
+// grad A . gF and grad V . gF (fixed order), which the global area and
+// volume terms need.
+//
+// force_adjoint_kernel (per force patch): the element forces evaluated with
+// dual numbers whose tangents are gF give (dF_int/dx) gF (= its transpose:
+// F_int is minus an energy gradient, so its Jacobian is symmetric); the
+// constants' cotangents are gF . dF/dk, summed per body in a fixed order.
+#include <cuda_runtime.h>
+
+#include "force_elems.cuh"
+#include "ibm_internal.cuh"
+
+namespace ibm {
+namespace {
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  if (i >= 0 && i < n) return i;
+  if (i < 0 && i >= -n) return i + n;
+  if (i >= n && i < 2 * n) return i - n;
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// per-direction MLS factors a, b = a beta and their first and second
+// derivatives with respect to the point's coordinate in cells (closed form
+// of the factorised weight; see the marker kernel)
+struct DirW2 {
+  float a[3][3], b[3][3];   // [order][node]
+};
+__device__ __forceinline__ void dir_weights_d2(float tp, float kappa, DirW2& o) {
+  float d[3] = {-1.f - tp, -tp, 1.f - tp};
+  float w[3], w1[3], w2[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    w[s] = __expf(-kappa * d[s] * d[s]);
+    w1[s] = 2.f * kappa * d[s] * w[s];
+    w2[s] = 2.f * kappa * w[s] * (2.f * kappa * d[s] * d[s] - 1.f);
+  }
+  const float invS = 1.f / (w[0] + w[1] + w[2]);
+  const float S1 = w1[0] + w1[1] + w1[2], S2 = w2[0] + w2[1] + w2[2];
+  float a[3], a1[3], a2[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    a[s] = w[s] * invS;
+    a1[s] = (w1[s] - a[s] * S1) * invS;
+  }
+#pragma unroll
+  for (int s = 0; s < 3; ++s) a2[s] = (w2[s] - 2.f * a1[s] * S1 - a[s] * S2) * invS;
+  float mu = 0.f, mu1 = -1.f, mu2 = 0.f;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    mu += a[s] * d[s];
+    mu1 += a1[s] * d[s];
+    mu2 += a2[s] * d[s] - a1[s];
+  }
+  const float e1 = -1.f - mu1, e2 = -mu2;   // derivatives of e_s = d_s - mu (same for all s)
+  float Q = 0.f, Q1 = 0.f, Q2 = 0.f;
+  float e[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    e[s] = d[s] - mu;
+    Q += a[s] * e[s] * e[s];
+    Q1 += a1[s] * e[s] * e[s] + 2.f * a[s] * e[s] * e1;
+    Q2 += a2[s] * e[s] * e[s] + 4.f * a1[s] * e[s] * e1 + 2.f * a[s] * e1 * e1 + 2.f * a[s] * e[s] * e2;
+  }
+  const float iQ = 1.f / Q;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const float P = mu * e[s], P1 = mu1 * e[s] + mu * e1, P2 = mu2 * e[s] + 2.f * mu1 * e1 + mu * e2;
+    const float beta = P * iQ;
+    const float beta1 = P1 * iQ - P * Q1 * iQ * iQ;
+    const float beta2 = P2 * iQ - 2.f * P1 * Q1 * iQ * iQ - P * Q2 * iQ * iQ +
+                        2.f * P * Q1 * Q1 * iQ * iQ * iQ;
+    o.a[0][s] = a[s];
+    o.a[1][s] = a1[s];
+    o.a[2][s] = a2[s];
+    o.b[0][s] = a[s] * beta;
+    o.b[1][s] = a1[s] * beta + a[s] * beta1;
+    o.b[2][s] = a2[s] * beta + 2.f * a1[s] * beta1 + a[s] * beta2;
+  }
+}
+
+// gradient (cells) and Hessian (cells; xx, yy, zz, xy, xz, yz) of the MLS
+// interpolant of one velocity component at a point
+__device__ void mls_grad_hess(const float* __restrict__ f, const Grid& g, const float (&tau)[3],
+                              int comp, const int (&G)[3], float kappa, float (&gr)[3],
+                              float (&hs)[6]) {
+  int c[3];
+  float tp[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float uu = tau[d] - (d == comp ? 0.f : 0.5f);
+    const float cc = floorf(uu + 0.5f);
+    tp[d] = uu - cc;
+    c[d] = G[d] + (int)cc;
+  }
+  DirW2 X, Y, Z;
+  dir_weights_d2(tp[0], kappa, X);
+  dir_weights_d2(tp[1], kappa, Y);
+  dir_weights_d2(tp[2], kappa, Z);
+  int ix[3], iy[3], iz[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    ix[s] = wrap(c[0] - 1 + s, g.n[0]);
+    iy[s] = wrap(c[1] - 1 + s, g.n[1]);
+    iz[s] = wrap(c[2] - 1 + s, g.n[2]);
+  }
+  // derivative orders of the nine needed patterns (x, y, z)
+  constexpr int OX[9] = {1, 0, 0, 2, 0, 0, 1, 1, 0};
+  constexpr int OY[9] = {0, 1, 0, 0, 2, 0, 1, 0, 1};
+  constexpr int OZ[9] = {0, 0, 1, 0, 0, 2, 0, 1, 1};
+  float acc[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) acc[p] = 0.f;
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      const float* r = f + ((size_t)iz[sz] * g.n[1] + iy[sy]) * g.n[0];
+      const float u0 = __ldg(r + ix[0]), u1 = __ldg(r + ix[1]), u2 = __ldg(r + ix[2]);
+      float XA[3], XB[3];
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        XA[o] = X.a[o][0] * u0 + X.a[o][1] * u1 + X.a[o][2] * u2;
+        XB[o] = X.b[o][0] * u0 + X.b[o][1] * u1 + X.b[o][2] * u2;
+      }
+#pragma unroll
+      for (int p = 0; p < 9; ++p) {
+        const float ay = Y.a[OY[p]][sy], by = Y.b[OY[p]][sy], az = Z.a[OZ[p]][sz], bz = Z.b[OZ[p]][sz];
+        acc[p] += (XA[OX[p]] - XB[OX[p]]) * ay * az - XA[OX[p]] * (by * az + ay * bz);
+      }
+    }
+  }
+  gr[0] = acc[0];
+  gr[1] = acc[1];
+  gr[2] = acc[2];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) hs[k] = acc[3 + k];
+}
+
+__device__ __forceinline__ float hess_at(const float (&hs)[6], int j, int k) {
+  if (j == k) return hs[j];
+  const int m = j + k;   // (0,1) -> 1, (0,2) -> 2, (1,2) -> 3
+  return hs[2 + m];
+}
+
+// force cotangent of vertex gv: dt (gv' + dt gx')/m (symplectic) or dt gv'/m
+__device__ __forceinline__ void force_cot(const DeviceTables& T, const StepConsts& sc, int V, int gv,
+                                          float inv_mass, const float* __restrict__ gxn,
+                                          const float* __restrict__ gvn, float (&o)[3]) {
+  if (T.clamp[gv]) {
+    o[0] = o[1] = o[2] = 0.f;
+    return;
+  }
+  const float s = sc.dt * inv_mass;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float gvv = __ldg(gvn + d * V + gv);
+    o[d] = sc.forward_euler ? s * gvv : s * (gvv + sc.dt * __ldg(gxn + d * V + gv));
+  }
+}
+
+__device__ __forceinline__ void cross3(const float (&a)[3], const float (&b)[3], float (&o)[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
+    DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
+    const float* __restrict__ u, const float* __restrict__ vv, const float* __restrict__ w,
+    const float* __restrict__ gxn, const float* __restrict__ gvn) {
+  __shared__ double s_red[2][kMT / 32];
+  __shared__ int s_last;
+  const int4 ch = T.chunks[blockIdx.x];
+  const BodyDev B = T.body[ch.x];
+  const TopoDev topo = T.topo[B.topo];
+  double dA = 0.0, dV = 0.0;
+  if ((int)threadIdx.x < ch.z) {
+    const int lf = __ldg(T.mface + topo.mface_off + ch.y + threadIdx.x);
+    const int gf = B.f_off + lf;
+    const int* tr = T.tri + topo.tri_off + 3 * lf;
+    const int id[3] = {B.v_off + __ldg(tr), B.v_off + __ldg(tr + 1), B.v_off + __ldg(tr + 2)};
+    float p[3][3], ga[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) p[k][d] = __ldg(x + d * V + id[k]);
+      force_cot(T, sc, V, id[k], B.inv_mass, gxn, gvn, ga[k]);
+    }
+    float e1[3], e2[3], N[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      e1[d] = p[1][d] - p[0][d];
+      e2[d] = p[2][d] - p[0][d];
+    }
+    cross3(e1, e2, N);
+    const float nn = sqrtf(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    const float area = 0.5f * nn, inv = 1.f / nn;
+    const float n[3] = {N[0] * inv, N[1] * inv, N[2] * inv};
+    // per-body sums grad A . gF and grad V . gF
+    {
+      float gVv[3], t[3];
+      const float cb[3] = {p[2][0] - p[1][0], p[2][1] - p[1][1], p[2][2] - p[1][2]};
+      const float ac[3] = {p[0][0] - p[2][0], p[0][1] - p[2][1], p[0][2] - p[2][2]};
+      const float ba[3] = {p[1][0] - p[0][0], p[1][1] - p[0][1], p[1][2] - p[0][2]};
+      float sA = 0.f, sV = 0.f;
+      cross3(n, cb, t);
+      sA += 0.5f * (t[0] * ga[0][0] + t[1] * ga[0][1] + t[2] * ga[0][2]);
+      cross3(n, ac, t);
+      sA += 0.5f * (t[0] * ga[1][0] + t[1] * ga[1][1] + t[2] * ga[1][2]);
+      cross3(n, ba, t);
+      sA += 0.5f * (t[0] * ga[2][0] + t[1] * ga[2][1] + t[2] * ga[2][2]);
+      if (B.closed) {
+        cross3(p[1], p[2], gVv);
+        sV += (gVv[0] * ga[0][0] + gVv[1] * ga[0][1] + gVv[2] * ga[0][2]) * (1.f / 6.f);
+        cross3(p[2], p[0], gVv);
+        sV += (gVv[0] * ga[1][0] + gVv[1] * ga[1][1] + gVv[2] * ga[1][2]) * (1.f / 6.f);
+        cross3(p[0], p[1], gVv);
+        sV += (gVv[0] * ga[2][0] + gVv[1] * ga[2][1] + gVv[2] * ga[2][2]) * (1.f / 6.f);
+      }
+      dA = sA;
+      dV = sV;
+    }
+    // traction cotangent: F_ext^v = sum over faces F_ext/3
+    float gF[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gF[d] = (ga[0][d] + ga[1][d] + ga[2][d]) * (1.f / 3.f);
+    const float third = 1.f / 3.f;
+    float c[3], tpp[3], tpm[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      c[d] = (p[0][d] + p[1][d] + p[2][d]) * third;
+      tpp[d] = fmaf(c[d] + sc.probe_h * n[d], g.invh[d], B.frac[d]);
+      tpm[d] = fmaf(c[d] - sc.probe_h * n[d], g.invh[d], B.frac[d]);
+    }
+    const bool two = !B.closed;
+    const float* fld[3] = {u, vv, w};
+    float G[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float gr[3], hs[6];
+      mls_grad_hess(fld[i], g, tpp, i, B.G, sc.kappa, gr, hs);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) G[i][j] = gr[j] * g.invh[j];
+      if (two) {
+        mls_grad_hess(fld[i], g, tpm, i, B.G, sc.kappa, gr, hs);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) G[i][j] -= gr[j] * g.invh[j];
+      }
+    }
+    // F = mu A (G + G^T) n
+    float Tn[3], TgF[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Tn[i] = 0.f;
+      TgF[i] = 0.f;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float Tij = G[i][j] + G[j][i];
+        Tn[i] += Tij * n[j];
+        TgF[i] += Tij * gF[j];
+      }
+    }
+    const float gArea = sc.mu * (gF[0] * Tn[0] + gF[1] * Tn[1] + gF[2] * Tn[2]);
+    float gn[3] = {sc.mu * area * TgF[0], sc.mu * area * TgF[1], sc.mu * area * TgF[2]};
+    // d/dp of G through the MLS Hessian: gp_k = sum_ij gG_ij H_ijk,
+    // gG_ij = mu A (gF_i n_j + gF_j n_i)
+    float gpp[3] = {0.f, 0.f, 0.f}, gpm[3] = {0.f, 0.f, 0.f};
+    const float s = sc.mu * area;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float gr[3], hs[6];
+      mls_grad_hess(fld[i], g, tpp, i, B.G, sc.kappa, gr, hs);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float gG = s * (gF[i] * n[j] + gF[j] * n[i]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gpp[k] += gG * hess_at(hs, j, k) * g.invh[j] * g.invh[k];
+      }
+      if (two) {
+        mls_grad_hess(fld[i], g, tpm, i, B.G, sc.kappa, gr, hs);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float gG = s * (gF[i] * n[j] + gF[j] * n[i]);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) gpm[k] -= gG * hess_at(hs, j, k) * g.invh[j] * g.invh[k];
+        }
+      }
+    }
+    // p+- = c +- h n
+    float gc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      gc[d] = gpp[d] + gpm[d];
+      gn[d] += sc.probe_h * (gpp[d] - gpm[d]);
+    }
+    // n = N/|N|, A = |N|/2
+    const float gnn = gn[0] * n[0] + gn[1] * n[1] + gn[2] * n[2];
+    float gN[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gN[d] = (gn[d] - gnn * n[d]) * inv + 0.5f * gArea * n[d];
+    // N = e1 x e2
+    float ge1[3], ge2[3];
+    cross3(e2, gN, ge1);
+    cross3(gN, e1, ge2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float gcd = gc[d] * third;
+      T.gxe[(0 * 3 + d) * (size_t)F + gf] = -ge1[d] - ge2[d] + gcd;
+      T.gxe[(1 * 3 + d) * (size_t)F + gf] = ge1[d] + gcd;
+      T.gxe[(2 * 3 + d) * (size_t)F + gf] = ge2[d] + gcd;
+    }
+  }
+  // fixed-order per-body sums of grad A . gF and grad V . gF
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dA += __shfl_down_sync(0xffffffffu, dA, o);
+    dV += __shfl_down_sync(0xffffffffu, dV, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_red[0][threadIdx.x >> 5] = dA;
+    s_red[1][threadIdx.x >> 5] = dV;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < kMT / 32; ++k) {
+      a += s_red[0][k];
+      b += s_red[1][k];
+    }
+    const int gc = B.chunk_off + ch.w;
+    T.partial2[2 * gc] = a;
+    T.partial2[2 * gc + 1] = b;
+    __threadfence();
+    s_last = (atomicAdd(T.counter2 + ch.x, 1) == B.n_chunk - 1);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    const volatile double* P = T.partial2;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < B.n_chunk; ++k) {
+      a += P[2 * (B.chunk_off + k)];
+      b += P[2 * (B.chunk_off + k) + 1];
+    }
+    T.dmeas[2 * ch.x] = a;
+    T.dmeas[2 * ch.x + 1] = b;
+    T.counter2[ch.x] = 0;
+  }
+}
+
+struct DSmem {
+  float *px, *py, *pz, *tx, *ty, *tz, *cx, *cy, *cz;
+  __device__ Vec<Dual> pos(int i) const {
+    return {Dual(px[i], tx[i]), Dual(py[i], ty[i]), Dual(pz[i], tz[i])};
+  }
+  __device__ Vec<float> cot(int i) const { return {tx[i], ty[i], tz[i]}; }
+  __device__ void put(int s, const Vec<Dual>& f) const {
+    cx[s] = f.x.d;
+    cy[s] = f.y.d;
+    cz[s] = f.z.d;
+  }
+};
+
+__device__ __forceinline__ float dotv(const Vec<float>& a, const Vec<Dual>& b) {
+  return a.x * b.x.v + a.y * b.y.v + a.z * b.z.v;
+}
+
+__global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
+    DeviceTables T, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
+    const float* __restrict__ gxn, const float* __restrict__ gvn, float* __restrict__ gx,
+    float* __restrict__ gvo, double* __restrict__ gparams) {
+  extern __shared__ float sm[];
+  __shared__ double s_red[3][kForceThreads / 32];
+  __shared__ int s_last;
+  const int2 wk = T.work[blockIdx.x];
+  const BodyDev B = T.body[wk.x];
+  const TopoDev topo = T.topo[B.topo];
+  const PatchHdr P = T.patch[topo.patch_off + wk.y];
+  DSmem S;
+  S.px = sm;
+  S.py = S.px + P.n_loc;
+  S.pz = S.py + P.n_loc;
+  S.tx = S.pz + P.n_loc;
+  S.ty = S.tx + P.n_loc;
+  S.tz = S.ty + P.n_loc;
+  S.cx = S.tz + P.n_loc;
+  S.cy = S.cx + P.n_slot;
+  S.cz = S.cy + P.n_slot;
+  for (int i = threadIdx.x; i < P.n_loc; i += blockDim.x) {
+    const int gvx = B.v_off + __ldg(T.loc_vert + P.loc_off + i);
+    S.px[i] = __ldg(x + gvx);
+    S.py[i] = __ldg(x + V + gvx);
+    S.pz[i] = __ldg(x + 2 * V + gvx);
+    float o[3];
+    force_cot(T, sc, V, gvx, B.inv_mass, gxn, gvn, o);
+    S.tx[i] = o[0];
+    S.ty[i] = o[1];
+    S.tz[i] = o[2];
+  }
+  // global-term coefficients and their derivatives along gF
+  const float2 cf = T.coef[wk.x];
+  const double dA = T.dmeas[2 * wk.x], dV = T.dmeas[2 * wk.x + 1];
+  const Dual cA(cf.x, (float)(B.kA / B.A0 * dA));
+  const Dual cV(cf.y, B.closed ? (float)(B.kv / B.V0 * dV) : 0.f);
+  double gks = 0.0, gkb = 0.0, gka = 0.0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < P.n_edge; k += blockDim.x) {
+    const PEdge r = T.pedge[P.edge_off + k];
+    const int ge = B.e_off + (r.eid & 0x7fffffff);
+    const bool hinge = r.l[3] != kNone;
+    const Vec<Dual> pa = S.pos(r.l[0]), pb = S.pos(r.l[1]);
+    const Vec<Dual> pc = hinge ? S.pos(r.l[2]) : pa, pd = hinge ? S.pos(r.l[3]) : pb;
+    const float2 cs0 = hinge ? __ldg(T.cs0 + ge) : make_float2(1.f, 0.f);
+    Vec<Dual> fa, fb, fc, fd, us[2], ub[4];
+    float es, eb;
+    edge_forces(pa, pb, pc, pd, hinge, __ldg(T.l0 + ge), cs0.x, cs0.y, B.ks, B.kb, fa, fb, fc, fd,
+                us, ub, es, eb);
+    S.put(k, fa);
+    S.put(P.n_edge + k, fb);
+    S.put(2 * P.n_edge + k, fc);
+    S.put(3 * P.n_edge + k, fd);
+    if (r.eid < 0) {   // owned edge: constants' cotangents
+      const Vec<float> ca = S.cot(r.l[0]), cb = S.cot(r.l[1]);
+      gks += dotv(ca, us[0]) + dotv(cb, us[1]);
+      if (hinge) {
+        const Vec<float> cc = S.cot(r.l[2]), cd = S.cot(r.l[3]);
+        gkb += dotv(ca, ub[0]) + dotv(cb, ub[1]) + dotv(cc, ub[2]) + dotv(cd, ub[3]);
+      }
+    }
+  }
+  const int fbase = 4 * P.n_edge;
+  for (int k = threadIdx.x; k < P.n_face; k += blockDim.x) {
+    const PFace r = T.pface[P.face_off + k];
+    Vec<Dual> f[3], gA[3], gV[3], ua[3];
+    float ea;
+    face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid), B.ka,
+                cA, cV, f, gA, gV, ua, ea);
+    S.put(fbase + k, f[0]);
+    S.put(fbase + P.n_face + k, f[1]);
+    S.put(fbase + 2 * P.n_face + k, f[2]);
+    if (r.owned)
+      gka += dotv(S.cot(r.l[0]), ua[0]) + dotv(S.cot(r.l[1]), ua[1]) + dotv(S.cot(r.l[2]), ua[2]);
+  }
+  __syncthreads();
+  const int* tri = T.tri + topo.tri_off;
+  for (int i = threadIdx.x; i < P.n_own; i += blockDim.x) {
+    const int s0 = __ldg(T.csr_ptr + P.csr_off + i), s1 = __ldg(T.csr_ptr + P.csr_off + i + 1);
+    float jx = 0.f, jy = 0.f, jz = 0.f;
+    for (int k = s0; k < s1; ++k) {
+      const int s = T.csr_slot[P.slot_off + k];
+      jx += S.cx[s];
+      jy += S.cy[s];
+      jz += S.cz[s];
+    }
+    const int lv = P.own0 + i;
+    const int gvx = B.v_off + lv;
+    // traction part: the cotangents the faces left for this corner
+    const int* vp = T.v2f_ptr + topo.v2f_ptr_off;
+    const int q0 = __ldg(vp + lv), q1 = __ldg(vp + lv + 1);
+    for (int q = q0; q < q1; ++q) {
+      const int lf = __ldg(T.v2f_idx + topo.v2f_idx_off + q);
+      const int corner = (__ldg(tri + 3 * lf) == lv) ? 0 : ((__ldg(tri + 3 * lf + 1) == lv) ? 1 : 2);
+      const size_t gf = (size_t)B.f_off + lf;
+      jx += __ldg(T.gxe + (corner * 3 + 0) * (size_t)F + gf);
+      jy += __ldg(T.gxe + (corner * 3 + 1) * (size_t)F + gf);
+      jz += __ldg(T.gxe + (corner * 3 + 2) * (size_t)F + gf);
+    }
+    const bool cl = T.clamp[gvx] != 0;
+    const float gx0 = __ldg(gxn + gvx), gx1 = __ldg(gxn + V + gvx), gx2 = __ldg(gxn + 2 * V + gvx);
+    gx[gvx] = gx0 + jx;
+    gx[V + gvx] = gx1 + jy;
+    gx[2 * V + gvx] = gx2 + jz;
+    gvo[gvx] = cl ? 0.f : __ldg(gvn + gvx) + sc.dt * gx0;
+    gvo[V + gvx] = cl ? 0.f : __ldg(gvn + V + gvx) + sc.dt * gx1;
+    gvo[2 * V + gvx] = cl ? 0.f : __ldg(gvn + 2 * V + gvx) + sc.dt * gx2;
+  }
+  // constants' cotangents: fixed-order per-patch sums, then per body
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gks += __shfl_down_sync(0xffffffffu, gks, o);
+    gkb += __shfl_down_sync(0xffffffffu, gkb, o);
+    gka += __shfl_down_sync(0xffffffffu, gka, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_red[0][threadIdx.x >> 5] = gks;
+    s_red[1][threadIdx.x >> 5] = gkb;
+    s_red[2][threadIdx.x >> 5] = gka;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < kForceThreads / 32; ++k) {
+      a += s_red[0][k];
+      b += s_red[1][k];
+      c += s_red[2][k];
+    }
+    T.wpart[3 * (size_t)blockIdx.x] = a;
+    T.wpart[3 * (size_t)blockIdx.x + 1] = b;
+    T.wpart[3 * (size_t)blockIdx.x + 2] = c;
+    __threadfence();
+    s_last = (atomicAdd(T.wcounter + wk.x, 1) == topo.n_patch - 1);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    const volatile double* W = T.wpart;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < topo.n_patch; ++k) {
+      a += W[3 * (size_t)(B.work_off + k)];
+      b += W[3 * (size_t)(B.work_off + k) + 1];
+      c += W[3 * (size_t)(B.work_off + k) + 2];
+    }
+    const double Ab = T.meas[2 * wk.x], Vb = T.meas[2 * wk.x + 1];
+    gparams[5 * wk.x + 0] = a;
+    gparams[5 * wk.x + 1] = b;
+    gparams[5 * wk.x + 2] = c;
+    gparams[5 * wk.x + 3] = -(Ab - B.A0) / B.A0 * dA;
+    gparams[5 * wk.x + 4] = B.closed ? -(Vb - B.V0) / B.V0 * dV : 0.0;
+    T.wcounter[wk.x] = 0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
+                            const float* w, const float* gx_next, const float* gv_next, float* gx,
+                            float* gv, double* gparams) {
+  if (c->n_chunks == 0) return cudaSuccess;
+  // area, volume and the global-term coefficients at x
+  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
+  if (e != cudaSuccess) return e;
+  ext_adjoint_kernel<<<c->n_chunks, kMT, 0, c->stream>>>(c->d, c->grid, c->sc, (int32_t)c->V,
+                                                         (int32_t)c->F, x, u, vv, w, gx_next,
+                                                         gv_next);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  force_adjoint_kernel<<<c->n_work, kForceThreads, c->adjoint_smem, c->stream>>>(
+      c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, gx_next, gv_next, gx, gv, gparams);
+  return cudaGetLastError();
+}
+
+cudaError_t set_adjoint_smem_limit(size_t bytes) {
+  return cudaFuncSetAttribute(force_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes);
+}
+
+}  // namespace ibm

@@ -24,25 +24,16 @@
 //   F = -(k_A (A - A0)/A0 + k_a (A_f - A0_f)/A0_f) grad A_f - k_v (V - V0)/V0 grad V.
 #include <cuda_runtime.h>
 
+#include "force_elems.cuh"
 #include "ibm_internal.cuh"
 
 namespace ibm {
 namespace {
 
-struct V3 {
-  float x, y, z;
-};
-__device__ __forceinline__ V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ V3 cross(V3 a, V3 b) {
-  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
-}
-__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ V3 scale(V3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
-
 struct Smem {
   float *px, *py, *pz, *cx, *cy, *cz;
-  __device__ V3 pos(int i) const { return {px[i], py[i], pz[i]}; }
-  __device__ void put(int s, V3 f) const {
+  __device__ Vec<float> pos(int i) const { return {px[i], py[i], pz[i]}; }
+  __device__ void put(int s, const Vec<float>& f) const {
     cx[s] = f.x;
     cy[s] = f.y;
     cz[s] = f.z;
@@ -79,7 +70,6 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     S.py[i] = __ldg(x + V + gv);
     S.pz[i] = __ldg(x + 2 * V + gv);
   }
-  // per-body global terms from the float64 area / volume sums
   // per-body global-term coefficients, formed once per body from the float64
   // area / volume sums by the marker kernel
   const float2 cf = T.coef[wk.x];
@@ -92,41 +82,17 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
   for (int k = threadIdx.x; k < P.n_edge; k += blockDim.x) {
     const PEdge r = T.pedge[P.edge_off + k];
     const int ge = B.e_off + (r.eid & 0x7fffffff);
-    const V3 pa = S.pos(r.l[0]), pb = S.pos(r.l[1]);
-    const V3 e = sub(pb, pa);
-    const float l2 = dot(e, e);
-    const float inv_l = rsqrtf(l2);
-    const float l = l2 * inv_l;
-    const float l0 = __ldg(T.l0 + ge);
-    const float s = B.ks * (l - l0) * inv_l;
-    V3 fa = scale(e, s), fb = scale(e, -s), fc = {0.f, 0.f, 0.f}, fd = {0.f, 0.f, 0.f};
-    if (want_e && (r.eid < 0)) eS += 0.5 * (double)B.ks * (double)(l - l0) * (double)(l - l0);
-    if (r.l[3] != kNone) {
-      const V3 pc = S.pos(r.l[2]), pd = S.pos(r.l[3]);
-      const V3 ac = sub(pc, pa), ad = sub(pd, pa);
-      const V3 N1 = cross(e, ac);
-      const V3 N2 = cross(sub(pd, pb), e);
-      const float q1 = dot(N1, N1), q2 = dot(N2, N2);
-      const float r1 = rsqrtf(q1), r2 = rsqrtf(q2);
-      const V3 n1 = scale(N1, r1), n2 = scale(N2, r2);
-      const float cth = dot(n1, n2);
-      const float sth = dot(cross(n1, n2), e) * inv_l;
-      const float2 cs0 = __ldg(T.cs0 + ge);
-      const float sdiff = sth * cs0.x - cth * cs0.y;  // sin(theta - theta0)
-      const float coef = -B.kb * sdiff;               // F = coef * grad theta
-      const V3 gc = scale(N1, -l * r1 * r1);
-      const V3 gd = scale(N2, -l * r2 * r2);
-      const float inv_l2 = inv_l * inv_l;
-      const float sc_ = dot(ac, e) * inv_l2, sd_ = dot(ad, e) * inv_l2;
-      const V3 ga = {-(1.f - sc_) * gc.x - (1.f - sd_) * gd.x, -(1.f - sc_) * gc.y - (1.f - sd_) * gd.y,
-                     -(1.f - sc_) * gc.z - (1.f - sd_) * gd.z};
-      const V3 gb = {-sc_ * gc.x - sd_ * gd.x, -sc_ * gc.y - sd_ * gd.y, -sc_ * gc.z - sd_ * gd.z};
-      fa = {fa.x + coef * ga.x, fa.y + coef * ga.y, fa.z + coef * ga.z};
-      fb = {fb.x + coef * gb.x, fb.y + coef * gb.y, fb.z + coef * gb.z};
-      fc = scale(gc, coef);
-      fd = scale(gd, coef);
-      if (want_e && (r.eid < 0))
-        eB += (double)B.kb * (1.0 - ((double)cth * cs0.x + (double)sth * cs0.y));
+    const bool hinge = r.l[3] != kNone;
+    const Vec<float> pa = S.pos(r.l[0]), pb = S.pos(r.l[1]);
+    const Vec<float> pc = hinge ? S.pos(r.l[2]) : pa, pd = hinge ? S.pos(r.l[3]) : pb;
+    const float2 cs0 = hinge ? __ldg(T.cs0 + ge) : make_float2(1.f, 0.f);
+    Vec<float> fa, fb, fc, fd, us[2], ub[4];
+    float es, eb;
+    edge_forces(pa, pb, pc, pd, hinge, __ldg(T.l0 + ge), cs0.x, cs0.y, B.ks, B.kb, fa, fb, fc, fd,
+                us, ub, es, eb);
+    if (want_e && (r.eid < 0)) {
+      eS += (double)es;
+      eB += (double)eb;
     }
     // slot layout [role][element]: consecutive threads hit consecutive banks
     S.put(k, fa);
@@ -138,22 +104,14 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
   const int fbase = 4 * P.n_edge;
   for (int k = threadIdx.x; k < P.n_face; k += blockDim.x) {
     const PFace r = T.pface[P.face_off + k];
-    const V3 pa = S.pos(r.l[0]), pb = S.pos(r.l[1]), pc = S.pos(r.l[2]);
-    const V3 N = cross(sub(pb, pa), sub(pc, pa));
-    const float q = dot(N, N);
-    const float rn = rsqrtf(q);
-    const float Af = 0.5f * q * rn;
-    const float A0f = __ldg(T.A0f + B.f_off + r.fid);
-    const float gA = cA + B.ka * (Af - A0f) / A0f;
-    const V3 n = scale(N, rn);
-    const float hA = -0.5f * gA, hV = -cV * (1.f / 6.f);
-    const V3 ga = cross(n, sub(pc, pb)), gb = cross(n, sub(pa, pc)), gcc = cross(n, sub(pb, pa));
-    const V3 va = cross(pb, pc), vb = cross(pc, pa), vc = cross(pa, pb);
-    S.put(fbase + k, {hA * ga.x + hV * va.x, hA * ga.y + hV * va.y, hA * ga.z + hV * va.z});
-    S.put(fbase + P.n_face + k, {hA * gb.x + hV * vb.x, hA * gb.y + hV * vb.y, hA * gb.z + hV * vb.z});
-    S.put(fbase + 2 * P.n_face + k,
-          {hA * gcc.x + hV * vc.x, hA * gcc.y + hV * vc.y, hA * gcc.z + hV * vc.z});
-    if (want_e && r.owned) eA += 0.5 * (double)B.ka * (double)(Af - A0f) * (double)(Af - A0f) / A0f;
+    Vec<float> f[3], gA[3], gV[3], ua[3];
+    float ea;
+    face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid), B.ka,
+                cA, cV, f, gA, gV, ua, ea);
+    S.put(fbase + k, f[0]);
+    S.put(fbase + P.n_face + k, f[1]);
+    S.put(fbase + 2 * P.n_face + k, f[2]);
+    if (want_e && r.owned) eA += (double)ea;
   }
   __syncthreads();
 

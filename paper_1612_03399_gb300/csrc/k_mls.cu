@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   float* vbox = reinterpret_cast<float*>(dyn + kRowTableBytes);
   __shared__ int s_lo[3], s_hi[3];
   __shared__ double s_red[2][kMT / 32];
-  __shared__ int s_last, s_fit, s_N;
+  __shared__ int s_last, s_N;
   __shared__ int s_warp[kMT / 32];
 
   const int4 ch = T.chunks[blockIdx.x];  // body, face-list offset, count, chunk index in body
