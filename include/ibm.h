@@ -189,6 +189,20 @@ ibm_status ibm_backward(ibm_ctx* ctx, const float* x, const float* u, const floa
                         const float* w, const float* gx_next, const float* gv_next, float* gx,
                         float* gv, double* gparams);
 
+/* Taylor deformation D = (L - B)/(L + B) of every closed body (Sec. 3.1's
+ * semi-axes L, B of a deformed drop), taken from the ellipsoid with the same
+ * volume second moments: semi-axes sqrt(5 lambda_i) of the second-moment
+ * tensor about the centroid, summed over signed tetrahedra in float64 in a
+ * fixed order.  D [B] float64 (0 for open bodies). */
+ibm_status ibm_taylor_deformation(ibm_ctx* ctx, const float* x, double* D);
+
+/* Adjoint of ibm_taylor_deformation at x: given gD [B] float64, writes
+ * gx [3][V] = d(sum_b gD_b D_b)/dx (overwritten, zero on open bodies) and D
+ * [B] (recomputed at x).  Bodies whose largest and smallest eigenvalues
+ * coincide (a sphere) have no derivative and get gx = 0. */
+ibm_status ibm_taylor_backward(ibm_ctx* ctx, const float* x, const double* gD, float* gx,
+                               double* D);
+
 /* Synchronise the stream and report the device error word (IBM_ERR_DEVICE if
  * a kernel flagged an out-of-range or non-finite value). */
 ibm_status ibm_check_device_error(ibm_ctx* ctx);

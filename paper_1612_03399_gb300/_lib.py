@@ -67,6 +67,8 @@ SIGNATURES = {
     "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
     "ibm_get_counters": (C.c_int, [P, C.POINTER(C.c_int64)]),
     "ibm_backward": (C.c_int, [P, P, P, P, P, P, P, P, P, P]),
+    "ibm_taylor_deformation": (C.c_int, [P, P, P]),
+    "ibm_taylor_backward": (C.c_int, [P, P, P, P, P]),
     "ibm_body_measures_noalloc": (C.c_int, [P, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]),
 }
 
@@ -243,6 +245,22 @@ class Context:
                                           _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv),
                                           _ptr(gp)))
         return gx, gv, gp
+
+    def taylor(self, x):
+        """Taylor deformation D [B] (float64) of every closed body at x."""
+        import torch
+        D = torch.empty(self.B, dtype=torch.float64, device=self.device)
+        self._check(self.lib.ibm_taylor_deformation(self.h, _ptr(x), _ptr(D)))
+        return D
+
+    def taylor_backward(self, x, gD):
+        """gx = d(sum gD D)/dx at x, and D."""
+        import torch
+        gD = gD.to(device=self.device, dtype=torch.float64).contiguous()
+        gx = self._vec(self.V)
+        D = torch.empty(self.B, dtype=torch.float64, device=self.device)
+        self._check(self.lib.ibm_taylor_backward(self.h, _ptr(x), _ptr(gD), _ptr(gx), _ptr(D)))
+        return gx, D
 
     def check_device_error(self):
         self._check(self.lib.ibm_check_device_error(self.h))

@@ -641,6 +641,9 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.gxe = zeros<float>(c, 9 * (size_t)F);
     d.wpart = zeros<double>(c, 3 * (size_t)c->n_work);
     d.wcounter = zeros<int32_t>(c, (size_t)n_bodies);
+    d.tpart = zeros<double>(c, 10 * (size_t)c->n_chunks);
+    d.taylor = zeros<double>(c, 24 * (size_t)n_bodies);
+    d.tgrad = zeros<double>(c, 10 * (size_t)n_bodies);
     check_cuda(cudaDeviceSynchronize(), "create");
     *out = c;
     return IBM_OK;
@@ -865,6 +868,21 @@ extern "C" ibm_status ibm_backward(ibm_ctx* c, const float* x, const float* u, c
   cudaSetDevice(c->device);
   return cuda_status(c, launch_backward(c, x, u, vv, w, gx_next, gv_next, gx, gv, gparams),
                      "ibm_backward");
+}
+
+extern "C" ibm_status ibm_taylor_deformation(ibm_ctx* c, const float* x, double* D) {
+  if (!c || !x || !D) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  cudaSetDevice(c->device);
+  return cuda_status(c, launch_taylor(c, x, D), "ibm_taylor_deformation");
+}
+
+extern "C" ibm_status ibm_taylor_backward(ibm_ctx* c, const float* x, const double* gD, float* gx,
+                                          double* D) {
+  if (!c || !x || !gD || !gx || !D) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  cudaSetDevice(c->device);
+  cudaError_t e = launch_taylor(c, x, D);
+  if (e == cudaSuccess) e = launch_taylor_backward(c, x, gD, gx);
+  return cuda_status(c, e, "ibm_taylor_backward");
 }
 
 extern "C" ibm_status ibm_check_device_error(ibm_ctx* c) {

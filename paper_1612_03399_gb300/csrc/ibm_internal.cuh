@@ -121,6 +121,9 @@ struct DeviceTables {
   float* gxe = nullptr;         // [9][F] per-face position cotangents (3 corners x 3)
   double* wpart = nullptr;      // [n_work][3] per-patch (g k_s, g k_b, g k_a)
   int32_t* wcounter = nullptr;  // [B]
+  double* tpart = nullptr;      // [n_chunks][10] per-chunk volume moments
+  double* taylor = nullptr;     // [B][24] moments, eigenvalues, extreme eigenvectors, gap
+  double* tgrad = nullptr;      // [B][10] cotangents of the moments
   int32_t* err = nullptr;       // device error word
 };
 
@@ -170,6 +173,8 @@ cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const flo
 cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
                             const float* w, const float* gx_next, const float* gv_next, float* gx,
                             float* gv, double* gparams);
+cudaError_t launch_taylor(ibm_ctx* c, const float* x, double* D);
+cudaError_t launch_taylor_backward(ibm_ctx* c, const float* x, const double* gD, float* gx);
 cudaError_t set_force_smem_limit(size_t bytes);
 cudaError_t set_adjoint_smem_limit(size_t bytes);
 cudaError_t set_marker_smem_limit();

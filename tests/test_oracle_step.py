@@ -170,3 +170,37 @@ def test_step_gradient_flows_to_constants():
         bb, _ = small_drop(level=1, n=16, r=0.2, ks=1.0 + s * h)
         vals.append(float(((O.step([bb], [x0], [v0], f, prm, with_spread=False)["x_next"][0] - x0) * w).sum()))
     assert float(g) == pytest.approx((vals[0] - vals[1]) / (2 * h), rel=1e-9)
+
+
+def test_rollout_loss_gradient_vs_central_differences():
+    """Reverse mode of the oracle through several steps and the Taylor
+    deformation equals central differences (h = 1e-4 relative) of the same
+    float64 loss in k_s and k_b: the FP64 reference the GPU adjoint is held to."""
+    v, t = W.icosphere(1)
+    c = np.array([0.5, 0.45, 0.5])
+    rest = c + 0.15 * v * np.array([1.1, 1.0, 0.95])
+    f = fields_of({"kind": "shear"}, 16)
+    prm = O.Params((16, 16, 16), dt=5e-3)
+
+    def loss_of(ks, kb, grad=False):
+        b = O.Body(rest, t, c, ks=1.0, kb=0.02, mass=1e-3)
+        b.ks = torch.tensor(ks, dtype=DT, requires_grad=grad)
+        b.kb = torch.tensor(kb, dtype=DT, requires_grad=grad)
+        x, vv = [b.rest.clone()], [torch.zeros_like(b.rest)]
+        for _ in range(4):
+            out = O.step([b], x, vv, f, prm, create_graph=grad, with_spread=False)
+            x, vv = out["x_next"], out["v_next"]
+        L = (O.taylor_deformation(x[0], b.tri, b.origin) - 0.02) ** 2
+        if grad:
+            return torch.autograd.grad(L, [b.ks, b.kb])
+        return float(L)
+
+    g_ks, g_kb = loss_of(1.0, 0.02, grad=True)
+    for val, g, which in ((1.0, g_ks, 0), (0.02, g_kb, 1)):
+        h = 1e-4 * val
+        args_p = [1.0, 0.02]
+        args_m = [1.0, 0.02]
+        args_p[which] += h
+        args_m[which] -= h
+        fd = (loss_of(*args_p) - loss_of(*args_m)) / (2 * h)
+        assert float(g) == pytest.approx(fd, rel=1e-4)
