@@ -107,10 +107,12 @@ def test_rollout_gradients_match_oracle_and_differences(record_error):
         record_error(f"g_x0[{i}]", H.rel_l2(ggx[i], ogx[i]))
         assert H.rel_l2(ggx[i], ogx[i]) <= 1e-4
     # central difference of the GPU loss along k_s -> k_s (1 + eps) for every
-    # body: the float32 forward limits this check to a large step and a loose
-    # bar (the 1e-4 bar against differences is met in float64 by the oracle,
-    # whose reverse mode the GPU adjoint matches above)
-    eps = 5e-2
+    # body.  Float32 positions make D uncertain by ~1e-7, so the loss change
+    # must be large: the loss is linear in this direction to 3e-6 over
+    # eps = 0.5 (checked in float64 with the oracle), and the bar is loose.
+    # The 1e-4 bar against differences is met in float64 by the oracle, whose
+    # reverse mode the GPU adjoint matches above.
+    eps = 0.5
     vals = []
     for s in (1.0, -1.0):
         kk = k.detach().clone()
