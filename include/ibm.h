@@ -203,6 +203,20 @@ ibm_status ibm_taylor_deformation(ibm_ctx* ctx, const float* x, double* D);
 ibm_status ibm_taylor_backward(ibm_ctx* ctx, const float* x, const double* gD, float* gx,
                                double* D);
 
+/* A CUDA graph of n_steps consecutive ibm_step calls (n_steps even, >= 2)
+ * with the footprint clear: steps alternate (xa, va) -> (xb, vb) and back,
+ * so after a launch the state is again in (xa, va).  The buffers and fields
+ * are bound at creation; ibm_graph_launch replays the whole sequence on the
+ * context's stream with one launch.  Creation captures on a private stream
+ * after the work already queued on the context's stream.  The context must
+ * outlive the graph. */
+typedef struct ibm_graph ibm_graph;
+ibm_status ibm_graph_create(ibm_ctx* ctx, float* xa, float* va, float* xb, float* vb,
+                            const float* u, const float* vv, const float* w, float* fx, float* fy,
+                            float* fz, int32_t n_steps, ibm_graph** out);
+ibm_status ibm_graph_launch(ibm_graph* graph);
+void ibm_graph_destroy(ibm_graph* graph);
+
 /* Synchronise the stream and report the device error word (IBM_ERR_DEVICE if
  * a kernel flagged an out-of-range or non-finite value). */
 ibm_status ibm_check_device_error(ibm_ctx* ctx);

@@ -67,6 +67,9 @@ SIGNATURES = {
     "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
     "ibm_get_counters": (C.c_int, [P, C.POINTER(C.c_int64)]),
     "ibm_backward": (C.c_int, [P, P, P, P, P, P, P, P, P, P]),
+    "ibm_graph_create": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, C.c_int32, C.POINTER(P)]),
+    "ibm_graph_launch": (C.c_int, [P]),
+    "ibm_graph_destroy": (None, [P]),
     "ibm_taylor_deformation": (C.c_int, [P, P, P]),
     "ibm_taylor_backward": (C.c_int, [P, P, P, P, P]),
     "ibm_body_measures_noalloc": (C.c_int, [P, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]),
@@ -246,6 +249,10 @@ class Context:
                                           _ptr(gp)))
         return gx, gv, gp
 
+    def graph(self, xa, va, xb, vb, fields, f, n_steps=2):
+        """A StepGraph replaying n_steps ping-pong steps with one launch."""
+        return StepGraph(self, xa, va, xb, vb, fields, f, n_steps)
+
     def taylor(self, x):
         """Taylor deformation D [B] (float64) of every closed body at x."""
         import torch
@@ -278,3 +285,33 @@ class Context:
         ms = (C.c_float * 3)()
         self._check(self.lib.ibm_get_phase_times(self.h, ms))
         return tuple(float(m) for m in ms)
+
+
+class StepGraph:
+    """ibm_graph_create / ibm_graph_launch: n_steps captured steps."""
+
+    def __init__(self, ctx, xa, va, xb, vb, fields, f, n_steps=2):
+        self.ctx = ctx
+        self._keep = (xa, va, xb, vb, fields, f)
+        u, vv, w = fields
+        fx, fy, fz = f
+        h = C.c_void_p()
+        ctx._check(ctx.lib.ibm_graph_create(ctx.h, _ptr(xa), _ptr(va), _ptr(xb), _ptr(vb), _ptr(u),
+                                            _ptr(vv), _ptr(w), _ptr(fx), _ptr(fy), _ptr(fz),
+                                            int(n_steps), C.byref(h)))
+        self.h = h
+        self.n_steps = n_steps
+
+    def launch(self):
+        self.ctx._check(self.ctx.lib.ibm_graph_launch(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.ibm_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

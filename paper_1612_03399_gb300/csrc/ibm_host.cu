@@ -809,7 +809,10 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[k], c->stream);
   };
   mark(0);
-  if (clear && c->have_prev) e = launch_clear(c, fx, fy, fz);
+  // the clear is a no-op for blocks that recorded no footprint (first step),
+  // so it is launched unconditionally: a captured step then clears whatever
+  // step ran before it
+  if (clear) e = launch_clear(c, fx, fy, fz);
   mark(1);
   if (e == cudaSuccess)
     e = launch_mls(c, x, v, u, vv, w, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz, true, true,
@@ -823,6 +826,87 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     c->timed = c->timing;
   }
   return cuda_status(c, e, "ibm_step");
+}
+
+struct ibm_graph {
+  ibm_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" ibm_status ibm_graph_create(ibm_ctx* c, float* xa, float* va, float* xb, float* vb,
+                                       const float* u, const float* vv, const float* w,
+                                       float* fx, float* fy, float* fz, int32_t n_steps,
+                                       ibm_graph** out) {
+  if (out) *out = nullptr;
+  if (!c || !xa || !va || !xb || !vb || !u || !vv || !w || !fx || !fy || !fz || !out)
+    return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (n_steps < 2 || (n_steps & 1))
+    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_graph_create: n_steps must be even and >= 2");
+  cudaSetDevice(c->device);
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_status(c, e, "cudaStreamCreate");
+  // order the capture after work already queued on the context's stream
+  cudaEvent_t ready = nullptr;
+  e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ready, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ready, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cap);
+  if (ready) cudaEventDestroy(ready);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    return cuda_status(c, e, "ibm_graph_create");
+  }
+  const cudaStream_t saved = c->stream;
+  const bool timing = c->timing;
+  c->stream = cap;
+  c->timing = false;
+  ibm_graph* g = new ibm_graph();
+  g->ctx = c;
+  ibm_status st = IBM_OK;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < n_steps && st == IBM_OK; ++k) {
+      const bool even = (k & 1) == 0;
+      st = ibm_step(c, even ? xa : xb, even ? va : vb, u, vv, w, even ? xb : xa, even ? vb : va,
+                    fx, fy, fz, IBM_STEP_CLEAR_PREV);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (e2 == cudaSuccess && st == IBM_OK) {
+      g->graph = graph;
+      e = cudaGraphInstantiate(&g->exec, graph, 0);
+    } else {
+      if (graph) cudaGraphDestroy(graph);
+      e = e2;
+    }
+  }
+  c->stream = saved;
+  c->timing = timing;
+  cudaStreamDestroy(cap);
+  if (st != IBM_OK || e != cudaSuccess) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return st != IBM_OK ? st : cuda_status(c, e, "ibm_graph_create");
+  }
+  *out = g;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_graph_launch(ibm_graph* g) {
+  if (!g || !g->exec) return IBM_ERR_INVALID_ARG;
+  cudaSetDevice(g->ctx->device);
+  return cuda_status(g->ctx, cudaGraphLaunch(g->exec, g->ctx->stream), "ibm_graph_launch");
+}
+
+extern "C" void ibm_graph_destroy(ibm_graph* g) {
+  if (!g) return;
+  cudaSetDevice(g->ctx->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
 }
 
 extern "C" ibm_status ibm_set_phase_timing(ibm_ctx* c, int32_t on) {
