@@ -112,7 +112,8 @@ struct DeviceTables {
                                 // (x, y, z lo, kind: 0 rows, 1 whole box, 2 rows in float4
                                 // groups), (x, y, z size, rows)
   int2* rowmap = nullptr;       // [n_chunks][kMaxRows] (global offset of the (y, z) row,
-                                //  first x wrapped | length << 16) of each footprint row
+                                //  first x wrapped | length << 16): the x-range of each
+                                //  footprint row that received a nonzero spread
   int32_t* stats = nullptr;     // [4] counters: marker blocks that did not fit shared memory
   // adjoint scratch
   double* partial2 = nullptr;   // [n_chunks][2] per-chunk (grad A . g, grad V . g)
@@ -127,12 +128,14 @@ struct DeviceTables {
   int32_t* err = nullptr;       // device error word
 };
 
-// marker-kernel dynamic shared memory: row tables, then the staged rows of
-// one velocity and one force component
+// marker-kernel dynamic shared memory: row tables (7 int arrays of kMaxRows,
+// one row id per staged float4 group), then two staging buffers of kMaxNodes
+// words (velocity components, double-buffered; then the fixed-point spread
+// accumulators of one force component)
 constexpr int kMaxRows = 1024;                                     // (y, z) rows per patch
-constexpr int kMaxNodes = 8960;                                    // staged nodes per component
-constexpr int kRowTableBytes = ((4 * (5 * kMaxRows + 1) + 2 * kMaxNodes) + 15) / 16 * 16;
-constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes + 16;
+constexpr int kMaxNodes = 8960;                                    // staged nodes per buffer
+constexpr int kRowTableBytes = ((4 * (7 * kMaxRows + 1) + 2 * (kMaxNodes / 4)) + 15) / 16 * 16;
+constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes;
 
 }  // namespace ibm
 

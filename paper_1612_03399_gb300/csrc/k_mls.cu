@@ -6,13 +6,16 @@
 // recursive coordinate bisection of the rest mesh), one thread per face.
 // The block builds a ROW MAP of its grid footprint: for every (y, z) row of
 // the nodes its 3x3x3 supports (centroids and probe ends) touch, the x-range
-// touched, padded to whole float4 groups.  One velocity component at a time,
-// the block stages those rows in shared memory (float4 loads), interpolates
-// and differentiates from shared memory, accumulates its spread
-// contributions on the same rows with shared atomics and flushes them with
-// float4 global atomics; the row map is recorded so the next step's clear
-// zeroes exactly those rows.  A patch whose footprint does not fit takes the
-// direct global path (scalar loads and atomics) and records its bounding box.
+// touched, padded to whole groups of 4 nodes (float4-aligned when the grid
+// allows).  The velocity components are staged in shared memory with
+// asynchronous copies, two buffers in flight, and interpolated and
+// differentiated from there.  The spread then accumulates one force component
+// at a time in exact fixed point (32-bit shared atomics on two words, a
+// power-of-two scale per block and component) and flushes it with float4
+// global atomics; the rows that received a nonzero spread are recorded so the
+// next step's clear zeroes exactly those.  A patch whose footprint does not
+// fit takes the direct global path (scalar loads and float atomics) and
+// records its bounding box.
 //
 // MLS with the linear basis and a weight that factorises over directions
 // (W = prod_d exp(-kappa delta_d^2), delta in cells) has an exact closed-form
@@ -227,15 +230,149 @@ __device__ __forceinline__ void grad_at(const float* f, const Acc& A, const floa
   mls_grad(f, A, X, Y, Z, gr);
 }
 
-// global offset of staged group (or node) q: its row's base plus the wrapped x
-__device__ __forceinline__ size_t row_node(int q, int gsz, const unsigned short* grow,
-                                           const int* off, const int* base, const int* x0w,
-                                           int nx) {
-  const int r = grow[q];
-  int xg = x0w[r] + (gsz * q - off[r]);
-  if (xg >= nx) xg -= nx;
-  return (size_t)base[r] + xg;
+// x >= 0 folded into [0, n)
+__device__ __forceinline__ int wrap_pos(int x, int n) {
+  if (x >= n) {
+    x -= n;
+    if (x >= n) x %= n;
+  }
+  return x;
 }
+
+// asynchronous global -> shared copies (cp.async: no register round trip, so
+// one thread's copies are all in flight at once)
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// the staged rows of the block, one float4 group (4 consecutive staged nodes
+// of one row) per entry of s_grow
+struct RowTable {
+  const unsigned short* grow;  // row of each group
+  const int* off;              // staged start of each row (a multiple of 4)
+  const int* base;             // global offset of the row's (y, z)
+  const int* x0w;              // first x of the row, wrapped into [0, nx)
+  int nx, vec4;
+  // global offset of node j (0..3) of group q
+  __device__ __forceinline__ size_t node(int q, int j) const {
+    const int r = grow[q];
+    return (size_t)base[r] + wrap_pos(x0w[r] + (4 * q - off[r]) + j, nx);
+  }
+};
+
+// issue the copies of one field component's staged rows into dst
+__device__ __forceinline__ void stage_async(float* dst, const float* __restrict__ src,
+                                            const RowTable& R, int ngroups) {
+  for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
+    if (R.vec4) {
+      cp_async16(dst + 4 * q, src + R.node(q, 0));   // x multiple of 4 and nx % 4 == 0
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cp_async4(dst + 4 * q + j, src + R.node(q, j));
+    }
+  }
+}
+
+// addressing factories: staged rows or the global field
+struct StagedRows {
+  const int* off_minus_x0;
+  int ylo, zlo, sy;
+  __device__ RowAcc at(const int (&c)[3]) const {
+    RowAcc A;
+    A.init(c, off_minus_x0, ylo, zlo, sy);
+    return A;
+  }
+};
+struct GlobalRows {
+  Grid g;
+  __device__ GlobalAcc at(const int (&c)[3]) const {
+    GlobalAcc A;
+    A.init(c, g);
+    return A;
+  }
+};
+
+// interpolated value at the centroid and full-derivative gradient (per unit
+// length) at the probe point(s) of one velocity component
+template <bool INTERP, bool PROBE, class Rows>
+__device__ __forceinline__ void velocity_component(const float* f, const Rows& R, int comp,
+                                                   const int (&G)[3], const float (&tc)[3],
+                                                   const float (&tp)[3], const float (&tm)[3],
+                                                   bool two, float kappa, const float (&invh)[3],
+                                                   float& Ul, float (&gr)[3]) {
+  if (INTERP) {
+    int cc[3];
+    float t3[3];
+    locate(tc, comp, G, cc, t3);
+    DirW X, Y, Z;
+    dir3(t3, kappa, X, Y, Z);
+    Ul = mls_value(f, R.at(cc), X, Y, Z);
+  }
+  if (PROBE) {
+    gr[0] = gr[1] = gr[2] = 0.f;
+#pragma unroll 1
+    for (int l = 0; l < (two ? 2 : 1); ++l) {
+      int cc[3];
+      float t3[3];
+      locate(l == 0 ? tp : tm, comp, G, cc, t3);
+      float gl[3];
+      grad_at(f, R.at(cc), t3, kappa, gl);
+      // open sheet: (tau+ - tau-) . n+
+      const float sgn = l == 0 ? 1.f : -1.f;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gr[j] += sgn * gl[j] * invh[j];
+    }
+  }
+}
+
+// bound on |phi| over the 27 nodes: phi = a_x a_y a_z - b_x a_y a_z - a_x b_y a_z
+// - a_x a_y b_z, so |phi| <= prod_d (max|a_d| + max|b_d|)
+__device__ __forceinline__ float phi_bound(const DirW& X, const DirW& Y, const DirW& Z) {
+  auto p = [](const DirW& W) {
+    return fmaxf(fmaxf(W.a[0], W.a[1]), W.a[2]) +
+           fmaxf(fmaxf(fabsf(W.b[0]), fabsf(W.b[1])), fabsf(W.b[2]));
+  };
+  return p(X) * p(Y) * p(Z);
+}
+
+// Spread in exact fixed point: the contribution coef*phi, already scaled by
+// the block's power of two so that |value| <= 2^38, is split into
+// hi = floor(value / 2^16) (|hi| <= 2^22) and lo = value - 2^16 hi in
+// [0, 2^16], each added with a native 32-bit shared atomic.  A node receives
+// at most kMT contributions, so neither word overflows, and the node's sum
+// 2^16 * sum(hi) + sum(lo) is independent of the order of the additions.
+__device__ __forceinline__ void mls_spread_fixed(int* hi, int* lo, const RowAcc& A, const DirW& X,
+                                                 const DirW& Y, const DirW& Z, float coef) {
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      const int r = A.row(sy, sz);
+      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
+      const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
+#pragma unroll
+      for (int sx = 0; sx < 3; ++sx) {
+        const float val = (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1;
+        const float hf = floorf(val * (1.f / 65536.f));
+        atomicAdd(hi + r + sx, (int)hf);
+        atomicAdd(lo + r + sx, __float2int_rn(fmaf(-hf, 65536.f, val)));
+      }
+    }
+  }
+}
+
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 
 template <bool MEASURE, bool INTERP, bool PROBE, bool SPREAD>
 __global__ void __launch_bounds__(kMT, 2) marker_kernel(
@@ -247,19 +384,21 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   constexpr bool FIELD = INTERP || PROBE || SPREAD;
   constexpr bool VEL = INTERP || PROBE;
   extern __shared__ __align__(16) unsigned char dyn[];
-  // dynamic shared memory: row tables, then staged rows (one velocity and one
-  // force component)
-  int* s_xmin = reinterpret_cast<int*>(dyn);              // [kMaxRows]  then: staged offset - x0
-  int* s_xmax = s_xmin + kMaxRows;                        // [kMaxRows]  then: row length
-  int* s_off = s_xmax + kMaxRows;                         // [kMaxRows + 1] staged row start
-  int* s_base = s_off + kMaxRows + 1;                     // [kMaxRows] global offset of row (y, z)
-  int* s_x0w = s_base + kMaxRows;                         // [kMaxRows] first x, wrapped
-  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_x0w + kMaxRows);  // [kMaxNodes]
-  float* vbox = reinterpret_cast<float*>(dyn + kRowTableBytes);
+  int* s_xmin = reinterpret_cast<int*>(dyn);   // [kMaxRows]  then: staged offset - x0
+  int* s_xmax = s_xmin + kMaxRows;             // [kMaxRows]  then: row length
+  int* s_off = s_xmax + kMaxRows;              // [kMaxRows + 1] staged row start
+  int* s_base = s_off + kMaxRows + 1;          // [kMaxRows] global offset of row (y, z)
+  int* s_x0w = s_base + kMaxRows;              // [kMaxRows] first x, wrapped
+  int* s_nzlo = s_x0w + kMaxRows;              // [kMaxRows] first / last group of the row
+  int* s_nzhi = s_nzlo + kMaxRows;             //   that received a nonzero spread
+  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_nzhi + kMaxRows);  // [kMaxNodes/4]
+  float* bufA = reinterpret_cast<float*>(dyn + kRowTableBytes);
+  float* bufB = bufA + kMaxNodes;
   __shared__ int s_lo[3], s_hi[3];
   __shared__ double s_red[2][kMT / 32];
   __shared__ int s_last, s_N;
   __shared__ int s_warp[kMT / 32];
+  __shared__ int s_bmax[3];
 
   const int4 ch = T.chunks[blockIdx.x];  // body, face-list offset, count, chunk index in body
   const BodyDev B = T.body[ch.x];
@@ -268,12 +407,14 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   if (FIELD && threadIdx.x < 3) {
     s_lo[threadIdx.x] = INT_MAX;
     s_hi[threadIdx.x] = INT_MIN;
+    s_bmax[threadIdx.x] = 0;
   }
   float Af = 0.f, Vf = 0.f;
   float nrm[3] = {0.f, 0.f, 0.f}, area = 0.f;
   float tc[3] = {0.f, 0.f, 0.f}, tp[3] = {0.f, 0.f, 0.f}, tm[3] = {0.f, 0.f, 0.f};
+  float vb[3] = {0.f, 0.f, 0.f};     // centroid velocity (interpolation) or marker force
   bool ok = false;
-  int ia = 0, ib = 0, ic = 0, gf = 0;
+  int gf = 0;
   if (active) {
     // threads of a warp take faces spread over the patch (t -> 8 (t % 32) + t / 32
     // for full patches), so that one warp's simultaneous shared atomics of the
@@ -282,15 +423,24 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
     const int lf = __ldg(T.mface + topo.mface_off + ch.y + slot);
     gf = B.f_off + lf;
     const int* tr = T.tri + topo.tri_off + 3 * lf;
-    ia = B.v_off + __ldg(tr);
-    ib = B.v_off + __ldg(tr + 1);
-    ic = B.v_off + __ldg(tr + 2);
+    const int ia = B.v_off + __ldg(tr), ib = B.v_off + __ldg(tr + 1), ic = B.v_off + __ldg(tr + 2);
     float xa[3], xb[3], xc[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       xa[d] = __ldg(x + d * V + ia);
       xb[d] = __ldg(x + d * V + ib);
       xc[d] = __ldg(x + d * V + ic);
+    }
+    // issued now, used after the row map: the velocity of the centroid
+    // (interpolation) or the given marker force (spread only)
+    if (INTERP) {
+      const float third = 1.f / 3.f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        vb[d] = (__ldg(v + d * V + ia) + __ldg(v + d * V + ib) + __ldg(v + d * V + ic)) * third;
+    } else if (SPREAD) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) vb[d] = __ldg(Fm_in + d * F + gf);
     }
     const float e1[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
     const float e2[3] = {xc[0] - xa[0], xc[1] - xa[1], xc[2] - xa[2]};
@@ -321,6 +471,38 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       if (!ok) atomicOr(T.err, ERR_NONFINITE);
     }
   }
+
+  // ---- per-body float64 area and volume: this chunk's partial ---------------
+  // fixed-order reduction (warp shuffles, warps in order) into one partial per
+  // chunk, published before the field work so that the arrival count is known
+  // early; the last chunk of the body to arrive sums the partials at the end
+  if (MEASURE) {
+    double a = (double)Af, vol = (double)Vf;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      vol += __shfl_down_sync(0xffffffffu, vol, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_red[0][threadIdx.x >> 5] = a;
+      s_red[1][threadIdx.x >> 5] = vol;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sa = 0.0, sv = 0.0;
+      for (int k = 0; k < kMT / 32; ++k) {
+        sa += s_red[0][k];
+        sv += s_red[1][k];
+      }
+      const int gc = B.chunk_off + ch.w;
+      T.partial[2 * gc] = sa;
+      T.partial[2 * gc + 1] = sv;
+      __threadfence();
+      const int arrived = atomicAdd(T.counter + ch.x, 1);
+      s_last = (arrived == B.n_chunk - 1);
+    }
+  }
+
   const bool mine = FIELD && active && ok;
   const bool two = PROBE && !B.closed;     // open sheet: probes on both sides
 
@@ -372,6 +554,8 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
         s_xmin[r] = INT_MAX;
         s_xmax[r] = INT_MIN;
+        s_nzlo[r] = INT_MAX;
+        s_nzhi[r] = INT_MIN;
       }
       __syncthreads();
       if (mine) {
@@ -395,8 +579,9 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
         }
       }
       __syncthreads();
-      // row lengths (whole float4 groups when the grid allows vector access)
-      // and their exclusive scan: thread t owns rows 4t .. 4t + 3
+      // row lengths in whole groups of 4 nodes (aligned to float4 in global
+      // memory when the grid allows vector access) and their exclusive scan:
+      // thread t owns rows 4t .. 4t + 3
       int len[4], run = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -407,6 +592,8 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
           if (vec4) {
             a = a - (((a % 4) + 4) % 4);
             b = b + ((4 - ((b % 4) + 4) % 4) % 4);
+          } else {
+            b = a + ((b - a + 3) & ~3);
           }
           s_xmin[r] = a;
           L = b - a;
@@ -443,12 +630,11 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       N = s_N;
       fit = N <= kMaxNodes;
       if (fit) {
-        // row id of every float4 group (vector path) or node (scalar path),
-        // then fold x0 into the row offset: s_xmin[r] = offset - x0
-        const int gsz = vec4 ? 4 : 1;
+        // row id of every group of 4 staged nodes, then fold x0 into the row
+        // offset: s_xmin[r] = offset - x0
         for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
           const int o = s_off[r], L = s_xmax[r];
-          for (int q = o / gsz; q < (o + L) / gsz; ++q) s_grow[q] = (unsigned short)r;
+          for (int q = o / 4; q < (o + L) / 4; ++q) s_grow[q] = (unsigned short)r;
         }
         __syncthreads();
         for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
@@ -464,97 +650,50 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
     if (!fit && threadIdx.x == 0) atomicAdd(T.stats, 1);
     __syncthreads();
   }
-  float* fbox = vbox + (VEL ? (N + 3) / 4 * 4 : 0);
+  const RowTable RT{s_grow, s_off, s_base, s_x0w, g.n[0], vec4};
+  const StagedRows SR{s_xmin, ylo, zlo, sy};
+  const GlobalRows GR{g};
+  const int ngroups = fit ? N / 4 : 0;
 
-  // ---- per component: stage, interpolate, spread, differentiate, flush ----
-  // Each component's interpolation, spreading and gradient use only that
-  // component's field, so the staged rows hold one component at a time.
-  // Traction t = (G + G^T) n: pass i yields (G n)_i and adds n_i G_i. to G^T n.
-  float tGn[3] = {0.f, 0.f, 0.f}, tGTn[3] = {0.f, 0.f, 0.f};
-  if (FIELD) {
-    const float third = 1.f / 3.f;
-    const float cl = area * sc.cl_scale;
-    const int gsz = vec4 ? 4 : 1;
-    const int ngroups = fit ? N / gsz : 0;
+  // ---- velocity: interpolation at the centroid, gradient at the probes -----
+  // The three components are staged in two buffers (u -> A, v -> B, w -> A),
+  // the copies of the next component in flight while the current one is used.
+  // Traction t = (G + G^T) n: component i yields (G n)_i and adds n_i G_i. to
+  // G^T n.
+  float Fl[3] = {vb[0], vb[1], vb[2]};   // marker force per component
+  if (VEL) {
+    float tGn[3] = {0.f, 0.f, 0.f}, tGTn[3] = {0.f, 0.f, 0.f};
+    if (fit) {
+      stage_async(bufA, u, RT, ngroups);
+      cp_async_commit();
+      stage_async(bufB, vv, RT, ngroups);
+      cp_async_commit();
+    }
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
-      float* frcc = comp == 0 ? fx : (comp == 1 ? fy : fz);
+      const float* buf = comp == 1 ? bufB : bufA;
       if (fit) {
-        __syncthreads();   // the previous component is done with the rows
-        for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
-          const size_t o = row_node(q, gsz, s_grow, s_off, s_base, s_x0w, g.n[0]);
-          if (vec4) {
-            if (VEL) reinterpret_cast<float4*>(vbox)[q] = __ldg(reinterpret_cast<const float4*>(velc + o));
-            if (SPREAD) reinterpret_cast<float4*>(fbox)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-          } else {
-            if (VEL) vbox[q] = __ldg(velc + o);
-            if (SPREAD) fbox[q] = 0.f;
-          }
-        }
-        __syncthreads();
+        if (comp < 2) cp_async_wait<1>(); else cp_async_wait<0>();
+        __syncthreads();   // every thread's copies of this component have landed
       }
       if (mine) {
-        if (INTERP || SPREAD) {
-          int cc[3];
-          float t3[3];
-          locate(tc, comp, B.G, cc, t3);
-          DirW X, Y, Z;
-          dir3(t3, sc.kappa, X, Y, Z);
-          float Fl;
-          if (INTERP) {
-            float Ul;
-            if (fit) {
-              RowAcc A;
-              A.init(cc, s_xmin, ylo, zlo, sy);
-              Ul = mls_value(vbox, A, X, Y, Z);
-            } else {
-              GlobalAcc A;
-              A.init(cc, g);
-              Ul = mls_value(velc, A, X, Y, Z);
-            }
-            const float vb = (__ldg(v + comp * V + ia) + __ldg(v + comp * V + ib) +
-                              __ldg(v + comp * V + ic)) * third;
-            Fl = (vb - Ul) * sc.inv_dt;
-            if (U) U[comp * F + gf] = Ul;
-            if (Fm) Fm[comp * F + gf] = Fl;
-          } else {
-            Fl = __ldg(Fm_in + comp * F + gf);
-          }
-          if (SPREAD) {
-            if (fit) {
-              RowAcc A;
-              A.init(cc, s_xmin, ylo, zlo, sy);
-              mls_spread(fbox, A, X, Y, Z, cl * Fl);
-            } else {
-              GlobalAcc A;
-              A.init(cc, g);
-              mls_spread(frcc, A, X, Y, Z, cl * Fl);
-            }
-          }
+        float Ul = 0.f, gr[3];
+        if (fit)
+          velocity_component<INTERP, PROBE>(buf, SR, comp, B.G, tc, tp, tm, two, sc.kappa, g.invh,
+                                            Ul, gr);
+        else
+          velocity_component<INTERP, PROBE>(velc, GR, comp, B.G, tc, tp, tm, two, sc.kappa,
+                                            g.invh, Ul, gr);
+        if (INTERP) {
+          const float Fc = (vb[comp] - Ul) * sc.inv_dt;
+          if (comp == 0) Fl[0] = Fc;
+          if (comp == 1) Fl[1] = Fc;
+          if (comp == 2) Fl[2] = Fc;
+          if (U) U[comp * F + gf] = Ul;
+          if (Fm) Fm[comp * F + gf] = Fc;
         }
         if (PROBE) {
-          float gr[3] = {0.f, 0.f, 0.f};
-#pragma unroll 1
-          for (int l = 0; l < (two ? 2 : 1); ++l) {
-            int cc[3];
-            float t3[3];
-            locate(l == 0 ? tp : tm, comp, B.G, cc, t3);
-            float gl[3];
-            if (fit) {
-              RowAcc A;
-              A.init(cc, s_xmin, ylo, zlo, sy);
-              grad_at(vbox, A, t3, sc.kappa, gl);
-            } else {
-              GlobalAcc A;
-              A.init(cc, g);
-              grad_at(velc, A, t3, sc.kappa, gl);
-            }
-            // open sheet: (tau+ - tau-) . n+
-            const float sgn = l == 0 ? 1.f : -1.f;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) gr[j] += sgn * gl[j] * g.invh[j];
-          }
           const float gn = gr[0] * nrm[0] + gr[1] * nrm[1] + gr[2] * nrm[2];
           const float ni = comp == 0 ? nrm[0] : (comp == 1 ? nrm[1] : nrm[2]);
           if (comp == 0) tGn[0] = gn;
@@ -564,19 +703,10 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
           for (int j = 0; j < 3; ++j) tGTn[j] += ni * gr[j];
         }
       }
-      if (SPREAD && fit) {
-        __syncthreads();
-        for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
-          const size_t o = row_node(q, gsz, s_grow, s_off, s_base, s_x0w, g.n[0]);
-          if (vec4) {
-            const float4 val = reinterpret_cast<const float4*>(fbox)[q];
-            if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f)
-              atomicAdd(reinterpret_cast<float4*>(frcc + o), val);
-          } else {
-            const float val = fbox[q];
-            if (val != 0.f) atomicAdd(frcc + o, val);
-          }
-        }
+      if (fit && comp == 0) {
+        __syncthreads();   // buffer A is free again
+        stage_async(bufA, w, RT, ngroups);
+        cp_async_commit();
       }
     }
     if (PROBE && mine) {
@@ -584,15 +714,94 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
 #pragma unroll
       for (int i = 0; i < 3; ++i) Fext[i * F + gf] = s * (tGn[i] + tGTn[i]);
     }
-    if (SPREAD && record) {
-      // footprint for the next step's clear: the row map (x0, length per
-      // row) when staged, the bounding box (flag 1) otherwise
+  }
+
+  // ---- spreading: one component at a time, exact fixed point in the two
+  // buffers (high and low words), flushed with float4 global atomics --------
+  if (SPREAD) {
+    const float cl = area * sc.cl_scale;
+    int* s_hiw = reinterpret_cast<int*>(bufA);
+    int* s_low = reinterpret_cast<int*>(bufB);
+    if (fit) {
+      if (VEL) __syncthreads();   // the velocity phase is done with the buffers
+      for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
+        reinterpret_cast<int4*>(s_hiw)[q] = make_int4(0, 0, 0, 0);
+        reinterpret_cast<int4*>(s_low)[q] = make_int4(0, 0, 0, 0);
+      }
+    }
+#pragma unroll 1
+    for (int comp = 0; comp < 3; ++comp) {
+      float* fc = comp == 0 ? fx : (comp == 1 ? fy : fz);
+      float coef = 0.f;
+      DirW X, Y, Z;
+      int cc[3];
+      if (mine) {
+        float t3[3];
+        locate(tc, comp, B.G, cc, t3);
+        dir3(t3, sc.kappa, X, Y, Z);
+        coef = cl * (comp == 0 ? Fl[0] : (comp == 1 ? Fl[1] : Fl[2]));
+      }
+      if (fit) {
+        // block-wide bound on |coef phi| (non-negative floats order as ints)
+        float bnd = mine ? fabsf(coef) * phi_bound(X, Y, Z) : 0.f;
+        if (!(bnd <= 3.0e38f)) bnd = __int_as_float(0x7f800000);   // inf or NaN: flagged below
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bnd = fmaxf(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_bmax[comp], __float_as_int(bnd));
+        __syncthreads();   // also: the buffers are zero
+        const float bm = __int_as_float(s_bmax[comp]);
+        if (!(bm <= 3.0e38f)) {
+          if (threadIdx.x == 0) atomicOr(T.err, ERR_NONFINITE);
+          continue;   // uniform over the block
+        }
+        if (bm == 0.f) continue;   // nothing to spread for this component
+        // scale 2^k with bm * 2^k < 2^38
+        const int k = min(38 - (ilogbf(bm) + 1), 120);
+        if (mine && coef != 0.f)
+          mls_spread_fixed(s_hiw, s_low, SR.at(cc), X, Y, Z, coef * pow2f(k));
+        __syncthreads();
+        const float inv_scale = pow2f(-k);
+        for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
+          const int4 h = reinterpret_cast<const int4*>(s_hiw)[q];
+          const int4 l = reinterpret_cast<const int4*>(s_low)[q];
+          if ((h.x | h.y | h.z | h.w | l.x | l.y | l.z | l.w) == 0) continue;
+          const float4 val = make_float4(fmaf((float)h.x, 65536.f, (float)l.x) * inv_scale,
+                                         fmaf((float)h.y, 65536.f, (float)l.y) * inv_scale,
+                                         fmaf((float)h.z, 65536.f, (float)l.z) * inv_scale,
+                                         fmaf((float)h.w, 65536.f, (float)l.w) * inv_scale);
+          reinterpret_cast<int4*>(s_hiw)[q] = make_int4(0, 0, 0, 0);
+          reinterpret_cast<int4*>(s_low)[q] = make_int4(0, 0, 0, 0);
+          if (vec4) {
+            atomicAdd(reinterpret_cast<float4*>(fc + RT.node(q, 0)), val);
+          } else {
+            if (val.x != 0.f) atomicAdd(fc + RT.node(q, 0), val.x);
+            if (val.y != 0.f) atomicAdd(fc + RT.node(q, 1), val.y);
+            if (val.z != 0.f) atomicAdd(fc + RT.node(q, 2), val.z);
+            if (val.w != 0.f) atomicAdd(fc + RT.node(q, 3), val.w);
+          }
+          const int r = s_grow[q];
+          atomicMin(&s_nzlo[r], q);
+          atomicMax(&s_nzhi[r], q);
+        }
+        __syncthreads();   // buffers zero again before the next component
+      } else if (mine) {
+        mls_spread(fc, GR.at(cc), X, Y, Z, coef);
+      }
+    }
+    if (record) {
+      // footprint for the next step's clear: per row the x-range of the groups
+      // that received a nonzero spread (staged), the bounding box (flag 1)
+      // otherwise
       const int gc = B.chunk_off + ch.w;
       if (fit) {
         for (int r = threadIdx.x; r < sy * sz; r += blockDim.x) {
-          const int L = s_xmax[r];
-          T.rowmap[(size_t)gc * kMaxRows + r] =
-              L > 0 ? make_int2(s_base[r], s_x0w[r] | (L << 16)) : make_int2(0, 0);
+          int2 e = make_int2(0, 0);
+          if (s_xmax[r] > 0 && s_nzlo[r] <= s_nzhi[r]) {
+            const int L = min(4 * (s_nzhi[r] - s_nzlo[r] + 1), g.n[0]);
+            const int x0 = wrap_pos(s_x0w[r] + (4 * s_nzlo[r] - s_off[r]), g.n[0]);
+            e = make_int2(s_base[r], x0 | (L << 16));
+          }
+          T.rowmap[(size_t)gc * kMaxRows + r] = e;
         }
       }
       if (threadIdx.x == 0) {
@@ -603,61 +812,47 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
     }
   }
 
-  // ---- per-body float64 area and volume ------------------------------------
+  // ---- per-body float64 area and volume: the last chunk sums the partials --
   if (MEASURE) {
-    // fixed-order reduction: warp shuffles, warps in order, one partial per
-    // chunk; the last chunk of the body to arrive sums the partials in order
-    double a = (double)Af, vol = (double)Vf;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      vol += __shfl_down_sync(0xffffffffu, vol, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      s_red[0][threadIdx.x >> 5] = a;
-      s_red[1][threadIdx.x >> 5] = vol;
-    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double sa = 0.0, sv = 0.0;
-      for (int k = 0; k < kMT / 32; ++k) {
-        sa += s_red[0][k];
-        sv += s_red[1][k];
-      }
-      const int gc = B.chunk_off + ch.w;
-      T.partial[2 * gc] = sa;
-      T.partial[2 * gc + 1] = sv;
+    if (s_last && threadIdx.x < 32) {
       __threadfence();
-      const int arrived = atomicAdd(T.counter + ch.x, 1);
-      s_last = (arrived == B.n_chunk - 1);
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-      __threadfence();
-      double ta = 0.0, tv = 0.0;
+      // lane k sums chunks k, k + 32, ... in order, then a fixed shuffle tree
       const volatile double* P = T.partial;
-      for (int k = 0; k < B.n_chunk; ++k) {
+      double ta = 0.0, tv = 0.0;
+      for (int k = threadIdx.x; k < B.n_chunk; k += 32) {
         ta += P[2 * (B.chunk_off + k)];
         tv += P[2 * (B.chunk_off + k) + 1];
       }
-      T.meas[2 * ch.x] = ta;
-      T.meas[2 * ch.x + 1] = tv;
-      const float cA = (float)(B.kA * ((ta - B.A0) / B.A0));
-      const float cV = B.closed ? (float)(B.kv * ((tv - B.V0) / B.V0)) : 0.f;
-      T.coef[ch.x] = make_float2(cA, cV);
-      T.counter[ch.x] = 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ta += __shfl_down_sync(0xffffffffu, ta, o);
+        tv += __shfl_down_sync(0xffffffffu, tv, o);
+      }
+      if (threadIdx.x == 0) {
+        T.meas[2 * ch.x] = ta;
+        T.meas[2 * ch.x + 1] = tv;
+        const float cA = (float)(B.kA * ((ta - B.A0) / B.A0));
+        const float cV = B.closed ? (float)(B.kv * ((tv - B.V0) / B.V0)) : 0.f;
+        T.coef[ch.x] = make_float2(cA, cV);
+        T.counter[ch.x] = 0;
+      }
     }
   }
 }
 
-// zero the force fields on the footprint each marker block recorded in its
-// last spread: its row map, or its bounding box when it took the global path
+// Zero the force fields on the footprint each marker block recorded in its
+// last spread: its rows' nonzero x-ranges, or its bounding box when it took
+// the global path.  Zeroing more than the footprint is harmless (everything
+// nonzero belongs to some recorded footprint), so vector rows are widened to
+// whole 32-byte sectors when nx allows, which avoids partial-sector writes.
 __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, float* __restrict__ fx,
                                                     float* __restrict__ fy, float* __restrict__ fz,
                                                     int vec4) {
   const int4 lo = T.boxes[2 * blockIdx.x];
   const int4 sz = T.boxes[2 * blockIdx.x + 1];
   if (sz.x <= 0 || sz.y <= 0 || sz.z <= 0) return;
+  const int nx = g.n[0];
   // float4 stores only for rows recorded in whole float4 groups
   vec4 = vec4 && lo.w == 2;
   if (lo.w == 1) {
@@ -666,8 +861,8 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
     for (long long idx = threadIdx.x; idx < N; idx += blockDim.x) {
       const int k = (int)(idx / sxy), rem = (int)(idx - (long long)k * sxy), j = rem / sz.x,
                 i = rem - j * sz.x;
-      const size_t o = ((size_t)wrap(lo.z + k, g.n[2]) * g.n[1] + wrap(lo.y + j, g.n[1])) * g.n[0] +
-                       wrap(lo.x + i, g.n[0]);
+      const size_t o = ((size_t)wrap(lo.z + k, g.n[2]) * g.n[1] + wrap(lo.y + j, g.n[1])) * nx +
+                       wrap(lo.x + i, nx);
       fx[o] = 0.f;
       fy[o] = 0.f;
       fz[o] = 0.f;
@@ -675,16 +870,20 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
   } else {
     const int nrows = sz.w;
     const int2* rm = T.rowmap + (size_t)blockIdx.x * kMaxRows;
-    // a warp per row, a lane per float4 group (vector grids) or node
-    const int lane = threadIdx.x & 31;
-    for (int r = threadIdx.x >> 5; r < nrows; r += blockDim.x >> 5) {
+    const bool sect = (nx % 8) == 0;
+    // a thread per row (rows are a few float4 groups long)
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
       const int2 e = rm[r];                  // (row base, first x wrapped | length << 16)
-      const int L = e.y >> 16, x0 = e.y & 0xFFFF;
+      int L = e.y >> 16, x0 = e.y & 0xFFFF;  // L <= nx, x0 < nx
       if (L <= 0) continue;
       if (vec4) {
-        for (int q = lane; q < L / 4; q += 32) {
-          int xg = x0 + 4 * q;
-          if (xg >= g.n[0]) xg -= g.n[0];
+        if (sect) {
+          L = min((L + (x0 & 7) + 7) & ~7, nx);
+          x0 &= ~7;
+        }
+        for (int q = 0; q < L; q += 4) {
+          int xg = x0 + q;
+          if (xg >= nx) xg -= nx;
           const size_t o = (size_t)e.x + xg;
           const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
           *reinterpret_cast<float4*>(fx + o) = z4;
@@ -692,9 +891,9 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
           *reinterpret_cast<float4*>(fz + o) = z4;
         }
       } else {
-        for (int q = lane; q < L; q += 32) {
+        for (int q = 0; q < L; ++q) {
           int xg = x0 + q;
-          if (xg >= g.n[0]) xg -= g.n[0];
+          if (xg >= nx) xg -= nx;
           const size_t o = (size_t)e.x + xg;
           fx[o] = 0.f;
           fy[o] = 0.f;
