@@ -321,6 +321,36 @@ void free_all(ibm_ctx* c) {
 
 bool is_fin(double v) { return std::isfinite(v); }
 
+// power-of-two scale 2^e with ref * 2^e in [2^39, 2^40): the body's sum then
+// has 2^22 of headroom in a 64-bit integer; false when 2^e is not a normal
+// float
+bool fixed_scale(double ref, float& s) {
+  int ex = 0;
+  std::frexp(ref, &ex);
+  const int e = 40 - ex;
+  if (!(ref > 0) || e < -120 || e > 120) return false;
+  s = std::ldexp(1.0f, e);
+  return true;
+}
+
+// fixed-point fields of a body record from A0, V0 and the constants
+bool set_fixed_point(BodyDev& R) {
+  if (!fixed_scale(R.A0, R.sA)) return false;
+  R.qA0 = std::llrint(R.A0 * (double)R.sA);
+  R.cA_unit = (float)((double)R.kA / ((double)R.sA * R.A0));
+  if (R.closed) {
+    if (!fixed_scale(R.V0, R.sV)) return false;
+    R.qV0 = std::llrint(R.V0 * (double)R.sV);
+    R.cV_unit = (float)((double)R.kv / ((double)R.sV * R.V0));
+  } else {
+    R.sV = 1.f;
+    R.qV0 = 0;
+    R.cV_unit = 0.f;
+  }
+  R.qlim = (float)(std::ldexp(1.0, 62) / (double)std::max(R.nf, 1));
+  return true;
+}
+
 ibm_status set_err(ibm_ctx* c, ibm_status s, const std::string& m) {
   if (c) c->err = m;
   return s;
@@ -533,6 +563,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       R.inv_mass = (float)(1.0 / Bd.mass);
       R.A0 = A0;
       R.V0 = Bd.closed ? V0 : 1.0;
+      if (!set_fixed_point(R))
+        fail(IBM_ERR_MESH, tag + "rest area or volume outside the supported range");
       R.chunk_off = (int32_t)chunks.size();
       const int nch = (int)T.mbound.size() - 1;
       R.n_chunk = nch;
@@ -550,6 +582,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     // concatenate the topology tables
     std::vector<TopoDev> td(topos.size());
     std::vector<int32_t> tri_all, v2f_ptr_all, v2f_idx_all, loc_all, csr_all, mface_all;
+    std::vector<int4> mtri_all;
     std::vector<int4> edge_all;
     std::vector<PatchHdr> patch_all;
     std::vector<PEdge> pedge_all;
@@ -574,6 +607,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       v2f_idx_all.insert(v2f_idx_all.end(), T.v2f_idx.begin(), T.v2f_idx.end());
       D.mface_off = (int32_t)mface_all.size();
       mface_all.insert(mface_all.end(), T.mface.begin(), T.mface.end());
+      for (const int32_t f : T.mface)
+        mtri_all.push_back(make_int4(T.tri[3 * f], T.tri[3 * f + 1], T.tri[3 * f + 2], f));
       D.patch_off = (int32_t)patch_all.size();
       const int32_t lo = (int32_t)loc_all.size(), eo2 = (int32_t)pedge_all.size(),
                     fo2 = (int32_t)pface_all.size(), co = (int32_t)csr_all.size(),
@@ -625,8 +660,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.rest = upload(c, rest);
     d.chunks = upload(c, chunks);
     d.work = upload(c, work);
-    d.partial = zeros<double>(c, 2 * (size_t)c->n_chunks);
-    d.counter = zeros<int32_t>(c, (size_t)n_bodies);
+    d.qsum = zeros<unsigned long long>(c, 2 * (size_t)n_bodies);
     d.meas = zeros<double>(c, 2 * (size_t)n_bodies);
     d.fext = zeros<float>(c, 3 * (size_t)F);
     d.err = zeros<int32_t>(c, 1);
@@ -634,6 +668,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.boxes = zeros<int4>(c, 2 * (size_t)c->n_chunks);
     d.rowmap = zeros<int2>(c, (size_t)kMaxRows * c->n_chunks);
     d.mface = upload(c, mface_all);
+    d.mtri = upload(c, mtri_all);
     d.stats = zeros<int32_t>(c, 4);
     d.partial2 = zeros<double>(c, 2 * (size_t)c->n_chunks);
     d.counter2 = zeros<int32_t>(c, (size_t)n_bodies);
@@ -731,6 +766,7 @@ extern "C" ibm_status ibm_set_body_constants(ibm_ctx* c, const double* k) {
     R.kA = (float)k[6 * b + 3];
     R.kv = R.closed ? (float)k[6 * b + 4] : 0.f;
     R.inv_mass = (float)(1.0 / k[6 * b + 5]);
+    set_fixed_point(R);
   }
   cudaSetDevice(c->device);
   // synchronous with respect to the host buffer (pageable source)
@@ -743,8 +779,11 @@ extern "C" ibm_status ibm_set_body_constants(ibm_ctx* c, const double* k) {
 extern "C" ibm_status ibm_body_measures(ibm_ctx* c, const float* x, double* out) {
   if (!c || !x || !out) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   cudaSetDevice(c->device);
-  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
+  cudaError_t e = zero_body_sums(c);
+  if (e == cudaSuccess)
+    e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                   nullptr, nullptr, nullptr, true, false, false, false, false);
+  if (e == cudaSuccess) e = launch_measure_finalize(c);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, c->d.meas, sizeof(double) * 2 * c->B, cudaMemcpyDeviceToDevice,
                         c->stream);
@@ -755,8 +794,11 @@ extern "C" ibm_status ibm_compute_forces(ibm_ctx* c, const float* x, float* F_in
                                          double* energy) {
   if (!c || !x || !F_int) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   cudaSetDevice(c->device);
-  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
+  cudaError_t e = zero_body_sums(c);
+  if (e == cudaSuccess)
+    e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                   nullptr, nullptr, nullptr, true, false, false, false, false);
+  if (e == cudaSuccess && energy) e = launch_measure_finalize(c);
   if (e == cudaSuccess && energy)
     e = cudaMemsetAsync(energy, 0, sizeof(double) * 5 * c->B, c->stream);
   if (e == cudaSuccess)
@@ -811,8 +853,8 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
   mark(0);
   // the clear is a no-op for blocks that recorded no footprint (first step),
   // so it is launched unconditionally: a captured step then clears whatever
-  // step ran before it
-  if (clear) e = launch_clear(c, fx, fy, fz);
+  // step ran before it.  It also zeroes the fixed-point body sums.
+  e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
   mark(1);
   if (e == cudaSuccess)
     e = launch_mls(c, x, v, u, vv, w, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz, true, true,

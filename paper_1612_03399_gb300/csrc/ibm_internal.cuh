@@ -26,6 +26,14 @@ struct BodyDev {
   int32_t work_off;                    // first force-kernel work item (patch) of this body
   int32_t pad1;
   double A0, V0;                       // rest area and volume (float64)
+  // Exact fixed-point body sums: a face's area (volume) contributes
+  // q = rint(value * sA) (sV), a power of two chosen from A0 (V0), and the
+  // q are summed with 64-bit integer atomics, independent of order.
+  int64_t qA0, qV0;                    // rest area and volume in fixed point
+  float sA, sV;                        // 2^eA, 2^eV
+  float cA_unit, cV_unit;              // k_A / (sA A0), k_v / (sV V0)
+  float qlim;                          // per-face bound on |q|: 2^62 / n_faces
+  float pad2;
 };
 
 // per distinct mesh topology (shared by every body with the same faces)
@@ -102,12 +110,12 @@ struct DeviceTables {
   int4* chunks = nullptr;       // (body, offset in the topology's mface list, count,
                                 //  chunk index in body): one marker patch each
   int2* work = nullptr;         // (body, patch index within topology)
-  double* partial = nullptr;    // [n_chunks][2] per-chunk (A, V)
-  int32_t* counter = nullptr;   // [B] chunk arrival counters
-  double* meas = nullptr;       // [B][2] (A, V)
-  float2* coef = nullptr;       // [B] (k_A (A - A0)/A0, k_v (V - V0)/V0) for the force kernel
+  unsigned long long* qsum = nullptr;  // [B][2] fixed-point (A, V) sums of the marker kernel
+  double* meas = nullptr;       // [B][2] (A, V) (formed from qsum by the finalize kernel)
+  float2* coef = nullptr;       // [B] (k_A (A - A0)/A0, k_v (V - V0)/V0) (likewise)
   float* fext = nullptr;        // [3][F] scratch marker traction (ibm_step)
   int32_t* mface = nullptr;     // faces of every topology in marker-patch order (body-local)
+  int4* mtri = nullptr;         // the same faces as (vertex a, b, c, face), body-local
   int4* boxes = nullptr;        // [n_chunks][2] footprint of each marker block's last spread:
                                 // (x, y, z lo, kind: 0 rows, 1 whole box, 2 rows in float4
                                 // groups), (x, y, z size, rows)
@@ -136,6 +144,20 @@ constexpr int kMaxRows = 1024;                                     // (y, z) row
 constexpr int kMaxNodes = 8960;                                    // staged nodes per buffer
 constexpr int kRowTableBytes = ((4 * (7 * kMaxRows + 1) + 2 * (kMaxNodes / 4)) + 15) / 16 * 16;
 constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes;
+
+// 64-bit integer to float without a 64-bit conversion instruction
+__device__ __forceinline__ float i64_to_float(long long d) {
+  return fmaf((float)(int)(d >> 32), 4294967296.f, (float)(unsigned)(d & 0xffffffffll));
+}
+
+// global-term coefficients k_A (A - A0)/A0 and k_v (V - V0)/V0 from the
+// fixed-point sums; the difference to the rest value is exact
+__device__ __forceinline__ float2 body_coef(const BodyDev& B, unsigned long long qa,
+                                            unsigned long long qv) {
+  const float cA = i64_to_float((long long)qa - B.qA0) * B.cA_unit;
+  const float cV = B.closed ? i64_to_float((long long)qv - B.qV0) * B.cV_unit : 0.f;
+  return make_float2(cA, cV);
+}
 
 }  // namespace ibm
 
@@ -169,6 +191,10 @@ cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* 
                        float* Fext, float* fx, float* fy, float* fz, bool measure, bool interp,
                        bool probe, bool spread, bool record_cells);
 cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz);
+// zero the fixed-point body sums (before a measuring marker launch that does
+// not follow a clear), and form meas / coef from them (after it)
+cudaError_t zero_body_sums(ibm_ctx* c);
+cudaError_t launch_measure_finalize(ibm_ctx* c);
 cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float* Fext,
                          float* Fint, float* x_out, float* v_out, double* energy, bool advance);
 cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,

@@ -543,8 +543,11 @@ cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const fl
                             float* gv, double* gparams) {
   if (c->n_chunks == 0) return cudaSuccess;
   // area, volume and the global-term coefficients at x
-  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
+  cudaError_t e = zero_body_sums(c);
+  if (e == cudaSuccess)
+    e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                   nullptr, nullptr, nullptr, true, false, false, false, false);
+  if (e == cudaSuccess) e = launch_measure_finalize(c);
   if (e != cudaSuccess) return e;
   ext_adjoint_kernel<<<c->n_chunks, kMT, 0, c->stream>>>(c->d, c->grid, c->sc, (int32_t)c->V,
                                                          (int32_t)c->F, x, u, vv, w, gx_next,

@@ -70,9 +70,9 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     S.py[i] = __ldg(x + V + gv);
     S.pz[i] = __ldg(x + 2 * V + gv);
   }
-  // per-body global-term coefficients, formed once per body from the float64
-  // area / volume sums by the marker kernel
-  const float2 cf = T.coef[wk.x];
+  // per-body global-term coefficients from the marker kernel's exact
+  // fixed-point area / volume sums
+  const float2 cf = body_coef(B, __ldg(T.qsum + 2 * wk.x), __ldg(T.qsum + 2 * wk.x + 1));
   const float cA = cf.x, cV = cf.y;
   const bool want_e = energy != nullptr;
   double eS = 0.0, eB = 0.0, eA = 0.0;

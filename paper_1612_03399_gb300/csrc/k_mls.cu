@@ -371,6 +371,14 @@ __device__ __forceinline__ void mls_spread_fixed(int* hi, int* lo, const RowAcc&
   }
 }
 
+// x (|x| < 2^62) rounded to a 64-bit integer without a 64-bit conversion:
+// hi = floor(x / 2^32) is exact and the remainder x - 2^32 hi lies in [0, 2^32)
+__device__ __forceinline__ long long to_fixed(float x) {
+  const float hf = floorf(x * 0x1p-32f);
+  const unsigned lo = __float2uint_rn(fmaf(-hf, 0x1p32f, x));
+  return (long long)(int)hf * 4294967296ll + (long long)lo;
+}
+
 // 2^k as a float, k in [-126, 127]
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 
@@ -395,8 +403,7 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   float* bufA = reinterpret_cast<float*>(dyn + kRowTableBytes);
   float* bufB = bufA + kMaxNodes;
   __shared__ int s_lo[3], s_hi[3];
-  __shared__ double s_red[2][kMT / 32];
-  __shared__ int s_last, s_N;
+  __shared__ int s_N;
   __shared__ int s_warp[kMT / 32];
   __shared__ int s_bmax[3];
 
@@ -420,10 +427,9 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
     // for full patches), so that one warp's simultaneous shared atomics of the
     // spread rarely meet on a node
     const int slot = (ch.z == kMT) ? 8 * (threadIdx.x & 31) + (threadIdx.x >> 5) : threadIdx.x;
-    const int lf = __ldg(T.mface + topo.mface_off + ch.y + slot);
-    gf = B.f_off + lf;
-    const int* tr = T.tri + topo.tri_off + 3 * lf;
-    const int ia = B.v_off + __ldg(tr), ib = B.v_off + __ldg(tr + 1), ic = B.v_off + __ldg(tr + 2);
+    const int4 mt = __ldg(T.mtri + topo.mface_off + ch.y + slot);
+    gf = B.f_off + mt.w;
+    const int ia = B.v_off + mt.x, ib = B.v_off + mt.y, ic = B.v_off + mt.z;
     float xa[3], xb[3], xc[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -472,34 +478,29 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
     }
   }
 
-  // ---- per-body float64 area and volume: this chunk's partial ---------------
-  // fixed-order reduction (warp shuffles, warps in order) into one partial per
-  // chunk, published before the field work so that the arrival count is known
-  // early; the last chunk of the body to arrive sums the partials at the end
+  // ---- per-body area and volume: exact fixed-point sums -------------------
+  // q = rint(value * 2^e) per face (2^e from the rest value), summed per warp
+  // and added with 64-bit integer atomics: the body's sum does not depend on
+  // the order of the additions
   if (MEASURE) {
-    double a = (double)Af, vol = (double)Vf;
+    long long qa = 0, qv = 0;
+    if (active) {
+      const float ya = Af * B.sA, yv = Vf * B.sV;
+      if (fabsf(ya) < B.qlim && fabsf(yv) < B.qlim) {
+        qa = to_fixed(ya);
+        qv = to_fixed(yv);
+      } else {
+        atomicOr(T.err, ERR_NONFINITE);
+      }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      vol += __shfl_down_sync(0xffffffffu, vol, o);
+      qa += __shfl_xor_sync(0xffffffffu, qa, o);
+      qv += __shfl_xor_sync(0xffffffffu, qv, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-      s_red[0][threadIdx.x >> 5] = a;
-      s_red[1][threadIdx.x >> 5] = vol;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sa = 0.0, sv = 0.0;
-      for (int k = 0; k < kMT / 32; ++k) {
-        sa += s_red[0][k];
-        sv += s_red[1][k];
-      }
-      const int gc = B.chunk_off + ch.w;
-      T.partial[2 * gc] = sa;
-      T.partial[2 * gc + 1] = sv;
-      __threadfence();
-      const int arrived = atomicAdd(T.counter + ch.x, 1);
-      s_last = (arrived == B.n_chunk - 1);
+    if ((threadIdx.x & 31) == 0 && (threadIdx.x >> 5) * 32 < ch.z) {
+      atomicAdd(T.qsum + 2 * ch.x, (unsigned long long)qa);
+      if (B.closed) atomicAdd(T.qsum + 2 * ch.x + 1, (unsigned long long)qv);
     }
   }
 
@@ -580,25 +581,27 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       }
       __syncthreads();
       // row lengths in whole groups of 4 nodes (aligned to float4 in global
-      // memory when the grid allows vector access) and their exclusive scan:
-      // thread t owns rows 4t .. 4t + 3
-      int len[4], run = 0;
+      // memory when the grid allows vector access), their exclusive scan, and
+      // per row: group -> row ids, global row offset, wrapped first x and
+      // staged offset - x0.  Thread t owns rows 4t .. 4t + 3.
+      int len[4], st[4], run = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = 4 * threadIdx.x + q;
-        int L = 0;
+        int L = 0, a = 0;
         if (r < (int)nrows && s_xmin[r] <= s_xmax[r]) {
-          int a = s_xmin[r], b = s_xmax[r] + 1;
+          a = s_xmin[r];
+          int b = s_xmax[r] + 1;
           if (vec4) {
             a = a - (((a % 4) + 4) % 4);
             b = b + ((4 - ((b % 4) + 4) % 4) % 4);
           } else {
             b = a + ((b - a + 3) & ~3);
           }
-          s_xmin[r] = a;
           L = b - a;
         }
         len[q] = L;
+        st[q] = a;
         run += L;
       }
       // block exclusive scan of run
@@ -619,6 +622,15 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
         if (r < kMaxRows) {
           s_off[r] = pos;
           s_xmax[r] = len[q];
+          if (len[q] > 0) {
+            // groups past kMaxNodes / 4 only occur when the block does not fit
+            const int q1 = min((pos + len[q]) / 4, kMaxNodes / 4);
+            for (int k = pos / 4; k < q1; ++k) s_grow[k] = (unsigned short)r;
+            const int yy = wrap(ylo + r % sy, g.n[1]), zz = wrap(zlo + r / sy, g.n[2]);
+            s_base[r] = (zz * g.n[1] + yy) * g.n[0];
+            s_x0w[r] = wrap(st[q], g.n[0]);
+            s_xmin[r] = pos - st[q];
+          }
         }
         pos += len[q];
       }
@@ -629,23 +641,6 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       __syncthreads();
       N = s_N;
       fit = N <= kMaxNodes;
-      if (fit) {
-        // row id of every group of 4 staged nodes, then fold x0 into the row
-        // offset: s_xmin[r] = offset - x0
-        for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
-          const int o = s_off[r], L = s_xmax[r];
-          for (int q = o / 4; q < (o + L) / 4; ++q) s_grow[q] = (unsigned short)r;
-        }
-        __syncthreads();
-        for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
-          if (s_xmax[r] > 0) {
-            const int yy = wrap(ylo + r % sy, g.n[1]), zz = wrap(zlo + r / sy, g.n[2]);
-            s_base[r] = (zz * g.n[1] + yy) * g.n[0];
-            s_x0w[r] = wrap(s_xmin[r], g.n[0]);
-            s_xmin[r] = s_off[r] - s_xmin[r];
-          }
-        }
-      }
     }
     if (!fit && threadIdx.x == 0) atomicAdd(T.stats, 1);
     __syncthreads();
@@ -811,34 +806,6 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
       }
     }
   }
-
-  // ---- per-body float64 area and volume: the last chunk sums the partials --
-  if (MEASURE) {
-    __syncthreads();
-    if (s_last && threadIdx.x < 32) {
-      __threadfence();
-      // lane k sums chunks k, k + 32, ... in order, then a fixed shuffle tree
-      const volatile double* P = T.partial;
-      double ta = 0.0, tv = 0.0;
-      for (int k = threadIdx.x; k < B.n_chunk; k += 32) {
-        ta += P[2 * (B.chunk_off + k)];
-        tv += P[2 * (B.chunk_off + k) + 1];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ta += __shfl_down_sync(0xffffffffu, ta, o);
-        tv += __shfl_down_sync(0xffffffffu, tv, o);
-      }
-      if (threadIdx.x == 0) {
-        T.meas[2 * ch.x] = ta;
-        T.meas[2 * ch.x + 1] = tv;
-        const float cA = (float)(B.kA * ((ta - B.A0) / B.A0));
-        const float cV = B.closed ? (float)(B.kv * ((tv - B.V0) / B.V0)) : 0.f;
-        T.coef[ch.x] = make_float2(cA, cV);
-        T.counter[ch.x] = 0;
-      }
-    }
-  }
 }
 
 // Zero the force fields on the footprint each marker block recorded in its
@@ -849,6 +816,14 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
 __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, float* __restrict__ fx,
                                                     float* __restrict__ fy, float* __restrict__ fz,
                                                     int vec4) {
+  // the first chunk of each body also zeroes the body's fixed-point sums
+  if (threadIdx.x == 0) {
+    const int4 ch = T.chunks[blockIdx.x];
+    if (ch.w == 0) {
+      T.qsum[2 * ch.x] = 0ull;
+      T.qsum[2 * ch.x + 1] = 0ull;
+    }
+  }
   const int4 lo = T.boxes[2 * blockIdx.x];
   const int4 sz = T.boxes[2 * blockIdx.x + 1];
   if (sz.x <= 0 || sz.y <= 0 || sz.z <= 0) return;
@@ -906,6 +881,17 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
   if (threadIdx.x == 0) T.boxes[2 * blockIdx.x + 1] = make_int4(0, 0, 0, 0);
 }
 
+// (A, V) in float64 and the global-term coefficients from the fixed-point sums
+__global__ void measure_finalize_kernel(DeviceTables T, int32_t nb) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const BodyDev B = T.body[b];
+  const unsigned long long qa = T.qsum[2 * b], qv = T.qsum[2 * b + 1];
+  T.meas[2 * b] = (double)(long long)qa / (double)B.sA;
+  T.meas[2 * b + 1] = B.closed ? (double)(long long)qv / (double)B.sV : 0.0;
+  T.coef[b] = body_coef(B, qa, qv);
+}
+
 // null (unused) pointers count as aligned
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -958,6 +944,18 @@ cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* 
   if (!measure && !interp && !probe && spread)
     return launch_t<false, false, false, true>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t zero_body_sums(ibm_ctx* c) {
+  if (c->B == 0) return cudaSuccess;
+  return cudaMemsetAsync(c->d.qsum, 0, sizeof(unsigned long long) * 2 * c->B, c->stream);
+}
+
+cudaError_t launch_measure_finalize(ibm_ctx* c) {
+  if (c->B == 0) return cudaSuccess;
+  measure_finalize_kernel<<<(unsigned)((c->B + 127) / 128), 128, 0, c->stream>>>(c->d,
+                                                                               (int32_t)c->B);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz) {
