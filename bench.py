@@ -112,6 +112,15 @@ def reduce_sum(ws, val, device):
     return float(t.item())
 
 
+def job_rate(ws, units_local, steps, ms_local, device):
+    """Whole-job throughput of independent replicas: the units every rank
+    processed (summed over ranks) times steps, over the slowest rank's time.
+    Returns (units per second, max ms)."""
+    t_max = reduce_max(ws, ms_local, device)
+    units = reduce_sum(ws, float(units_local), device)
+    return units * steps / (t_max * 1e-3), t_max
+
+
 # ---------------------------------------------------------------------------
 # algorithmic byte model of the two main kernels
 # ---------------------------------------------------------------------------
@@ -372,10 +381,8 @@ def run_gb300(args, ws, rank, local):
     ctx.check_device_error()
     graph.close()
     barrier(ws)
-    t_max = reduce_max(ws, total_ms, device)
-    nodes_all = reduce_sum(ws, float(ctx.V), device)
-    value = nodes_all * n_steps / (t_max * 1e-3)
-    value_steps = nodes_all * args.steps / (reduce_max(ws, step_ms, device) * 1e-3)
+    value, t_max = job_rate(ws, ctx.V, n_steps, total_ms, device)
+    value_steps, _ = job_rate(ws, ctx.V, args.steps, step_ms, device)
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
@@ -399,9 +406,9 @@ def run_gb300(args, ws, rank, local):
             e2e_ms += ev0.elapsed_time(ev1)
             xh, xo = xo, xh
             vh, vo = vo, vh
-        e2e_max = reduce_max(ws, e2e_ms, device)
+        e2e_value, _ = job_rate(ws, ctx.V, args.steps, e2e_ms, device)
         nbytes = 2 * 3 * ctx.V * 4
-        e2e = {"value": nodes_all * args.steps / (e2e_max * 1e-3), "unit": UNIT,
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     if rank != 0:
         return

@@ -140,8 +140,8 @@ struct DeviceTables {
 // one row id per staged float4 group), then two staging buffers of kMaxNodes
 // words (velocity components, double-buffered; then the fixed-point spread
 // accumulators of one force component)
-constexpr int kMaxRows = 1024;                                     // (y, z) rows per patch
-constexpr int kMaxNodes = 8960;                                    // staged nodes per buffer
+constexpr int kMaxRows = 4 * kMT;                                  // (y, z) rows per patch
+constexpr int kMaxNodes = 35 * kMT;                                // staged nodes per buffer
 constexpr int kRowTableBytes = ((4 * (7 * kMaxRows + 1) + 2 * (kMaxNodes / 4)) + 15) / 16 * 16;
 constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes;
 

@@ -44,33 +44,33 @@ struct DirWD {
 };
 
 // per-direction closed-form MLS factors for the fractional offset tp in
-// [-1/2, 1/2) of the point from its nearest node (cells)
+// [-1/2, 1/2) of the point from its nearest node (cells).  The weights enter
+// only through their ratios to the nearest node's,
+//   w(-1)/w(0) = exp(-kappa (1 + 2 tp)),  w(+1)/w(0) = exp(-kappa (1 - 2 tp)),
+// both in (0, 1], so two exponentials suffice and nothing overflows.
 __device__ __forceinline__ void dir_weights(float tp, float kappa, DirW& o) {
+  const float rm = __expf(-kappa * fmaf(2.f, tp, 1.f)), rp = __expf(-kappa * fmaf(-2.f, tp, 1.f));
+  const float invS = __fdividef(1.f, 1.f + rm + rp);
+  const float a0 = rm * invS, a1 = invS, a2 = rp * invS;
   const float d0 = -1.f - tp, d1 = -tp, d2 = 1.f - tp;
-  const float w0 = __expf(-kappa * d0 * d0), w1 = __expf(-kappa * d1 * d1),
-              w2 = __expf(-kappa * d2 * d2);
-  const float invS = 1.f / (w0 + w1 + w2);
-  const float a0 = w0 * invS, a1 = w1 * invS, a2 = w2 * invS;
   const float mu = a0 * d0 + a1 * d1 + a2 * d2;
   const float e0 = d0 - mu, e1 = d1 - mu, e2 = d2 - mu;
   const float s2 = a0 * e0 * e0 + a1 * e1 * e1 + a2 * e2 * e2;
-  const float r = mu / s2;
+  const float r = __fdividef(mu, s2);
   o.a[0] = a0; o.a[1] = a1; o.a[2] = a2;
   o.b[0] = a0 * r * e0; o.b[1] = a1 * r * e1; o.b[2] = a2 * r * e2;
 }
 
 // the same factors and their derivatives with respect to the point's
-// coordinate (in cells): the node offsets move as d delta / dt = -1
+// coordinate (in cells): the node offsets move as d delta / dt = -1, the
+// weight ratios as d rm / dt = -2 kappa rm, d rp / dt = 2 kappa rp
 __device__ __forceinline__ void dir_weights_d(float tp, float kappa, DirWD& o) {
-  float d[3] = {-1.f - tp, -tp, 1.f - tp};
-  float w[3], dw[3];
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    w[s] = __expf(-kappa * d[s] * d[s]);
-    dw[s] = w[s] * 2.f * kappa * d[s];
-  }
-  const float invS = 1.f / (w[0] + w[1] + w[2]);
-  const float dS = dw[0] + dw[1] + dw[2];
+  const float d[3] = {-1.f - tp, -tp, 1.f - tp};
+  const float rm = __expf(-kappa * fmaf(2.f, tp, 1.f)), rp = __expf(-kappa * fmaf(-2.f, tp, 1.f));
+  const float w[3] = {rm, 1.f, rp};
+  const float dw[3] = {-2.f * kappa * rm, 0.f, 2.f * kappa * rp};
+  const float invS = __fdividef(1.f, 1.f + rm + rp);
+  const float dS = dw[0] + dw[2];
   float a[3], da[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -84,7 +84,7 @@ __device__ __forceinline__ void dir_weights_d(float tp, float kappa, DirWD& o) {
   for (int s = 0; s < 3; ++s) e[s] = d[s] - mu;
   const float s2 = a[0] * e[0] * e[0] + a[1] * e[1] * e[1] + a[2] * e[2] * e[2];
   const float ds2 = da[0] * e[0] * e[0] + da[1] * e[1] * e[1] + da[2] * e[2] * e[2];
-  const float inv_s2 = 1.f / s2;
+  const float inv_s2 = __fdividef(1.f, s2);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const float beta = mu * e[s] * inv_s2;
@@ -213,12 +213,6 @@ __device__ __forceinline__ void mls_spread(float* f, const Acc& A, const DirW& X
   }
 }
 
-__device__ __forceinline__ void dir3(const float (&tp)[3], float kappa, DirW& X, DirW& Y, DirW& Z) {
-  dir_weights(tp[0], kappa, X);
-  dir_weights(tp[1], kappa, Y);
-  dir_weights(tp[2], kappa, Z);
-}
-
 // full-derivative MLS gradient (in cells) of component `comp` at a point
 template <class Acc>
 __device__ __forceinline__ void grad_at(const float* f, const Acc& A, const float (&tp)[3],
@@ -302,36 +296,72 @@ struct GlobalRows {
   }
 };
 
-// interpolated value at the centroid and full-derivative gradient (per unit
-// length) at the probe point(s) of one velocity component
-template <bool INTERP, bool PROBE, class Rows>
-__device__ __forceinline__ void velocity_component(const float* f, const Rows& R, int comp,
-                                                   const int (&G)[3], const float (&tc)[3],
-                                                   const float (&tp)[3], const float (&tm)[3],
-                                                   bool two, float kappa, const float (&invh)[3],
-                                                   float& Ul, float (&gr)[3]) {
-  if (INTERP) {
+// Nearest node and offset of a point on both lattices of every direction:
+// unshifted (the direction of the velocity component itself) and shifted by
+// half a cell (the other two components); the same values locate() gives.
+// Component c uses the unshifted lattice in direction c and the shifted one
+// in the other two, so the three components need six direction factors, not
+// nine.
+struct PointLat {
+  int cu[3], cs[3];
+  float tu[3], ts[3];
+  __device__ __forceinline__ void init(const float (&t)[3], const int (&G)[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float c0 = floorf(t[d] + 0.5f), c1 = floorf(t[d]);
+      tu[d] = t[d] - c0;
+      cu[d] = G[d] + (int)c0;
+      ts[d] = (t[d] - 0.5f) - c1;
+      cs[d] = G[d] + (int)c1;
+    }
+  }
+  __device__ __forceinline__ void node(int comp, int (&c)[3]) const {
+    c[0] = comp == 0 ? cu[0] : cs[0];
+    c[1] = comp == 1 ? cu[1] : cs[1];
+    c[2] = comp == 2 ? cu[2] : cs[2];
+  }
+};
+
+// The direction factors of the centroid for component comp, computed on
+// first use in the order 0, 1, 2: (Xu, Ys, Zs), then (Xs, Yu), then Zu.
+struct CentroidW {
+  DirW Xu, Xs, Yu, Ys, Zu, Zs;
+  __device__ __forceinline__ void prepare(int comp, const PointLat& P, float kappa) {
+    if (comp == 0) {
+      dir_weights(P.tu[0], kappa, Xu);
+      dir_weights(P.ts[1], kappa, Ys);
+      dir_weights(P.ts[2], kappa, Zs);
+    } else if (comp == 1) {
+      dir_weights(P.ts[0], kappa, Xs);
+      dir_weights(P.tu[1], kappa, Yu);
+    } else {
+      dir_weights(P.tu[2], kappa, Zu);
+    }
+  }
+  __device__ __forceinline__ const DirW& X(int comp) const { return comp == 0 ? Xu : Xs; }
+  __device__ __forceinline__ const DirW& Y(int comp) const { return comp == 1 ? Yu : Ys; }
+  __device__ __forceinline__ const DirW& Z(int comp) const { return comp == 2 ? Zu : Zs; }
+};
+
+// full-derivative gradient (per unit length) of one velocity component at the
+// probe point(s); an open sheet takes the difference of its two sides
+template <class Rows>
+__device__ __forceinline__ void probe_gradient(const float* f, const Rows& R, int comp,
+                                               const int (&G)[3], const float (&tp)[3],
+                                               const float (&tm)[3], bool two, float kappa,
+                                               const float (&invh)[3], float (&gr)[3]) {
+  gr[0] = gr[1] = gr[2] = 0.f;
+#pragma unroll 1
+  for (int l = 0; l < (two ? 2 : 1); ++l) {
     int cc[3];
     float t3[3];
-    locate(tc, comp, G, cc, t3);
-    DirW X, Y, Z;
-    dir3(t3, kappa, X, Y, Z);
-    Ul = mls_value(f, R.at(cc), X, Y, Z);
-  }
-  if (PROBE) {
-    gr[0] = gr[1] = gr[2] = 0.f;
-#pragma unroll 1
-    for (int l = 0; l < (two ? 2 : 1); ++l) {
-      int cc[3];
-      float t3[3];
-      locate(l == 0 ? tp : tm, comp, G, cc, t3);
-      float gl[3];
-      grad_at(f, R.at(cc), t3, kappa, gl);
-      // open sheet: (tau+ - tau-) . n+
-      const float sgn = l == 0 ? 1.f : -1.f;
+    locate(l == 0 ? tp : tm, comp, G, cc, t3);
+    float gl[3];
+    grad_at(f, R.at(cc), t3, kappa, gl);
+    // open sheet: (tau+ - tau-) . n+
+    const float sgn = l == 0 ? 1.f : -1.f;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) gr[j] += sgn * gl[j] * invh[j];
-    }
+    for (int j = 0; j < 3; ++j) gr[j] += sgn * gl[j] * invh[j];
   }
 }
 
@@ -383,7 +413,7 @@ __device__ __forceinline__ long long to_fixed(float x) {
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 
 template <bool MEASURE, bool INTERP, bool PROBE, bool SPREAD>
-__global__ void __launch_bounds__(kMT, 2) marker_kernel(
+__global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ v, const float* __restrict__ u, const float* __restrict__ vv,
     const float* __restrict__ w, float* __restrict__ U, float* __restrict__ Fm,
@@ -423,10 +453,11 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   bool ok = false;
   int gf = 0;
   if (active) {
-    // threads of a warp take faces spread over the patch (t -> 8 (t % 32) + t / 32
-    // for full patches), so that one warp's simultaneous shared atomics of the
-    // spread rarely meet on a node
-    const int slot = (ch.z == kMT) ? 8 * (threadIdx.x & 31) + (threadIdx.x >> 5) : threadIdx.x;
+    // threads of a warp take faces spread over the patch (t -> W (t % 32) + t / 32
+    // with W warps, for full patches), so that one warp's simultaneous shared
+    // atomics of the spread rarely meet on a node
+    const int slot =
+        (ch.z == kMT) ? (kMT / 32) * (threadIdx.x & 31) + (threadIdx.x >> 5) : threadIdx.x;
     const int4 mt = __ldg(T.mtri + topo.mface_off + ch.y + slot);
     gf = B.f_off + mt.w;
     const int ia = B.v_off + mt.x, ib = B.v_off + mt.y, ic = B.v_off + mt.z;
@@ -656,8 +687,11 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
   // Traction t = (G + G^T) n: component i yields (G n)_i and adds n_i G_i. to
   // G^T n.
   float Fl[3] = {vb[0], vb[1], vb[2]};   // marker force per component
+  PointLat PC;                           // the centroid on every lattice
+  PC.init(tc, B.G);
   if (VEL) {
     float tGn[3] = {0.f, 0.f, 0.f}, tGTn[3] = {0.f, 0.f, 0.f};
+    CentroidW CW;
     if (fit) {
       stage_async(bufA, u, RT, ngroups);
       cp_async_commit();
@@ -668,19 +702,17 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
     for (int comp = 0; comp < 3; ++comp) {
       const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
       const float* buf = comp == 1 ? bufB : bufA;
+      if (INTERP && mine) CW.prepare(comp, PC, sc.kappa);
       if (fit) {
         if (comp < 2) cp_async_wait<1>(); else cp_async_wait<0>();
         __syncthreads();   // every thread's copies of this component have landed
       }
       if (mine) {
-        float Ul = 0.f, gr[3];
-        if (fit)
-          velocity_component<INTERP, PROBE>(buf, SR, comp, B.G, tc, tp, tm, two, sc.kappa, g.invh,
-                                            Ul, gr);
-        else
-          velocity_component<INTERP, PROBE>(velc, GR, comp, B.G, tc, tp, tm, two, sc.kappa,
-                                            g.invh, Ul, gr);
         if (INTERP) {
+          int cc[3];
+          PC.node(comp, cc);
+          const float Ul = fit ? mls_value(buf, SR.at(cc), CW.X(comp), CW.Y(comp), CW.Z(comp))
+                               : mls_value(velc, GR.at(cc), CW.X(comp), CW.Y(comp), CW.Z(comp));
           const float Fc = (vb[comp] - Ul) * sc.inv_dt;
           if (comp == 0) Fl[0] = Fc;
           if (comp == 1) Fl[1] = Fc;
@@ -689,6 +721,11 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
           if (Fm) Fm[comp * F + gf] = Fc;
         }
         if (PROBE) {
+          float gr[3];
+          if (fit)
+            probe_gradient(buf, SR, comp, B.G, tp, tm, two, sc.kappa, g.invh, gr);
+          else
+            probe_gradient(velc, GR, comp, B.G, tp, tm, two, sc.kappa, g.invh, gr);
           const float gn = gr[0] * nrm[0] + gr[1] * nrm[1] + gr[2] * nrm[2];
           const float ni = comp == 0 ? nrm[0] : (comp == 1 ? nrm[1] : nrm[2]);
           if (comp == 0) tGn[0] = gn;
@@ -724,18 +761,20 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
         reinterpret_cast<int4*>(s_low)[q] = make_int4(0, 0, 0, 0);
       }
     }
-#pragma unroll 1
+    CentroidW CW;
+#pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       float* fc = comp == 0 ? fx : (comp == 1 ? fy : fz);
       float coef = 0.f;
-      DirW X, Y, Z;
       int cc[3];
       if (mine) {
-        float t3[3];
-        locate(tc, comp, B.G, cc, t3);
-        dir3(t3, sc.kappa, X, Y, Z);
-        coef = cl * (comp == 0 ? Fl[0] : (comp == 1 ? Fl[1] : Fl[2]));
+        CW.prepare(comp, PC, sc.kappa);
+        PC.node(comp, cc);
+        coef = cl * Fl[comp];
       }
+      const DirW& X = CW.X(comp);
+      const DirW& Y = CW.Y(comp);
+      const DirW& Z = CW.Z(comp);
       if (fit) {
         // block-wide bound on |coef phi| (non-negative floats order as ints)
         float bnd = mine ? fabsf(coef) * phi_bound(X, Y, Z) : 0.f;
@@ -812,7 +851,8 @@ __global__ void __launch_bounds__(kMT, 2) marker_kernel(
 // last spread: its rows' nonzero x-ranges, or its bounding box when it took
 // the global path.  Zeroing more than the footprint is harmless (everything
 // nonzero belongs to some recorded footprint), so vector rows are widened to
-// whole 32-byte sectors when nx allows, which avoids partial-sector writes.
+// whole 32-byte sectors when nx allows, which avoids partial-sector writes
+// (widening further to 64 bytes measured slower: more bytes written).
 __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, float* __restrict__ fx,
                                                     float* __restrict__ fy, float* __restrict__ fz,
                                                     int vec4) {
@@ -845,17 +885,15 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
   } else {
     const int nrows = sz.w;
     const int2* rm = T.rowmap + (size_t)blockIdx.x * kMaxRows;
-    const bool sect = (nx % 8) == 0;
+    const int al = nx % 8 == 0 ? 8 : 4;   // widening, in floats
     // a thread per row (rows are a few float4 groups long)
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
       const int2 e = rm[r];                  // (row base, first x wrapped | length << 16)
       int L = e.y >> 16, x0 = e.y & 0xFFFF;  // L <= nx, x0 < nx
       if (L <= 0) continue;
       if (vec4) {
-        if (sect) {
-          L = min((L + (x0 & 7) + 7) & ~7, nx);
-          x0 &= ~7;
-        }
+        L = min((L + (x0 & (al - 1)) + al - 1) & ~(al - 1), nx);
+        x0 &= ~(al - 1);
         for (int q = 0; q < L; q += 4) {
           int xg = x0 + q;
           if (xg >= nx) xg -= nx;

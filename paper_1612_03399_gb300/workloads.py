@@ -471,10 +471,14 @@ def shear_drops(n_bodies=256, level=4, n=256, radius=0.04, seed=3, steps=50):
                     notes={"D_target": target, "relaxed_placements": relaxed})
 
 
-def membranes(level=8, n=512, leaflet_faces=100_000, seed=4, steps=100):
+def membranes(level=8, n=512, leaflet_faces=100_000, seed=4, steps=100, dt=1e-4):
     """One closed ellipsoidal membrane (semi-axes 0.3, 0.3, 0.45) plus two
     clamped elliptic leaflet sheets (semi-axes 0.12, 0.08) at z = 0.5 +- 0.1
-    inside it; Fourier velocity with amplitude 2."""
+    inside it; Fourier velocity with amplitude 2.
+
+    dt = 1e-4: the leaflets' edges (about 8e-4) make their stiffest bending
+    mode omega ~ 7e3 for unit node mass, and the explicit step needs
+    omega dt < 2 (dt = 1e-3 would give 7.3)."""
     rng = np.random.default_rng(seed)
     v, t = icosphere(level)
     c = np.array([0.5, 0.5, 0.5])
@@ -488,7 +492,7 @@ def membranes(level=8, n=512, leaflet_faces=100_000, seed=4, steps=100):
                            ks=10.0, kb=1.0, ka=1.0, kA=0.0, kv=0.0, radius=0.12))
     fld = fourier_modes(32, 8, 2.0, rng)
     return Workload(name=f"membranes_L{level}_n{n}", bodies=bodies, grid=Grid((n, n, n)),
-                    field=fld, steps=steps, seed=seed)
+                    field=fld, steps=steps, seed=seed, dt=dt)
 
 
 def perturb_positions(wl: Workload, scale: float, seed: int, stretch: float = 0.0):

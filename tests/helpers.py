@@ -103,6 +103,16 @@ def tie_free(wl, xs_abs, margin=2e-5):
     return True
 
 
+def tie_flags(wl, xs_abs, margin=2e-5):
+    """Per body: faces whose centroid, and faces whose probe end(s), lie
+    within `margin` cells of a nearest-node switch."""
+    out = []
+    for p in marker_locations(wl, xs_abs):
+        d = tie_distance(p.reshape(-1, 3), wl.grid).reshape(-1, 3)
+        out.append({"centroid": d[:, 0] < margin, "probe": d[:, 1:].min(1) < margin})
+    return out
+
+
 def tie_mask(wl, xs_abs, margin=2e-5):
     """Per-face boolean (concatenated over bodies): True = safely away from
     every switch."""

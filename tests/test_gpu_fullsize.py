@@ -1,9 +1,12 @@
-"""Parity at the benchmarked size and launch configuration: 1000 icosphere
-drops on a 512^3 grid, one ibm_step exactly as bench.py runs it.  The oracle
-recomputes a sample of well-separated bodies on the same grid and field
-(their supports overlap no other body's, so the spread force on their
-footprint is theirs alone); the whole-field total force is checked against
-the markers' forces (no net gain or loss, Eq. mls_cl)."""
+"""Parity at the benchmarked sizes and launch configuration: one ibm_step
+exactly as bench.py runs it, on the three throughput workloads (1000 drops on
+512^3; 4096 uneven bodies of icosphere levels 2-5 on 768^3; the large
+membrane with two leaflet sheets on 512^3).  The oracle recomputes a sample
+of well-separated bodies on the same grid and field (their supports overlap
+no other body's, so the spread force on their footprint is theirs alone):
+three drops; one body of every level; one full leaflet sheet (open, clamped,
+two-sided probes).  The whole-field total force is checked against the
+markers' forces (no net gain or loss, Eq. mls_cl)."""
 import numpy as np
 import pytest
 import torch
@@ -18,34 +21,69 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda"
 
 
-def isolated(wl, k, min_gap_cells=10):
+def bound_radius(b):
+    return float(np.linalg.norm(b.rest - b.origin, axis=1).max())
+
+
+def isolated(wl, min_gap_cells=7.0):
+    """Indices of bodies whose bounding spheres keep min_gap_cells from every
+    other.  A marker spreads onto nodes at most 2 cells away per axis (2 sqrt 3
+    = 3.46 cells), so a gap above 6.93 cells keeps two bodies' footprints
+    disjoint."""
     c = np.array([b.origin for b in wl.bodies])
-    r = np.array([b.radius for b in wl.bodies])
+    r = np.array([bound_radius(b) for b in wl.bodies])
     h = wl.grid.h[0]
     d = c[:, None, :] - c[None, :, :]
     d -= np.round(d)
     gap = np.linalg.norm(d, axis=2) - r[:, None] - r[None, :]
     np.fill_diagonal(gap, np.inf)
-    ok = np.where(gap.min(1) > min_gap_cells * h)[0]
-    return ok[:k]
+    return np.where(gap.min(1) > min_gap_cells * h)[0]
 
 
-def test_full_size_step_sampled_parity(record_error):
-    wl = W.batched_drops(1000, 3, 512, seed=1)
+def pick_drops(wl):
+    return [int(i) for i in isolated(wl)[:3]]
+
+
+def pick_levels(wl):
+    ok = isolated(wl)
+    out = []
+    for lev in (2, 3, 4, 5):
+        cand = [int(i) for i in ok if wl.bodies[i].level == lev]
+        assert cand, f"no isolated body of level {lev}"
+        out.append(cand[0])
+    return out
+
+
+def pick_leaflet(wl):
+    assert not wl.bodies[1].closed
+    return [1]
+
+
+CASES = {
+    "drops1000": (lambda: W.batched_drops(1000, 3, 512, seed=1), pick_drops, 0.2),
+    "uneven4096": (lambda: W.uneven_bodies(4096, 768, seed=1), pick_levels, 0.2),
+    "membranes": (lambda: W.membranes(8, 512, seed=1), pick_leaflet, 0.05),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_full_size_step_sampled_parity(case, record_error):
+    make, pick_fn, vmax = CASES[case]
+    wl = make()
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
     fields = H.fields_for(wl, DEV)
     x, v = ctx.init_state()
     rng = np.random.default_rng(0)
     x += torch.tensor(rng.uniform(-1e-4, 1e-4, tuple(x.shape)), dtype=torch.float32, device=DEV)
-    v = torch.tensor(rng.uniform(-0.2, 0.2, tuple(v.shape)), dtype=torch.float32, device=DEV)
+    v = torch.tensor(rng.uniform(-vmax, vmax, tuple(v.shape)), dtype=torch.float32, device=DEV)
     n = wl.grid.n
     f = tuple(torch.zeros((n[2], n[1], n[0]), dtype=torch.float32, device=DEV) for _ in range(3))
     x1, v1 = torch.empty_like(x), torch.empty_like(v)
     ctx.step(x, v, fields, x1, v1, f)
     ctx.check_device_error()
+    assert ctx.counters()["marker_box_fallbacks"] == 0
     # whole-field conservation: sum_k dV f^k = sum_l dV^l F_l
     _, Fm, _ = ctx.interpolate(x, v, fields, U=False, F_marker=True, F_ext=False)
-    A = torch.zeros(ctx.F, dtype=torch.float64, device=DEV)
     xs_all = H.split_state(ctx, wl, x)
     areas = []
     for i, b in enumerate(wl.bodies):
@@ -58,33 +96,50 @@ def test_full_size_step_sampled_parity(record_error):
     rhs = (A[None, :] * hl * Fm.double()).sum(1)
     lhs = torch.stack([fi.double().sum() for fi in f]) * dV
     cons = float((lhs - rhs).abs().max() / rhs.abs().max())
-    record_error("conservation", cons)
+    record_error(f"{case}:conservation", cons)
     assert cons <= 1e-5
     # sampled bodies, recomputed by the oracle alone
-    pick = [int(i) for i in isolated(wl, 3)]
-    assert len(pick) == 3
+    pick = pick_fn(wl)
     sub = W.Workload(name="sample", bodies=[wl.bodies[i] for i in pick], grid=wl.grid,
                      field=wl.field, dt=wl.dt)
     ob = H.oracle_bodies(sub)
     xs = [torch.tensor(xs_all[i] + wl.bodies[i].origin) for i in pick]
     vall = H.split_state(ctx, wl, v)
     vs = [torch.tensor(vall[i]) for i in pick]
-    assert H.tie_free(sub, xs)
+    # Near a half-cell switch of the nearest-node choice the float32 kernel and
+    # the float64 oracle may pick different (both valid) stencils; with 1e5
+    # faces some markers always lie that close.  Those are left out: vertices
+    # of faces whose probe is near a switch, grid nodes within reach of a
+    # centroid near a switch.  Everything else must agree.
+    ties = H.tie_flags(sub, xs)
     f64 = tuple(fi.double().cpu() for fi in fields)
     out = O.step(ob, xs, vs, f64, H.oracle_params(sub))
     xg, vg = H.split_state(ctx, wl, x1), H.split_state(ctx, wl, v1)
     for j, i in enumerate(pick):
         xo = out["x_next"][j].numpy() - wl.bodies[i].origin
         assert H.rel_l2(xg[i], xo) <= 1e-6
-        vo = out["v_next"][j].numpy()
-        dv_o = vo - vs[j].numpy()
+        keep = np.ones(len(xo), dtype=bool)
+        keep[wl.bodies[i].tri[ties[j]["probe"]].ravel()] = False
+        record_error(f"{case}:dv_excluded_fraction[{i}]", 1.0 - keep.mean())
+        assert keep.mean() > 0.99
+        vo = out["v_next"][j].numpy()[keep]
+        v0 = vs[j].numpy()[keep]
+        dv_o = vo - v0
         store = np.linalg.norm(0.5 * np.spacing(np.abs(vo).astype(np.float32)).astype(np.float64))
-        excess = max(0.0, np.linalg.norm((vg[i] - vs[j].numpy()) - dv_o) - store) / np.linalg.norm(dv_o)
-        record_error(f"dv[{i}]", excess)
+        excess = max(0.0, np.linalg.norm((vg[i][keep] - v0) - dv_o) - store) / np.linalg.norm(dv_o)
+        record_error(f"{case}:dv[{i}]", excess)
         assert excess <= 1e-5
     fo = out["f"].numpy()
     mask = np.abs(fo).sum(0) > 0
+    for j, i in enumerate(pick):
+        c = H.marker_locations(W.Workload(name="one", bodies=[wl.bodies[i]], grid=wl.grid,
+                                          field=wl.field), [xs[j]])[0][:, 0]
+        for t in c[ties[j]["centroid"]] / np.array(wl.grid.h):
+            lo = np.floor(t).astype(int) - 2
+            ix, iy, iz = (np.arange(lo[d], lo[d] + 5) % n[d] for d in range(3))
+            mask[np.ix_(iz, iy, ix)] = False
+    record_error(f"{case}:f_nodes_compared", float(mask.sum()))
     got = torch.stack(f).cpu().numpy()
     e = H.rel_l2(got[:, mask], fo[:, mask])
-    record_error("f_sampled", e)
+    record_error(f"{case}:f_sampled", e)
     assert e <= 1e-5
