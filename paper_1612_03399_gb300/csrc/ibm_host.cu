@@ -321,6 +321,12 @@ void free_all(ibm_ctx* c) {
 
 bool is_fin(double v) { return std::isfinite(v); }
 
+// select body-sum buffer p (0 or 1) for the launches that follow
+void use_parity(ibm_ctx* c, int p) {
+  c->qpar = p;
+  c->d.qsum = c->qsum_base + 2 * (size_t)c->B * p;
+}
+
 // power-of-two scale 2^e with ref * 2^e in [2^39, 2^40): the body's sum then
 // has 2^22 of headroom in a 64-bit integer; false when 2^e is not a normal
 // float
@@ -660,7 +666,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.rest = upload(c, rest);
     d.chunks = upload(c, chunks);
     d.work = upload(c, work);
-    d.qsum = zeros<unsigned long long>(c, 2 * (size_t)n_bodies);
+    c->qsum_base = zeros<unsigned long long>(c, 4 * (size_t)n_bodies);
+    d.qsum = c->qsum_base;
     d.meas = zeros<double>(c, 2 * (size_t)n_bodies);
     d.fext = zeros<float>(c, 3 * (size_t)F);
     d.err = zeros<int32_t>(c, 1);
@@ -846,6 +853,7 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     return set_err(c, IBM_ERR_INVALID_ARG, "ibm_step: outputs must not alias the inputs");
   cudaSetDevice(c->device);
   const bool clear = (flags & IBM_STEP_CLEAR_PREV) != 0;
+  use_parity(c, c->qpar ^ 1);
   cudaError_t e = cudaSuccess;
   auto mark = [&](int k) {
     if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[k], c->stream);
@@ -907,13 +915,45 @@ extern "C" ibm_status ibm_graph_create(ibm_ctx* c, float* xa, float* va, float* 
   ibm_graph* g = new ibm_graph();
   g->ctx = c;
   ibm_status st = IBM_OK;
-  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  // A side stream carries each step's clear of the previous footprint: inside
+  // the graph the force fields of intermediate steps are never observed, so
+  // step k+1's clear runs concurrently with step k's force kernel (it needs
+  // only step k's recorded footprint); step k+1's marker kernel waits for it.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_marker = nullptr, ev_clear = nullptr;
+  e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_marker, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_clear, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int k = 0; k < n_steps && st == IBM_OK; ++k) {
+    for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
       const bool even = (k & 1) == 0;
-      st = ibm_step(c, even ? xa : xb, even ? va : vb, u, vv, w, even ? xb : xa, even ? vb : va,
-                    fx, fy, fz, IBM_STEP_CLEAR_PREV);
+      const float* x = even ? xa : xb;
+      const float* v = even ? va : vb;
+      use_parity(c, c->qpar ^ 1);
+      if (k == 0) e = launch_clear(c, fx, fy, fz);
+      if (e == cudaSuccess)
+        e = launch_mls(c, x, v, u, vv, w, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz, true,
+                       true, true, true, true);
+      const bool next = k + 1 < n_steps;
+      if (next && e == cudaSuccess) {
+        e = cudaEventRecord(ev_marker, cap);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_marker, 0);
+        // the next step's clear, with the next step's body-sum buffer
+        const int p = c->qpar;
+        c->stream = side;
+        use_parity(c, p ^ 1);
+        if (e == cudaSuccess) e = launch_clear(c, fx, fy, fz);
+        use_parity(c, p);
+        c->stream = cap;
+        if (e == cudaSuccess) e = cudaEventRecord(ev_clear, side);
+      }
+      if (e == cudaSuccess)
+        e = launch_force(c, x, v, c->d.fext, nullptr, even ? xb : xa, even ? vb : va, nullptr,
+                         true);
+      if (next && e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev_clear, 0);
     }
+    if (e != cudaSuccess) st = cuda_status(c, e, "ibm_graph_create");
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
     if (e2 == cudaSuccess && st == IBM_OK) {
@@ -926,7 +966,11 @@ extern "C" ibm_status ibm_graph_create(ibm_ctx* c, float* xa, float* va, float* 
   }
   c->stream = saved;
   c->timing = timing;
+  if (st == IBM_OK && e == cudaSuccess) c->have_prev = true;
   cudaStreamDestroy(cap);
+  if (side) cudaStreamDestroy(side);
+  if (ev_marker) cudaEventDestroy(ev_marker);
+  if (ev_clear) cudaEventDestroy(ev_clear);
   if (st != IBM_OK || e != cudaSuccess) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);

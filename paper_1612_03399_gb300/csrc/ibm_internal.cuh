@@ -110,7 +110,8 @@ struct DeviceTables {
   int4* chunks = nullptr;       // (body, offset in the topology's mface list, count,
                                 //  chunk index in body): one marker patch each
   int2* work = nullptr;         // (body, patch index within topology)
-  unsigned long long* qsum = nullptr;  // [B][2] fixed-point (A, V) sums of the marker kernel
+  unsigned long long* qsum = nullptr;  // [B][2] fixed-point (A, V) sums of the marker kernel:
+                                       // one of two buffers, alternating between steps
   double* meas = nullptr;       // [B][2] (A, V) (formed from qsum by the finalize kernel)
   float2* coef = nullptr;       // [B] (k_A (A - A0)/A0, k_v (V - V0)/V0) (likewise)
   float* fext = nullptr;        // [3][F] scratch marker traction (ibm_step)
@@ -176,6 +177,11 @@ struct ibm_ctx {
   size_t adjoint_smem = 0;
   int32_t max_own = 0;
   bool have_prev = false;
+  // the body sums alternate between two buffers from one ibm_step to the next,
+  // so that a step's clear may zero its buffer while the previous step's force
+  // kernel still reads the other (overlap inside captured multi-step graphs)
+  unsigned long long* qsum_base = nullptr;   // [2][B][2]
+  int qpar = 0;
   bool timing = false;          // record phase events in ibm_step
   bool timed = false;           // a timed step has been recorded
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

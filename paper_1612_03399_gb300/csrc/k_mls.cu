@@ -343,27 +343,29 @@ struct CentroidW {
   __device__ __forceinline__ const DirW& Z(int comp) const { return comp == 2 ? Zu : Zs; }
 };
 
-// full-derivative gradient (per unit length) of one velocity component at the
-// probe point(s); an open sheet takes the difference of its two sides
-template <class Rows>
-__device__ __forceinline__ void probe_gradient(const float* f, const Rows& R, int comp,
-                                               const int (&G)[3], const float (&tp)[3],
-                                               const float (&tm)[3], bool two, float kappa,
-                                               const float (&invh)[3], float (&gr)[3]) {
-  gr[0] = gr[1] = gr[2] = 0.f;
-#pragma unroll 1
-  for (int l = 0; l < (two ? 2 : 1); ++l) {
-    int cc[3];
+// nearest node and derivative factors of one component at a probe point
+struct ProbeW {
+  int cc[3];
+  DirWD X, Y, Z;
+  __device__ __forceinline__ void prepare(const float (&t)[3], int comp, const int (&G)[3],
+                                          float kappa) {
     float t3[3];
-    locate(l == 0 ? tp : tm, comp, G, cc, t3);
+    locate(t, comp, G, cc, t3);
+    dir_weights_d(t3[0], kappa, X);
+    dir_weights_d(t3[1], kappa, Y);
+    dir_weights_d(t3[2], kappa, Z);
+  }
+  // full-derivative gradient per unit length, times sgn, added to gr
+  template <class Rows>
+  __device__ __forceinline__ void add_gradient(const float* f, const Rows& R,
+                                               const float (&invh)[3], float sgn,
+                                               float (&gr)[3]) const {
     float gl[3];
-    grad_at(f, R.at(cc), t3, kappa, gl);
-    // open sheet: (tau+ - tau-) . n+
-    const float sgn = l == 0 ? 1.f : -1.f;
+    mls_grad(f, R.at(cc), X, Y, Z, gl);
 #pragma unroll
     for (int j = 0; j < 3; ++j) gr[j] += sgn * gl[j] * invh[j];
   }
-}
+};
 
 // bound on |phi| over the 27 nodes: phi = a_x a_y a_z - b_x a_y a_z - a_x b_y a_z
 // - a_x a_y b_z, so |phi| <= prod_d (max|a_d| + max|b_d|)
@@ -702,12 +704,35 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     for (int comp = 0; comp < 3; ++comp) {
       const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
       const float* buf = comp == 1 ? bufB : bufA;
+      // the centroid's factors first: their arithmetic overlaps the copies
+      // still in flight (the probe's as well would not fit in registers)
       if (INTERP && mine) CW.prepare(comp, PC, sc.kappa);
       if (fit) {
         if (comp < 2) cp_async_wait<1>(); else cp_async_wait<0>();
         __syncthreads();   // every thread's copies of this component have landed
       }
       if (mine) {
+        if (PROBE) {
+          // open sheet: (tau+ - tau-) . n+
+          float gr[3] = {0.f, 0.f, 0.f};
+          ProbeW P0;
+          P0.prepare(tp, comp, B.G, sc.kappa);
+          if (fit) P0.add_gradient(buf, SR, g.invh, 1.f, gr);
+          else P0.add_gradient(velc, GR, g.invh, 1.f, gr);
+          if (two) {
+            ProbeW P1;
+            P1.prepare(tm, comp, B.G, sc.kappa);
+            if (fit) P1.add_gradient(buf, SR, g.invh, -1.f, gr);
+            else P1.add_gradient(velc, GR, g.invh, -1.f, gr);
+          }
+          const float gn = gr[0] * nrm[0] + gr[1] * nrm[1] + gr[2] * nrm[2];
+          const float ni = comp == 0 ? nrm[0] : (comp == 1 ? nrm[1] : nrm[2]);
+          if (comp == 0) tGn[0] = gn;
+          if (comp == 1) tGn[1] = gn;
+          if (comp == 2) tGn[2] = gn;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) tGTn[j] += ni * gr[j];
+        }
         if (INTERP) {
           int cc[3];
           PC.node(comp, cc);
@@ -719,20 +744,6 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
           if (comp == 2) Fl[2] = Fc;
           if (U) U[comp * F + gf] = Ul;
           if (Fm) Fm[comp * F + gf] = Fc;
-        }
-        if (PROBE) {
-          float gr[3];
-          if (fit)
-            probe_gradient(buf, SR, comp, B.G, tp, tm, two, sc.kappa, g.invh, gr);
-          else
-            probe_gradient(velc, GR, comp, B.G, tp, tm, two, sc.kappa, g.invh, gr);
-          const float gn = gr[0] * nrm[0] + gr[1] * nrm[1] + gr[2] * nrm[2];
-          const float ni = comp == 0 ? nrm[0] : (comp == 1 ? nrm[1] : nrm[2]);
-          if (comp == 0) tGn[0] = gn;
-          if (comp == 1) tGn[1] = gn;
-          if (comp == 2) tGn[2] = gn;
-#pragma unroll
-          for (int j = 0; j < 3; ++j) tGTn[j] += ni * gr[j];
         }
       }
       if (fit && comp == 0) {
