@@ -130,8 +130,11 @@ ibm_status ibm_init_state(ibm_ctx* ctx, float* x, float* v);
 ibm_status ibm_set_body_constants(ibm_ctx* ctx, const double* consts);
 
 /* Per-body surface area A and enclosed volume V (Sec. 2.3: the global area
- * and volume of the potentials), summed in float64 in a fixed order:
- * out[B][2] = (A, V); V is 0 for open bodies. */
+ * and volume of the potentials): out[B][2] float64 = (A, V); V is 0 for open
+ * bodies.  Each face's float32 area (signed tetrahedron volume) is scaled by a
+ * power of two chosen from the body's rest value, rounded to a 64-bit
+ * integer and summed exactly, so the sums are independent of summation order
+ * and carry a resolution of 2^-39 of the rest value (headroom 2^22). */
 ibm_status ibm_body_measures(ibm_ctx* ctx, const float* x, double* out);
 
 /* (a) Internal forces F_int = -grad(W_e + W_b + W_a + W_A + W_v) at x
@@ -207,9 +210,12 @@ ibm_status ibm_taylor_backward(ibm_ctx* ctx, const float* x, const double* gD, f
  * with the footprint clear: steps alternate (xa, va) -> (xb, vb) and back,
  * so after a launch the state is again in (xa, va).  The buffers and fields
  * are bound at creation; ibm_graph_launch replays the whole sequence on the
- * context's stream with one launch.  Creation captures on a private stream
- * after the work already queued on the context's stream.  The context must
- * outlive the graph. */
+ * context's stream with one launch.  Inside the graph the force fields of the
+ * intermediate steps are never observed, so each step's footprint clear runs
+ * concurrently with the previous step's force kernel; after a launch fx, fy,
+ * fz hold exactly the last step's forces.  Creation captures on a private
+ * stream after the work already queued on the context's stream.  The context
+ * must outlive the graph. */
 typedef struct ibm_graph ibm_graph;
 ibm_status ibm_graph_create(ibm_ctx* ctx, float* xa, float* va, float* xb, float* vb,
                             const float* u, const float* vv, const float* w, float* fx, float* fy,

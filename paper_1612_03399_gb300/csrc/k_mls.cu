@@ -296,53 +296,6 @@ struct GlobalRows {
   }
 };
 
-// Nearest node and offset of a point on both lattices of every direction:
-// unshifted (the direction of the velocity component itself) and shifted by
-// half a cell (the other two components); the same values locate() gives.
-// Component c uses the unshifted lattice in direction c and the shifted one
-// in the other two, so the three components need six direction factors, not
-// nine.
-struct PointLat {
-  int cu[3], cs[3];
-  float tu[3], ts[3];
-  __device__ __forceinline__ void init(const float (&t)[3], const int (&G)[3]) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const float c0 = floorf(t[d] + 0.5f), c1 = floorf(t[d]);
-      tu[d] = t[d] - c0;
-      cu[d] = G[d] + (int)c0;
-      ts[d] = (t[d] - 0.5f) - c1;
-      cs[d] = G[d] + (int)c1;
-    }
-  }
-  __device__ __forceinline__ void node(int comp, int (&c)[3]) const {
-    c[0] = comp == 0 ? cu[0] : cs[0];
-    c[1] = comp == 1 ? cu[1] : cs[1];
-    c[2] = comp == 2 ? cu[2] : cs[2];
-  }
-};
-
-// The direction factors of the centroid for component comp, computed on
-// first use in the order 0, 1, 2: (Xu, Ys, Zs), then (Xs, Yu), then Zu.
-struct CentroidW {
-  DirW Xu, Xs, Yu, Ys, Zu, Zs;
-  __device__ __forceinline__ void prepare(int comp, const PointLat& P, float kappa) {
-    if (comp == 0) {
-      dir_weights(P.tu[0], kappa, Xu);
-      dir_weights(P.ts[1], kappa, Ys);
-      dir_weights(P.ts[2], kappa, Zs);
-    } else if (comp == 1) {
-      dir_weights(P.ts[0], kappa, Xs);
-      dir_weights(P.tu[1], kappa, Yu);
-    } else {
-      dir_weights(P.tu[2], kappa, Zu);
-    }
-  }
-  __device__ __forceinline__ const DirW& X(int comp) const { return comp == 0 ? Xu : Xs; }
-  __device__ __forceinline__ const DirW& Y(int comp) const { return comp == 1 ? Yu : Ys; }
-  __device__ __forceinline__ const DirW& Z(int comp) const { return comp == 2 ? Zu : Zs; }
-};
-
 // nearest node and derivative factors of one component at a probe point
 struct ProbeW {
   int cc[3];
@@ -689,24 +642,31 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   // Traction t = (G + G^T) n: component i yields (G n)_i and adds n_i G_i. to
   // G^T n.
   float Fl[3] = {vb[0], vb[1], vb[2]};   // marker force per component
-  PointLat PC;                           // the centroid on every lattice
-  PC.init(tc, B.G);
   if (VEL) {
     float tGn[3] = {0.f, 0.f, 0.f}, tGTn[3] = {0.f, 0.f, 0.f};
-    CentroidW CW;
     if (fit) {
       stage_async(bufA, u, RT, ngroups);
       cp_async_commit();
       stage_async(bufB, vv, RT, ngroups);
       cp_async_commit();
     }
-#pragma unroll
+    // the components in a loop, not unrolled: the unrolled kernel measured
+    // slower (instruction fetch stalls)
+#pragma unroll 1
     for (int comp = 0; comp < 3; ++comp) {
       const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
       const float* buf = comp == 1 ? bufB : bufA;
       // the centroid's factors first: their arithmetic overlaps the copies
       // still in flight (the probe's as well would not fit in registers)
-      if (INTERP && mine) CW.prepare(comp, PC, sc.kappa);
+      DirW CX, CY, CZ;
+      int ccC[3];
+      if (INTERP && mine) {
+        float t3[3];
+        locate(tc, comp, B.G, ccC, t3);
+        dir_weights(t3[0], sc.kappa, CX);
+        dir_weights(t3[1], sc.kappa, CY);
+        dir_weights(t3[2], sc.kappa, CZ);
+      }
       if (fit) {
         if (comp < 2) cp_async_wait<1>(); else cp_async_wait<0>();
         __syncthreads();   // every thread's copies of this component have landed
@@ -734,11 +694,9 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
           for (int j = 0; j < 3; ++j) tGTn[j] += ni * gr[j];
         }
         if (INTERP) {
-          int cc[3];
-          PC.node(comp, cc);
-          const float Ul = fit ? mls_value(buf, SR.at(cc), CW.X(comp), CW.Y(comp), CW.Z(comp))
-                               : mls_value(velc, GR.at(cc), CW.X(comp), CW.Y(comp), CW.Z(comp));
-          const float Fc = (vb[comp] - Ul) * sc.inv_dt;
+          const float Ul = fit ? mls_value(buf, SR.at(ccC), CX, CY, CZ)
+                               : mls_value(velc, GR.at(ccC), CX, CY, CZ);
+          const float Fc = ((comp == 0 ? vb[0] : (comp == 1 ? vb[1] : vb[2])) - Ul) * sc.inv_dt;
           if (comp == 0) Fl[0] = Fc;
           if (comp == 1) Fl[1] = Fc;
           if (comp == 2) Fl[2] = Fc;
@@ -772,20 +730,22 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
         reinterpret_cast<int4*>(s_low)[q] = make_int4(0, 0, 0, 0);
       }
     }
-    CentroidW CW;
-#pragma unroll
+    // the components in a loop, not unrolled: the unrolled kernel measured
+    // slower (instruction fetch stalls)
+#pragma unroll 1
     for (int comp = 0; comp < 3; ++comp) {
       float* fc = comp == 0 ? fx : (comp == 1 ? fy : fz);
       float coef = 0.f;
       int cc[3];
+      DirW X, Y, Z;
       if (mine) {
-        CW.prepare(comp, PC, sc.kappa);
-        PC.node(comp, cc);
-        coef = cl * Fl[comp];
+        float t3[3];
+        locate(tc, comp, B.G, cc, t3);
+        dir_weights(t3[0], sc.kappa, X);
+        dir_weights(t3[1], sc.kappa, Y);
+        dir_weights(t3[2], sc.kappa, Z);
+        coef = cl * (comp == 0 ? Fl[0] : (comp == 1 ? Fl[1] : Fl[2]));
       }
-      const DirW& X = CW.X(comp);
-      const DirW& Y = CW.Y(comp);
-      const DirW& Z = CW.Z(comp);
       if (fit) {
         // block-wide bound on |coef phi| (non-negative floats order as ints)
         float bnd = mine ? fabsf(coef) * phi_bound(X, Y, Z) : 0.f;
