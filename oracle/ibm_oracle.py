@@ -49,10 +49,16 @@ reason, in the design notes of the repository):
      "internal force of the previous time step"; v^0 = 0.  Forward Euler is a
      flag.
   R9 x in W_e is l - l0 with l0 the rest length; k_e = k_s uniform.
-  R10 frozen flow: p = 0, no marker-acceleration term, viscosity mu (1), probe
-     length h = mean grid spacing.
+  R10 frozen flow: p = 0 unless a pressure field is supplied, viscosity mu
+     (1), probe length h = mean grid spacing.
   R11 the probe gradient uses the full derivative of the shape function.
   R12 node mass m per body (1 for drops).
+  R16 pressure (when supplied) lives at the cell centres, (i+1/2, j+1/2,
+     k+1/2) h; the marker acceleration Du/Dt of the correction
+     p_l = p* + h (Du/Dt).n is the mean of the face's three vertex
+     accelerations, which the caller supplies (e.g. (v^n - v^(n-1))/dt).
+  R17 open sheets: each side takes p^+- = p*^+- + h (Du/Dt).n^+- with
+     n^+- = +-n^+, and the load is -(p^+ - p^-) n^+ A.
 """
 from __future__ import annotations
 
@@ -62,8 +68,9 @@ import torch
 
 DT = torch.float64
 
-MAC_OFFSET = ((0.0, 0.5, 0.5), (0.5, 0.0, 0.5), (0.5, 0.5, 0.0))
-"""Offsets in cells of the u, v, w node lattices (reading R5)."""
+MAC_OFFSET = ((0.0, 0.5, 0.5), (0.5, 0.0, 0.5), (0.5, 0.5, 0.0), (0.5, 0.5, 0.5))
+"""Offsets in cells of the u, v, w node lattices (reading R5) and of the
+cell-centred pressure lattice (index 3, reading R16)."""
 
 
 # --------------------------------------------------------------------------
@@ -345,20 +352,36 @@ def spread(F, P, A_l, n, h, alpha, out=None):
     return torch.stack(fields)
 
 
-def probe_traction(fields, C, nrm, A_l, n, h, alpha, mu, probe_h, two_sided):
-    """External load per face, F_ext = (-p n + tau . n) A (Sec. 2.2) with
-    p = 0 for the frozen flow (reading R10) and tau = mu (grad u + grad u^T)
-    from the MLS gradient at the probe end c + h n.  Two-sided for open
-    sheets: F_ext = (tau+ - tau-) . n+ A."""
+def probe_traction(fields, C, nrm, A_l, n, h, alpha, mu, probe_h, two_sided, pressure=None,
+                   accel=None):
+    """External load per face, F_ext = (-p n + tau . n) A (Sec. 2.2), with
+    tau = mu (grad u + grad u^T) from the MLS gradient at the probe end
+    c + h n, and p = 0 (frozen flow, reading R10) or, with a pressure field,
+    p = p* + h (Du/Dt).n with p* interpolated at the probe end and Du/Dt the
+    marker acceleration accel [M,3] (zero if None; reading R16).  Two-sided
+    for open sheets: F_ext = (-(p+ - p-) n+ + (tau+ - tau-) . n+) A, each side
+    with its own normal +-n+ (reading R17)."""
 
     def tau_dot_n(Pp):
         G = torch.stack([interpolate_gradient(fields[i], Pp, i, n, h, alpha) for i in range(3)], 1)
         tau = mu * (G + G.transpose(1, 2))                       # [M,3,3], G[i,j] = du_i/dx_j
         return torch.einsum("mij,mj->mi", tau, nrm)
 
+    def marker_pressure(side):
+        ns = side * nrm
+        p_star = interpolate(pressure, C + probe_h * ns, 3, n, h, alpha)
+        if accel is None:
+            return p_star
+        return p_star + probe_h * (accel * ns).sum(1)
+
     F = tau_dot_n(C + probe_h * nrm)
     if two_sided:
         F = F - tau_dot_n(C - probe_h * nrm)
+    if pressure is not None:
+        p = marker_pressure(1.0)
+        if two_sided:
+            p = p - marker_pressure(-1.0)
+        F = F - p[:, None] * nrm
     return F * A_l[:, None]
 
 
@@ -386,21 +409,29 @@ class Params:
         self.forward_euler = bool(forward_euler)
 
 
-def step(bodies, xs, vs, fields, prm: Params, create_graph=False, with_spread=True):
+def step(bodies, xs, vs, fields, prm: Params, create_graph=False, with_spread=True,
+         pressure=None, accels=None):
     """One step for every body.  xs, vs: lists of [V,3] absolute positions
-    and velocities; fields: (u, v, w) [nz,ny,nx] float64.  Returns a dict with
-    x_next, v_next (lists), F_int, F_ext_vertex (lists), and per-marker U,
-    F_marker, F_ext_face, plus the spread force fields f [3,nz,ny,nx]."""
+    and velocities; fields: (u, v, w) [nz,ny,nx] float64; pressure: None or
+    the cell-centred pressure [nz,ny,nx]; accels: None or a list of [V,3]
+    vertex accelerations (the marker acceleration is their face mean).
+    Returns a dict with x_next, v_next (lists), F_int, F_ext_vertex (lists),
+    and per-marker U, F_marker, F_ext_face, plus the spread force fields
+    f [3,nz,ny,nx]."""
     n, h, alpha, dt = prm.n, prm.h, prm.alpha, prm.dt
     x_next, v_next, Fint_l, Fextv_l = [], [], [], []
     Us, Fms, Fes, Ps, As = [], [], [], [], []
-    for b, x, v in zip(bodies, xs, vs):
+    for ib, (b, x, v) in enumerate(zip(bodies, xs, vs)):
         C, nrm, A_l = face_geometry(x, b.tri)                                # steps 1, 2
+        acc_l = None
+        if pressure is not None and accels is not None:
+            a = accels[ib]
+            acc_l = (a[b.tri[:, 0]] + a[b.tri[:, 1]] + a[b.tri[:, 2]]) / 3.0
         Vb = (v[b.tri[:, 0]] + v[b.tri[:, 1]] + v[b.tri[:, 2]]) / 3.0       # marker velocity
         U = torch.stack([interpolate(fields[i], C, i, n, h, alpha) for i in range(3)], 1)   # 3b
         Fm = (Vb - U) / dt                                                   # F = (V^b - U)/dt
         Fe = probe_traction(fields, C, nrm, A_l, n, h, alpha, prm.mu, prm.probe_h,
-                            two_sided=not b.closed)                          # 4a
+                            two_sided=not b.closed, pressure=pressure, accel=acc_l)   # 4a
         Fev = distribute_to_vertices(Fe, b.tri, b.nv)
         Fi = b.internal_forces(x, create_graph=create_graph)                # 4c
         acc = (Fev + Fi) / b.mass

@@ -392,6 +392,55 @@ def sample_field(spec: dict, grid: Grid, device="cpu", dtype=None):
     return tuple(out)
 
 
+PRESSURE_OFFSET = (0.5, 0.5, 0.5)
+"""Node offsets, in cells, of the pressure lattice: cell centres."""
+
+
+def pressure_modes(n_modes: int, kmax: int, amplitude: float, rng: np.random.Generator):
+    """Random scalar Fourier modes p(x) = sum_m a_m sin(2 pi k_m.x + p_m),
+    integer wavevectors 1 <= |k_m| <= kmax, amplitudes a_m = amplitude * U[-1, 1]."""
+    ks = []
+    while len(ks) < n_modes:
+        k = rng.integers(-kmax, kmax + 1, 3)
+        if 1.0 <= np.linalg.norm(k) <= kmax:
+            ks.append(k)
+    a = amplitude * rng.uniform(-1.0, 1.0, n_modes)
+    phase = rng.uniform(0.0, 2.0 * math.pi, n_modes)
+    return {"kind": "fourier", "k": np.array(ks, dtype=np.int64), "a": a, "phase": phase}
+
+
+def sample_pressure(spec: dict, grid: Grid, device="cpu", dtype=None):
+    """A scalar field [nz, ny, nx] at the cell centres: {"kind": "uniform",
+    "p": p0}, {"kind": "linear", "p": p0, "G": (gx, gy, gz)} (p = p0 + G.x) or
+    a pressure_modes() dict."""
+    import torch
+    dtype = dtype or torch.float32
+    nx, ny, nz = grid.n
+    hx, hy, hz = grid.h
+    off = PRESSURE_OFFSET
+    x = (torch.arange(nx, dtype=torch.float64, device=device) + off[0]) * hx
+    y = (torch.arange(ny, dtype=torch.float64, device=device) + off[1]) * hy
+    z = (torch.arange(nz, dtype=torch.float64, device=device) + off[2]) * hz
+    if spec["kind"] == "uniform":
+        return torch.full((nz, ny, nx), float(spec["p"]), dtype=dtype, device=device)
+    if spec["kind"] == "linear":
+        g = [float(v) for v in spec["G"]]
+        f = (float(spec["p"]) + g[0] * x.view(1, 1, nx) + g[1] * y.view(1, ny, 1)
+             + g[2] * z.view(nz, 1, 1)).expand(nz, ny, nx)
+        return f.to(dtype).contiguous()
+    cdt = torch.complex128 if dtype == torch.float64 else torch.complex64
+    acc = torch.zeros((nz, ny, nx), dtype=dtype, device=device)
+    for m in range(len(spec["phase"])):
+        k = spec["k"][m]
+        a = float(spec["a"][m])
+        ex = torch.exp(1j * (2 * math.pi * k[0] / grid.L[0]) * x).to(cdt)
+        ey = torch.exp(1j * (2 * math.pi * k[1] / grid.L[1]) * y).to(cdt)
+        ez = torch.exp(1j * ((2 * math.pi * k[2] / grid.L[2]) * z + float(spec["phase"][m]))).to(cdt)
+        plane = (ez.view(nz, 1) * ey.view(1, ny)) * a
+        acc += (plane.view(nz, ny, 1) * ex.view(1, 1, nx)).imag.to(dtype)
+    return acc.contiguous()
+
+
 # --------------------------------------------------------------------------
 # named workloads (the benchmarked configurations and their small variants)
 # --------------------------------------------------------------------------
