@@ -146,11 +146,16 @@ ibm_status ibm_compute_forces(ibm_ctx* ctx, const float* x, float* F_int, double
 /* (b) MLS interpolation at the face centroids of the staggered velocity
  * (u, v, w) (Sec. 2.2, Eqs. mls..mls_Q), direct-forcing marker force
  * F = (V^b - U)/dt with V^b the mean velocity of the face's three nodes, and
- * probe traction F_ext = (tau . n) A (p = 0, frozen flow; two probes on open
- * sheets).  Outputs [3][F], each may be NULL. */
+ * probe traction F_ext = (-p n + tau . n) A (two probes on open sheets:
+ * F_ext = (-(p+ - p-) n+ + (tau+ - tau-) . n+) A).
+ * p: NULL (p = 0) or the pressure [nz][ny][nx] at the cell centres
+ * ((i+1/2, j+1/2, k+1/2) h); the marker pressure is p* + h (Du/Dt).n with p*
+ * interpolated at the probe end and Du/Dt the mean over the face's three
+ * vertices of accel [3][V] (NULL: zero), each side of an open sheet with its
+ * own normal.  Outputs [3][F], each may be NULL. */
 ibm_status ibm_interpolate(ibm_ctx* ctx, const float* x, const float* v, const float* u,
-                           const float* vv, const float* w, float* U, float* F_marker,
-                           float* F_ext);
+                           const float* vv, const float* w, const float* p, const float* accel,
+                           float* U, float* F_marker, float* F_ext);
 
 /* (c) Node update with F_ext^v = sum over faces of F_ext/3 (Sec. 2.3) and the
  * given F_int: symplectic (default) or forward Euler; clamped nodes keep x and
@@ -168,12 +173,13 @@ ibm_status ibm_spread(ibm_ctx* ctx, const float* x, const float* F_marker, float
                                    context spread to, before spreading this step   */
 
 /* One whole step (a)-(d) in three launches: x, v -> x_out, v_out (must not
- * alias x, v), spreading this step's marker forces into fx, fy, fz.  With
+ * alias x, v), spreading this step's marker forces into fx, fy, fz.  p and
+ * accel as in ibm_interpolate (both may be NULL).  With
  * IBM_STEP_CLEAR_PREV the fields hold exactly this step's forces afterwards,
  * provided they held only the previous ibm_step's forces (or zeros) before. */
 ibm_status ibm_step(ibm_ctx* ctx, const float* x, const float* v, const float* u,
-                    const float* vv, const float* w, float* x_out, float* v_out, float* fx,
-                    float* fy, float* fz, uint32_t flags);
+                    const float* vv, const float* w, const float* p, const float* accel,
+                    float* x_out, float* v_out, float* fx, float* fy, float* fz, uint32_t flags);
 
 /* Adjoint of one step (a vector-Jacobian product, loose coupling with the
  * flow frozen; Sec. 2.3 node update, Sec. 2.2 traction, Sec. 2.3 potentials):
@@ -186,11 +192,14 @@ ibm_status ibm_step(ibm_ctx* ctx, const float* x, const float* v, const float* u
  * terms) and through the probe traction (area, normal and the MLS velocity
  * gradient at the probe end, with its second derivatives) is included; the
  * spread force field is not differentiated (it does not feed the state).
- * Outputs must not alias the cotangents.  Per-body sums are in a fixed order;
- * the result is deterministic. */
+ * p and accel are the ones the step used (NULL allowed); the pressure load's
+ * dependence on x (area, normal, the MLS pressure gradient at the probe
+ * ends) is included, accel is held fixed.  Outputs must not alias the
+ * cotangents.  Per-body sums are in a fixed order; the result is
+ * deterministic. */
 ibm_status ibm_backward(ibm_ctx* ctx, const float* x, const float* u, const float* vv,
-                        const float* w, const float* gx_next, const float* gv_next, float* gx,
-                        float* gv, double* gparams);
+                        const float* w, const float* p, const float* accel, const float* gx_next,
+                        const float* gv_next, float* gx, float* gv, double* gparams);
 
 /* Taylor deformation D = (L - B)/(L + B) of every closed body (Sec. 3.1's
  * semi-axes L, B of a deformed drop), taken from the ellipsoid with the same
@@ -218,8 +227,9 @@ ibm_status ibm_taylor_backward(ibm_ctx* ctx, const float* x, const double* gD, f
  * must outlive the graph. */
 typedef struct ibm_graph ibm_graph;
 ibm_status ibm_graph_create(ibm_ctx* ctx, float* xa, float* va, float* xb, float* vb,
-                            const float* u, const float* vv, const float* w, float* fx, float* fy,
-                            float* fz, int32_t n_steps, ibm_graph** out);
+                            const float* u, const float* vv, const float* w, const float* p,
+                            const float* accel, float* fx, float* fy, float* fz, int32_t n_steps,
+                            ibm_graph** out);
 ibm_status ibm_graph_launch(ibm_graph* graph);
 void ibm_graph_destroy(ibm_graph* graph);
 

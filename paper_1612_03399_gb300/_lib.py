@@ -58,16 +58,17 @@ SIGNATURES = {
     "ibm_set_body_constants": (C.c_int, [P, C.POINTER(C.c_double)]),
     "ibm_body_measures": (C.c_int, [P, P, P]),
     "ibm_compute_forces": (C.c_int, [P, P, P, P]),
-    "ibm_interpolate": (C.c_int, [P, P, P, P, P, P, P, P, P]),
+    "ibm_interpolate": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P]),
     "ibm_advance": (C.c_int, [P, P, P, P, P, P, P]),
     "ibm_spread": (C.c_int, [P, P, P, P, P, P]),
-    "ibm_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
+    "ibm_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
     "ibm_check_device_error": (C.c_int, [P]),
     "ibm_set_phase_timing": (C.c_int, [P, C.c_int32]),
     "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
     "ibm_get_counters": (C.c_int, [P, C.POINTER(C.c_int64)]),
-    "ibm_backward": (C.c_int, [P, P, P, P, P, P, P, P, P, P]),
-    "ibm_graph_create": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, C.c_int32, C.POINTER(P)]),
+    "ibm_backward": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P]),
+    "ibm_graph_create": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_int32,
+                                   C.POINTER(P)]),
     "ibm_graph_launch": (C.c_int, [P]),
     "ibm_graph_destroy": (None, [P]),
     "ibm_taylor_deformation": (C.c_int, [P, P, P]),
@@ -210,13 +211,15 @@ class Context:
         self._check(self.lib.ibm_compute_forces(self.h, _ptr(x), _ptr(F), _ptr(E)))
         return (F, E) if energy else F
 
-    def interpolate(self, x, v, fields, U=True, F_marker=True, F_ext=True):
+    def interpolate(self, x, v, fields, U=True, F_marker=True, F_ext=True, p=None, accel=None):
+        """(U, F_marker, F_ext) per face; p: optional cell-centred pressure
+        [nz, ny, nx], accel: optional vertex accelerations [3, V]."""
         u, vv, w = fields
         Uo = self._vec(self.F) if U else None
         Fm = self._vec(self.F) if F_marker else None
         Fe = self._vec(self.F) if F_ext else None
         self._check(self.lib.ibm_interpolate(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
-                                             _ptr(Uo), _ptr(Fm), _ptr(Fe)))
+                                             _ptr(p), _ptr(accel), _ptr(Uo), _ptr(Fm), _ptr(Fe)))
         return Uo, Fm, Fe
 
     def advance(self, x, v, F_int, F_ext, x_out=None, v_out=None):
@@ -231,27 +234,27 @@ class Context:
         self._check(self.lib.ibm_spread(self.h, _ptr(x), _ptr(F_marker), _ptr(fx), _ptr(fy), _ptr(fz)))
         return f
 
-    def step(self, x, v, fields, x_out, v_out, f, clear=True):
+    def step(self, x, v, fields, x_out, v_out, f, clear=True, p=None, accel=None):
         u, vv, w = fields
         fx, fy, fz = f
         self._check(self.lib.ibm_step(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
-                                      _ptr(x_out), _ptr(v_out), _ptr(fx), _ptr(fy), _ptr(fz),
-                                      IBM_STEP_CLEAR_PREV if clear else 0))
+                                      _ptr(p), _ptr(accel), _ptr(x_out), _ptr(v_out), _ptr(fx),
+                                      _ptr(fy), _ptr(fz), IBM_STEP_CLEAR_PREV if clear else 0))
 
-    def backward(self, x, fields, gx_next, gv_next):
+    def backward(self, x, fields, gx_next, gv_next, p=None, accel=None):
         """Cotangents (gx, gv, gparams [B, 5]) of one step from x (ibm_backward)."""
         import torch
         u, vv, w = fields
         gx, gv = self._vec(self.V), self._vec(self.V)
         gp = torch.empty((self.B, 5), dtype=torch.float64, device=self.device)
-        self._check(self.lib.ibm_backward(self.h, _ptr(x), _ptr(u), _ptr(vv), _ptr(w),
-                                          _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv),
-                                          _ptr(gp)))
+        self._check(self.lib.ibm_backward(self.h, _ptr(x), _ptr(u), _ptr(vv), _ptr(w), _ptr(p),
+                                          _ptr(accel), _ptr(gx_next), _ptr(gv_next), _ptr(gx),
+                                          _ptr(gv), _ptr(gp)))
         return gx, gv, gp
 
-    def graph(self, xa, va, xb, vb, fields, f, n_steps=2):
+    def graph(self, xa, va, xb, vb, fields, f, n_steps=2, p=None, accel=None):
         """A StepGraph replaying n_steps ping-pong steps with one launch."""
-        return StepGraph(self, xa, va, xb, vb, fields, f, n_steps)
+        return StepGraph(self, xa, va, xb, vb, fields, f, n_steps, p, accel)
 
     def taylor(self, x):
         """Taylor deformation D [B] (float64) of every closed body at x."""
@@ -290,15 +293,15 @@ class Context:
 class StepGraph:
     """ibm_graph_create / ibm_graph_launch: n_steps captured steps."""
 
-    def __init__(self, ctx, xa, va, xb, vb, fields, f, n_steps=2):
+    def __init__(self, ctx, xa, va, xb, vb, fields, f, n_steps=2, p=None, accel=None):
         self.ctx = ctx
-        self._keep = (xa, va, xb, vb, fields, f)
+        self._keep = (xa, va, xb, vb, fields, f, p, accel)
         u, vv, w = fields
         fx, fy, fz = f
         h = C.c_void_p()
         ctx._check(ctx.lib.ibm_graph_create(ctx.h, _ptr(xa), _ptr(va), _ptr(xb), _ptr(vb), _ptr(u),
-                                            _ptr(vv), _ptr(w), _ptr(fx), _ptr(fy), _ptr(fz),
-                                            int(n_steps), C.byref(h)))
+                                            _ptr(vv), _ptr(w), _ptr(p), _ptr(accel), _ptr(fx),
+                                            _ptr(fy), _ptr(fz), int(n_steps), C.byref(h)))
         self.h = h
         self.n_steps = n_steps
 

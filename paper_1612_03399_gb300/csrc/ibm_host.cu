@@ -789,7 +789,7 @@ extern "C" ibm_status ibm_body_measures(ibm_ctx* c, const float* x, double* out)
   cudaError_t e = zero_body_sums(c);
   if (e == cudaSuccess)
     e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                   nullptr, nullptr, nullptr, true, false, false, false, false);
+                   nullptr, nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
   if (e == cudaSuccess) e = launch_measure_finalize(c);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, c->d.meas, sizeof(double) * 2 * c->B, cudaMemcpyDeviceToDevice,
@@ -804,7 +804,7 @@ extern "C" ibm_status ibm_compute_forces(ibm_ctx* c, const float* x, float* F_in
   cudaError_t e = zero_body_sums(c);
   if (e == cudaSuccess)
     e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                   nullptr, nullptr, nullptr, true, false, false, false, false);
+                   nullptr, nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
   if (e == cudaSuccess && energy) e = launch_measure_finalize(c);
   if (e == cudaSuccess && energy)
     e = cudaMemsetAsync(energy, 0, sizeof(double) * 5 * c->B, c->stream);
@@ -814,16 +814,16 @@ extern "C" ibm_status ibm_compute_forces(ibm_ctx* c, const float* x, float* F_in
 }
 
 extern "C" ibm_status ibm_interpolate(ibm_ctx* c, const float* x, const float* v, const float* u,
-                                      const float* vv, const float* w, float* U, float* Fm,
-                                      float* Fext) {
+                                      const float* vv, const float* w, const float* p,
+                                      const float* accel, float* U, float* Fm, float* Fext) {
   if (!c || !x || !u || !vv || !w) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   if (Fm && !v) return set_err(c, IBM_ERR_INVALID_ARG, "F_marker needs the vertex velocities");
   const bool interp = U || Fm;
   const bool probe = Fext != nullptr;
   if (!interp && !probe) return IBM_OK;
   cudaSetDevice(c->device);
-  cudaError_t e = launch_mls(c, x, v, u, vv, w, U, Fm, nullptr, Fext, nullptr, nullptr, nullptr,
-                             false, interp, probe, false, false);
+  cudaError_t e = launch_mls(c, x, v, u, vv, w, p, accel, U, Fm, nullptr, Fext, nullptr, nullptr,
+                             nullptr, false, interp, probe, false, false);
   return cuda_status(c, e, "ibm_interpolate");
 }
 
@@ -839,14 +839,15 @@ extern "C" ibm_status ibm_spread(ibm_ctx* c, const float* x, const float* Fm, fl
                                  float* fz) {
   if (!c || !x || !Fm || !fx || !fy || !fz) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   cudaSetDevice(c->device);
-  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Fm,
-                             nullptr, fx, fy, fz, false, false, false, true, false);
+  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, Fm, nullptr, fx, fy, fz, false, false, false, true, false);
   return cuda_status(c, e, "ibm_spread");
 }
 
 extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const float* u,
-                               const float* vv, const float* w, float* x_out, float* v_out,
-                               float* fx, float* fy, float* fz, uint32_t flags) {
+                               const float* vv, const float* w, const float* p,
+                               const float* accel, float* x_out, float* v_out, float* fx,
+                               float* fy, float* fz, uint32_t flags) {
   if (!c || !x || !v || !u || !vv || !w || !x_out || !v_out || !fx || !fy || !fz)
     return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   if (x_out == x || v_out == v || x_out == v || v_out == x)
@@ -865,8 +866,8 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
   e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
   mark(1);
   if (e == cudaSuccess)
-    e = launch_mls(c, x, v, u, vv, w, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz, true, true,
-                   true, true, clear);
+    e = launch_mls(c, x, v, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz,
+                   true, true, true, true, clear);
   mark(2);
   if (e == cudaSuccess)
     e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true);
@@ -886,8 +887,8 @@ struct ibm_graph {
 
 extern "C" ibm_status ibm_graph_create(ibm_ctx* c, float* xa, float* va, float* xb, float* vb,
                                        const float* u, const float* vv, const float* w,
-                                       float* fx, float* fy, float* fz, int32_t n_steps,
-                                       ibm_graph** out) {
+                                       const float* p, const float* accel, float* fx, float* fy,
+                                       float* fz, int32_t n_steps, ibm_graph** out) {
   if (out) *out = nullptr;
   if (!c || !xa || !va || !xb || !vb || !u || !vv || !w || !fx || !fy || !fz || !out)
     return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
@@ -933,8 +934,8 @@ extern "C" ibm_status ibm_graph_create(ibm_ctx* c, float* xa, float* va, float* 
       use_parity(c, c->qpar ^ 1);
       if (k == 0) e = launch_clear(c, fx, fy, fz);
       if (e == cudaSuccess)
-        e = launch_mls(c, x, v, u, vv, w, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz, true,
-                       true, true, true, true);
+        e = launch_mls(c, x, v, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, fx, fy,
+                       fz, true, true, true, true, true);
       const bool next = k + 1 < n_steps;
       if (next && e == cudaSuccess) {
         e = cudaEventRecord(ev_marker, cap);
@@ -1029,14 +1030,16 @@ extern "C" ibm_status ibm_get_phase_times(ibm_ctx* c, float* ms) {
 }
 
 extern "C" ibm_status ibm_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
-                                   const float* w, const float* gx_next, const float* gv_next,
-                                   float* gx, float* gv, double* gparams) {
+                                   const float* w, const float* p, const float* accel,
+                                   const float* gx_next, const float* gv_next, float* gx,
+                                   float* gv, double* gparams) {
   if (!c || !x || !u || !vv || !w || !gx_next || !gv_next || !gx || !gv || !gparams)
     return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   if (gx == gx_next || gv == gv_next || gx == gv_next || gv == gx_next)
     return set_err(c, IBM_ERR_INVALID_ARG, "ibm_backward: outputs must not alias the cotangents");
   cudaSetDevice(c->device);
-  return cuda_status(c, launch_backward(c, x, u, vv, w, gx_next, gv_next, gx, gv, gparams),
+  return cuda_status(c, launch_backward(c, x, u, vv, w, p, accel, gx_next, gv_next, gx, gv,
+                                       gparams),
                      "ibm_backward");
 }
 

@@ -192,10 +192,13 @@ struct ibm_ctx {
 
 namespace ibm {
 // kernel launchers (defined in the kernel translation units)
+// p, accel: optional cell-centred pressure and vertex accelerations (probe
+// pressure with the marker-acceleration correction)
 cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* u,
-                       const float* vv, const float* w, float* U, float* Fm, const float* Fm_in,
-                       float* Fext, float* fx, float* fy, float* fz, bool measure, bool interp,
-                       bool probe, bool spread, bool record_cells);
+                       const float* vv, const float* w, const float* p, const float* accel,
+                       float* U, float* Fm, const float* Fm_in, float* Fext, float* fx, float* fy,
+                       float* fz, bool measure, bool interp, bool probe, bool spread,
+                       bool record_cells);
 cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz);
 // zero the fixed-point body sums (before a measuring marker launch that does
 // not follow a clear), and form meas / coef from them (after it)
@@ -206,8 +209,9 @@ cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float
 cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,
                            const float* Fext, float* x_out, float* v_out);
 cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
-                            const float* w, const float* gx_next, const float* gv_next, float* gx,
-                            float* gv, double* gparams);
+                            const float* w, const float* p, const float* accel,
+                            const float* gx_next, const float* gv_next, float* gx, float* gv,
+                            double* gparams);
 cudaError_t launch_taylor(ibm_ctx* c, const float* x, double* D);
 cudaError_t launch_taylor_backward(ibm_ctx* c, const float* x, const double* gD, float* gx);
 cudaError_t set_force_smem_limit(size_t bytes);

@@ -152,6 +152,61 @@ __device__ void mls_grad_hess(const float* __restrict__ f, const Grid& g, const 
   for (int k = 0; k < 6; ++k) hs[k] = acc[3 + k];
 }
 
+// value and gradient (cells) of the MLS interpolant of one field at a point
+// (comp 0-2: velocity lattices, 3: cell centres)
+__device__ void mls_val_grad(const float* __restrict__ f, const Grid& g, const float (&tau)[3],
+                             int comp, const int (&G)[3], float kappa, float& val,
+                             float (&gr)[3]) {
+  int c[3];
+  float tp[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float uu = tau[d] - (d == comp ? 0.f : 0.5f);
+    const float cc = floorf(uu + 0.5f);
+    tp[d] = uu - cc;
+    c[d] = G[d] + (int)cc;
+  }
+  DirW2 X, Y, Z;
+  dir_weights_d2(tp[0], kappa, X);
+  dir_weights_d2(tp[1], kappa, Y);
+  dir_weights_d2(tp[2], kappa, Z);
+  int ix[3], iy[3], iz[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    ix[s] = wrap(c[0] - 1 + s, g.n[0]);
+    iy[s] = wrap(c[1] - 1 + s, g.n[1]);
+    iz[s] = wrap(c[2] - 1 + s, g.n[2]);
+  }
+  // derivative orders of the value and the three first derivatives
+  constexpr int OX[4] = {0, 1, 0, 0};
+  constexpr int OY[4] = {0, 0, 1, 0};
+  constexpr int OZ[4] = {0, 0, 0, 1};
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      const float* r = f + ((size_t)iz[sz] * g.n[1] + iy[sy]) * g.n[0];
+      const float u0 = __ldg(r + ix[0]), u1 = __ldg(r + ix[1]), u2 = __ldg(r + ix[2]);
+      float XA[2], XB[2];
+#pragma unroll
+      for (int o = 0; o < 2; ++o) {
+        XA[o] = X.a[o][0] * u0 + X.a[o][1] * u1 + X.a[o][2] * u2;
+        XB[o] = X.b[o][0] * u0 + X.b[o][1] * u1 + X.b[o][2] * u2;
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const float ay = Y.a[OY[p]][sy], by = Y.b[OY[p]][sy], az = Z.a[OZ[p]][sz], bz = Z.b[OZ[p]][sz];
+        acc[p] += (XA[OX[p]] - XB[OX[p]]) * ay * az - XA[OX[p]] * (by * az + ay * bz);
+      }
+    }
+  }
+  val = acc[0];
+  gr[0] = acc[1];
+  gr[1] = acc[2];
+  gr[2] = acc[3];
+}
+
 __device__ __forceinline__ float hess_at(const float (&hs)[6], int j, int k) {
   if (j == k) return hs[j];
   const int m = j + k;   // (0,1) -> 1, (0,2) -> 2, (1,2) -> 3
@@ -183,6 +238,7 @@ __device__ __forceinline__ void cross3(const float (&a)[3], const float (&b)[3],
 __global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
     DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ u, const float* __restrict__ vv, const float* __restrict__ w,
+    const float* __restrict__ pr, const float* __restrict__ accel,
     const float* __restrict__ gxn, const float* __restrict__ gvn) {
   __shared__ double s_red[2][kMT / 32];
   __shared__ int s_last;
@@ -276,7 +332,7 @@ __global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
         TgF[i] += Tij * gF[j];
       }
     }
-    const float gArea = sc.mu * (gF[0] * Tn[0] + gF[1] * Tn[1] + gF[2] * Tn[2]);
+    float gArea = sc.mu * (gF[0] * Tn[0] + gF[1] * Tn[1] + gF[2] * Tn[2]);
     float gn[3] = {sc.mu * area * TgF[0], sc.mu * area * TgF[1], sc.mu * area * TgF[2]};
     // d/dp of G through the MLS Hessian: gp_k = sum_ij gG_ij H_ijk,
     // gG_ij = mu A (gF_i n_j + gF_j n_i)
@@ -308,6 +364,45 @@ __global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
     for (int d = 0; d < 3; ++d) {
       gc[d] = gpp[d] + gpm[d];
       gn[d] += sc.probe_h * (gpp[d] - gpm[d]);
+    }
+    if (pr) {
+      // pressure load -A P n with P = p*(c + h n) [- p*(c - h n)] + k h a.n,
+      // k = 1 (closed) or 2 (open; each side with its own normal); the
+      // marker acceleration a is an input and is held fixed
+      float am[3] = {0.f, 0.f, 0.f};
+      if (accel) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          am[d] = (__ldg(accel + d * V + id[0]) + __ldg(accel + d * V + id[1]) +
+                   __ldg(accel + d * V + id[2])) * third;
+      }
+      float P, gpr[3], dPdc[3], dPdn[3];
+      mls_val_grad(pr, g, tpp, 3, B.G, sc.kappa, P, gpr);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dPdc[d] = gpr[d] * g.invh[d];
+        dPdn[d] = sc.probe_h * dPdc[d];
+      }
+      if (two) {
+        float Pm;
+        mls_val_grad(pr, g, tpm, 3, B.G, sc.kappa, Pm, gpr);
+        P -= Pm;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float gd = gpr[d] * g.invh[d];
+          dPdc[d] -= gd;
+          dPdn[d] += sc.probe_h * gd;
+        }
+      }
+      const float kh = (two ? 2.f : 1.f) * sc.probe_h;
+      P += kh * (am[0] * n[0] + am[1] * n[1] + am[2] * n[2]);
+      const float gFn = gF[0] * n[0] + gF[1] * n[1] + gF[2] * n[2];
+      gArea -= P * gFn;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        gn[d] -= area * (P * gF[d] + gFn * (dPdn[d] + kh * am[d]));
+        gc[d] -= area * gFn * dPdc[d];
+      }
     }
     // n = N/|N|, A = |N|/2
     const float gnn = gn[0] * n[0] + gn[1] * n[1] + gn[2] * n[2];
@@ -539,19 +634,20 @@ __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
 }  // namespace
 
 cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
-                            const float* w, const float* gx_next, const float* gv_next, float* gx,
-                            float* gv, double* gparams) {
+                            const float* w, const float* pr, const float* accel,
+                            const float* gx_next, const float* gv_next, float* gx, float* gv,
+                            double* gparams) {
   if (c->n_chunks == 0) return cudaSuccess;
   // area, volume and the global-term coefficients at x
   cudaError_t e = zero_body_sums(c);
   if (e == cudaSuccess)
     e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                   nullptr, nullptr, nullptr, true, false, false, false, false);
+                   nullptr, nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
   if (e == cudaSuccess) e = launch_measure_finalize(c);
   if (e != cudaSuccess) return e;
   ext_adjoint_kernel<<<c->n_chunks, kMT, 0, c->stream>>>(c->d, c->grid, c->sc, (int32_t)c->V,
-                                                         (int32_t)c->F, x, u, vv, w, gx_next,
-                                                         gv_next);
+                                                         (int32_t)c->F, x, u, vv, w, pr, accel,
+                                                         gx_next, gv_next);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   force_adjoint_kernel<<<c->n_work, kForceThreads, c->adjoint_smem, c->stream>>>(

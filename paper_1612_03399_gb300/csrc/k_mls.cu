@@ -371,9 +371,10 @@ template <bool MEASURE, bool INTERP, bool PROBE, bool SPREAD>
 __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ v, const float* __restrict__ u, const float* __restrict__ vv,
-    const float* __restrict__ w, float* __restrict__ U, float* __restrict__ Fm,
-    const float* __restrict__ Fm_in, float* __restrict__ Fext, float* __restrict__ fx,
-    float* __restrict__ fy, float* __restrict__ fz, int record, int vec4) {
+    const float* __restrict__ w, const float* __restrict__ pr, const float* __restrict__ accel,
+    float* __restrict__ U, float* __restrict__ Fm, const float* __restrict__ Fm_in,
+    float* __restrict__ Fext, float* __restrict__ fx, float* __restrict__ fy,
+    float* __restrict__ fz, int record, int vec4) {
   constexpr bool FIELD = INTERP || PROBE || SPREAD;
   constexpr bool VEL = INTERP || PROBE;
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -405,6 +406,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   float nrm[3] = {0.f, 0.f, 0.f}, area = 0.f;
   float tc[3] = {0.f, 0.f, 0.f}, tp[3] = {0.f, 0.f, 0.f}, tm[3] = {0.f, 0.f, 0.f};
   float vb[3] = {0.f, 0.f, 0.f};     // centroid velocity (interpolation) or marker force
+  float am[3] = {0.f, 0.f, 0.f};     // marker acceleration
   bool ok = false;
   int gf = 0;
   if (active) {
@@ -433,6 +435,14 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     } else if (SPREAD) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) vb[d] = __ldg(Fm_in + d * F + gf);
+    }
+    // marker acceleration (pressure correction): mean of the vertices'
+    if (PROBE && pr && accel) {
+      const float third = 1.f / 3.f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        am[d] = (__ldg(accel + d * V + ia) + __ldg(accel + d * V + ib) +
+                 __ldg(accel + d * V + ic)) * third;
     }
     const float e1[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
     const float e2[3] = {xc[0] - xa[0], xc[1] - xa[1], xc[2] - xa[2]};
@@ -644,6 +654,10 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   float Fl[3] = {vb[0], vb[1], vb[2]};   // marker force per component
   if (VEL) {
     float tGn[3] = {0.f, 0.f, 0.f}, tGTn[3] = {0.f, 0.f, 0.f};
+    // with a pressure field it is staged as a fourth component (u -> A,
+    // v -> B, w -> A, p -> B); the jump P = p+ - p- (open) or p (closed)
+    const bool press = PROBE && pr != nullptr;
+    float Pj = 0.f;
     if (fit) {
       stage_async(bufA, u, RT, ngroups);
       cp_async_commit();
@@ -653,14 +667,14 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     // the components in a loop, not unrolled: the unrolled kernel measured
     // slower (instruction fetch stalls)
 #pragma unroll 1
-    for (int comp = 0; comp < 3; ++comp) {
-      const float* velc = comp == 0 ? u : (comp == 1 ? vv : w);
-      const float* buf = comp == 1 ? bufB : bufA;
+    for (int comp = 0; comp < (press ? 4 : 3); ++comp) {
+      const float* velc = comp == 0 ? u : (comp == 1 ? vv : (comp == 2 ? w : pr));
+      const float* buf = (comp & 1) ? bufB : bufA;
       // the centroid's factors first: their arithmetic overlaps the copies
       // still in flight (the probe's as well would not fit in registers)
       DirW CX, CY, CZ;
       int ccC[3];
-      if (INTERP && mine) {
+      if (INTERP && mine && comp < 3) {
         float t3[3];
         locate(tc, comp, B.G, ccC, t3);
         dir_weights(t3[0], sc.kappa, CX);
@@ -668,10 +682,27 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
         dir_weights(t3[2], sc.kappa, CZ);
       }
       if (fit) {
-        if (comp < 2) cp_async_wait<1>(); else cp_async_wait<0>();
+        // one later group (the next component) may still be in flight
+        if (comp < 2 || (comp == 2 && press)) cp_async_wait<1>(); else cp_async_wait<0>();
         __syncthreads();   // every thread's copies of this component have landed
       }
-      if (mine) {
+      if (mine && comp == 3) {
+        // probe pressure p* and the correction h (Du/Dt).n, per side with its
+        // own normal: P = p*+ + h a.n (closed), p*+ - p*- + 2 h a.n (open)
+        const float an = am[0] * nrm[0] + am[1] * nrm[1] + am[2] * nrm[2];
+#pragma unroll 1
+        for (int l = 0; l < (two ? 2 : 1); ++l) {
+          int cc[3];
+          float t3[3];
+          locate(l == 0 ? tp : tm, 3, B.G, cc, t3);
+          DirW X, Y, Z;
+          dir_weights(t3[0], sc.kappa, X);
+          dir_weights(t3[1], sc.kappa, Y);
+          dir_weights(t3[2], sc.kappa, Z);
+          const float ps = fit ? mls_value(buf, SR.at(cc), X, Y, Z) : mls_value(pr, GR.at(cc), X, Y, Z);
+          Pj += (l == 0 ? 1.f : -1.f) * ps + sc.probe_h * an;
+        }
+      } else if (mine) {
         if (PROBE) {
           // open sheet: (tau+ - tau-) . n+
           float gr[3] = {0.f, 0.f, 0.f};
@@ -709,11 +740,16 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
         stage_async(bufA, w, RT, ngroups);
         cp_async_commit();
       }
+      if (fit && comp == 1 && press) {
+        __syncthreads();   // buffer B is free again
+        stage_async(bufB, pr, RT, ngroups);
+        cp_async_commit();
+      }
     }
     if (PROBE && mine) {
       const float s = sc.mu * area;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Fext[i * F + gf] = s * (tGn[i] + tGTn[i]);
+      for (int i = 0; i < 3; ++i) Fext[i * F + gf] = s * (tGn[i] + tGTn[i]) - area * Pj * nrm[i];
     }
   }
 
@@ -906,15 +942,16 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 template <bool M, bool I, bool P, bool S>
 cudaError_t launch_t(ibm_ctx* c, const float* x, const float* v, const float* u, const float* vv,
-                     const float* w, float* U, float* Fm, const float* Fm_in, float* Fext,
-                     float* fx, float* fy, float* fz, int record) {
+                     const float* w, const float* pr, const float* accel, float* U, float* Fm,
+                     const float* Fm_in, float* Fext, float* fx, float* fy, float* fz,
+                     int record) {
   if (c->n_chunks == 0) return cudaSuccess;
   const size_t smem = (I || P || S) ? kMarkerSmemBytes : 0;
-  const int vec4 = c->vec4 && aligned16(u) && aligned16(vv) && aligned16(w) && aligned16(fx) &&
-                   aligned16(fy) && aligned16(fz);
+  const int vec4 = c->vec4 && aligned16(u) && aligned16(vv) && aligned16(w) && aligned16(pr) &&
+                   aligned16(fx) && aligned16(fy) && aligned16(fz);
   marker_kernel<M, I, P, S><<<c->n_chunks, kMT, smem, c->stream>>>(
-      c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, U, Fm, Fm_in, Fext,
-      fx, fy, fz, record, vec4);
+      c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, pr, accel, U, Fm,
+      Fm_in, Fext, fx, fy, fz, record, vec4);
   return cudaGetLastError();
 }
 
@@ -936,22 +973,20 @@ cudaError_t set_marker_smem_limit() {
 }
 
 cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* u,
-                       const float* vv, const float* w, float* U, float* Fm, const float* Fm_in,
-                       float* Fext, float* fx, float* fy, float* fz, bool measure, bool interp,
-                       bool probe, bool spread, bool record_box) {
+                       const float* vv, const float* w, const float* pr, const float* accel,
+                       float* U, float* Fm, const float* Fm_in, float* Fext, float* fx, float* fy,
+                       float* fz, bool measure, bool interp, bool probe, bool spread,
+                       bool record_box) {
   const int rb = record_box ? 1 : 0;
-  if (measure && interp && probe && spread)
-    return launch_t<true, true, true, true>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
-  if (measure && !interp && !probe && !spread)
-    return launch_t<true, false, false, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
-  if (!measure && interp && probe && !spread)
-    return launch_t<false, true, true, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
-  if (!measure && interp && !probe && !spread)
-    return launch_t<false, true, false, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
-  if (!measure && !interp && probe && !spread)
-    return launch_t<false, false, true, false>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
-  if (!measure && !interp && !probe && spread)
-    return launch_t<false, false, false, true>(c, x, v, u, vv, w, U, Fm, Fm_in, Fext, fx, fy, fz, rb);
+#define L(M, I, P, S) \
+  launch_t<M, I, P, S>(c, x, v, u, vv, w, pr, accel, U, Fm, Fm_in, Fext, fx, fy, fz, rb)
+  if (measure && interp && probe && spread) return L(true, true, true, true);
+  if (measure && !interp && !probe && !spread) return L(true, false, false, false);
+  if (!measure && interp && probe && !spread) return L(false, true, true, false);
+  if (!measure && interp && !probe && !spread) return L(false, true, false, false);
+  if (!measure && !interp && probe && !spread) return L(false, false, true, false);
+  if (!measure && !interp && !probe && spread) return L(false, false, false, true);
+#undef L
   return cudaErrorInvalidValue;
 }
 
