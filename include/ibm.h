@@ -233,6 +233,22 @@ ibm_status ibm_graph_create(ibm_ctx* ctx, float* xa, float* va, float* xb, float
 ibm_status ibm_graph_launch(ibm_graph* graph);
 void ibm_graph_destroy(ibm_graph* graph);
 
+/* Read a GTS (GNU Triangulated Surface) file, the format the paper's meshes
+ * are exported in (Sec. 5): a header line "nv ne nf", nv lines "x y z", ne
+ * lines of two 1-based vertex indices (edges), nf lines of three 1-based edge
+ * indices (faces); blank lines and lines starting with '#' are skipped, and
+ * anything after the numbers on a line is ignored.  A face's vertex order
+ * follows its edges: the vertex of e1 not on e2, the vertex e1 and e2 share,
+ * then the vertex of e2 not on e1 (so an oriented mesh stays oriented).
+ * Two calls: with xyz and tri NULL it sets *n_vert and *n_face; then with
+ * HOST buffers xyz[n_vert][3] (float64) and tri[n_face][3] (int32, 0-based)
+ * and the sizes of the first call it fills them.  No context and no GPU are
+ * needed.  Errors: IBM_ERR_INVALID_ARG (unreadable file, malformed line,
+ * buffers not matching), IBM_ERR_MESH (index out of range, edges of a face
+ * not forming a triangle); the message is in ibm_last_error(NULL). */
+ibm_status ibm_gts_read(const char* path, int64_t* n_vert, int64_t* n_face, double* xyz,
+                        int32_t* tri);
+
 /* Synchronise the stream and report the device error word (IBM_ERR_DEVICE if
  * a kernel flagged an out-of-range or non-finite value). */
 ibm_status ibm_check_device_error(ibm_ctx* ctx);

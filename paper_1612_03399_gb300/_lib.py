@@ -74,6 +74,7 @@ SIGNATURES = {
     "ibm_taylor_deformation": (C.c_int, [P, P, P]),
     "ibm_taylor_backward": (C.c_int, [P, P, P, P, P]),
     "ibm_body_measures_noalloc": (C.c_int, [P, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]),
+    "ibm_gts_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), P, P]),
 }
 
 _lib = None
