@@ -108,6 +108,16 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     float ea;
     face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid), B.ka,
                 cA, cV, f, gA, gV, ua, ea);
+    if (ADVANCE) {
+      // F_ext^v = sum over the vertex's faces of F_ext / 3: each face adds a
+      // third of its load to its corner slots, gathered with the forces
+      const int gf = B.f_off + r.fid;
+      const float third = 1.f / 3.f;
+      const Vec<float> fe = {__ldg(Fext + gf) * third, __ldg(Fext + F + gf) * third,
+                             __ldg(Fext + 2 * F + gf) * third};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) f[c] = vadd(f[c], fe);
+    }
     S.put(fbase + k, f[0]);
     S.put(fbase + P.n_face + k, f[1]);
     S.put(fbase + 2 * P.n_face + k, f[2]);
@@ -132,19 +142,8 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
       Fint[V + gv] = fy;
       Fint[2 * V + gv] = fz;
     } else {
-      // F_ext^v = sum over the vertex's faces of F_ext / 3
-      const int* vp = T.v2f_ptr + topo.v2f_ptr_off;
-      const int q0 = __ldg(vp + lv), q1 = __ldg(vp + lv + 1);
-      float ex = 0.f, ey = 0.f, ez = 0.f;
-      for (int q = q0; q < q1; ++q) {
-        const int gf = B.f_off + __ldg(T.v2f_idx + topo.v2f_idx_off + q);
-        ex += __ldg(Fext + gf);
-        ey += __ldg(Fext + F + gf);
-        ez += __ldg(Fext + 2 * F + gf);
-      }
-      const float third = 1.f / 3.f;
-      const float ax = (fx + ex * third) * B.inv_mass, ay = (fy + ey * third) * B.inv_mass,
-                  az = (fz + ez * third) * B.inv_mass;
+      // the gathered slots hold F_int + F_ext^v
+      const float ax = fx * B.inv_mass, ay = fy * B.inv_mass, az = fz * B.inv_mass;
       const float x0 = S.px[i], y0 = S.py[i], z0 = S.pz[i];
       float vx = __ldg(v + gv), vy = __ldg(v + V + gv), vz = __ldg(v + 2 * V + gv);
       float nx, ny, nz;
