@@ -59,6 +59,11 @@ reason, in the design notes of the repository):
      accelerations, which the caller supplies (e.g. (v^n - v^(n-1))/dt).
   R17 open sheets: each side takes p^+- = p*^+- + h (Du/Dt).n^+- with
      n^+- = +-n^+, and the load is -(p^+ - p^-) n^+ A.
+  R18 non-uniform meshes and materials: k_e per edge by van Gelder's model,
+     k_e = k_s sum over the edge's faces of A_T / l_e^2 (rest values; k_s is
+     then the membrane's E t); per-face material multipliers of (k_s, k_b,
+     k_a): an edge takes the mean of its faces' (the area-weighted sum under
+     van Gelder), a hinge the mean of its two faces', a face its own.
 """
 from __future__ import annotations
 
@@ -179,7 +184,8 @@ class Body:
     """
 
     def __init__(self, rest, tri, origin, closed=True, clamped=None, ks=1.0, kb=0.01,
-                 ka=1.0, kA=1.0, kv=1.0, mass=1.0, theta0_zero=False):
+                 ka=1.0, kA=1.0, kv=1.0, mass=1.0, theta0_zero=False, spring_model=0,
+                 face_material=None):
         self.rest = torch.as_tensor(rest, dtype=DT)
         self.nv = self.rest.shape[0]
         self.topo = build_topology(tri, self.nv)
@@ -210,15 +216,42 @@ class Body:
             self.V0 = enclosed_volume(self.rest, self.tri, self.origin) if closed else torch.tensor(0.0, dtype=DT)
             if closed and self.V0 <= 0:
                 raise MeshError("closed body has non-positive rest volume (inward faces?)")
+            self._element_scales(spring_model, face_material)
+
+    def _element_scales(self, spring_model, face_material):
+        """Per-element multipliers of k_s (edges), k_b (hinges) and k_a (faces)
+        (reading R18).  face_material [F,3]: per-face (m_s, m_b, m_a), ones if
+        None.  Spring model 0: m_e = mean of m_s over the edge's faces;
+        model 1 (van Gelder): m_e = sum over the edge's faces T of
+        m_s(T) A_T / l_e^2 (rest areas and lengths), so that k_s is the
+        membrane's E t.  A hinge takes the mean m_b of its two faces."""
+        F = self.tri.shape[0]
+        m = (torch.ones(F, 3, dtype=DT) if face_material is None
+             else torch.as_tensor(face_material, dtype=DT).reshape(F, 3))
+        ef = self.topo["efaces"]
+        has2 = ef[:, 1] >= 0
+        f0, f1 = ef[:, 0], ef[:, 1].clamp(min=0)
+        ms0, ms1 = m[f0, 0], torch.where(has2, m[f1, 0], torch.zeros_like(m[f0, 0]))
+        if spring_model == 0:
+            self.m_edge = (ms0 + ms1) / torch.where(has2, 2.0, 1.0).to(DT)
+        elif spring_model == 1:
+            A0 = self.A0f
+            area = ms0 * A0[f0] + torch.where(has2, ms1 * A0[f1], torch.zeros_like(ms1))
+            self.m_edge = area / self.l0 ** 2
+        else:
+            raise ValueError("spring_model must be 0 or 1")
+        inner = ef[:, 1] >= 0
+        self.m_hinge = 0.5 * (m[ef[inner, 0], 1] + m[ef[inner, 1], 1])
+        self.m_face = m[:, 2].clone()
 
     def energy_terms(self, x):
         """W_e, W_b, W_a (local), W_A (global), W_v of Sec. 2.3 at positions x."""
         l = edge_lengths(x, self.topo["edges"])
-        We = 0.5 * self.ks * ((l - self.l0) ** 2).sum()                       # Eq. elaspot
+        We = 0.5 * self.ks * (self.m_edge * (l - self.l0) ** 2).sum()         # Eq. elaspot
         cos, sin = hinge_angle(x, self.hinge_edges, self.hinge_wings)
-        Wb = (self.kb * (1.0 - (cos * self.cos0 + sin * self.sin0))).sum()    # W_b = k_b(1-cos(th-th0))
+        Wb = (self.kb * self.m_hinge * (1.0 - (cos * self.cos0 + sin * self.sin0))).sum()
         _, _, Af = face_geometry(x, self.tri)
-        Wa = (0.5 * self.ka * (Af - self.A0f) ** 2 / self.A0f).sum()          # Eq. areapot, per face
+        Wa = (0.5 * self.ka * self.m_face * (Af - self.A0f) ** 2 / self.A0f).sum()   # Eq. areapot
         A = Af.sum()
         WA = 0.5 * self.kA * (A - self.A0) ** 2 / self.A0                     # Eq. areapot, per body
         if self.closed:
