@@ -76,7 +76,15 @@ typedef struct {
   double mass;             /* node mass m (Sec. 2.3; 1 for drops)                  */
   int32_t closed;          /* 1 closed surface (one outward probe), 0 open sheet
                               (two probes, Sec. 2.2)                               */
-  int32_t reserved;
+  int32_t spring_model;    /* 0: k_e = ks on every edge; 1: van Gelder's model for
+                              non-uniform meshes (Sec. 2.3), k_e = ks sum over the
+                              edge's faces T of A_T / l_e^2 (rest values), ks then
+                              being the membrane's E t                             */
+  const float* face_material; /* host [n_face][3] or NULL: per-face multipliers of
+                              (ks, kb, ka), >= 0 (e.g. two materials in one mesh);
+                              an edge's spring takes the mean of its faces' (the
+                              area-weighted sum under van Gelder), a hinge the mean
+                              of its two faces', a face its own                    */
 } ibm_body_desc;
 
 typedef struct {

@@ -31,7 +31,7 @@ class BodyDesc(C.Structure):
                 ("clamped", C.POINTER(C.c_uint8)), ("origin", C.c_double * 3),
                 ("ks", C.c_double), ("kb", C.c_double), ("ka", C.c_double), ("kA", C.c_double),
                 ("kv", C.c_double), ("mass", C.c_double), ("closed", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("spring_model", C.c_int32), ("face_material", C.POINTER(C.c_float))]
 
 
 class GridDesc(C.Structure):
@@ -142,6 +142,12 @@ class Context:
             d.ks, d.kb, d.ka, d.kA, d.kv, d.mass = (float(b.ks), float(b.kb), float(b.ka),
                                                     float(b.kA), float(b.kv), float(b.mass))
             d.closed = 1 if b.closed else 0
+            d.spring_model = int(getattr(b, "spring_model", 0))
+            fm = getattr(b, "face_material", None)
+            if fm is not None:
+                fm = np.ascontiguousarray(fm, dtype=np.float32).reshape(len(tri), 3)
+                d.face_material = fm.ctypes.data_as(C.POINTER(C.c_float))
+                self._keep.append(fm)
         g = GridDesc()
         for k in range(3):
             g.n[k] = int(grid.n[k])

@@ -41,6 +41,7 @@ struct HostTopo {
   bool has_boundary = false;
   std::vector<int32_t> tri;
   std::vector<int4> edge;  // a, b, c, d
+  std::vector<int2> eface; // face holding a->b, face holding b->a (-1 if none)
   std::vector<int32_t> v2f_ptr, v2f_idx;
   std::vector<PatchHdr> patch;
   std::vector<int32_t> loc_vert;
@@ -64,8 +65,9 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
   T.nv = nv;
   T.nf = nf;
   T.tri.assign(tri, tri + 3 * (size_t)nf);
-  std::unordered_map<uint64_t, int32_t> half;
+  std::unordered_map<uint64_t, int32_t> half, hface;
   half.reserve((size_t)nf * 6);
+  hface.reserve((size_t)nf * 6);
   for (int f = 0; f < nf; ++f) {
     const int a = tri[3 * f], b = tri[3 * f + 1], c = tri[3 * f + 2];
     if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv)
@@ -74,6 +76,7 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
       fail(IBM_ERR_MESH, "face " + std::to_string(f) + " repeats a vertex");
     const int hp[3][3] = {{a, b, c}, {b, c, a}, {c, a, b}};
     for (auto& h : hp) {
+      hface.emplace(key2(h[0], h[1]), f);
       if (!half.emplace(key2(h[0], h[1]), h[2]).second)
         fail(IBM_ERR_MESH, "edge (" + std::to_string(h[0]) + "," + std::to_string(h[1]) +
                                ") is used twice in the same direction: non-manifold or "
@@ -93,6 +96,8 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
       if (s < 0) T.has_boundary = true;
       und.emplace(k, (int32_t)T.edge.size());
       T.edge.push_back(make_int4(h[0], h[1], h[2], s));
+      const auto jt = hface.find(key2(h[1], h[0]));
+      T.eface.push_back(make_int2(f, jt == hface.end() ? -1 : jt->second));
     }
   }
   T.ne = (int)T.edge.size();
@@ -488,6 +493,17 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     c->n_topo = (int)topos.size();
     std::vector<float> rest(3 * V), l0(E), A0f(F);
     std::vector<float2> cs0(E);
+    // per-element multipliers of k_s (edges), k_b (hinges), k_a (faces);
+    // filled only when some body has a non-uniform spring model or materials
+    std::vector<float> kse, kbe, kaf;
+    bool any_varied = false;
+    for (int b = 0; b < n_bodies; ++b)
+      any_varied = any_varied || bodies[b].spring_model != 0 || bodies[b].face_material != nullptr;
+    if (any_varied) {
+      kse.assign(E, 1.f);
+      kbe.assign(E, 1.f);
+      kaf.assign(F, 1.f);
+    }
     std::vector<uint8_t> clamp(V, 0);
     std::vector<int4> chunks;
     std::vector<int2> work;
@@ -533,13 +549,46 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
         cs0[eo + e] = cs;
       }
       double A0 = 0.0, V0 = 0.0;
+      std::vector<double> a0(T.nf);
       for (int f = 0; f < T.nf; ++f) {
         const D3 xa = x[T.tri[3 * f]], xb = x[T.tri[3 * f + 1]], xc = x[T.tri[3 * f + 2]];
         const double a = 0.5 * dnorm(dcross(dsub(xb, xa), dsub(xc, xa)));
         if (!(a > 0)) fail(IBM_ERR_MESH, tag + "degenerate (zero-area) rest face");
         A0f[fo + f] = (float)a;
+        a0[f] = a;
         A0 += a;
         V0 += ddot(xa, dcross(xb, xc)) / 6.0;
+      }
+      const bool varied = Bd.spring_model != 0 || Bd.face_material != nullptr;
+      if (Bd.spring_model != 0 && Bd.spring_model != 1)
+        fail(IBM_ERR_INVALID_ARG, tag + "spring_model must be 0 (uniform) or 1 (van Gelder)");
+      if (varied) {
+        // face multipliers (m_s, m_b, m_a); an edge takes the mean of its
+        // faces' m_s, or under van Gelder sum_T m_s(T) A_T / l^2; a hinge the
+        // mean of its two faces' m_b; a face its own m_a
+        auto mat = [&](int f, int j) -> double {
+          return Bd.face_material ? (double)Bd.face_material[3 * f + j] : 1.0;
+        };
+        if (Bd.face_material)
+          for (int f = 0; f < T.nf; ++f)
+            for (int j = 0; j < 3; ++j)
+              if (!(mat(f, j) >= 0.0) || !is_fin(mat(f, j)))
+                fail(IBM_ERR_INVALID_ARG, tag + "face_material must be finite and >= 0");
+        for (int e = 0; e < T.ne; ++e) {
+          const int2 ef = T.eface[e];
+          const int4 Ed = T.edge[e];
+          const double l = dnorm(dsub(x[Ed.y], x[Ed.x]));
+          double ms;
+          if (Bd.spring_model == 1) {
+            ms = mat(ef.x, 0) * a0[ef.x] + (ef.y >= 0 ? mat(ef.y, 0) * a0[ef.y] : 0.0);
+            ms /= l * l;
+          } else {
+            ms = ef.y >= 0 ? 0.5 * (mat(ef.x, 0) + mat(ef.y, 0)) : mat(ef.x, 0);
+          }
+          kse[eo + e] = (float)ms;
+          kbe[eo + e] = ef.y >= 0 ? (float)(0.5 * (mat(ef.x, 1) + mat(ef.y, 1))) : 0.f;
+        }
+        for (int f = 0; f < T.nf; ++f) kaf[fo + f] = (float)mat(f, 2);
       }
       if (Bd.closed && !(V0 > 0))
         fail(IBM_ERR_MESH, tag + "closed body with non-positive rest volume (faces oriented inward?)");
@@ -553,6 +602,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       R.nf = Bd.n_face;
       R.ne = T.ne;
       R.closed = Bd.closed ? 1 : 0;
+      R.varied = varied ? 1 : 0;
       for (int d = 0; d < 3; ++d) {
         const double o = Bd.origin[d] / h[d];
         const double Gd = std::floor(o);
@@ -662,6 +712,11 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.l0 = upload(c, l0);
     d.cs0 = upload(c, cs0);
     d.A0f = upload(c, A0f);
+    if (any_varied) {
+      d.kse = upload(c, kse);
+      d.kbe = upload(c, kbe);
+      d.kaf = upload(c, kaf);
+    }
     d.clamp = upload(c, clamp);
     d.rest = upload(c, rest);
     d.chunks = upload(c, chunks);

@@ -33,7 +33,7 @@ struct BodyDev {
   float sA, sV;                        // 2^eA, 2^eV
   float cA_unit, cV_unit;              // k_A / (sA A0), k_v / (sV V0)
   float qlim;                          // per-face bound on |q|: 2^62 / n_faces
-  float pad2;
+  int32_t varied;                      // 1: per-element multipliers kse, kbe, kaf apply
 };
 
 // per distinct mesh topology (shared by every body with the same faces)
@@ -105,6 +105,9 @@ struct DeviceTables {
   float* l0 = nullptr;          // [E] rest edge lengths
   float2* cs0 = nullptr;        // [E] (cos theta0, sin theta0) per hinge edge
   float* A0f = nullptr;         // [F] rest face areas
+  float* kse = nullptr;         // [E] multiplier of k_s per edge (van Gelder / materials),
+  float* kbe = nullptr;         // [E] of k_b per hinge edge, [F] of k_a per face;
+  float* kaf = nullptr;         //     null when every body is uniform
   uint8_t* clamp = nullptr;     // [V]
   float* rest = nullptr;        // [3][V] body-frame rest positions
   int4* chunks = nullptr;       // (body, offset in the topology's mface list, count,

@@ -524,18 +524,22 @@ __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
     const float2 cs0 = hinge ? __ldg(T.cs0 + ge) : make_float2(1.f, 0.f);
     Vec<Dual> fa, fb, fc, fd, us[2], ub[4];
     float es, eb;
-    edge_forces(pa, pb, pc, pd, hinge, __ldg(T.l0 + ge), cs0.x, cs0.y, B.ks, B.kb, fa, fb, fc, fd,
-                us, ub, es, eb);
+    // per-edge multipliers m: the forces use m k, the constants' cotangents
+    // scale the per-unit-k forces by m
+    const float ms = B.varied ? __ldg(T.kse + ge) : 1.f;
+    const float mb = B.varied ? __ldg(T.kbe + ge) : 1.f;
+    edge_forces(pa, pb, pc, pd, hinge, __ldg(T.l0 + ge), cs0.x, cs0.y, B.ks * ms, B.kb * mb, fa, fb,
+                fc, fd, us, ub, es, eb);
     S.put(k, fa);
     S.put(P.n_edge + k, fb);
     S.put(2 * P.n_edge + k, fc);
     S.put(3 * P.n_edge + k, fd);
     if (r.eid < 0) {   // owned edge: constants' cotangents
       const Vec<float> ca = S.cot(r.l[0]), cb = S.cot(r.l[1]);
-      gks += dotv(ca, us[0]) + dotv(cb, us[1]);
+      gks += ms * (dotv(ca, us[0]) + dotv(cb, us[1]));
       if (hinge) {
         const Vec<float> cc = S.cot(r.l[2]), cd = S.cot(r.l[3]);
-        gkb += dotv(ca, ub[0]) + dotv(cb, ub[1]) + dotv(cc, ub[2]) + dotv(cd, ub[3]);
+        gkb += mb * (dotv(ca, ub[0]) + dotv(cb, ub[1]) + dotv(cc, ub[2]) + dotv(cd, ub[3]));
       }
     }
   }
@@ -544,13 +548,15 @@ __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
     const PFace r = T.pface[P.face_off + k];
     Vec<Dual> f[3], gA[3], gV[3], ua[3];
     float ea;
-    face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid), B.ka,
-                cA, cV, f, gA, gV, ua, ea);
+    const float ma = B.varied ? __ldg(T.kaf + B.f_off + r.fid) : 1.f;
+    face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid),
+                B.ka * ma, cA, cV, f, gA, gV, ua, ea);
     S.put(fbase + k, f[0]);
     S.put(fbase + P.n_face + k, f[1]);
     S.put(fbase + 2 * P.n_face + k, f[2]);
     if (r.owned)
-      gka += dotv(S.cot(r.l[0]), ua[0]) + dotv(S.cot(r.l[1]), ua[1]) + dotv(S.cot(r.l[2]), ua[2]);
+      gka += ma * (dotv(S.cot(r.l[0]), ua[0]) + dotv(S.cot(r.l[1]), ua[1]) +
+                   dotv(S.cot(r.l[2]), ua[2]));
   }
   __syncthreads();
   const int* tri = T.tri + topo.tri_off;

@@ -88,8 +88,11 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     const float2 cs0 = hinge ? __ldg(T.cs0 + ge) : make_float2(1.f, 0.f);
     Vec<float> fa, fb, fc, fd, us[2], ub[4];
     float es, eb;
-    edge_forces(pa, pb, pc, pd, hinge, __ldg(T.l0 + ge), cs0.x, cs0.y, B.ks, B.kb, fa, fb, fc, fd,
-                us, ub, es, eb);
+    // per-edge constants (van Gelder springs, materials) where the body has them
+    const float ks = B.varied ? B.ks * __ldg(T.kse + ge) : B.ks;
+    const float kb = B.varied ? B.kb * __ldg(T.kbe + ge) : B.kb;
+    edge_forces(pa, pb, pc, pd, hinge, __ldg(T.l0 + ge), cs0.x, cs0.y, ks, kb, fa, fb, fc, fd, us,
+                ub, es, eb);
     if (want_e && (r.eid < 0)) {
       eS += (double)es;
       eB += (double)eb;
@@ -106,7 +109,8 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     const PFace r = T.pface[P.face_off + k];
     Vec<float> f[3], gA[3], gV[3], ua[3];
     float ea;
-    face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid), B.ka,
+    const float ka = B.varied ? B.ka * __ldg(T.kaf + B.f_off + r.fid) : B.ka;
+    face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid), ka,
                 cA, cV, f, gA, gV, ua, ea);
     if (ADVANCE) {
       // F_ext^v = sum over the vertex's faces of F_ext / 3: each face adds a

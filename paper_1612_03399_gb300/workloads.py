@@ -207,6 +207,8 @@ class Body:
     mass: float = 1.0
     level: int = -1                  # icosphere level, -1 for other meshes
     radius: float = 0.0              # bounding radius about `origin`
+    spring_model: int = 0            # 0 uniform k_e = ks, 1 van Gelder (ks = E t)
+    face_material: np.ndarray | None = None  # [F,3] multipliers of (ks, kb, ka)
 
 
 @dataclass

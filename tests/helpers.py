@@ -15,7 +15,9 @@ DT = torch.float64
 
 def oracle_bodies(wl, theta0_zero=False):
     return [O.Body(b.rest, b.tri, b.origin, closed=b.closed, clamped=b.clamped, ks=b.ks, kb=b.kb,
-                   ka=b.ka, kA=b.kA, kv=b.kv, mass=b.mass, theta0_zero=theta0_zero)
+                   ka=b.ka, kA=b.kA, kv=b.kv, mass=b.mass, theta0_zero=theta0_zero,
+                   spring_model=getattr(b, "spring_model", 0),
+                   face_material=getattr(b, "face_material", None))
             for b in wl.bodies]
 
 
