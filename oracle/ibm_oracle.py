@@ -64,6 +64,11 @@ reason, in the design notes of the repository):
      then the membrane's E t); per-face material multipliers of (k_s, k_b,
      k_a): an edge takes the mean of its faces' (the area-weighted sum under
      van Gelder), a hinge the mean of its two faces', a face its own.
+  R19 strong coupling (Sec. 2.3) with the flow frozen: the fluid-structure
+     iteration reduces to Hamming's fourth-order predictor-corrector for
+     y = (x, v), y' = (v, (F_int + F_ext^v)/m), one corrector application per
+     step as in the classical scheme, started by three classical Runge-Kutta
+     steps.
 """
 from __future__ import annotations
 
@@ -491,6 +496,97 @@ def step(bodies, xs, vs, fields, prm: Params, create_graph=False, with_spread=Tr
            "markers": torch.cat(Ps), "areas": torch.cat(As)}
     if with_spread:
         out["f"] = spread(out["F_marker"], out["markers"], out["areas"], n, h, alpha)
+    return out
+
+
+# --------------------------------------------------------------------------
+# strong coupling: Hamming's fourth-order predictor-corrector (Sec. 2.3)
+# --------------------------------------------------------------------------
+
+
+def accelerations(bodies, xs, fields, prm: Params, pressure=None, accels=None):
+    """a = (F_int + F_ext^v)/m per vertex at positions xs (the right-hand side
+    of m x'' = F_ext + F_int, Sec. 2.3); clamped nodes get a = 0."""
+    n, h, alpha = prm.n, prm.h, prm.alpha
+    out = []
+    for ib, (b, x) in enumerate(zip(bodies, xs)):
+        C, nrm, A_l = face_geometry(x, b.tri)
+        acc_l = None
+        if pressure is not None and accels is not None:
+            a = accels[ib]
+            acc_l = (a[b.tri[:, 0]] + a[b.tri[:, 1]] + a[b.tri[:, 2]]) / 3.0
+        Fe = probe_traction(fields, C, nrm, A_l, n, h, alpha, prm.mu, prm.probe_h,
+                            two_sided=not b.closed, pressure=pressure, accel=acc_l)
+        acc = (distribute_to_vertices(Fe, b.tri, b.nv) + b.internal_forces(x)) / b.mass
+        out.append(torch.where(b.clamped[:, None], torch.zeros_like(acc), acc))
+    return out
+
+
+def rk4_step(f, y, dt):
+    """One classical fourth-order Runge-Kutta step of y' = f(y)."""
+    k1 = f(y)
+    k2 = f(y + 0.5 * dt * k1)
+    k3 = f(y + 0.5 * dt * k2)
+    k4 = f(y + dt * k3)
+    return y + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+
+
+class Hamming:
+    """Hamming's fourth-order predictor-corrector for y' = f(y) (reading
+    R19), started by three classical Runge-Kutta steps:
+      predictor  p = y_{n-3} + 4h/3 (2 f_n - f_{n-1} + 2 f_{n-2})      (Milne)
+      modifier   m = p - 112/121 (p_n - c_n)
+      corrector  c = (9 y_n - y_{n-2})/8 + 3h/8 (f(m) + 2 f_n - f_{n-1})
+      final      y_{n+1} = c + 9/121 (p - c)
+    with p_n - c_n = 0 on the first Hamming step.  Each Hamming step
+    evaluates f twice (at y_n and at m)."""
+
+    def __init__(self, f, y0, dt):
+        self.f, self.dt = f, dt
+        self.ys = [y0]            # y_0 .. y_n (the last four are kept)
+        self.fs = []              # f(y_k) for the kept y_k
+        self.pc = None            # p_n - c_n
+
+    def step(self):
+        h, f = self.dt, self.f
+        if len(self.ys) < 4:                      # start-up
+            self.ys.append(rk4_step(f, self.ys[-1], h))
+            return self.ys[-1]
+        y = self.ys
+        while len(self.fs) < len(y):
+            self.fs.append(f(y[len(self.fs)]))
+        fn, fn1, fn2 = self.fs[-1], self.fs[-2], self.fs[-3]
+        p = y[-4] + (4.0 * h / 3.0) * (2.0 * fn - fn1 + 2.0 * fn2)
+        m = p if self.pc is None else p - (112.0 / 121.0) * self.pc
+        c = (9.0 * y[-1] - y[-3]) / 8.0 + (3.0 * h / 8.0) * (f(m) + 2.0 * fn - fn1)
+        yn = c + (9.0 / 121.0) * (p - c)
+        self.pc = p - c
+        self.ys = self.ys[-3:] + [yn]
+        self.fs = self.fs[-3:]
+        return yn
+
+
+def hamming_rollout(bodies, xs, vs, fields, prm: Params, n_steps, pressure=None, accels=None):
+    """n_steps of the Hamming predictor-corrector (three RK4 start-up steps)
+    for every body at once; y = (x, v), f(y) = (v, a(x)).  Returns the lists
+    of positions and velocities after each step."""
+    sizes = [len(x) for x in xs]
+
+    def pack(xl, vl):
+        return torch.stack([torch.cat(xl), torch.cat(vl)])
+
+    def unpack(y):
+        return list(torch.split(y[0], sizes)), list(torch.split(y[1], sizes))
+
+    def f(y):
+        xl, vl = unpack(y)
+        al = accelerations(bodies, xl, fields, prm, pressure, accels)
+        return torch.stack([y[1], torch.cat(al)])
+
+    H = Hamming(f, pack(xs, vs), prm.dt)
+    out = []
+    for _ in range(n_steps):
+        out.append(unpack(H.step()))
     return out
 
 
