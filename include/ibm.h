@@ -189,6 +189,26 @@ ibm_status ibm_step(ibm_ctx* ctx, const float* x, const float* v, const float* u
                     const float* vv, const float* w, const float* p, const float* accel,
                     float* x_out, float* v_out, float* fx, float* fy, float* fz, uint32_t flags);
 
+/* Strong coupling (Sec. 2.3; the flow frozen, so the fluid-structure
+ * iteration reduces to the structural integrator): one step of Hamming's
+ * fourth-order predictor-corrector for y = (x, v), y' = (v, (F_int +
+ * F_ext^v)/m): Milne predictor, Hamming modifier and corrector, final
+ * correction, with two acceleration evaluations per step; the first three
+ * steps after creation or ibm_pc_reset are classical Runge-Kutta steps (four
+ * evaluations each).  Arguments, clamping, the spread of this step's marker
+ * forces at (x, v) and the flags are as in ibm_step; p, accel may be NULL.
+ * The context keeps the history (the three previous states and
+ * accelerations), so each call's (x, v) must be the previous call's
+ * (x_out, v_out); the first call allocates the history (about 24 [3][V]
+ * float arrays), so make it before capturing a stream. */
+ibm_status ibm_step_pc(ibm_ctx* ctx, const float* x, const float* v, const float* u,
+                       const float* vv, const float* w, const float* p, const float* accel,
+                       float* x_out, float* v_out, float* fx, float* fy, float* fz,
+                       uint32_t flags);
+/* Forget the predictor-corrector history: the next ibm_step_pc starts a new
+ * trajectory with Runge-Kutta steps. */
+ibm_status ibm_pc_reset(ibm_ctx* ctx);
+
 /* Adjoint of one step (a vector-Jacobian product, loose coupling with the
  * flow frozen; Sec. 2.3 node update, Sec. 2.2 traction, Sec. 2.3 potentials):
  * given cotangents gx_next, gv_next [3][V] of the positions and velocities

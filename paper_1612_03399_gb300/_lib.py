@@ -62,6 +62,8 @@ SIGNATURES = {
     "ibm_advance": (C.c_int, [P, P, P, P, P, P, P]),
     "ibm_spread": (C.c_int, [P, P, P, P, P, P]),
     "ibm_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
+    "ibm_step_pc": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
+    "ibm_pc_reset": (C.c_int, [P]),
     "ibm_check_device_error": (C.c_int, [P]),
     "ibm_set_phase_timing": (C.c_int, [P, C.c_int32]),
     "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
@@ -247,6 +249,19 @@ class Context:
         self._check(self.lib.ibm_step(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
                                       _ptr(p), _ptr(accel), _ptr(x_out), _ptr(v_out), _ptr(fx),
                                       _ptr(fy), _ptr(fz), IBM_STEP_CLEAR_PREV if clear else 0))
+
+    def step_pc(self, x, v, fields, x_out, v_out, f, clear=True, p=None, accel=None):
+        """One Hamming predictor-corrector step (ibm_step_pc); the context
+        keeps the history, so (x, v) must be the previous call's outputs."""
+        u, vv, w = fields
+        fx, fy, fz = f
+        self._check(self.lib.ibm_step_pc(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
+                                         _ptr(p), _ptr(accel), _ptr(x_out), _ptr(v_out),
+                                         _ptr(fx), _ptr(fy), _ptr(fz),
+                                         IBM_STEP_CLEAR_PREV if clear else 0))
+
+    def pc_reset(self):
+        self._check(self.lib.ibm_pc_reset(self.h))
 
     def backward(self, x, fields, gx_next, gv_next, p=None, accel=None):
         """Cotangents (gx, gv, gparams [B, 5]) of one step from x (ibm_backward)."""

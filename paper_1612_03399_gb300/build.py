@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libibm_gb300.so")
 SOURCES = ["ibm_host.cu", "k_mls.cu", "k_force.cu", "k_adjoint.cu", "k_taylor.cu",
-           "ibm_noalloc.cu", "ibm_gts.cu"]
+           "ibm_noalloc.cu", "ibm_gts.cu", "k_pc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -10,7 +10,9 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <initializer_list>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "ibm_internal.cuh"
@@ -932,6 +934,174 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     c->timed = c->timing;
   }
   return cuda_status(c, e, "ibm_step");
+}
+
+namespace {
+
+// acceleration a = (F_int + F_ext^v)/m at positions x: body sums, probe
+// traction (the marker kernel's measure and probe parts) and the force
+// kernel in its acceleration mode
+cudaError_t eval_accel(ibm_ctx* c, const float* x, const float* u, const float* vv,
+                       const float* w, const float* p, const float* accel, float* a) {
+  cudaError_t e = zero_body_sums(c);
+  if (e == cudaSuccess)
+    e = launch_mls(c, x, nullptr, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, nullptr,
+                   nullptr, nullptr, true, false, true, false, false);
+  if (e == cudaSuccess) e = launch_accel(c, x, c->d.fext, a);
+  return e;
+}
+
+void pc_allocate(ibm_ctx* c) {
+  auto& P = c->pc;
+  if (P.pcx) return;
+  const size_t n = 3 * (size_t)c->V;
+  for (int k = 0; k < 3; ++k) {
+    P.yx[k] = zeros<float>(c, n);
+    P.yv[k] = zeros<float>(c, n);
+    P.a[k] = zeros<float>(c, n);
+  }
+  P.pcx = zeros<float>(c, n);
+  P.pcv = zeros<float>(c, n);
+  P.px = zeros<float>(c, n);
+  P.pv = zeros<float>(c, n);
+  P.mx = zeros<float>(c, n);
+  P.mv = zeros<float>(c, n);
+  P.am = zeros<float>(c, n);
+  P.sx = zeros<float>(c, n);
+  P.v2 = zeros<float>(c, n);
+  P.v3 = zeros<float>(c, n);
+  P.v4 = zeros<float>(c, n);
+  P.a2 = zeros<float>(c, n);
+  P.a3 = zeros<float>(c, n);
+  P.a4 = zeros<float>(c, n);
+}
+
+LinComb lc(std::initializer_list<std::pair<float, const float*>> terms) {
+  LinComb L{};
+  for (const auto& t : terms) {
+    L.c[L.k] = t.first;
+    L.in[L.k] = t.second;
+    ++L.k;
+  }
+  return L;
+}
+
+}  // namespace
+
+extern "C" ibm_status ibm_pc_reset(ibm_ctx* c) {
+  if (!c) return IBM_ERR_INVALID_ARG;
+  c->pc.steps = 0;
+  c->pc.have_pc = false;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_step_pc(ibm_ctx* c, const float* x, const float* v, const float* u,
+                                  const float* vv, const float* w, const float* p,
+                                  const float* accel, float* x_out, float* v_out, float* fx,
+                                  float* fy, float* fz, uint32_t flags) {
+  if (!c || !x || !v || !u || !vv || !w || !x_out || !v_out || !fx || !fy || !fz)
+    return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (x_out == x || v_out == v || x_out == v || v_out == x)
+    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_step_pc: outputs must not alias the inputs");
+  cudaSetDevice(c->device);
+  try {
+    pc_allocate(c);
+  } catch (Failure& f) {
+    return set_err(c, f.s, f.msg);
+  }
+  auto& P = c->pc;
+  const float h = c->sc.dt;
+  const bool clear = (flags & IBM_STEP_CLEAR_PREV) != 0;
+  use_parity(c, c->qpar ^ 1);
+  // at y_n: footprint clear, interpolation, spreading, probe traction, body
+  // sums (as ibm_step), then a_n
+  cudaError_t e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
+  if (e == cudaSuccess)
+    e = launch_mls(c, x, v, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz,
+                   true, true, true, true, clear);
+  float* an = P.a[0];
+  if (e == cudaSuccess) e = launch_accel(c, x, c->d.fext, an);
+  if (P.steps < 3) {
+    // classical Runge-Kutta start-up: k_i = (v_i, a_i)
+    if (e == cudaSuccess) e = launch_lincomb(c, P.sx, lc({{1.f, x}, {0.5f * h, v}}));
+    if (e == cudaSuccess) e = launch_lincomb(c, P.v2, lc({{1.f, v}, {0.5f * h, an}}));
+    if (e == cudaSuccess) e = eval_accel(c, P.sx, u, vv, w, p, accel, P.a2);
+    if (e == cudaSuccess) e = launch_lincomb(c, P.sx, lc({{1.f, x}, {0.5f * h, P.v2}}));
+    if (e == cudaSuccess) e = launch_lincomb(c, P.v3, lc({{1.f, v}, {0.5f * h, P.a2}}));
+    if (e == cudaSuccess) e = eval_accel(c, P.sx, u, vv, w, p, accel, P.a3);
+    if (e == cudaSuccess) e = launch_lincomb(c, P.sx, lc({{1.f, x}, {h, P.v3}}));
+    if (e == cudaSuccess) e = launch_lincomb(c, P.v4, lc({{1.f, v}, {h, P.a3}}));
+    if (e == cudaSuccess) e = eval_accel(c, P.sx, u, vv, w, p, accel, P.a4);
+    const float s = h / 6.f;
+    if (e == cudaSuccess)
+      e = launch_lincomb(c, x_out, lc({{1.f, x}, {s, v}, {2.f * s, P.v2}, {2.f * s, P.v3},
+                                       {s, P.v4}}));
+    if (e == cudaSuccess)
+      e = launch_lincomb(c, v_out, lc({{1.f, v}, {s, an}, {2.f * s, P.a2}, {2.f * s, P.a3},
+                                       {s, P.a4}}));
+    P.have_pc = false;
+  } else {
+    HamPredict Pr{};
+    Pr.x3 = P.yx[2];
+    Pr.v3 = P.yv[2];
+    Pr.vn = v;
+    Pr.vn1 = P.yv[0];
+    Pr.vn2 = P.yv[1];
+    Pr.an = an;
+    Pr.an1 = P.a[1];
+    Pr.an2 = P.a[2];
+    Pr.pcx = P.pcx;
+    Pr.pcv = P.pcv;
+    Pr.px = P.px;
+    Pr.pv = P.pv;
+    Pr.mx = P.mx;
+    Pr.mv = P.mv;
+    Pr.h = h;
+    Pr.first = P.have_pc ? 0 : 1;
+    if (e == cudaSuccess) e = launch_ham_predict(c, Pr);
+    if (e == cudaSuccess) e = eval_accel(c, P.mx, u, vv, w, p, accel, P.am);
+    HamCorrect Co{};
+    Co.xn = x;
+    Co.vn = v;
+    Co.x2 = P.yx[1];
+    Co.v2 = P.yv[1];
+    Co.vn1 = P.yv[0];
+    Co.an = an;
+    Co.an1 = P.a[1];
+    Co.mv = P.mv;
+    Co.am = P.am;
+    Co.px = P.px;
+    Co.pv = P.pv;
+    Co.clamp = c->d.clamp;
+    Co.xo = x_out;
+    Co.vo = v_out;
+    Co.pcx = P.pcx;
+    Co.pcv = P.pcv;
+    Co.h = h;
+    if (e == cudaSuccess) e = launch_ham_correct(c, Co);
+    P.have_pc = true;
+  }
+  // history: y_n joins the ring (its oldest buffer is reused), a_n likewise
+  if (e == cudaSuccess) {
+    float* ox = P.yx[2];
+    float* ov = P.yv[2];
+    P.yx[2] = P.yx[1];
+    P.yv[2] = P.yv[1];
+    P.yx[1] = P.yx[0];
+    P.yv[1] = P.yv[0];
+    P.yx[0] = ox;
+    P.yv[0] = ov;
+    const size_t bytes = sizeof(float) * 3 * (size_t)c->V;
+    e = cudaMemcpyAsync(ox, x, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ov, v, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    float* oa = P.a[2];
+    P.a[2] = P.a[1];
+    P.a[1] = P.a[0];
+    P.a[0] = oa;
+    ++P.steps;
+    c->have_prev = clear;
+  }
+  return cuda_status(c, e, "ibm_step_pc");
 }
 
 struct ibm_graph {

@@ -149,6 +149,26 @@ constexpr int kMaxNodes = 35 * kMT;                                // staged nod
 constexpr int kRowTableBytes = ((4 * (7 * kMaxRows + 1) + 2 * (kMaxNodes / 4)) + 15) / 16 * 16;
 constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes;
 
+// elementwise combinations of [3][V] arrays for the strong-coupling integrator
+constexpr int kLinCombMax = 6;
+struct LinComb {              // out = sum_j c[j] in[j], j < k
+  const float* in[kLinCombMax];
+  float c[kLinCombMax];
+  int k;
+};
+struct HamPredict {           // predictor p and modified value m (x and v parts)
+  const float *x3, *v3, *vn, *vn1, *vn2, *an, *an1, *an2, *pcx, *pcv;
+  float *px, *pv, *mx, *mv;
+  float h;
+  int first;                  // no p_n - c_n yet: m = p
+};
+struct HamCorrect {           // corrector, final value and p - c
+  const float *xn, *vn, *x2, *v2, *vn1, *an, *an1, *mv, *am, *px, *pv;
+  const uint8_t* clamp;
+  float *xo, *vo, *pcx, *pcv;
+  float h;
+};
+
 // 64-bit integer to float without a 64-bit conversion instruction
 __device__ __forceinline__ float i64_to_float(long long d) {
   return fmaf((float)(int)(d >> 32), 4294967296.f, (float)(unsigned)(d & 0xffffffffll));
@@ -185,6 +205,19 @@ struct ibm_ctx {
   // kernel still reads the other (overlap inside captured multi-step graphs)
   unsigned long long* qsum_base = nullptr;   // [2][B][2]
   int qpar = 0;
+  // strong coupling (Hamming predictor-corrector): history and scratch, each
+  // array [3][V], allocated on the first ibm_step_pc
+  struct PCState {
+    int steps = 0;              // steps since ibm_pc_reset; the first three are Runge-Kutta
+    bool have_pc = false;       // p_n - c_n of the previous step is available
+    float* yx[3] = {};          // x of y_{n-1}, y_{n-2}, y_{n-3}
+    float* yv[3] = {};          // v of the same
+    float* a[3] = {};           // a_n, a_{n-1}, a_{n-2}
+    float *pcx = nullptr, *pcv = nullptr, *px = nullptr, *pv = nullptr, *mx = nullptr,
+          *mv = nullptr, *am = nullptr;
+    float *sx = nullptr, *v2 = nullptr, *v3 = nullptr, *v4 = nullptr, *a2 = nullptr,
+          *a3 = nullptr, *a4 = nullptr;   // Runge-Kutta stages
+  } pc;
   bool timing = false;          // record phase events in ibm_step
   bool timed = false;           // a timed step has been recorded
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -211,6 +244,11 @@ cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float
                          float* Fint, float* x_out, float* v_out, double* energy, bool advance);
 cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,
                            const float* Fext, float* x_out, float* v_out);
+// a = (F_int + F_ext^v)/m at x (zero on clamped nodes), from per-face F_ext
+cudaError_t launch_accel(ibm_ctx* c, const float* x, const float* Fext, float* a);
+cudaError_t launch_lincomb(ibm_ctx* c, float* out, const LinComb& L);
+cudaError_t launch_ham_predict(ibm_ctx* c, const HamPredict& P);
+cudaError_t launch_ham_correct(ibm_ctx* c, const HamCorrect& C);
 cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
                             const float* w, const float* p, const float* accel,
                             const float* gx_next, const float* gv_next, float* gx, float* gv,

@@ -46,7 +46,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <bool ADVANCE>
+// MODE 0: F_int only; 1: F_int + F_ext^v and the node update; 2: the
+// acceleration (F_int + F_ext^v)/m, zero on clamped nodes, into Fint
+template <int MODE>
 __global__ void __launch_bounds__(kForceThreads) force_kernel(
     DeviceTables T, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ v, const float* __restrict__ Fext, float* __restrict__ Fint,
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     const float ka = B.varied ? B.ka * __ldg(T.kaf + B.f_off + r.fid) : B.ka;
     face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid), ka,
                 cA, cV, f, gA, gV, ua, ea);
-    if (ADVANCE) {
+    if (MODE != 0) {
       // F_ext^v = sum over the vertex's faces of F_ext / 3: each face adds a
       // third of its load to its corner slots, gathered with the forces
       const int gf = B.f_off + r.fid;
@@ -141,10 +143,15 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     }
     const int lv = P.own0 + i;
     const int gv = B.v_off + lv;
-    if (!ADVANCE) {
+    if (MODE == 0) {
       Fint[gv] = fx;
       Fint[V + gv] = fy;
       Fint[2 * V + gv] = fz;
+    } else if (MODE == 2) {
+      const bool cl = T.clamp[gv] != 0;
+      Fint[gv] = cl ? 0.f : fx * B.inv_mass;
+      Fint[V + gv] = cl ? 0.f : fy * B.inv_mass;
+      Fint[2 * V + gv] = cl ? 0.f : fz * B.inv_mass;
     } else {
       // the gathered slots hold F_int + F_ext^v
       const float ax = fx * B.inv_mass, ay = fy * B.inv_mass, az = fz * B.inv_mass;
@@ -248,11 +255,18 @@ cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float
                          float* Fint, float* x_out, float* v_out, double* energy, bool advance) {
   if (c->n_work == 0) return cudaSuccess;
   if (advance)
-    force_kernel<true><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
+    force_kernel<1><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
         c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, Fext, Fint, x_out, v_out, energy);
   else
-    force_kernel<false><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
+    force_kernel<0><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
         c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, Fext, Fint, x_out, v_out, energy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accel(ibm_ctx* c, const float* x, const float* Fext, float* a) {
+  if (c->n_work == 0) return cudaSuccess;
+  force_kernel<2><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
+      c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, nullptr, Fext, a, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -266,10 +280,13 @@ cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const flo
 }
 
 cudaError_t set_force_smem_limit(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(force_kernel<true>,
+  cudaError_t e = cudaFuncSetAttribute(force_kernel<1>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(force_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(force_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(force_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)bytes);
 }
 

@@ -964,6 +964,7 @@ cudaError_t set_marker_smem_limit() {
     e = cudaFuncSetAttribute(marker_kernel<M, I, P, S>,                                      \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kMarkerSmemBytes);
   SET(true, true, true, true)
+  SET(true, false, true, false)
   SET(false, true, true, false)
   SET(false, true, false, false)
   SET(false, false, true, false)
@@ -982,6 +983,7 @@ cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* 
   launch_t<M, I, P, S>(c, x, v, u, vv, w, pr, accel, U, Fm, Fm_in, Fext, fx, fy, fz, rb)
   if (measure && interp && probe && spread) return L(true, true, true, true);
   if (measure && !interp && !probe && !spread) return L(true, false, false, false);
+  if (measure && !interp && probe && !spread) return L(true, false, true, false);
   if (!measure && interp && probe && !spread) return L(false, true, true, false);
   if (!measure && interp && !probe && !spread) return L(false, true, false, false);
   if (!measure && !interp && probe && !spread) return L(false, false, true, false);
