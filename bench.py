@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--patch", type=int, default=0)
+    ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "hamming"],
+                    help="hamming: the strong-coupling predictor-corrector step (ibm_step_pc), "
+                         "steps launched one by one")
     ap.add_argument("--bodies", type=int, default=0,
                     help="profiling only: fewer drops on the same grid (drops1000 workload)")
     return ap.parse_args()
@@ -334,8 +337,11 @@ def run_gb300(args, ws, rank, local):
     f = tuple(torch.zeros((nz, ny, nx), dtype=torch.float32, device=device) for _ in range(3))
     xa, va = ctx.init_state()
     xb, vb = torch.empty_like(xa), torch.empty_like(va)
-    bytes_model = byte_model(wl, ctx, xa, device) if rank == 0 else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)   # > L2 (129 MB)
+    if args.integrator == "hamming":
+        return run_hamming(args, ws, rank, ctx, wl, descr, fields, f, xa, va, xb, vb, flush,
+                           device, patch)
+    bytes_model = byte_model(wl, ctx, xa, device) if rank == 0 else None
     ctx.set_phase_timing(True)
     for _ in range(max(args.warmup, 3)):
         ctx.step(xa, va, fields, xb, vb, f)
@@ -453,6 +459,52 @@ def run_gb300(args, ws, rank, local):
                                 "kind": "oracle",
                                 "sample": f"{nb} of the {ctx.B} bodies ({nodes} nodes) on the full "
                                           f"grid and field, 2 steps, {secs:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def run_hamming(args, ws, rank, ctx, wl, descr, fields, f, xa, va, xb, vb, flush, device,
+                patch):
+    """Throughput of the strong-coupling step (ibm_step_pc): Hamming's
+    predictor-corrector, two acceleration evaluations per step, after the
+    three Runge-Kutta start-up steps; steps launched one by one."""
+    stream = torch.cuda.current_stream(device)
+    ctx.pc_reset()
+    for _ in range(3 + max(args.warmup, 3)):
+        ctx.step_pc(xa, va, fields, xb, vb, f)
+        xa, va, xb, vb = xb, vb, xa, va
+    ctx.check_device_error()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(device.index)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    total = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        ctx.step_pc(xa, va, fields, xb, vb, f)
+        ev1.record(stream)
+        ev1.synchronize()
+        total += ev0.elapsed_time(ev1)
+        xa, va, xb, vb = xb, vb, xa, va
+    clk = clocks.stop()
+    ctx.check_device_error()
+    barrier(ws)
+    value, t_max = job_rate(ws, ctx.V, args.steps, total, device)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": descr, "integrator": "Hamming predictor-corrector (ibm_step_pc)",
+                   "bodies": ctx.B, "vertices": ctx.V, "grid": list(wl.grid.n),
+                   "l2": "flushed between timed steps (256 MiB write)", "patch_size": patch},
+        # per step: clear, marker, force (acceleration), predictor, marker, force, corrector
+        "gpu_launches": 7 * args.steps,
+        "clocks": clk,
+    }
     print(json.dumps(line), flush=True)
 
 
