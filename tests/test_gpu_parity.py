@@ -308,3 +308,46 @@ def test_single_triangle_and_tiny_grid():
     if H.tie_free(wl, xs):
         assert H.rel_l2(U.double().cpu().numpy().T, out["U"].numpy()) <= 1e-5
         assert H.rel_l2(Fe.double().cpu().numpy().T, out["F_ext_face"].numpy()) <= 1e-5
+
+
+def test_scalar_row_path_two_steps_with_pressure(record_error):
+    """nx not a multiple of 4: rows are staged, flushed and cleared node by
+    node instead of in float4 groups.  Two steps (the second clears the
+    first's footprint), with a pressure field (staged like a velocity
+    component), against the oracle on the second step."""
+    wl = mixed_workload(n=(37, 41, 33), L=(1.0, 1.1, 0.9))
+    ob = H.oracle_bodies(wl)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    rel = tie_free_state(wl, 40, scale=0.03, stretch=0.03)
+    x = H.state_tensor(wl, rel)
+    v = torch.zeros_like(x)
+    fields = H.fields_for(wl, DEV)
+    rng = np.random.default_rng(8)
+    spec = W.pressure_modes(8, 3, 5.0, rng)
+    p = W.sample_pressure(spec, wl.grid, device=DEV)
+    p64 = W.sample_pressure(spec, wl.grid, dtype=torch.float64)
+    nx, ny, nz = wl.grid.n
+    f = tuple(torch.zeros((nz, ny, nx), dtype=torch.float32, device=DEV) for _ in range(3))
+    x1, v1 = torch.empty_like(x), torch.empty_like(v)
+    x2, v2 = torch.empty_like(x), torch.empty_like(v)
+    ctx.step(x, v, fields, x1, v1, f, p=p)
+    ctx.step(x1, v1, fields, x2, v2, f, p=p)
+    ctx.check_device_error()
+    xs = H.to_abs(wl, H.split_state(ctx, wl, x1))
+    if not H.tie_free(wl, xs):
+        pytest.skip("second-step markers too close to a nearest-node switch")
+    vs = [torch.tensor(a) for a in H.split_state(ctx, wl, v1)]
+    out = O.step(ob, xs, vs, tuple(t.double().cpu() for t in fields), H.oracle_params(wl),
+                 pressure=p64)
+    vg = H.split_state(ctx, wl, v2)
+    for i in range(len(ob)):
+        vo = out["v_next"][i].numpy()
+        dv_o = vo - vs[i].numpy()
+        store = np.linalg.norm(0.5 * np.spacing(np.abs(vo).astype(np.float32)).astype(np.float64))
+        excess = max(0.0, np.linalg.norm((vg[i] - vs[i].numpy()) - dv_o) - store) / np.linalg.norm(dv_o)
+        record_error(f"dv[{i}]", excess)
+        assert excess <= 1e-5, (i, excess)
+    got = torch.stack(f).double().cpu().numpy()
+    e = H.rel_l2(got, out["f"].numpy())
+    record_error("f", e)
+    assert e <= 1e-5
