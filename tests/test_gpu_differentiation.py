@@ -123,3 +123,18 @@ def test_rollout_gradients_match_oracle_and_differences(record_error):
     directional = float((gk[:, 0] * k.detach().cpu().numpy()[:, 0]).sum())
     record_error("fd_ks_directional", abs(fd - directional) / abs(directional))
     assert fd == pytest.approx(directional, rel=5e-2)
+
+
+def test_calibration_lowers_the_loss(record_error):
+    """Gradient descent on log k_s, log k_b per drop (calibrate.py) lowers
+    sum (D - D*)^2 over a few iterations, targets above the initial D."""
+    from paper_1612_03399_gb300.autograd import Simulation
+    from paper_1612_03399_gb300.calibrate import calibrate
+    wl = shear_drops()
+    sim = Simulation(wl.bodies, wl.grid, wl.field, dt=wl.dt)
+    x0, v0 = sim.ctx.init_state()
+    target = np.array([0.05, 0.08, 0.06])
+    _, hist = calibrate(sim, x0, v0, target, n_steps=6, checkpoint_every=3, iters=4, lr=0.3)
+    losses = [h["loss"] for h in hist]
+    record_error("calibration_loss_ratio", losses[-1] / losses[0])
+    assert all(b < a for a, b in zip(losses, losses[1:])), losses
