@@ -893,15 +893,18 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
     const int nrows = sz.w;
     const int2* rm = T.rowmap + (size_t)blockIdx.x * kMaxRows;
     const int al = nx % 8 == 0 ? 8 : 4;   // widening, in floats
-    // a thread per row (rows are a few float4 groups long)
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+    // eight lanes per row: each store instruction of a warp covers four rows
+    // with one contiguous 128-byte span each (a thread per row would scatter
+    // 32 rows over one instruction)
+    const int sub = threadIdx.x & 7;
+    for (int r = threadIdx.x >> 3; r < nrows; r += blockDim.x >> 3) {
       const int2 e = rm[r];                  // (row base, first x wrapped | length << 16)
       int L = e.y >> 16, x0 = e.y & 0xFFFF;  // L <= nx, x0 < nx
       if (L <= 0) continue;
       if (vec4) {
         L = min((L + (x0 & (al - 1)) + al - 1) & ~(al - 1), nx);
         x0 &= ~(al - 1);
-        for (int q = 0; q < L; q += 4) {
+        for (int q = 4 * sub; q < L; q += 32) {
           int xg = x0 + q;
           if (xg >= nx) xg -= nx;
           const size_t o = (size_t)e.x + xg;
@@ -911,7 +914,7 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
           *reinterpret_cast<float4*>(fz + o) = z4;
         }
       } else {
-        for (int q = 0; q < L; ++q) {
+        for (int q = sub; q < L; q += 8) {
           int xg = x0 + q;
           if (xg >= nx) xg -= nx;
           const size_t o = (size_t)e.x + xg;
