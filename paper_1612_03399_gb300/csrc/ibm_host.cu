@@ -328,6 +328,20 @@ void free_all(ibm_ctx* c) {
 
 bool is_fin(double v) { return std::isfinite(v); }
 
+// Within every full marker patch, store face t of the marker block's threads
+// at position t, where thread t works on face W (t % 32) + t / 32 of the
+// patch's spatial order (W warps): the warp's faces are spread over the patch
+// (its simultaneous shared atomics of the spread rarely meet on a node) while
+// its loads of the face records stay contiguous.
+void interleave_full_patches(std::vector<int32_t>& mface, const std::vector<int32_t>& mbound) {
+  std::vector<int32_t> tmp(kMT);
+  for (size_t k = 0; k + 1 < mbound.size(); ++k) {
+    if (mbound[k + 1] - mbound[k] != kMT) continue;
+    for (int t = 0; t < kMT; ++t) tmp[t] = mface[mbound[k] + (kMT / 32) * (t & 31) + (t >> 5)];
+    std::copy(tmp.begin(), tmp.end(), mface.begin() + mbound[k]);
+  }
+}
+
 // select body-sum buffer p (0 or 1) for the launches that follow
 void use_parity(ibm_ctx* c, int p) {
   c->qpar = p;
@@ -468,6 +482,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
         try {
           build_topology(topos.back(), B.tri, B.n_vert, B.n_face, P);
           marker_patches(B.tri, B.n_face, B.rest, topos.back().mface, topos.back().mbound);
+          interleave_full_patches(topos.back().mface, topos.back().mbound);
         } catch (Failure& f) {
           f.msg = "body " + std::to_string(b) + ": " + f.msg;
           throw;

@@ -410,12 +410,10 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   bool ok = false;
   int gf = 0;
   if (active) {
-    // threads of a warp take faces spread over the patch (t -> W (t % 32) + t / 32
-    // with W warps, for full patches), so that one warp's simultaneous shared
-    // atomics of the spread rarely meet on a node
-    const int slot =
-        (ch.z == kMT) ? (kMT / 32) * (threadIdx.x & 31) + (threadIdx.x >> 5) : threadIdx.x;
-    const int4 mt = __ldg(T.mtri + topo.mface_off + ch.y + slot);
+    // full patches are stored so that a warp's faces are spread over the patch
+    // (its shared atomics of the spread rarely meet on a node) while thread t
+    // reads record t
+    const int4 mt = __ldg(T.mtri + topo.mface_off + ch.y + threadIdx.x);
     gf = B.f_off + mt.w;
     const int ia = B.v_off + mt.x, ib = B.v_off + mt.y, ic = B.v_off + mt.z;
     float xa[3], xb[3], xc[3];
