@@ -1,0 +1,313 @@
+"""Pins of the flow-solver oracle (Sec. 2.1 fluid phase, Sec. 5 coupled step):
+discrete identities of the staggered operators, exact solves, the RK3
+amplification polynomial, Crank-Nicolson diffusion of a single mode, the
+Taylor-Green vortex, and Galilean consistency of the coupled step; no GPU."""
+import math
+
+import numpy as np
+import torch
+
+from oracle import ibm_oracle as O
+from oracle import ns_oracle as N
+from paper_1612_03399_gb300 import workloads as W
+
+DT = torch.float64
+
+
+def grid(n, L=(1.0, 1.0, 1.0)):
+    h = tuple(L[d] / n[d] for d in range(3))
+    return n, h
+
+
+def rand_field(n, seed, k=3):
+    g = torch.Generator().manual_seed(seed)
+    return torch.randn((k, n[2], n[1], n[0]), generator=g, dtype=DT)
+
+
+def curl_field(n, h, seed):
+    """Solenoidal MAC field as the discrete curl of an edge vector potential
+    (A_x at (i+1/2, j, k) h, A_y at (i, j+1/2, k) h, A_z at (i, j, k+1/2) h);
+    forward differences commute, so its divergence vanishes identically,
+    independently of the oracle's projection."""
+    A = rand_field(n, seed)
+    fd = lambda f, d: (N.shift(f, d, 1) - f) / h[d]
+    u = fd(A[2], 1) - fd(A[1], 2)
+    v = fd(A[0], 2) - fd(A[2], 0)
+    w = fd(A[1], 0) - fd(A[0], 1)
+    return torch.stack([u, v, w])
+
+
+def mac_coords(n, h, comp):
+    """Node coordinates [nz,ny,nx] (x, y, z) of lattice comp (0..2 velocity, 3 pressure)."""
+    off = O.MAC_OFFSET[comp]
+    ax = [torch.arange(n[d], dtype=DT) * h[d] + off[d] * h[d] for d in range(3)]
+    z, y, x = torch.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return x, y, z
+
+
+def test_curl_field_is_solenoidal():
+    n, h = grid((12, 10, 8))
+    u = curl_field(n, h, 0)
+    assert float(N.divergence(u, h).abs().max()) < 1e-12 * float(u.abs().max()) / min(h)
+
+
+def test_divergence_and_gradient_are_negative_adjoints():
+    """Summation by parts on the periodic grid: sum p div(u) = -sum u . grad(p)."""
+    n, h = grid((12, 10, 8), (1.0, 1.3, 0.7))
+    u = rand_field(n, 1)
+    p = rand_field(n, 2, 1)[0]
+    lhs = float((p * N.divergence(u, h)).sum())
+    rhs = -float((u * N.gradient(p, h)).sum())
+    assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1.0)
+
+
+def test_divergence_of_gradient_is_the_laplacian():
+    n, h = grid((12, 10, 8), (1.0, 1.3, 0.7))
+    p = rand_field(n, 3, 1)[0]
+    assert torch.allclose(N.divergence(N.gradient(p, h), h), N.laplacian(p, h), atol=1e-9)
+
+
+def test_advection_conserves_momentum():
+    """Divergence form: every difference telescopes, so sum_k H_c = 0."""
+    n, h = grid((12, 10, 8))
+    u = rand_field(n, 4)
+    H = N.advection(u, h)
+    for c in range(3):
+        assert abs(float(H[c].sum())) < 1e-10 * float(H[c].abs().sum())
+
+
+def test_advection_conserves_kinetic_energy_of_solenoidal_fields():
+    """For a discretely solenoidal u the second-order staggered divergence form
+    is energy conserving: sum_c sum_k u_c H_c = 0 (to rounding)."""
+    n, h = grid((12, 10, 8), (1.0, 1.2, 0.9))
+    u = curl_field(n, h, 5)
+    H = N.advection(u, h)
+    e = float((u * H).sum())
+    assert abs(e) < 1e-11 * float((u * H).abs().sum())
+    # and not for a field with divergence (the pin would not be vacuous)
+    ur = rand_field(n, 6)
+    Hr = N.advection(ur, h)
+    assert abs(float((ur * Hr).sum())) > 1e-6 * float((ur * Hr).abs().sum())
+
+
+def test_advection_of_a_wave_by_a_uniform_stream():
+    """u = U0, v = sin(k x): H_u = H_w = 0 and H_v = -U0 cos(k x) sin(k h)/h
+    (centred difference of the transported wave)."""
+    n, h = grid((16, 4, 4))
+    U0, k = 0.7, 2.0 * math.pi * 3
+    x, _, _ = mac_coords(n, h, 1)
+    u = torch.stack([torch.full_like(x, U0), torch.sin(k * x), torch.zeros_like(x)])
+    H = N.advection(u, h)
+    assert float(H[0].abs().max()) < 1e-12 and float(H[2].abs().max()) < 1e-12
+    ref = -U0 * torch.cos(k * x) * math.sin(k * h[0]) / h[0]
+    assert torch.allclose(H[1], ref, atol=1e-12)
+
+
+def test_poisson_solve_residual():
+    n, h = grid((12, 10, 8), (1.0, 1.3, 0.7))
+    r = rand_field(n, 7, 1)[0]
+    r = r - r.mean()
+    phi = N.solve_poisson(r, n, h)
+    assert torch.allclose(N.laplacian(phi, h), r, atol=1e-9 * float(r.abs().max()))
+    assert abs(float(phi.mean())) < 1e-12
+
+
+def test_factorised_solve_inverts_the_three_factors():
+    """(1 - a d_xx)(1 - a d_yy)(1 - a d_zz) x = rhs, each factor applied with
+    its own three-point stencil."""
+    n, h = grid((12, 10, 8), (1.0, 1.3, 0.7))
+    rhs = rand_field(n, 8, 1)[0]
+    a = 3e-4
+    x = N.solve_factorised(rhs, a, n, h)
+    y = x
+    for d in range(3):
+        y = y - a * (N.shift(y, d, 1) - 2.0 * y + N.shift(y, d, -1)) / h[d] ** 2
+    assert torch.allclose(y, rhs, atol=1e-10 * float(rhs.abs().max()))
+
+
+def test_projection():
+    """The corrected field is solenoidal; a solenoidal field passes unchanged
+    and leaves the pressure unchanged."""
+    flow = N.Flow((12, 10, 8), nu=0.1, dt=1e-2)
+    u = rand_field(flow.n, 9)
+    p = rand_field(flow.n, 10, 1)[0]
+    for l in range(3):
+        un, pn = N.project(flow, l, u, p)
+        assert float(N.divergence(un, flow.h).abs().max()) < 1e-9 * float(u.abs().max()) / min(flow.h)
+    us = curl_field(flow.n, flow.h, 11)
+    un, pn = N.project(flow, 1, us, p)
+    assert torch.allclose(un, us, atol=1e-10 * float(us.abs().max()))
+    assert torch.allclose(pn, p, atol=1e-9)
+
+
+def test_rk3_amplification_of_an_advected_wave():
+    """With nu = 0, v = Im(e^{i k x}) carried by u = U0 evolves as a single
+    linear mode, v' = Im(R(z) e^{i k x}) with z = -i U0 dt sin(k h)/h; the
+    three-substep scheme is third order, so R(z) = 1 + z + z^2/2 + z^3/6."""
+    flow = N.Flow((16, 4, 4), nu=0.0, dt=0.02)
+    U0, k = 0.8, 2.0 * math.pi * 2
+    x, _, _ = mac_coords(flow.n, flow.h, 1)
+    u = torch.stack([torch.full_like(x, U0), torch.sin(k * x), torch.zeros_like(x)])
+    p = torch.zeros_like(x)
+    un, pn = N.ns_step(flow, u, p)
+    z = -1j * U0 * flow.dt * math.sin(k * flow.h[0]) / flow.h[0]
+    R = 1 + z + z * z / 2 + z ** 3 / 6
+    ref = R.real * torch.sin(k * x) + R.imag * torch.cos(k * x)
+    assert torch.allclose(un[1], ref, atol=1e-12)
+    assert torch.allclose(un[0], u[0], atol=1e-12)
+    assert float(un[2].abs().max()) < 1e-12 and float(pn.abs().max()) < 1e-10
+
+
+def test_crank_nicolson_diffusion_of_a_mode():
+    """U0 = 0, nu > 0, v = sin(k x): per substep the Crank-Nicolson factor
+    (1 + a_l lam)/(1 - a_l lam), a_l = alpha_l dt nu/2, lam the eigenvalue of
+    the second difference; the product is exp(nu lam dt) to second order."""
+    flow = N.Flow((16, 4, 4), nu=0.05, dt=0.01)
+    k = 2.0 * math.pi * 3
+    x, _, _ = mac_coords(flow.n, flow.h, 1)
+    u = torch.stack([torch.zeros_like(x), torch.sin(k * x), torch.zeros_like(x)])
+    un, _ = N.ns_step(flow, u, torch.zeros_like(x))
+    lam = -(4.0 / flow.h[0] ** 2) * math.sin(k * flow.h[0] / 2) ** 2
+    g = 1.0
+    for a in N.ALPHA:
+        al = a * flow.dt * flow.nu / 2.0
+        g *= (1.0 + al * lam) / (1.0 - al * lam)
+    assert torch.allclose(un[1], g * torch.sin(k * x), atol=1e-12)
+    s = flow.nu * lam * flow.dt
+    assert abs(g - math.exp(s)) <= abs(s) ** 3
+    assert sum(N.ALPHA) == 1.0 or abs(sum(N.ALPHA) - 1.0) < 1e-15
+
+
+def test_taylor_green_vortex_decay():
+    """u = sin x cos y, v = -cos x sin y in a 2 pi box is an exact solution of
+    Eqs. ns, con that keeps its shape and decays as exp(-2 nu t); the
+    discrete solution follows it to O(h^2 + dt^2)."""
+    L = (2 * math.pi, 2 * math.pi, 2 * math.pi / 8)
+    errs = []
+    for m in (16, 32):
+        flow = N.Flow((m, m, 4), L=L, nu=0.05, dt=0.02)
+        xu, yu, _ = mac_coords(flow.n, flow.h, 0)
+        xv, yv, _ = mac_coords(flow.n, flow.h, 1)
+        u0 = torch.stack([torch.sin(xu) * torch.cos(yu), -torch.cos(xv) * torch.sin(yv),
+                          torch.zeros_like(xu)])
+        u, p = u0.clone(), torch.zeros_like(xu)
+        steps = 25
+        for _ in range(steps):
+            u, p = N.ns_step(flow, u, p)
+        T = steps * flow.dt
+        amp = float((u * u0).sum() / (u0 * u0).sum())
+        errs.append(abs(amp / math.exp(-2 * flow.nu * T) - 1.0))
+        shape = u - amp * u0
+        assert float(shape.abs().max()) < 1e-3
+        assert float(N.divergence(u, flow.h).abs().max()) < 1e-10
+    assert errs[1] < 1e-3
+    assert errs[1] < errs[0] / 3.0      # second-order convergence in h
+
+
+def small_drop(level=1, r=0.2, centre=(0.5, 0.5, 0.5), **k):
+    v, t = W.icosphere(level)
+    c = np.array(centre)
+    return O.Body(c + r * v, t, c, **k)
+
+
+def test_coupled_step_without_bodies_is_the_flow_step():
+    flow = N.Flow((12, 10, 8), nu=0.1, dt=1e-2)
+    prm = O.Params(flow.n, dt=flow.dt, mu=flow.nu)
+    u = curl_field(flow.n, flow.h, 12)
+    p = rand_field(flow.n, 13, 1)[0]
+    _, _, uc, pc, _ = N.coupled_step([], [], [], u, p, flow, prm)
+    un, pn = N.ns_step(flow, u, p)
+    assert torch.equal(uc, un) and torch.equal(pc, pn)
+
+
+def test_coupled_step_uniform_flow_translates_bodies():
+    """A body at rest shape moving with a uniform stream U0: no slip at the
+    markers (MLS reproduces constants), so the forcing vanishes, the flow
+    stays uniform with zero pressure, and the body translates by dt U0."""
+    n = (16, 16, 16)
+    flow = N.Flow(n, nu=0.1, dt=1e-3)
+    prm = O.Params(n, dt=flow.dt, mu=flow.nu)
+    b = small_drop(level=1, ks=1.0, kb=0.05)
+    U0 = torch.tensor([0.3, -0.2, 0.5], dtype=DT)
+    u = U0[:, None, None, None].expand(3, n[2], n[1], n[0]).clone()
+    p = torch.zeros((n[2], n[1], n[0]), dtype=DT)
+    x = b.rest.clone()
+    v = U0.expand_as(x).clone()
+    xs, vs, un, pn, f = N.coupled_step([b], [x], [v], u, p, flow, prm)
+    assert float(f.abs().max()) < 1e-9
+    assert torch.allclose(un, u, atol=1e-10)
+    assert float(pn.abs().max()) < 1e-9
+    assert torch.allclose(xs[0], x + flow.dt * U0, atol=1e-12)
+    assert torch.allclose(vs[0], v, atol=1e-9)
+
+
+def test_forcing_reduces_the_slip_at_the_markers():
+    """A body at rest in a uniform stream: the corrected provisional velocity
+    u* + dt f has a smaller slip U - V^b at the markers than u* (the direct
+    forcing pushes the flow toward the body velocity, Sec. 2.2)."""
+    n = (16, 16, 16)
+    prm = O.Params(n, dt=1e-3, mu=0.1)
+    b = small_drop(level=2)
+    U0 = torch.tensor([0.3, -0.2, 0.5], dtype=DT)
+    u = U0[:, None, None, None].expand(3, n[2], n[1], n[0]).clone()
+    x = b.rest.clone()
+    v = torch.zeros_like(x)
+    f = N.ibm_forcing([b], [x], [v], u, prm)
+    C, _, _ = O.face_geometry(x, b.tri)
+
+    def slip(field):
+        U = torch.stack([O.interpolate(field[i], C, i, n, prm.h, prm.alpha) for i in range(3)], 1)
+        return float(U.norm(dim=1).mean())
+
+    assert slip(u + prm.dt * f) < 0.6 * slip(u)
+
+
+def test_pressure_update_keeps_the_substep_consistent():
+    """For fields that vary along x only the factorised operator is exact, and
+    the pressure update p + phi - a lap(phi), a = alpha dt nu/2, makes the
+    projected substep satisfy the Crank-Nicolson momentum equation with the
+    new pressure: (1 - a lap)(u_l - u) = dt (gamma H + rho H_prev
+    - alpha grad p_l + alpha nu lap u) to rounding (lap and grad commute on
+    the periodic grid)."""
+    flow = N.Flow((16, 4, 4), nu=0.7, dt=0.02)
+    h = flow.h
+    g = torch.Generator().manual_seed(14)
+    ux = torch.randn(flow.n[0], generator=g, dtype=DT)
+    px = torch.randn(flow.n[0], generator=g, dtype=DT)
+    shape = (flow.n[2], flow.n[1], flow.n[0])
+    u = torch.stack([ux.expand(shape).clone(), torch.zeros(shape, dtype=DT),
+                     torch.zeros(shape, dtype=DT)])
+    p = px.expand(shape).clone()
+    H_prev = N.advection(u * 0.5, h)
+    for l in (0, 1):
+        us, H = N.predict(flow, l, u, p, H_prev)
+        ul, pl = N.project(flow, l, us, p)
+        a = N.ALPHA[l] * flow.dt * flow.nu / 2.0
+        G = N.gradient(pl, h)
+        for c in range(3):
+            d = ul[c] - u[c]
+            lhs = d - a * N.laplacian(d, h)
+            rhs = N.GAMMA[l] * H[c] - N.ALPHA[l] * G[c] + N.ALPHA[l] * flow.nu * N.laplacian(u[c], h)
+            if N.RHO[l] != 0.0:
+                rhs = rhs + N.RHO[l] * H_prev[c]
+            assert torch.allclose(lhs, flow.dt * rhs, atol=1e-12), (l, c)
+        assert float((pl - p).abs().max()) > 1e-3      # the substep did correct the pressure
+
+
+def test_coupled_step_slows_the_flow_at_a_resting_body():
+    """A body at rest in a uniform stream: through the coupled step the flow
+    at its markers is pushed toward the body velocity (zero), while without
+    the body it stays uniform."""
+    n = (16, 16, 16)
+    flow = N.Flow(n, nu=0.1, dt=1e-3)
+    prm = O.Params(n, dt=flow.dt, mu=flow.nu)
+    b = small_drop(level=2, ks=1.0, kb=0.05)
+    U0 = torch.tensor([0.3, -0.2, 0.5], dtype=DT)
+    u = U0[:, None, None, None].expand(3, n[2], n[1], n[0]).clone()
+    p = torch.zeros((n[2], n[1], n[0]), dtype=DT)
+    x = b.rest.clone()
+    v = torch.zeros_like(x)
+    _, _, un, _, _ = N.coupled_step([b], [x], [v], u, p, flow, prm)
+    C, _, _ = O.face_geometry(x, b.tri)
+    U = torch.stack([O.interpolate(un[i], C, i, n, prm.h, prm.alpha) for i in range(3)], 1)
+    assert float(U.norm(dim=1).mean()) < 0.6 * float(U0.norm())
