@@ -277,6 +277,65 @@ void ibm_graph_destroy(ibm_graph* graph);
 ibm_status ibm_gts_read(const char* path, int64_t* n_vert, int64_t* n_face, double* xyz,
                         int32_t* tri);
 
+/* ---- The fluid phase and the coupled step (Sec. 2.1; Sec. 5 step 3) -------
+ * Incompressible Navier-Stokes, Eqs. ns and con, density 1 and kinematic
+ * viscosity nu = 1/Re, on the triply periodic MAC grid of the conventions
+ * above, with the pressure at the cell centres (i+1/2, j+1/2, k+1/2) h.
+ * Second-order centred conservative differences (divergence form) for the
+ * nonlinear terms, 7-point Laplacians for the viscous terms, and the
+ * self-starting three-substep RK3 fractional step: substep l = 0, 1, 2 with
+ * gamma = (8/15, 5/12, 3/4), rho = (0, -17/60, -5/12), alpha = gamma + rho,
+ *   (u* - u)/dt = gamma_l H(u) + rho_l H(u_prev) - alpha_l grad p
+ *                 + alpha_l nu/2 lap(u* + u)                      (predictor)
+ * with the implicit operator approximately factorised into
+ * (1 - a d_xx)(1 - a d_yy)(1 - a d_zz), a = alpha_l dt nu/2, then
+ *   lap(phi) = div(u*)/(alpha_l dt),  u = u* - alpha_l dt grad(phi),
+ *   p <- p + phi - a lap(phi)                                      (projection).
+ * In the periodic box both implicit operators are diagonal in Fourier space
+ * and are solved there exactly (cuFFT transforms, float32).  A flow object
+ * owns its work arrays (about eleven fields) and FFT plans; velocity and
+ * pressure fields are caller-owned device arrays [nz][ny][nx]. */
+typedef struct ibm_flow ibm_flow;
+
+/* Create a solver for grid (n >= 4 per direction; the reserved field is
+ * ignored) with viscosity nu >= 0 and time step dt > 0, on the current
+ * device; its calls run on the legacy default stream until
+ * ibm_flow_set_stream.  Errors (message in ibm_last_error(NULL)):
+ * IBM_ERR_INVALID_ARG, IBM_ERR_OOM, IBM_ERR_CUDA (no device, FFT plan). */
+ibm_status ibm_flow_create(const ibm_grid_desc* grid, double nu, double dt, ibm_flow** out);
+ibm_status ibm_flow_set_stream(ibm_flow* flow, void* stream);
+void ibm_flow_destroy(ibm_flow* flow);
+
+/* Predictor of RK3 substep `substep` (0, 1, 2): u, v, w <- u* in place, with
+ * p the pressure of the previous substep.  The nonlinear terms H(u) are kept
+ * in the flow object for the next substep's rho term, so the substeps of one
+ * time step must run in order (substep 0 needs none). */
+ibm_status ibm_flow_predict(ibm_flow* flow, int32_t substep, float* u, float* v, float* w,
+                            const float* p);
+
+/* Projection of substep `substep`: the provisional field u* + f_scale f
+ * (fx, fy, fz on the u, v, w lattices; all three NULL: no forcing) is made
+ * discretely solenoidal, u, v, w <- u; p is updated in place. */
+ibm_status ibm_flow_project(ibm_flow* flow, int32_t substep, float* u, float* v, float* w,
+                            float* p, const float* fx, const float* fy, const float* fz,
+                            float f_scale);
+
+/* One loosely coupled time step (Sec. 5 steps 1-4) on the context's stream:
+ * three substeps of predictor, IBM forcing and projection, where the forcing
+ * interpolates u* at the face centroids of x, forms F = (V^b - U*)/dt with
+ * V^b the centroid velocity of xv, spreads it into fx, fy, fz (overwritten:
+ * the last substep's forcing is left there) and adds dt f to u* (markers at
+ * x throughout); then the bodies advance x, xv -> x_out, v_out as ibm_step
+ * does, with the probe traction and pressure of the new u, v, w, p (no
+ * acceleration correction).  ctx NULL: the flow alone (x ... fz may be
+ * NULL).  The context's grid and dt must equal the flow's and its mu the
+ * flow's nu (density 1); x_out, v_out must not alias x, xv.  Errors:
+ * IBM_ERR_INVALID_ARG on a mismatch or a null argument (message in
+ * ibm_last_error(NULL) and, with a context, ibm_last_error(ctx)). */
+ibm_status ibm_flow_step(ibm_flow* flow, ibm_ctx* ctx, const float* x, const float* xv,
+                         float* x_out, float* v_out, float* u, float* v, float* w, float* p,
+                         float* fx, float* fy, float* fz);
+
 /* Synchronise the stream and report the device error word (IBM_ERR_DEVICE if
  * a kernel flagged an out-of-range or non-finite value). */
 ibm_status ibm_check_device_error(ibm_ctx* ctx);

@@ -77,6 +77,12 @@ SIGNATURES = {
     "ibm_taylor_backward": (C.c_int, [P, P, P, P, P]),
     "ibm_body_measures_noalloc": (C.c_int, [P, C.c_int64, P, P, C.c_int32, C.c_int32, P, P, P]),
     "ibm_gts_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), P, P]),
+    "ibm_flow_create": (C.c_int, [C.POINTER(GridDesc), C.c_double, C.c_double, C.POINTER(P)]),
+    "ibm_flow_set_stream": (C.c_int, [P, P]),
+    "ibm_flow_destroy": (None, [P]),
+    "ibm_flow_predict": (C.c_int, [P, C.c_int32, P, P, P, P]),
+    "ibm_flow_project": (C.c_int, [P, C.c_int32, P, P, P, P, P, P, P, C.c_float]),
+    "ibm_flow_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P]),
 }
 
 _lib = None
@@ -333,6 +339,71 @@ class StepGraph:
     def close(self):
         if getattr(self, "h", None):
             self.ctx.lib.ibm_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Flow:
+    """The fluid phase (ibm_flow_*): incompressible Navier-Stokes with the RK3
+    fractional step on the periodic MAC grid of `grid` (workloads.Grid).
+    Velocity and pressure are caller tensors float32 [nz, ny, nx] updated in
+    place; the work arrays and FFT plans belong to the library."""
+
+    def __init__(self, grid, nu, dt, device=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the flow solver needs a CUDA device; there is no CPU fallback")
+        self.lib = library()
+        self.device = torch.device("cuda", device)
+        g = GridDesc()
+        for k in range(3):
+            g.n[k] = int(grid.n[k])
+            g.L[k] = float(grid.L[k])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.ibm_flow_create(C.byref(g), float(nu), float(dt), C.byref(h))
+        if st != 0:
+            raise IBMError(st, self.lib.ibm_last_error(None).decode())
+        self.h = h
+        self.grid, self.nu, self.dt = grid, float(nu), float(dt)
+        self.set_stream(torch.cuda.current_stream(self.device))
+
+    def _check(self, st, ctx=None):
+        if st != 0:
+            raise IBMError(st, self.lib.ibm_last_error(None).decode())
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self.lib.ibm_flow_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def predict(self, substep, fields, p):
+        u, vv, w = fields
+        self._check(self.lib.ibm_flow_predict(self.h, int(substep), _ptr(u), _ptr(vv), _ptr(w),
+                                              _ptr(p)))
+
+    def project(self, substep, fields, p, f=None, f_scale=0.0):
+        u, vv, w = fields
+        fx, fy, fz = f if f is not None else (None, None, None)
+        self._check(self.lib.ibm_flow_project(self.h, int(substep), _ptr(u), _ptr(vv), _ptr(w),
+                                              _ptr(p), _ptr(fx), _ptr(fy), _ptr(fz),
+                                              float(f_scale)))
+
+    def step(self, fields, p, ctx=None, x=None, v=None, x_out=None, v_out=None, f=None):
+        """One coupled step (ibm_flow_step); without ctx the flow alone."""
+        u, vv, w = fields
+        fx, fy, fz = f if f is not None else (None, None, None)
+        self._check(self.lib.ibm_flow_step(self.h, ctx.h if ctx is not None else None, _ptr(x),
+                                           _ptr(v), _ptr(x_out), _ptr(v_out), _ptr(u), _ptr(vv),
+                                           _ptr(w), _ptr(p), _ptr(fx), _ptr(fy), _ptr(fz)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ibm_flow_destroy(self.h)
             self.h = None
 
     def __del__(self):

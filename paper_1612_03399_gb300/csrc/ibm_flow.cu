@@ -1,0 +1,473 @@
+// The fluid phase (Sec. 2.1): incompressible Navier-Stokes on the triply
+// periodic MAC grid with the three-substep RK3 fractional step.
+//
+// Per substep l:
+//   rhs_kernel      H(u) (divergence form), and R = dt (gamma_l H + rho_l H_prev
+//                   - alpha_l grad p + alpha_l nu lap u) for the three
+//                   components, one thread per cell computing the u, v and w
+//                   nodes of that cell index
+//   R2C (batch 3) -> cn_scale_kernel -> C2R: the factorised Crank-Nicolson
+//                   operator (1 - a d_xx)(1 - a d_yy)(1 - a d_zz),
+//                   a = alpha_l dt nu / 2, is diagonal in Fourier space
+//   add_kernel      u* = u + du
+//   div_kernel      div(u* + s f)
+//   R2C -> poisson_scale_kernel -> C2R: lap(phi) = div / (alpha_l dt)
+//   project_kernel  u = u* + s f - alpha_l dt grad(phi),
+//                   p <- p + phi - a lap(phi)
+// The eigenvalues of the periodic second difference, -(4/h^2) sin^2(pi k/n),
+// are tabulated per direction in float64 on the host and stored as float.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "ibm.h"
+#include "ibm_internal.cuh"
+
+struct ibm_flow {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n[3] = {0, 0, 0};
+  double L[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+  double nu = 0, dt = 0;
+  size_t N = 0, NC = 0;         // cells; complex coefficients of one field
+  float* H[2] = {nullptr, nullptr};   // [3][N] nonlinear terms, ping-pong
+  int hcur = 0;                 // H[hcur] holds the last predictor's H(u)
+  int last = -1;                // last predicted substep of the current step
+  float* R = nullptr;           // [3][N] right-hand sides, then increments
+  float* rp = nullptr;          // [N] divergence, then phi
+  cufftComplex* S = nullptr;    // [3][NC] spectra
+  float* lam = nullptr;         // [n_x/2 + 1 | n_y | n_z] eigenvalues
+  cufftHandle r2c3 = 0, c2r3 = 0, r2c1 = 0, c2r1 = 0;
+  bool plans = false;
+};
+
+namespace ibm {
+namespace {
+
+constexpr double kGamma[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+constexpr double kRho[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
+struct FGrid {
+  int nx, ny, nz;
+  float ih[3], ih2[3];   // 1/h, 1/h^2
+};
+
+struct Vec3 {
+  float* c[3];
+};
+struct CVec3 {
+  const float* c[3];
+};
+
+__device__ __forceinline__ int dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
+
+// H(u) and the predictor's right-hand side at the u, v and w nodes of cell
+// index (i, j, k).  Products for the d-derivative of component c are formed
+// where the difference needs them: at the cell centres for d = c (mean of the
+// two neighbouring c nodes, squared), at the (c, d) edges otherwise (mean of
+// u_d along c times mean of u_c along d).
+__global__ void __launch_bounds__(256) rhs_kernel(FGrid G, const float* __restrict__ u,
+                                                  const float* __restrict__ v,
+                                                  const float* __restrict__ w,
+                                                  const float* __restrict__ p, CVec3 Hp, Vec3 Ho,
+                                                  Vec3 Ro, float gam, float rho, float alpha,
+                                                  float nu, float dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  const int nx = G.nx, ny = G.ny, nz = G.nz;
+  const int im = dec(i, nx), ip = inc(i, nx), jm = dec(j, ny), jp = inc(j, ny), km = dec(k, nz),
+            kp = inc(k, nz);
+  auto at = [&](int a, int b, int c) { return ((size_t)c * ny + b) * nx + a; };
+  const size_t o = at(i, j, k);
+  const float U = __ldg(u + o), Uip = __ldg(u + at(ip, j, k)), Uim = __ldg(u + at(im, j, k)),
+              Ujp = __ldg(u + at(i, jp, k)), Ujm = __ldg(u + at(i, jm, k)),
+              Ukp = __ldg(u + at(i, j, kp)), Ukm = __ldg(u + at(i, j, km)),
+              Uip_jm = __ldg(u + at(ip, jm, k)), Uip_km = __ldg(u + at(ip, j, km));
+  const float V = __ldg(v + o), Vip = __ldg(v + at(ip, j, k)), Vim = __ldg(v + at(im, j, k)),
+              Vjp = __ldg(v + at(i, jp, k)), Vjm = __ldg(v + at(i, jm, k)),
+              Vkp = __ldg(v + at(i, j, kp)), Vkm = __ldg(v + at(i, j, km)),
+              Vim_jp = __ldg(v + at(im, jp, k)), Vjp_km = __ldg(v + at(i, jp, km));
+  const float W = __ldg(w + o), Wip = __ldg(w + at(ip, j, k)), Wim = __ldg(w + at(im, j, k)),
+              Wjp = __ldg(w + at(i, jp, k)), Wjm = __ldg(w + at(i, jm, k)),
+              Wkp = __ldg(w + at(i, j, kp)), Wkm = __ldg(w + at(i, j, km)),
+              Wim_kp = __ldg(w + at(im, j, kp)), Wjm_kp = __ldg(w + at(i, jm, kp));
+  const float P = __ldg(p + o), Pim = __ldg(p + at(im, j, k)), Pjm = __ldg(p + at(i, jm, k)),
+              Pkm = __ldg(p + at(i, j, km));
+  float H[3];
+  {  // u nodes
+    const float cp = 0.5f * (U + Uip), cm = 0.5f * (Uim + U);
+    const float xx = (cp * cp - cm * cm) * G.ih[0];
+    const float yy = (0.5f * (Vjp + Vim_jp) * 0.5f * (Ujp + U) - 0.5f * (V + Vim) * 0.5f * (U + Ujm)) * G.ih[1];
+    const float zz = (0.5f * (Wkp + Wim_kp) * 0.5f * (Ukp + U) - 0.5f * (W + Wim) * 0.5f * (U + Ukm)) * G.ih[2];
+    H[0] = -(xx + yy + zz);
+  }
+  {  // v nodes
+    const float xx = (0.5f * (Uip + Uip_jm) * 0.5f * (Vip + V) - 0.5f * (U + Ujm) * 0.5f * (V + Vim)) * G.ih[0];
+    const float cp = 0.5f * (V + Vjp), cm = 0.5f * (Vjm + V);
+    const float yy = (cp * cp - cm * cm) * G.ih[1];
+    const float zz = (0.5f * (Wkp + Wjm_kp) * 0.5f * (Vkp + V) - 0.5f * (W + Wjm) * 0.5f * (V + Vkm)) * G.ih[2];
+    H[1] = -(xx + yy + zz);
+  }
+  {  // w nodes
+    const float xx = (0.5f * (Uip + Uip_km) * 0.5f * (Wip + W) - 0.5f * (U + Ukm) * 0.5f * (W + Wim)) * G.ih[0];
+    const float yy = (0.5f * (Vjp + Vjp_km) * 0.5f * (Wjp + W) - 0.5f * (V + Vkm) * 0.5f * (W + Wjm)) * G.ih[1];
+    const float cp = 0.5f * (W + Wkp), cm = 0.5f * (Wkm + W);
+    const float zz = (cp * cp - cm * cm) * G.ih[2];
+    H[2] = -(xx + yy + zz);
+  }
+  const float Gp[3] = {(P - Pim) * G.ih[0], (P - Pjm) * G.ih[1], (P - Pkm) * G.ih[2]};
+  const float Lu[3] = {
+      (Uip - 2.f * U + Uim) * G.ih2[0] + (Ujp - 2.f * U + Ujm) * G.ih2[1] + (Ukp - 2.f * U + Ukm) * G.ih2[2],
+      (Vip - 2.f * V + Vim) * G.ih2[0] + (Vjp - 2.f * V + Vjm) * G.ih2[1] + (Vkp - 2.f * V + Vkm) * G.ih2[2],
+      (Wip - 2.f * W + Wim) * G.ih2[0] + (Wjp - 2.f * W + Wjm) * G.ih2[1] + (Wkp - 2.f * W + Wkm) * G.ih2[2]};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float r = gam * H[c] - alpha * Gp[c] + alpha * nu * Lu[c];
+    if (Hp.c[c] != nullptr) r += rho * __ldg(Hp.c[c] + o);
+    Ho.c[c][o] = H[c];
+    Ro.c[c][o] = dt * r;
+  }
+}
+
+// spectra [batch][nz][ny][nx/2+1] times norm / prod_d (1 - a lam_d)
+__global__ void cn_scale_kernel(cufftComplex* __restrict__ S, int nxh, int ny, int nz, int batch,
+                                const float* __restrict__ lam, float a, float norm) {
+  const size_t total = (size_t)batch * nz * ny * nxh;
+  const float* lx = lam;
+  const float* ly = lam + nxh;
+  const float* lz = ly + ny;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q % nxh);
+    const size_t r = q / nxh;
+    const int j = (int)(r % ny);
+    const int k = (int)((r / ny) % nz);
+    const float d = (1.f - a * __ldg(lx + i)) * (1.f - a * __ldg(ly + j)) * (1.f - a * __ldg(lz + k));
+    const float s = norm / d;
+    S[q].x *= s;
+    S[q].y *= s;
+  }
+}
+
+// spectrum of div / (alpha dt): times scale / (lam_x + lam_y + lam_z), mean 0
+__global__ void poisson_scale_kernel(cufftComplex* __restrict__ S, int nxh, int ny, int nz,
+                                     const float* __restrict__ lam, float scale) {
+  const size_t total = (size_t)nz * ny * nxh;
+  const float* lx = lam;
+  const float* ly = lam + nxh;
+  const float* lz = ly + ny;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q % nxh);
+    const size_t r = q / nxh;
+    const int j = (int)(r % ny);
+    const int k = (int)(r / ny);
+    const float l = __ldg(lx + i) + __ldg(ly + j) + __ldg(lz + k);
+    const float s = q == 0 ? 0.f : scale / l;
+    S[q].x *= s;
+    S[q].y *= s;
+  }
+}
+
+// u_c += du_c, du = [3][N]
+__global__ void add_kernel(Vec3 u, const float* __restrict__ du, size_t N) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 3 * N;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q / N);
+    const size_t o = q - (size_t)c * N;
+    float* uc = c == 0 ? u.c[0] : (c == 1 ? u.c[1] : u.c[2]);
+    uc[o] += __ldg(du + q);
+  }
+}
+
+// div(u* + s f) at the cell centres
+__global__ void __launch_bounds__(256) div_kernel(FGrid G, CVec3 u, CVec3 f, float s,
+                                                  float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  const int nx = G.nx, ny = G.ny, nz = G.nz;
+  const size_t o = ((size_t)k * ny + j) * nx + i;
+  const size_t oi = ((size_t)k * ny + j) * nx + inc(i, nx);
+  const size_t oj = ((size_t)k * ny + inc(j, ny)) * nx + i;
+  const size_t ok = ((size_t)inc(k, nz) * ny + j) * nx + i;
+  float d = (__ldg(u.c[0] + oi) - __ldg(u.c[0] + o)) * G.ih[0] +
+            (__ldg(u.c[1] + oj) - __ldg(u.c[1] + o)) * G.ih[1] +
+            (__ldg(u.c[2] + ok) - __ldg(u.c[2] + o)) * G.ih[2];
+  if (f.c[0] != nullptr) {
+    d += s * ((__ldg(f.c[0] + oi) - __ldg(f.c[0] + o)) * G.ih[0] +
+              (__ldg(f.c[1] + oj) - __ldg(f.c[1] + o)) * G.ih[1] +
+              (__ldg(f.c[2] + ok) - __ldg(f.c[2] + o)) * G.ih[2]);
+  }
+  out[o] = d;
+}
+
+// u = u* + s f - alpha dt grad(phi); p <- p + phi - a lap(phi)
+__global__ void __launch_bounds__(256) project_kernel(FGrid G, Vec3 u, float* __restrict__ p,
+                                                      const float* __restrict__ phi, CVec3 f,
+                                                      float s, float adt, float a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  const int nx = G.nx, ny = G.ny, nz = G.nz;
+  auto at = [&](int a_, int b, int c) { return ((size_t)c * ny + b) * nx + a_; };
+  const size_t o = at(i, j, k);
+  const float F = __ldg(phi + o);
+  const float Fim = __ldg(phi + at(dec(i, nx), j, k)), Fip = __ldg(phi + at(inc(i, nx), j, k));
+  const float Fjm = __ldg(phi + at(i, dec(j, ny), k)), Fjp = __ldg(phi + at(i, inc(j, ny), k));
+  const float Fkm = __ldg(phi + at(i, j, dec(k, nz))), Fkp = __ldg(phi + at(i, j, inc(k, nz)));
+  const float g[3] = {(F - Fim) * G.ih[0], (F - Fjm) * G.ih[1], (F - Fkm) * G.ih[2]};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float val = u.c[c][o] - adt * g[c];
+    if (f.c[0] != nullptr) val += s * __ldg(f.c[c] + o);
+    u.c[c][o] = val;
+  }
+  const float lap = (Fip - 2.f * F + Fim) * G.ih2[0] + (Fjp - 2.f * F + Fjm) * G.ih2[1] +
+                    (Fkp - 2.f * F + Fkm) * G.ih2[2];
+  p[o] += F - a * lap;
+}
+
+FGrid fgrid(const ibm_flow* fl) {
+  FGrid G;
+  G.nx = fl->n[0];
+  G.ny = fl->n[1];
+  G.nz = fl->n[2];
+  for (int d = 0; d < 3; ++d) {
+    G.ih[d] = (float)(1.0 / fl->h[d]);
+    G.ih2[d] = (float)(1.0 / (fl->h[d] * fl->h[d]));
+  }
+  return G;
+}
+
+dim3 cell_grid(const ibm_flow* fl) {
+  return dim3((unsigned)((fl->n[0] + 31) / 32), (unsigned)((fl->n[1] + 7) / 8), (unsigned)fl->n[2]);
+}
+
+unsigned flat_blocks(size_t total) {
+  const size_t b = (total + 255) / 256;
+  return (unsigned)(b < (size_t)152 * 16 ? (b > 0 ? b : 1) : (size_t)152 * 16);
+}
+
+cudaError_t fft_status(cufftResult r) {
+  return r == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+}
+
+cudaError_t set_plan_streams(ibm_flow* fl, cudaStream_t s) {
+  for (cufftHandle h : {fl->r2c3, fl->c2r3, fl->r2c1, fl->c2r1})
+    if (cufftSetStream(h, s) != CUFFT_SUCCESS) return cudaErrorUnknown;
+  return cudaSuccess;
+}
+
+void release(ibm_flow* fl) {
+  if (fl->plans) {
+    cufftDestroy(fl->r2c3);
+    cufftDestroy(fl->c2r3);
+    cufftDestroy(fl->r2c1);
+    cufftDestroy(fl->c2r1);
+  }
+  for (void* q : {(void*)fl->H[0], (void*)fl->H[1], (void*)fl->R, (void*)fl->rp, (void*)fl->S,
+                  (void*)fl->lam})
+    if (q) cudaFree(q);
+}
+
+ibm_status flow_err(ibm_status s, const std::string& m) {
+  set_global_error(m);
+  return s;
+}
+
+}  // namespace
+
+cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, const float* p,
+                         cudaStream_t s) {
+  const FGrid G = fgrid(fl);
+  const float dt = (float)fl->dt, nu = (float)fl->nu;
+  const double alpha = kGamma[l] + kRho[l];
+  CVec3 Hp{{nullptr, nullptr, nullptr}};
+  if (kRho[l] != 0.0)
+    for (int c = 0; c < 3; ++c) Hp.c[c] = fl->H[fl->hcur] + c * fl->N;
+  float* Hn = fl->H[fl->hcur ^ 1];
+  const Vec3 Ho{{Hn, Hn + fl->N, Hn + 2 * fl->N}};
+  const Vec3 Ro{{fl->R, fl->R + fl->N, fl->R + 2 * fl->N}};
+  cudaError_t e = set_plan_streams(fl, s);
+  if (e != cudaSuccess) return e;
+  rhs_kernel<<<cell_grid(fl), dim3(32, 8), 0, s>>>(G, u, v, w, p, Hp, Ho, Ro, (float)kGamma[l],
+                                                     (float)kRho[l], (float)alpha, nu, dt);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = fft_status(cufftExecR2C(fl->r2c3, fl->R, fl->S));
+  if (e == cudaSuccess) {
+    const int nxh = fl->n[0] / 2 + 1;
+    cn_scale_kernel<<<flat_blocks(3 * fl->NC), 256, 0, s>>>(
+        fl->S, nxh, fl->n[1], fl->n[2], 3, fl->lam, (float)(alpha * fl->dt * fl->nu / 2.0),
+        (float)(1.0 / (double)fl->N));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = fft_status(cufftExecC2R(fl->c2r3, fl->S, fl->R));
+  if (e == cudaSuccess) {
+    add_kernel<<<flat_blocks(3 * fl->N), 256, 0, s>>>(Vec3{{u, v, w}}, fl->R, fl->N);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    fl->hcur ^= 1;
+    fl->last = l;
+  }
+  return e;
+}
+
+cudaError_t flow_project(ibm_flow* fl, int l, float* u, float* v, float* w, float* p,
+                         const float* fx, const float* fy, const float* fz, float fscale,
+                         cudaStream_t s) {
+  const FGrid G = fgrid(fl);
+  const double alpha = kGamma[l] + kRho[l];
+  const CVec3 f{{fx, fy, fz}};
+  cudaError_t e = set_plan_streams(fl, s);
+  if (e != cudaSuccess) return e;
+  div_kernel<<<cell_grid(fl), dim3(32, 8), 0, s>>>(G, CVec3{{u, v, w}}, f, fscale, fl->rp);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = fft_status(cufftExecR2C(fl->r2c1, fl->rp, fl->S));
+  if (e == cudaSuccess) {
+    const int nxh = fl->n[0] / 2 + 1;
+    poisson_scale_kernel<<<flat_blocks(fl->NC), 256, 0, s>>>(
+        fl->S, nxh, fl->n[1], fl->n[2], fl->lam, (float)(1.0 / ((double)fl->N * alpha * fl->dt)));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = fft_status(cufftExecC2R(fl->c2r1, fl->S, fl->rp));
+  if (e == cudaSuccess) {
+    project_kernel<<<cell_grid(fl), dim3(32, 8), 0, s>>>(
+        G, Vec3{{u, v, w}}, p, fl->rp, f, fscale, (float)(alpha * fl->dt),
+        (float)(alpha * fl->dt * fl->nu / 2.0));
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+bool flow_matches(const ibm_flow* fl, const ibm_grid_desc& g, double dt, double mu) {
+  for (int d = 0; d < 3; ++d)
+    if (g.n[d] != fl->n[d] || std::fabs(g.L[d] - fl->L[d]) > 1e-12 * std::fabs(fl->L[d]))
+      return false;
+  return std::fabs(dt - fl->dt) <= 1e-12 * fl->dt && std::fabs(mu - fl->nu) <= 1e-12 * (1.0 + fl->nu);
+}
+
+cudaStream_t flow_stream(const ibm_flow* fl) { return fl->stream; }
+int flow_device(const ibm_flow* fl) { return fl->device; }
+size_t flow_cells(const ibm_flow* fl) { return fl->N; }
+
+}  // namespace ibm
+
+using ibm::flow_err;
+
+extern "C" ibm_status ibm_flow_create(const ibm_grid_desc* grid, double nu, double dt,
+                                      ibm_flow** out) {
+  if (out) *out = nullptr;
+  if (!grid || !out) return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_create: null argument");
+  for (int d = 0; d < 3; ++d)
+    if (grid->n[d] < 4 || !(grid->L[d] > 0.0) || !std::isfinite(grid->L[d]))
+      return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_create: grid needs n >= 4 and L > 0");
+  if (!(nu >= 0.0) || !std::isfinite(nu) || !(dt > 0.0) || !std::isfinite(dt))
+    return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_create: needs nu >= 0 and dt > 0");
+  ibm_flow* fl = new ibm_flow();
+  cudaGetDevice(&fl->device);
+  for (int d = 0; d < 3; ++d) {
+    fl->n[d] = grid->n[d];
+    fl->L[d] = grid->L[d];
+    fl->h[d] = grid->L[d] / grid->n[d];
+  }
+  fl->nu = nu;
+  fl->dt = dt;
+  const int nx = fl->n[0], ny = fl->n[1], nz = fl->n[2], nxh = nx / 2 + 1;
+  fl->N = (size_t)nx * ny * nz;
+  fl->NC = (size_t)nxh * ny * nz;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&fl->H[b], 3 * fl->N * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&fl->R, 3 * fl->N * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&fl->rp, fl->N * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&fl->S, 3 * fl->NC * sizeof(cufftComplex));
+  if (e == cudaSuccess) e = cudaMalloc(&fl->lam, (size_t)(nxh + ny + nz) * sizeof(float));
+  if (e == cudaSuccess) {
+    std::vector<float> lam;
+    const int m[3] = {nxh, ny, nz};
+    for (int d = 0; d < 3; ++d)
+      for (int q = 0; q < m[d]; ++q) {
+        const double s = std::sin(M_PI * q / fl->n[d]);
+        lam.push_back((float)(-(4.0 / (fl->h[d] * fl->h[d])) * s * s));
+      }
+    e = cudaMemcpy(fl->lam, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    ibm::release(fl);
+    delete fl;
+    cudaGetLastError();
+    return flow_err(e == cudaErrorMemoryAllocation ? IBM_ERR_OOM : IBM_ERR_CUDA,
+                    std::string("ibm_flow_create: ") + cudaGetErrorString(e));
+  }
+  int dims[3] = {nz, ny, nx};
+  cufftResult r = cufftPlanMany(&fl->r2c3, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 3);
+  bool ok = r == CUFFT_SUCCESS;
+  if (ok) ok = cufftPlanMany(&fl->c2r3, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 3) == CUFFT_SUCCESS;
+  if (ok) ok = cufftPlan3d(&fl->r2c1, nz, ny, nx, CUFFT_R2C) == CUFFT_SUCCESS;
+  if (ok) ok = cufftPlan3d(&fl->c2r1, nz, ny, nx, CUFFT_C2R) == CUFFT_SUCCESS;
+  if (!ok) {
+    // plans created so far are destroyed individually
+    for (cufftHandle h : {fl->r2c3, fl->c2r3, fl->r2c1, fl->c2r1})
+      if (h) cufftDestroy(h);
+    fl->plans = false;
+    ibm::release(fl);
+    delete fl;
+    return flow_err(IBM_ERR_CUDA, "ibm_flow_create: cuFFT plan creation failed");
+  }
+  fl->plans = true;
+  *out = fl;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_flow_set_stream(ibm_flow* fl, void* stream) {
+  if (!fl) return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_set_stream: null flow");
+  fl->stream = static_cast<cudaStream_t>(stream);
+  return IBM_OK;
+}
+
+extern "C" void ibm_flow_destroy(ibm_flow* fl) {
+  if (!fl) return;
+  cudaSetDevice(fl->device);
+  cudaStreamSynchronize(fl->stream);
+  ibm::release(fl);
+  delete fl;
+}
+
+extern "C" ibm_status ibm_flow_predict(ibm_flow* fl, int32_t substep, float* u, float* v,
+                                       float* w, const float* p) {
+  if (!fl || !u || !v || !w || !p) return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_predict: null argument");
+  if (substep < 0 || substep > 2)
+    return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_predict: substep must be 0, 1 or 2");
+  if (substep > 0 && fl->last != substep - 1)
+    return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_predict: substeps must run in order");
+  cudaSetDevice(fl->device);
+  const cudaError_t e = ibm::flow_predict(fl, substep, u, v, w, p, fl->stream);
+  if (e != cudaSuccess)
+    return flow_err(IBM_ERR_CUDA, std::string("ibm_flow_predict: ") + cudaGetErrorString(e));
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_flow_project(ibm_flow* fl, int32_t substep, float* u, float* v,
+                                       float* w, float* p, const float* fx, const float* fy,
+                                       const float* fz, float f_scale) {
+  if (!fl || !u || !v || !w || !p) return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_project: null argument");
+  if (substep < 0 || substep > 2)
+    return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_project: substep must be 0, 1 or 2");
+  const bool any = fx || fy || fz;
+  if (any && !(fx && fy && fz))
+    return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_project: give all three force fields or none");
+  cudaSetDevice(fl->device);
+  const cudaError_t e = ibm::flow_project(fl, substep, u, v, w, p, fx, fy, fz, f_scale, fl->stream);
+  if (e != cudaSuccess)
+    return flow_err(IBM_ERR_CUDA, std::string("ibm_flow_project: ") + cudaGetErrorString(e));
+  return IBM_OK;
+}

@@ -951,6 +951,60 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
   return cuda_status(c, e, "ibm_step");
 }
 
+// One loosely coupled time step (Sec. 5 steps 1-4): per RK3 substep the flow's
+// predictor, the IBM forcing of the provisional velocity (marker kernel:
+// interpolation at the centroids of x and spread of F = (V^b - U*)/dt, steps
+// 3b-3d) and the pressure correction (3e); then the bodies advance with the
+// probe traction and pressure of the new flow and the internal forces (4).
+extern "C" ibm_status ibm_flow_step(ibm_flow* fl, ibm_ctx* c, const float* x, const float* xv,
+                                    float* x_out, float* v_out, float* u, float* vv, float* w,
+                                    float* p, float* fx, float* fy, float* fz) {
+  auto bad = [&](const char* m) {
+    set_global_error(m);
+    return set_err(c, IBM_ERR_INVALID_ARG, m);
+  };
+  if (!fl || !u || !vv || !w || !p) return bad("ibm_flow_step: null argument");
+  if (c) {
+    if (!x || !xv || !x_out || !v_out || !fx || !fy || !fz) return bad("ibm_flow_step: null argument");
+    if (x_out == x || v_out == xv || x_out == xv || v_out == x)
+      return bad("ibm_flow_step: outputs must not alias the inputs");
+    if (c->device != flow_device(fl)) return bad("ibm_flow_step: flow and context on different devices");
+    if (!flow_matches(fl, c->gdesc, c->prm.dt, c->prm.mu))
+      return bad("ibm_flow_step: the context's grid, dt and mu must equal the flow's grid, dt and nu");
+  }
+  cudaSetDevice(flow_device(fl));
+  const cudaStream_t s = c ? c->stream : flow_stream(fl);
+  const size_t cells = flow_cells(fl);
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+    e = flow_predict(fl, l, u, vv, w, p, s);
+    if (c && e == cudaSuccess) {
+      for (float* f : {fx, fy, fz})
+        if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, cells * sizeof(float), s);
+      if (e == cudaSuccess)
+        e = launch_mls(c, x, xv, u, vv, w, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, fx,
+                       fy, fz, false, true, false, true, false);
+    }
+    if (e == cudaSuccess)
+      e = flow_project(fl, l, u, vv, w, p, c ? fx : nullptr, c ? fy : nullptr, c ? fz : nullptr,
+                       c ? (float)c->prm.dt : 0.f, s);
+  }
+  if (c && e == cudaSuccess) {
+    use_parity(c, c->qpar ^ 1);
+    e = zero_body_sums(c);
+    if (e == cudaSuccess)
+      e = launch_mls(c, x, nullptr, u, vv, w, p, nullptr, nullptr, nullptr, nullptr, c->d.fext,
+                     nullptr, nullptr, nullptr, true, false, true, false, false);
+    if (e == cudaSuccess) e = launch_force(c, x, xv, c->d.fext, nullptr, x_out, v_out, nullptr, true);
+  }
+  if (e != cudaSuccess) {
+    const std::string m = std::string("ibm_flow_step: ") + cudaGetErrorString(e);
+    set_global_error(m);
+    return set_err(c, IBM_ERR_CUDA, m);
+  }
+  return IBM_OK;
+}
+
 namespace {
 
 // acceleration a = (F_int + F_ext^v)/m at positions x: body sums, probe

@@ -260,4 +260,15 @@ cudaError_t set_adjoint_smem_limit(size_t bytes);
 cudaError_t set_marker_smem_limit();
 // message returned by ibm_last_error(NULL)
 void set_global_error(const std::string& msg);
+// the fluid phase (ibm_flow.cu): one RK3 predictor / projection on stream s,
+// and the checks ibm_flow_step makes against a context
+cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, const float* p,
+                         cudaStream_t s);
+cudaError_t flow_project(ibm_flow* fl, int l, float* u, float* v, float* w, float* p,
+                         const float* fx, const float* fy, const float* fz, float fscale,
+                         cudaStream_t s);
+bool flow_matches(const ibm_flow* fl, const ibm_grid_desc& g, double dt, double mu);
+cudaStream_t flow_stream(const ibm_flow* fl);
+int flow_device(const ibm_flow* fl);
+size_t flow_cells(const ibm_flow* fl);
 }  // namespace ibm

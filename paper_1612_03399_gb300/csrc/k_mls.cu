@@ -970,6 +970,7 @@ cudaError_t set_marker_smem_limit() {
   SET(false, true, false, false)
   SET(false, false, true, false)
   SET(false, false, false, true)
+  SET(false, true, false, true)
 #undef SET
   return e;
 }
@@ -989,6 +990,7 @@ cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* 
   if (!measure && interp && !probe && !spread) return L(false, true, false, false);
   if (!measure && !interp && probe && !spread) return L(false, false, true, false);
   if (!measure && !interp && !probe && spread) return L(false, false, false, true);
+  if (!measure && interp && !probe && spread) return L(false, true, false, true);
 #undef L
   return cudaErrorInvalidValue;
 }

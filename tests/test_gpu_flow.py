@@ -1,0 +1,253 @@
+"""The fluid phase and the coupled step on the GPU (ibm_flow_*) against the
+FP64 flow oracle, through the C ABI.
+
+Bar: relative L2 <= 1e-5 for velocities and spread forces (the float32
+stencils and FFTs round at ~1e-7 relative); bodies as in the step parity
+tests (positions relative to the body size, velocity changes beyond half an
+ulp of float32 storage).  The pressure correction phi solves
+lap(phi) = div(u*)/(alpha_l dt): the float32 divergence of a field carries
+rounding ~3 eps |u|/h (three differences of size |u|/h), which the Poisson
+solve (grid-scale modes scaled by ~h^2/8) and the 1/(alpha_l dt) turn into
+an absolute pressure error ~3 eps |u| h/(8 alpha_l dt) per substep; the
+pressure bar is relative L2 <= 1e-5 plus that floor summed over the
+substeps taken.  Grids are anisotropic and not multiples of the 32 x 8
+thread blocks."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ibm_oracle as O
+from oracle import ns_oracle as N
+from paper_1612_03399_gb300 import _lib
+from paper_1612_03399_gb300 import workloads as W
+
+import helpers as H
+from test_gpu_parity import mixed_workload, tie_free_state
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+DT = torch.float64
+
+
+def curl_field(n, h, seed, amp=1.0):
+    """Solenoidal MAC field: discrete curl of a random edge vector potential."""
+    g = torch.Generator().manual_seed(seed)
+    A = torch.randn((3, n[2], n[1], n[0]), generator=g, dtype=DT) * amp * min(h)
+    fd = lambda f, d: (N.shift(f, d, 1) - f) / h[d]
+    return torch.stack([fd(A[2], 1) - fd(A[1], 2), fd(A[0], 2) - fd(A[2], 0),
+                        fd(A[1], 0) - fd(A[0], 1)])
+
+
+def to_dev(t):
+    return t.to(torch.float32).to(DEV).contiguous()
+
+
+def fields_dev(u):
+    return tuple(to_dev(u[c]) for c in range(3))
+
+
+def stack_cpu(fields):
+    return torch.stack([f.double().cpu() for f in fields])
+
+
+def rel(a, b):
+    return H.rel_l2(a.numpy(), b.numpy())
+
+
+EPS32 = 2.0 ** -24
+
+
+def pressure_ok(pg, po, u_max, h_min, dt, substeps):
+    """rms(pg - po) <= 1e-5 rms(po) + sum over the substeps taken of
+    3 eps |u|_max h_min / (8 alpha_l dt).  Returns (relative error, ok)."""
+    a, b = pg.numpy(), po.numpy()
+    n = np.sqrt(a.size)
+    floor = sum(3 * EPS32 * u_max * h_min / (8 * N.ALPHA[l] * dt) for l in substeps)
+    err = np.linalg.norm(a - b) / n
+    return H.rel_l2(a, b), err <= 1e-5 * np.linalg.norm(b) / n + floor
+
+
+def test_substeps_match_oracle(record_error):
+    """Predictor and projection of each substep, from the same inputs."""
+    grid = W.Grid((40, 36, 20), (1.0, 0.9, 0.5))
+    flow_o = N.Flow(grid.n, grid.L, nu=0.02, dt=1e-2)
+    u0 = curl_field(grid.n, grid.h, 1)
+    g = torch.Generator().manual_seed(2)
+    p0 = torch.randn((grid.n[2], grid.n[1], grid.n[0]), generator=g, dtype=DT)
+    fl = _lib.Flow(grid, nu=flow_o.nu, dt=flow_o.dt)
+    u, p = fields_dev(u0), to_dev(p0)
+    uo, po, Hp = u0.clone(), p0.clone(), None
+    for l in range(3):
+        fl.predict(l, u, p)
+        us_o, Hp = N.predict(flow_o, l, uo, po, Hp)
+        e = rel(stack_cpu(u), us_o)
+        record_error(f"u*[{l}]", e)
+        assert e <= 1e-5, (l, e)
+        # continue both from the oracle's provisional field
+        u = fields_dev(us_o)
+        fl.project(l, u, p)
+        uo, po = N.project(flow_o, l, us_o, po)
+        eu = rel(stack_cpu(u), uo)
+        ep, pok = pressure_ok(p.double().cpu(), po, float(us_o.abs().max()), min(grid.h),
+                              flow_o.dt, [l])
+        record_error(f"u[{l}]", eu)
+        record_error(f"p[{l}]", ep)
+        assert eu <= 1e-5 and pok, (l, eu, ep)
+        div = N.divergence(stack_cpu(u), grid.h)
+        assert float(div.abs().max()) * min(grid.h) <= 1e-5 * float(uo.abs().max())
+        u, p = fields_dev(uo), to_dev(po)
+    fl.close()
+
+
+def test_flow_steps_match_oracle(record_error):
+    """Five whole steps of the flow alone (ibm_flow_step without a context),
+    from the Fourier field of the mixed workload (its discrete divergence is
+    removed by the first projection)."""
+    wl = mixed_workload()
+    flow_o = N.Flow(wl.grid.n, wl.grid.L, nu=0.05, dt=5e-3)
+    fl = _lib.Flow(wl.grid, nu=flow_o.nu, dt=flow_o.dt)
+    u = tuple(f.clone() for f in H.fields_for(wl, DEV))
+    p = torch.zeros_like(u[0])
+    uo, po = stack_cpu(u), torch.zeros(u[0].shape, dtype=DT)
+    for s in range(5):
+        fl.step(u, p)
+        uo, po = N.ns_step(flow_o, uo, po)
+        eu = rel(stack_cpu(u), uo)
+        ep, pok = pressure_ok(p.double().cpu(), po, float(uo.abs().max()), min(wl.grid.h),
+                              flow_o.dt, [0, 1, 2] * (s + 1))
+        record_error(f"u[{s}]", eu)
+        record_error(f"p[{s}]", ep)
+        assert eu <= 1e-5 and pok, (s, eu, ep)
+    fl.close()
+
+
+def coupled_case(seed):
+    wl = mixed_workload()
+    rel_x = tie_free_state(wl, seed, scale=0.03, stretch=0.03)
+    rng = np.random.default_rng(seed)
+    vs = []
+    for b in wl.bodies:
+        v = rng.uniform(-0.2, 0.2, (len(b.rest), 3))
+        if b.clamped is not None:
+            v[b.clamped] = 0.0
+        vs.append(v)
+    return wl, rel_x, vs
+
+
+def test_coupled_step_matches_oracle(record_error):
+    """One loosely coupled step: flow, pressure, the last substep's spread
+    forcing, and the bodies."""
+    wl, rel_x, vs = coupled_case(20)
+    ob = H.oracle_bodies(wl)
+    prm = H.oracle_params(wl)
+    flow_o = N.Flow(wl.grid.n, wl.grid.L, nu=wl.mu, dt=wl.dt)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    fl = _lib.Flow(wl.grid, nu=wl.mu, dt=wl.dt)
+    x = H.state_tensor(wl, rel_x)
+    v = H.state_tensor(wl, vs)
+    u = tuple(f.clone() for f in H.fields_for(wl, DEV))
+    p = torch.zeros_like(u[0])
+    f = tuple(torch.empty_like(u[0]) for _ in range(3))
+    x1, v1 = torch.empty_like(x), torch.empty_like(v)
+    uo = stack_cpu(u)
+    fl.step(u, p, ctx=ctx, x=x, v=v, x_out=x1, v_out=v1, f=f)
+    ctx.check_device_error()
+    xs = H.to_abs(wl, H.split_state(ctx, wl, x))
+    vso = [torch.tensor(a) for a in H.split_state(ctx, wl, v)]
+    xo, vo, uo, po, fo = N.coupled_step(ob, xs, vso, uo, torch.zeros(u[0].shape, dtype=DT),
+                                        flow_o, prm)
+    for name, a, b in (("u", stack_cpu(u), uo), ("f", stack_cpu(f), fo)):
+        e = rel(a, b)
+        record_error(name, e)
+        assert e <= 1e-5, (name, e)
+    ep, pok = pressure_ok(p.double().cpu(), po, float(uo.abs().max()), min(wl.grid.h), wl.dt,
+                          [0, 1, 2])
+    record_error("p", ep)
+    assert pok, ep
+    xg = H.split_state(ctx, wl, x1)
+    vg = H.split_state(ctx, wl, v1)
+    for i, b in enumerate(wl.bodies):
+        size = float(np.linalg.norm(b.rest - b.origin, axis=1).max())
+        xr = xo[i].numpy() - b.origin
+        ex = np.linalg.norm(xg[i] - xr) / (size * np.sqrt(len(xr)))
+        dvo = vo[i].numpy() - vs[i]
+        store = np.linalg.norm(0.5 * np.spacing(np.abs(vo[i].numpy()).astype(np.float32)).astype(np.float64))
+        ev = max(0.0, np.linalg.norm((vg[i] - vs[i]) - dvo) - store) / np.linalg.norm(dvo)
+        record_error(f"x[{i}]", ex)
+        record_error(f"dv[{i}]", ev)
+        assert ex <= 1e-5 and ev <= 1e-5, (i, ex, ev)
+    fl.close()
+
+
+def test_coupled_steps_track_oracle(record_error):
+    """Three coupled steps from a state whose markers stay clear of
+    nearest-node switches along the oracle's trajectory."""
+    steps = 3
+    u_init = H.fields_for(mixed_workload(), DEV)
+    for seed in range(30, 60):
+        wl, rel_x, vs = coupled_case(seed)
+        ob = H.oracle_bodies(wl)
+        prm = H.oracle_params(wl)
+        flow_o = N.Flow(wl.grid.n, wl.grid.L, nu=wl.mu, dt=wl.dt)
+        xs = H.to_abs(wl, [r.astype(np.float32).astype(np.float64) for r in rel_x])
+        vso = [torch.tensor(v.astype(np.float32).astype(np.float64)) for v in vs]
+        uo = stack_cpu(u_init)
+        po = torch.zeros(uo.shape[1:], dtype=DT)
+        traj, ok = [], True
+        for _ in range(steps):
+            xs, vso, uo, po, _ = N.coupled_step(ob, xs, vso, uo, po, flow_o, prm)
+            traj.append((xs, vso, uo, po))
+            # GPU and oracle positions differ by ~1e-7 cells here, so a
+            # 2e-6-cell margin keeps both on the same stencils
+            if not H.tie_free(wl, xs, margin=2e-6):
+                ok = False
+                break
+        if ok:
+            break
+    assert ok, "no tie-free trajectory found"
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    fl = _lib.Flow(wl.grid, nu=wl.mu, dt=wl.dt)
+    x = H.state_tensor(wl, rel_x)
+    v = H.state_tensor(wl, vs)
+    u = tuple(t.clone() for t in u_init)
+    p = torch.zeros_like(u[0])
+    f = tuple(torch.empty_like(u[0]) for _ in range(3))
+    for k in range(steps):
+        x1, v1 = torch.empty_like(x), torch.empty_like(v)
+        fl.step(u, p, ctx=ctx, x=x, v=v, x_out=x1, v_out=v1, f=f)
+        x, v = x1, v1
+        xs, _, uo, po = traj[k]
+        eu = rel(stack_cpu(u), uo)
+        ep, pok = pressure_ok(p.double().cpu(), po, float(uo.abs().max()), min(wl.grid.h), wl.dt,
+                              [0, 1, 2] * (k + 1))
+        record_error(f"u[{k}]", eu)
+        record_error(f"p[{k}]", ep)
+        assert eu <= 1e-5 and pok, (k, eu, ep)
+        xg = H.split_state(ctx, wl, x)
+        for i, b in enumerate(wl.bodies):
+            size = float(np.linalg.norm(b.rest - b.origin, axis=1).max())
+            xr = xs[i].numpy() - b.origin
+            ex = np.linalg.norm(xg[i] - xr) / (size * np.sqrt(len(xr)))
+            record_error(f"x[{k}][{i}]", ex)
+            assert ex <= 1e-5, (k, i, ex)
+    ctx.check_device_error()
+    fl.close()
+
+
+def test_flow_rejects_bad_use():
+    wl = mixed_workload()
+    with pytest.raises(_lib.IBMError):
+        _lib.Flow(W.Grid((2, 8, 8)), nu=0.1, dt=1e-3)
+    with pytest.raises(_lib.IBMError):
+        _lib.Flow(wl.grid, nu=-1.0, dt=1e-3)
+    fl = _lib.Flow(wl.grid, nu=0.1, dt=1e-3)
+    u = tuple(torch.zeros((wl.grid.n[2], wl.grid.n[1], wl.grid.n[0]), device=DEV) for _ in range(3))
+    p = torch.zeros_like(u[0])
+    with pytest.raises(_lib.IBMError):
+        fl.predict(1, u, p)              # substep 1 before substep 0
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=2e-3, mu=0.1)
+    x, v = ctx.init_state()
+    with pytest.raises(_lib.IBMError):   # dt differs from the flow's
+        fl.step(u, p, ctx=ctx, x=x, v=v, x_out=torch.empty_like(x), v_out=torch.empty_like(v),
+                f=tuple(torch.zeros_like(u[0]) for _ in range(3)))
+    fl.close()
