@@ -71,6 +71,10 @@ def parse():
                          "steps launched one by one")
     ap.add_argument("--bodies", type=int, default=0,
                     help="profiling only: fewer drops on the same grid (drops1000 workload)")
+    ap.add_argument("--coupled", action="store_true",
+                    help="the coupled step (ibm_flow_step: RK3 Navier-Stokes with the IBM "
+                         "forcing per substep, then the body update) on the workload's bodies "
+                         "and grid, dt at CFL 0.5 of the initial field, nu = mu = 0.01")
     return ap.parse_args()
 
 
@@ -508,11 +512,207 @@ def run_hamming(args, ws, rank, ctx, wl, descr, fields, f, xa, va, xb, vb, flush
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the coupled step (flow solved)
+# ---------------------------------------------------------------------------
+
+COUPLED_NU, COUPLED_CFL = 1e-2, 0.5
+
+
+def cfl_dt(fields, h, cfl):
+    """Time step with sum_d max|u_d| dt / h_d = cfl: the explicit RK3
+    advection is stable for centred differences up to sqrt(3)."""
+    rate = sum(float(f.abs().max()) / hd for f, hd in zip(fields, h))
+    return cfl / rate
+
+
+def flow_bytes(n):
+    """Algorithmic bytes per time step of the flow solver's own kernels
+    (float32 fields of N cells, spectra of NC = nz ny (nx/2+1) complex
+    values), summed over the three substeps: what each kernel must read and
+    write once."""
+    N = n[0] * n[1] * n[2]
+    NC = n[2] * n[1] * (n[0] // 2 + 1)
+    return {
+        # u, v, w, p read; H and R (3 each) written; H_prev (3) read in substeps 1, 2
+        "rhs": 4 * N * (3 * (4 + 6) + 2 * 3),
+        "cn_scale": 3 * 3 * NC * 8 * 2,       # three spectra read and written
+        "add": 3 * 4 * N * 9,                 # u, du read, u written (3 components)
+        "div": 3 * 4 * N * 7,                 # u*, f read (3 + 3), divergence written
+        "poisson_scale": 3 * NC * 8 * 2,
+        "project": 3 * 4 * N * 12,            # u*, f, phi, p read; u, p written
+    }
+
+
+def run_coupled(args, ws, rank, local):
+    from paper_1612_03399_gb300 import _lib
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    make, descr = WORKLOADS[args.workload]
+    if args.workload == "drops1000":
+        # the direct forcing needs faces no larger than about two grid cells
+        # (its per-marker gain is about A_l/h^2 with the narrow MLS kernel);
+        # the level-3 drops have faces up to 2.2 h^2 on 512^3, 0.6 h^2 on 256^3
+        make = lambda seed: W.batched_drops(1000, 3, 256, seed=seed)  # noqa: E731
+        descr = descr.replace("512^3", "256^3")
+    wl = make(1 + rank)
+    fields = W.sample_field(wl.field, wl.grid, device=device, dtype=torch.float32)
+    dt = cfl_dt(fields, wl.grid.h, COUPLED_CFL)
+    hm = sum(wl.grid.h) / 3
+    max_face_h2 = max(float(np.linalg.norm(np.cross(b.rest[b.tri[:, 1]] - b.rest[b.tri[:, 0]],
+                                                     b.rest[b.tri[:, 2]] - b.rest[b.tri[:, 0]]),
+                                            axis=1).max()) / 2 for b in wl.bodies) / hm ** 2
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=dt, mu=COUPLED_NU, alpha=wl.alpha,
+                       patch_size=args.patch if args.patch else 256, device=local)
+    flow = _lib.Flow(wl.grid, nu=COUPLED_NU, dt=dt, device=local)
+    stream = torch.cuda.current_stream(device)
+    u = tuple(t.clone() for t in fields)
+    p = torch.zeros_like(u[0])
+    f = tuple(torch.zeros_like(u[0]) for _ in range(3))
+    xa, va = ctx.init_state()
+    xb, vb = torch.empty_like(xa), torch.empty_like(va)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def step():
+        nonlocal xa, va, xb, vb
+        flow.step(u, p, ctx=ctx, x=xa, v=va, x_out=xb, v_out=vb, f=f)
+        xa, va, xb, vb = xb, vb, xa, va
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ctx.check_device_error()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    total = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        total += ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    ctx.check_device_error()
+    barrier(ws)
+    value, t_max = job_rate(ws, ctx.V, args.steps, total, device)
+    ncell = wl.grid.n[0] * wl.grid.n[1] * wl.grid.n[2]
+    cells, _ = job_rate(ws, ncell, args.steps, total, device)
+    # phases: the same steps with CUDA events between the kernels
+    flow.set_phase_timing(True)
+    phases = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        step()
+        phases.append(flow.phase_times())
+    flow.set_phase_timing(False)
+    ph = {k: float(np.mean([q[k] for q in phases])) for k in phases[0]}
+    e2e = None
+    if not args.no_e2e:
+        xh, vh = xa.cpu().pin_memory(), va.cpu().pin_memory()
+        xo, vo = torch.empty_like(xh).pin_memory(), torch.empty_like(vh).pin_memory()
+        barrier(ws)
+        e2e_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            xa.copy_(xh, non_blocking=True)
+            va.copy_(vh, non_blocking=True)
+            flow.step(u, p, ctx=ctx, x=xa, v=va, x_out=xb, v_out=vb, f=f)
+            xo.copy_(xb, non_blocking=True)
+            vo.copy_(vb, non_blocking=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            e2e_ms += ev0.elapsed_time(ev1)
+            xh, xo = xo, xh
+            vh, vo = vo, vh
+        e2e_value, _ = job_rate(ws, ctx.V, args.steps, e2e_ms, device)
+        nbytes = 2 * 3 * ctx.V * 4
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes,
+               "note": "body state (x, v) copied in and out every step; the flow fields are "
+                       "the device-resident Eulerian state"}
+    ctx.check_device_error()
+    if rank != 0:
+        return
+    fb = flow_bytes(wl.grid.n)
+    own = {k: ph[k] for k in fb}
+    dom = max(own, key=own.get)
+    peak, peak_kind = hbm_peak()
+    achieved = fb[dom] / (ph[dom] * 1e-3) / 1e9
+    fft_ms = sum(ph[k] for k in ("fft_fwd3", "fft_inv3", "fft_fwd1", "fft_inv1"))
+    step_ms = sum(ph.values())
+    line = {
+        "metric": "Lagrangian node-steps/s, coupled step (RK3 flow + IBM forcing per substep + "
+                  "body update)",
+        "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "cell_steps_per_s": cells,
+        "config": {"workload": descr + f"; flow solved: dt {dt:.3g} (CFL {COUPLED_CFL} of the "
+                   "initial field), nu = mu = 0.01, p0 = 0",
+                   "bodies": ctx.B, "vertices": ctx.V, "faces": ctx.F, "grid": list(wl.grid.n),
+                   "max_face_area_h2": max_face_h2,
+                   "l2": "flushed between timed steps (256 MiB write); fields of 64 MiB each",
+                   "parallelism": f"{ws} independent replica(s)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_bytes": fb[dom] / 3},
+        "phases_ms": ph,
+        "fft_share": fft_ms / step_ms,
+        "other_kernel": {k: {"algorithmic_bytes_per_step": fb[k],
+                             "achieved_gbs": fb[k] / (ph[k] * 1e-3) / 1e9} for k in fb},
+        # per step: 3 x (rhs, cn_scale, add, marker, div, poisson_scale, project) + marker + force;
+        # cuFFT's own kernels and the memsets not counted
+        "gpu_launches": 23 * args.steps,
+        "timing": "coupled steps launched one by one; phases from CUDA events between the "
+                  "kernels of separately timed steps",
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = coupled_oracle_rate(wl)
+    print(json.dumps(line), flush=True)
+
+
+def coupled_oracle_rate(wl):
+    """The flow oracle's coupled step, as it stands, on the host cores: one
+    step of 4 of the bodies on a 128^3 grid (the full 512^3 FFTs in float64
+    take minutes); rates per node-step and per cell-step."""
+    from oracle import ibm_oracle as O
+    from oracle import ns_oracle as N
+    sub = wl.bodies[:4]
+    n = (128, 128, 128)
+    grid = W.Grid(n, wl.grid.L)
+    ob = [O.Body(b.rest, b.tri, b.origin, closed=b.closed, clamped=b.clamped, ks=b.ks, kb=b.kb,
+                 ka=b.ka, kA=b.kA, kv=b.kv, mass=b.mass) for b in sub]
+    u = W.sample_field(wl.field, grid, device="cpu", dtype=torch.float64)
+    dt = cfl_dt(u, grid.h, COUPLED_CFL)
+    u = torch.stack(list(u))
+    prm = O.Params(n, wl.grid.L, dt=dt, mu=COUPLED_NU, alpha=wl.alpha)
+    flow = N.Flow(n, wl.grid.L, nu=COUPLED_NU, dt=dt)
+    p = torch.zeros(u.shape[1:], dtype=torch.float64)
+    xs = [torch.tensor(b.rest) for b in sub]
+    vs = [torch.zeros_like(x) for x in xs]
+    t0 = time.perf_counter()
+    N.coupled_step(ob, xs, vs, u, p, flow, prm)
+    secs = time.perf_counter() - t0
+    nodes = sum(len(b.rest) for b in sub)
+    return {"value": nodes / secs, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "cell_steps_per_s": n[0] * n[1] * n[2] / secs,
+            "sample": f"1 coupled step of {len(sub)} bodies ({nodes} nodes) on a 128^3 grid, "
+                      f"{secs:.1f} s"}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.coupled:
+        run_coupled(args, ws, rank, local)
     else:
         run_gb300(args, ws, rank, local)
     if ws > 1:

@@ -329,12 +329,31 @@ ibm_status ibm_flow_project(ibm_flow* flow, int32_t substep, float* u, float* v,
  * does, with the probe traction and pressure of the new u, v, w, p (no
  * acceleration correction).  ctx NULL: the flow alone (x ... fz may be
  * NULL).  The context's grid and dt must equal the flow's and its mu the
- * flow's nu (density 1); x_out, v_out must not alias x, xv.  Errors:
+ * flow's nu (density 1); x_out, v_out must not alias x, xv.  Stability: with
+ * the narrow MLS kernel a marker corrects its nearest node with a gain of
+ * about A_l/h^2, so faces must stay below about two grid cells in area (the
+ * paper's meshes keep triangles near the grid size); coarser meshes make the
+ * slip, and then the flow, grow from substep to substep.  Errors:
  * IBM_ERR_INVALID_ARG on a mismatch or a null argument (message in
  * ibm_last_error(NULL) and, with a context, ibm_last_error(ctx)). */
 ibm_status ibm_flow_step(ibm_flow* flow, ibm_ctx* ctx, const float* x, const float* xv,
                          float* x_out, float* v_out, float* u, float* v, float* w, float* p,
                          float* fx, float* fy, float* fz);
+
+/* Phase timing of the flow (profiling aid, no counterpart in the paper):
+ * when on, every predictor and projection records CUDA events around its
+ * kernels and FFTs, and ibm_flow_step also around the body update.
+ * ibm_flow_get_phase_times waits for the last recorded events and writes host
+ * ms[13], each summed over substeps 0, 1, 2 of the last ones recorded:
+ * (advection and right-hand side, forward FFT x3, Crank-Nicolson scaling,
+ * inverse FFT x3, u* update, IBM forcing (the time between predictor and
+ * projection: force-field zeroing and the marker kernel), divergence,
+ * forward FFT, Poisson scaling, inverse FFT, projection), then the body
+ * update's marker kernel (body sums, probe traction) and force kernel
+ * (0 when no coupled step was timed).  IBM_ERR_INVALID_ARG until each
+ * substep has been timed once. */
+ibm_status ibm_flow_set_phase_timing(ibm_flow* flow, int32_t on);
+ibm_status ibm_flow_get_phase_times(ibm_flow* flow, float* ms);
 
 /* Synchronise the stream and report the device error word (IBM_ERR_DEVICE if
  * a kernel flagged an out-of-range or non-finite value). */

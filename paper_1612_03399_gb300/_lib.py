@@ -83,7 +83,12 @@ SIGNATURES = {
     "ibm_flow_predict": (C.c_int, [P, C.c_int32, P, P, P, P]),
     "ibm_flow_project": (C.c_int, [P, C.c_int32, P, P, P, P, P, P, P, C.c_float]),
     "ibm_flow_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P]),
+    "ibm_flow_set_phase_timing": (C.c_int, [P, C.c_int32]),
+    "ibm_flow_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
 }
+
+FLOW_PHASES = ("rhs", "fft_fwd3", "cn_scale", "fft_inv3", "add", "ibm_forcing", "div",
+               "fft_fwd1", "poisson_scale", "fft_inv1", "project", "body_marker", "body_force")
 
 _lib = None
 
@@ -400,6 +405,15 @@ class Flow:
         self._check(self.lib.ibm_flow_step(self.h, ctx.h if ctx is not None else None, _ptr(x),
                                            _ptr(v), _ptr(x_out), _ptr(v_out), _ptr(u), _ptr(vv),
                                            _ptr(w), _ptr(p), _ptr(fx), _ptr(fy), _ptr(fz)))
+
+    def set_phase_timing(self, on):
+        self._check(self.lib.ibm_flow_set_phase_timing(self.h, 1 if on else 0))
+
+    def phase_times(self):
+        """Milliseconds per phase of the last timed step (FLOW_PHASES order)."""
+        ms = (C.c_float * len(FLOW_PHASES))()
+        self._check(self.lib.ibm_flow_get_phase_times(self.h, ms))
+        return dict(zip(FLOW_PHASES, (float(m) for m in ms)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -42,6 +42,13 @@ struct ibm_flow {
   float* lam = nullptr;         // [n_x/2 + 1 | n_y | n_z] eigenvalues
   cufftHandle r2c3 = 0, c2r3 = 0, r2c1 = 0, c2r1 = 0;
   bool plans = false;
+  // phase timing (profiling aid): events at the 12 kernel boundaries of each
+  // substep and the 3 of the body update
+  bool timing = false;
+  cudaEvent_t ev[3][12] = {};
+  cudaEvent_t evs[3] = {};
+  bool have_sub[3] = {false, false, false};
+  bool have_struct = false;
 };
 
 namespace ibm {
@@ -277,6 +284,11 @@ void release(ibm_flow* fl) {
   for (void* q : {(void*)fl->H[0], (void*)fl->H[1], (void*)fl->R, (void*)fl->rp, (void*)fl->S,
                   (void*)fl->lam})
     if (q) cudaFree(q);
+  for (auto& row : fl->ev)
+    for (cudaEvent_t& ev : row)
+      if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t& ev : fl->evs)
+    if (ev) cudaEventDestroy(ev);
 }
 
 ibm_status flow_err(ibm_status s, const std::string& m) {
@@ -285,6 +297,21 @@ ibm_status flow_err(ibm_status s, const std::string& m) {
 }
 
 }  // namespace
+
+// record boundary k of substep l (k = 0..11) when phase timing is on
+cudaError_t flow_mark(ibm_flow* fl, int l, int k, cudaStream_t s) {
+  if (!fl->timing) return cudaSuccess;
+  return cudaEventRecord(fl->ev[l][k], s);
+}
+
+// record boundary k (0..2) of the body update: its start, after the marker
+// kernel (body sums and probe traction), after the force kernel
+cudaError_t flow_mark_struct(ibm_flow* fl, int k, cudaStream_t s) {
+  if (!fl->timing) return cudaSuccess;
+  const cudaError_t e = cudaEventRecord(fl->evs[k], s);
+  if (e == cudaSuccess && k == 2) fl->have_struct = true;
+  return e;
+}
 
 cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, const float* p,
                          cudaStream_t s) {
@@ -299,10 +326,14 @@ cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, cons
   const Vec3 Ro{{fl->R, fl->R + fl->N, fl->R + 2 * fl->N}};
   cudaError_t e = set_plan_streams(fl, s);
   if (e != cudaSuccess) return e;
+  e = flow_mark(fl, l, 0, s);
+  if (e != cudaSuccess) return e;
   rhs_kernel<<<cell_grid(fl), dim3(32, 8), 0, s>>>(G, u, v, w, p, Hp, Ho, Ro, (float)kGamma[l],
                                                      (float)kRho[l], (float)alpha, nu, dt);
   e = cudaGetLastError();
+  if (e == cudaSuccess) e = flow_mark(fl, l, 1, s);
   if (e == cudaSuccess) e = fft_status(cufftExecR2C(fl->r2c3, fl->R, fl->S));
+  if (e == cudaSuccess) e = flow_mark(fl, l, 2, s);
   if (e == cudaSuccess) {
     const int nxh = fl->n[0] / 2 + 1;
     cn_scale_kernel<<<flat_blocks(3 * fl->NC), 256, 0, s>>>(
@@ -310,11 +341,14 @@ cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, cons
         (float)(1.0 / (double)fl->N));
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = flow_mark(fl, l, 3, s);
   if (e == cudaSuccess) e = fft_status(cufftExecC2R(fl->c2r3, fl->S, fl->R));
+  if (e == cudaSuccess) e = flow_mark(fl, l, 4, s);
   if (e == cudaSuccess) {
     add_kernel<<<flat_blocks(3 * fl->N), 256, 0, s>>>(Vec3{{u, v, w}}, fl->R, fl->N);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = flow_mark(fl, l, 5, s);
   if (e == cudaSuccess) {
     fl->hcur ^= 1;
     fl->last = l;
@@ -330,22 +364,30 @@ cudaError_t flow_project(ibm_flow* fl, int l, float* u, float* v, float* w, floa
   const CVec3 f{{fx, fy, fz}};
   cudaError_t e = set_plan_streams(fl, s);
   if (e != cudaSuccess) return e;
+  e = flow_mark(fl, l, 6, s);
+  if (e != cudaSuccess) return e;
   div_kernel<<<cell_grid(fl), dim3(32, 8), 0, s>>>(G, CVec3{{u, v, w}}, f, fscale, fl->rp);
   e = cudaGetLastError();
+  if (e == cudaSuccess) e = flow_mark(fl, l, 7, s);
   if (e == cudaSuccess) e = fft_status(cufftExecR2C(fl->r2c1, fl->rp, fl->S));
+  if (e == cudaSuccess) e = flow_mark(fl, l, 8, s);
   if (e == cudaSuccess) {
     const int nxh = fl->n[0] / 2 + 1;
     poisson_scale_kernel<<<flat_blocks(fl->NC), 256, 0, s>>>(
         fl->S, nxh, fl->n[1], fl->n[2], fl->lam, (float)(1.0 / ((double)fl->N * alpha * fl->dt)));
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = flow_mark(fl, l, 9, s);
   if (e == cudaSuccess) e = fft_status(cufftExecC2R(fl->c2r1, fl->S, fl->rp));
+  if (e == cudaSuccess) e = flow_mark(fl, l, 10, s);
   if (e == cudaSuccess) {
     project_kernel<<<cell_grid(fl), dim3(32, 8), 0, s>>>(
         G, Vec3{{u, v, w}}, p, fl->rp, f, fscale, (float)(alpha * fl->dt),
         (float)(alpha * fl->dt * fl->nu / 2.0));
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = flow_mark(fl, l, 11, s);
+  if (e == cudaSuccess && fl->timing) fl->have_sub[l] = true;
   return e;
 }
 
@@ -469,5 +511,54 @@ extern "C" ibm_status ibm_flow_project(ibm_flow* fl, int32_t substep, float* u, 
   const cudaError_t e = ibm::flow_project(fl, substep, u, v, w, p, fx, fy, fz, f_scale, fl->stream);
   if (e != cudaSuccess)
     return flow_err(IBM_ERR_CUDA, std::string("ibm_flow_project: ") + cudaGetErrorString(e));
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_flow_set_phase_timing(ibm_flow* fl, int32_t on) {
+  if (!fl) return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_set_phase_timing: null flow");
+  cudaSetDevice(fl->device);
+  if (on && !fl->ev[0][0]) {
+    for (auto& row : fl->ev)
+      for (cudaEvent_t& ev : row) {
+        const cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess)
+          return flow_err(IBM_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+      }
+    for (cudaEvent_t& ev : fl->evs) {
+      const cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess)
+        return flow_err(IBM_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+  }
+  fl->timing = on != 0;
+  for (bool& b : fl->have_sub) b = false;
+  fl->have_struct = false;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_flow_get_phase_times(ibm_flow* fl, float* ms) {
+  if (!fl || !ms) return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_get_phase_times: null argument");
+  for (bool b : fl->have_sub)
+    if (!b)
+      return flow_err(IBM_ERR_INVALID_ARG,
+                      "ibm_flow_get_phase_times: no timed substep 0, 1 and 2 recorded");
+  cudaSetDevice(fl->device);
+  cudaError_t e = cudaEventSynchronize(fl->ev[2][11]);
+  for (int k = 0; k < 11; ++k) {
+    ms[k] = 0.f;
+    for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, fl->ev[l][k], fl->ev[l][k + 1]);
+      ms[k] += t;
+    }
+  }
+  ms[11] = ms[12] = 0.f;
+  if (e == cudaSuccess && fl->have_struct) {
+    e = cudaEventSynchronize(fl->evs[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[11], fl->evs[0], fl->evs[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[12], fl->evs[1], fl->evs[2]);
+  }
+  if (e != cudaSuccess)
+    return flow_err(IBM_ERR_CUDA, std::string("ibm_flow_get_phase_times: ") + cudaGetErrorString(e));
   return IBM_OK;
 }

@@ -991,11 +991,14 @@ extern "C" ibm_status ibm_flow_step(ibm_flow* fl, ibm_ctx* c, const float* x, co
   }
   if (c && e == cudaSuccess) {
     use_parity(c, c->qpar ^ 1);
-    e = zero_body_sums(c);
+    e = flow_mark_struct(fl, 0, s);
+    if (e == cudaSuccess) e = zero_body_sums(c);
     if (e == cudaSuccess)
       e = launch_mls(c, x, nullptr, u, vv, w, p, nullptr, nullptr, nullptr, nullptr, c->d.fext,
                      nullptr, nullptr, nullptr, true, false, true, false, false);
+    if (e == cudaSuccess) e = flow_mark_struct(fl, 1, s);
     if (e == cudaSuccess) e = launch_force(c, x, xv, c->d.fext, nullptr, x_out, v_out, nullptr, true);
+    if (e == cudaSuccess) e = flow_mark_struct(fl, 2, s);
   }
   if (e != cudaSuccess) {
     const std::string m = std::string("ibm_flow_step: ") + cudaGetErrorString(e);

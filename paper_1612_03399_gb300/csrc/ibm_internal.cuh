@@ -271,4 +271,7 @@ bool flow_matches(const ibm_flow* fl, const ibm_grid_desc& g, double dt, double 
 cudaStream_t flow_stream(const ibm_flow* fl);
 int flow_device(const ibm_flow* fl);
 size_t flow_cells(const ibm_flow* fl);
+// phase-timing events (no-ops unless timing is on)
+cudaError_t flow_mark(ibm_flow* fl, int l, int k, cudaStream_t s);
+cudaError_t flow_mark_struct(ibm_flow* fl, int k, cudaStream_t s);
 }  // namespace ibm

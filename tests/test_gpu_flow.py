@@ -251,3 +251,30 @@ def test_flow_rejects_bad_use():
         fl.step(u, p, ctx=ctx, x=x, v=v, x_out=torch.empty_like(x), v_out=torch.empty_like(v),
                 f=tuple(torch.zeros_like(u[0]) for _ in range(3)))
     fl.close()
+
+
+def test_flow_phase_times():
+    """The phase-timing aid: refused before three substeps were timed, then
+    13 non-negative phases whose sum is the step's device time."""
+    wl, rel_x, vs = coupled_case(20)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    fl = _lib.Flow(wl.grid, nu=wl.mu, dt=wl.dt)
+    x = H.state_tensor(wl, rel_x)
+    v = H.state_tensor(wl, vs)
+    u = tuple(t.clone() for t in H.fields_for(wl, DEV))
+    p = torch.zeros_like(u[0])
+    f = tuple(torch.empty_like(u[0]) for _ in range(3))
+    fl.set_phase_timing(True)
+    with pytest.raises(_lib.IBMError):
+        fl.phase_times()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fl.step(u, p, ctx=ctx, x=x, v=v, x_out=torch.empty_like(x), v_out=torch.empty_like(v), f=f)
+    e1.record()
+    e1.synchronize()
+    ph = fl.phase_times()
+    assert list(ph) == list(_lib.FLOW_PHASES)
+    assert all(t >= 0.0 for t in ph.values())
+    assert ph["rhs"] > 0 and ph["ibm_forcing"] > 0 and ph["body_force"] > 0
+    assert sum(ph.values()) <= e0.elapsed_time(e1) * 1.05 + 0.05
+    fl.close()
