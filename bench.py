@@ -205,14 +205,15 @@ def hbm_peak():
 
 def ncu_traffic(kernel_key):
     """DRAM bytes per launch of `kernel_key` from the committed ncu summary,
-    or None when the kernels changed since those counters were taken."""
+    or None when the kernel's sources changed since those counters were
+    taken (each kernel carries the digest of the files it is built from)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         from paper_1612_03399_gb300 import build as B
         d = json.load(open(p))
-        if d.get("source_digest") != B._digest():
+        if d.get("digests", {}).get(kernel_key) != B.kernel_digest(kernel_key):
             return None
         return d.get("kernels", {}).get(kernel_key)
     except Exception:

@@ -304,6 +304,8 @@ typedef struct ibm_flow ibm_flow;
  * IBM_ERR_INVALID_ARG, IBM_ERR_OOM, IBM_ERR_CUDA (no device, FFT plan). */
 ibm_status ibm_flow_create(const ibm_grid_desc* grid, double nu, double dt, ibm_flow** out);
 ibm_status ibm_flow_set_stream(ibm_flow* flow, void* stream);
+/* Waits for the device to finish (coupled steps may still run on a
+ * context's stream), then frees everything the flow owns.  NULL is ignored. */
 void ibm_flow_destroy(ibm_flow* flow);
 
 /* Predictor of RK3 substep `substep` (0, 1, 2): u, v, w <- u* in place, with

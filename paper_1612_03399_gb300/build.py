@@ -42,6 +42,33 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+# the sources each profiled kernel is compiled from (for per-kernel digests)
+KERNEL_SOURCES = {
+    "marker": ["k_mls.cu", "ibm_internal.cuh"],
+    "clear": ["k_mls.cu", "ibm_internal.cuh"],
+    "forcing": ["k_mls.cu", "ibm_internal.cuh"],
+    "body_marker": ["k_mls.cu", "ibm_internal.cuh"],
+    "force": ["k_force.cu", "force_elems.cuh", "ibm_internal.cuh"],
+    "rhs": ["ibm_flow.cu", "ibm_internal.cuh"],
+    "cn_scale": ["ibm_flow.cu", "ibm_internal.cuh"],
+    "add": ["ibm_flow.cu", "ibm_internal.cuh"],
+    "div": ["ibm_flow.cu", "ibm_internal.cuh"],
+    "poisson_scale": ["ibm_flow.cu", "ibm_internal.cuh"],
+    "project": ["ibm_flow.cu", "ibm_internal.cuh"],
+}
+
+
+def kernel_digest(key: str) -> str:
+    """Digest of the sources and flags one profiled kernel is built from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[key] + ["../../include/ibm.h"]:
+        p = os.path.normpath(os.path.join(CSRC, name))
+        h.update(name.encode())
+        h.update(open(p, "rb").read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if sources changed) and return the path of the library."""
     os.makedirs(BUILD, exist_ok=True)

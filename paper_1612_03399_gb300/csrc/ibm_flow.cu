@@ -479,7 +479,8 @@ extern "C" ibm_status ibm_flow_set_stream(ibm_flow* fl, void* stream) {
 extern "C" void ibm_flow_destroy(ibm_flow* fl) {
   if (!fl) return;
   cudaSetDevice(fl->device);
-  cudaStreamSynchronize(fl->stream);
+  // coupled steps run on a context's stream: wait for all work on the device
+  cudaDeviceSynchronize();
   ibm::release(fl);
   delete fl;
 }
