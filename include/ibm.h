@@ -250,9 +250,11 @@ ibm_status ibm_taylor_backward(ibm_ctx* ctx, const float* x, const double* gD, f
  * context's stream with one launch.  Inside the graph the force fields of the
  * intermediate steps are never observed, so each step's footprint clear runs
  * concurrently with the previous step's force kernel; after a launch fx, fy,
- * fz hold exactly the last step's forces.  Creation captures on a private
- * stream after the work already queued on the context's stream.  The context
- * must outlive the graph. */
+ * fz hold exactly the last step's forces.  As in ibm_step, each force kernel
+ * may start while the marker kernel before it finishes (programmatic launch:
+ * it waits for the marker kernel before using its results).  Creation
+ * captures on a private stream after the work already queued on the
+ * context's stream.  The context must outlive the graph. */
 typedef struct ibm_graph ibm_graph;
 ibm_status ibm_graph_create(ibm_ctx* ctx, float* xa, float* va, float* xb, float* vb,
                             const float* u, const float* vv, const float* w, const float* p,

@@ -72,10 +72,6 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     S.py[i] = __ldg(x + V + gv);
     S.pz[i] = __ldg(x + 2 * V + gv);
   }
-  // per-body global-term coefficients from the marker kernel's exact
-  // fixed-point area / volume sums
-  const float2 cf = body_coef(B, __ldg(T.qsum + 2 * wk.x), __ldg(T.qsum + 2 * wk.x + 1));
-  const float cA = cf.x, cV = cf.y;
   const bool want_e = energy != nullptr;
   double eS = 0.0, eB = 0.0, eA = 0.0;
   __syncthreads();
@@ -105,6 +101,15 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     S.put(2 * P.n_edge + k, fc);
     S.put(3 * P.n_edge + k, fd);
   }
+  // Everything above reads only static tables and positions written two
+  // launches back; the marker kernel launched just before (it lets this grid
+  // start once all its blocks run) produces the body sums and F_ext, so the
+  // face part waits for it to complete (a no-op without that launch mode).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // per-body global-term coefficients from the marker kernel's exact
+  // fixed-point area / volume sums
+  const float2 cf = body_coef(B, __ldg(T.qsum + 2 * wk.x), __ldg(T.qsum + 2 * wk.x + 1));
+  const float cA = cf.x, cV = cf.y;
   // faces: local area, global area, volume
   const int fbase = 4 * P.n_edge;
   for (int k = threadIdx.x; k < P.n_face; k += blockDim.x) {
@@ -251,23 +256,38 @@ __global__ void __launch_bounds__(kForceThreads) advance_kernel(
 
 }  // namespace
 
+// Force kernels are launched with programmatic stream serialisation: they
+// may start while the preceding marker kernel's last blocks still run (the
+// marker kernel allows it from the start of every block) and wait for its
+// completion before the face part; after any other preceding work they start
+// as usual, when it has completed.
+template <int MODE>
+cudaError_t launch_force_mode(ibm_ctx* c, const float* x, const float* v, const float* Fext,
+                              float* Fint, float* x_out, float* v_out, double* energy) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)c->n_work);
+  cfg.blockDim = dim3(kForceThreads);
+  cfg.dynamicSmemBytes = c->force_smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, force_kernel<MODE>, c->d, c->sc, (int32_t)c->V, (int32_t)c->F,
+                            x, v, Fext, Fint, x_out, v_out, energy);
+}
+
 cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float* Fext,
                          float* Fint, float* x_out, float* v_out, double* energy, bool advance) {
   if (c->n_work == 0) return cudaSuccess;
-  if (advance)
-    force_kernel<1><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
-        c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, Fext, Fint, x_out, v_out, energy);
-  else
-    force_kernel<0><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
-        c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, Fext, Fint, x_out, v_out, energy);
-  return cudaGetLastError();
+  return advance ? launch_force_mode<1>(c, x, v, Fext, Fint, x_out, v_out, energy)
+                 : launch_force_mode<0>(c, x, v, Fext, Fint, x_out, v_out, energy);
 }
 
 cudaError_t launch_accel(ibm_ctx* c, const float* x, const float* Fext, float* a) {
   if (c->n_work == 0) return cudaSuccess;
-  force_kernel<2><<<c->n_work, kForceThreads, c->force_smem, c->stream>>>(
-      c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, nullptr, Fext, a, nullptr, nullptr, nullptr);
-  return cudaGetLastError();
+  return launch_force_mode<2>(c, x, nullptr, Fext, a, nullptr, nullptr, nullptr);
 }
 
 cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,

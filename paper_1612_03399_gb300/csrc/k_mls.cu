@@ -393,6 +393,9 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   __shared__ int s_warp[kMT / 32];
   __shared__ int s_bmax[3];
 
+  // a force kernel launched after this one may start once every block of
+  // this grid runs (it waits for this grid's results before using them)
+  asm volatile("griddepcontrol.launch_dependents;");
   const int4 ch = T.chunks[blockIdx.x];  // body, face-list offset, count, chunk index in body
   const BodyDev B = T.body[ch.x];
   const TopoDev topo = T.topo[B.topo];
