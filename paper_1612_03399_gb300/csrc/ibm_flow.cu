@@ -142,55 +142,65 @@ __global__ void __launch_bounds__(256) rhs_kernel(FGrid G, const float* __restri
   }
 }
 
-// spectra [batch][nz][ny][nx/2+1] times norm / prod_d (1 - a lam_d)
-__global__ void cn_scale_kernel(cufftComplex* __restrict__ S, int nxh, int ny, int nz, int batch,
-                                const float* __restrict__ lam, float a, float norm) {
-  const size_t total = (size_t)batch * nz * ny * nxh;
+// Spectra are [batch][nz][ny][nx/2+1]: one warp-wide row of x coefficients
+// per threadIdx.y, rows (j, k) grid-strided over blockIdx.x, the batch in
+// blockIdx.y (one division per row, none per coefficient).
+constexpr int kRowThreads = 32, kRowsPerBlock = 8;
+
+// times norm / prod_d (1 - a lam_d)
+__global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
+    cn_scale_kernel(cufftComplex* __restrict__ S, int nxh, int ny, int nz,
+                    const float* __restrict__ lam, float a, float norm) {
   const float* lx = lam;
   const float* ly = lam + nxh;
   const float* lz = ly + ny;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
-       q += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nxh);
-    const size_t r = q / nxh;
-    const int j = (int)(r % ny);
-    const int k = (int)((r / ny) % nz);
-    const float d = (1.f - a * __ldg(lx + i)) * (1.f - a * __ldg(ly + j)) * (1.f - a * __ldg(lz + k));
-    const float s = norm / d;
-    S[q].x *= s;
-    S[q].y *= s;
+  cufftComplex* Sb = S + (size_t)blockIdx.y * nz * ny * nxh;
+  for (int r = blockIdx.x * kRowsPerBlock + threadIdx.y; r < ny * nz;
+       r += gridDim.x * kRowsPerBlock) {
+    const int k = r / ny, j = r - k * ny;
+    const float dyz = norm / ((1.f - a * __ldg(ly + j)) * (1.f - a * __ldg(lz + k)));
+    cufftComplex* row = Sb + (size_t)r * nxh;
+    for (int i = threadIdx.x; i < nxh; i += kRowThreads) {
+      const float s = dyz / (1.f - a * __ldg(lx + i));
+      cufftComplex c = row[i];
+      c.x *= s;
+      c.y *= s;
+      row[i] = c;
+    }
   }
 }
 
 // spectrum of div / (alpha dt): times scale / (lam_x + lam_y + lam_z), mean 0
-__global__ void poisson_scale_kernel(cufftComplex* __restrict__ S, int nxh, int ny, int nz,
-                                     const float* __restrict__ lam, float scale) {
-  const size_t total = (size_t)nz * ny * nxh;
+__global__ void __launch_bounds__(kRowThreads * kRowsPerBlock)
+    poisson_scale_kernel(cufftComplex* __restrict__ S, int nxh, int ny, int nz,
+                         const float* __restrict__ lam, float scale) {
   const float* lx = lam;
   const float* ly = lam + nxh;
   const float* lz = ly + ny;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
-       q += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nxh);
-    const size_t r = q / nxh;
-    const int j = (int)(r % ny);
-    const int k = (int)(r / ny);
-    const float l = __ldg(lx + i) + __ldg(ly + j) + __ldg(lz + k);
-    const float s = q == 0 ? 0.f : scale / l;
-    S[q].x *= s;
-    S[q].y *= s;
+  for (int r = blockIdx.x * kRowsPerBlock + threadIdx.y; r < ny * nz;
+       r += gridDim.x * kRowsPerBlock) {
+    const int k = r / ny, j = r - k * ny;
+    const float lyz = __ldg(ly + j) + __ldg(lz + k);
+    cufftComplex* row = S + (size_t)r * nxh;
+    for (int i = threadIdx.x; i < nxh; i += kRowThreads) {
+      const float l = __ldg(lx + i) + lyz;
+      const float s = (r == 0 && i == 0) ? 0.f : scale / l;
+      cufftComplex c = row[i];
+      c.x *= s;
+      c.y *= s;
+      row[i] = c;
+    }
   }
 }
 
-// u_c += du_c, du = [3][N]
+// u_c += du_c, du = [3][N]; the component in blockIdx.y
 __global__ void add_kernel(Vec3 u, const float* __restrict__ du, size_t N) {
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 3 * N;
-       q += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(q / N);
-    const size_t o = q - (size_t)c * N;
-    float* uc = c == 0 ? u.c[0] : (c == 1 ? u.c[1] : u.c[2]);
-    uc[o] += __ldg(du + q);
-  }
+  const int c = blockIdx.y;
+  float* uc = c == 0 ? u.c[0] : (c == 1 ? u.c[1] : u.c[2]);
+  const float* dc = du + (size_t)c * N;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N;
+       q += (size_t)gridDim.x * blockDim.x)
+    uc[q] += __ldg(dc + q);
 }
 
 // div(u* + s f) at the cell centres
@@ -257,6 +267,13 @@ FGrid fgrid(const ibm_flow* fl) {
 
 dim3 cell_grid(const ibm_flow* fl) {
   return dim3((unsigned)((fl->n[0] + 31) / 32), (unsigned)((fl->n[1] + 7) / 8), (unsigned)fl->n[2]);
+}
+
+// blocks for the row kernels: enough rows in flight, at most one pass over them
+unsigned row_blocks(const ibm_flow* fl) {
+  const int rows = fl->n[1] * fl->n[2];
+  const int b = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
+  return (unsigned)(b < 152 * 32 ? b : 152 * 32);
 }
 
 unsigned flat_blocks(size_t total) {
@@ -336,8 +353,8 @@ cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, cons
   if (e == cudaSuccess) e = flow_mark(fl, l, 2, s);
   if (e == cudaSuccess) {
     const int nxh = fl->n[0] / 2 + 1;
-    cn_scale_kernel<<<flat_blocks(3 * fl->NC), 256, 0, s>>>(
-        fl->S, nxh, fl->n[1], fl->n[2], 3, fl->lam, (float)(alpha * fl->dt * fl->nu / 2.0),
+    cn_scale_kernel<<<dim3(row_blocks(fl), 3), dim3(kRowThreads, kRowsPerBlock), 0, s>>>(
+        fl->S, nxh, fl->n[1], fl->n[2], fl->lam, (float)(alpha * fl->dt * fl->nu / 2.0),
         (float)(1.0 / (double)fl->N));
     e = cudaGetLastError();
   }
@@ -345,7 +362,7 @@ cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, cons
   if (e == cudaSuccess) e = fft_status(cufftExecC2R(fl->c2r3, fl->S, fl->R));
   if (e == cudaSuccess) e = flow_mark(fl, l, 4, s);
   if (e == cudaSuccess) {
-    add_kernel<<<flat_blocks(3 * fl->N), 256, 0, s>>>(Vec3{{u, v, w}}, fl->R, fl->N);
+    add_kernel<<<dim3(flat_blocks(fl->N), 3), 256, 0, s>>>(Vec3{{u, v, w}}, fl->R, fl->N);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = flow_mark(fl, l, 5, s);
@@ -373,7 +390,7 @@ cudaError_t flow_project(ibm_flow* fl, int l, float* u, float* v, float* w, floa
   if (e == cudaSuccess) e = flow_mark(fl, l, 8, s);
   if (e == cudaSuccess) {
     const int nxh = fl->n[0] / 2 + 1;
-    poisson_scale_kernel<<<flat_blocks(fl->NC), 256, 0, s>>>(
+    poisson_scale_kernel<<<row_blocks(fl), dim3(kRowThreads, kRowsPerBlock), 0, s>>>(
         fl->S, nxh, fl->n[1], fl->n[2], fl->lam, (float)(1.0 / ((double)fl->N * alpha * fl->dt)));
     e = cudaGetLastError();
   }
