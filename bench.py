@@ -233,6 +233,7 @@ class Clocks:
         self.index = index
         self.proc = None
         self.path = None
+        self.skip = 0
 
     def start(self):
         try:
@@ -240,8 +241,13 @@ class Clocks:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=self.fh,
+                                          "-i", str(self.index), "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
+            # the timed region starts once the sampler delivers readings
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
+            self.skip = sum(1 for line in open(self.path) if line.strip())
         except Exception:
             self.proc = None
 
@@ -256,6 +262,9 @@ class Clocks:
         self.fh.close()
         rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
         os.unlink(self.path)
+        # readings taken before the timed region started are dropped, but one
+        # is kept when the region was shorter than the sampling interval
+        rows = rows[self.skip:] or rows[-1:]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:

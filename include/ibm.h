@@ -295,7 +295,7 @@ ibm_status ibm_gts_read(const char* path, int64_t* n_vert, int64_t* n_face, doub
  *   p <- p + phi - a lap(phi)                                      (projection).
  * In the periodic box both implicit operators are diagonal in Fourier space
  * and are solved there exactly (cuFFT transforms, float32).  A flow object
- * owns its work arrays (about eleven fields) and FFT plans; velocity and
+ * owns its work arrays (about thirteen fields) and FFT plans; velocity and
  * pressure fields are caller-owned device arrays [nz][ny][nx]. */
 typedef struct ibm_flow ibm_flow;
 
