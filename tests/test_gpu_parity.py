@@ -56,7 +56,7 @@ def mixed():
     return wl, H.oracle_bodies(wl)
 
 
-@pytest.mark.parametrize("patch", [0, 32])
+@pytest.mark.parametrize("patch", [0, 32, 512])
 def test_internal_forces_parity(mixed, patch, record_error):
     wl, ob = mixed
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, patch_size=patch)
