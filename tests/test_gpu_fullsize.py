@@ -1,7 +1,10 @@
 """Parity at the benchmarked sizes and launch configuration: one ibm_step
-exactly as bench.py runs it, on the three throughput workloads (1000 drops on
-512^3; 4096 uneven bodies of icosphere levels 2-5 on 768^3; the large
-membrane with two leaflet sheets on 512^3).  The oracle recomputes a sample
+with the force patch size bench.py's autotuner selects on each workload
+(256 vertices on the 1000 drops, 128 on the others), on the three
+throughput workloads (1000 drops on 512^3; 4096 uneven bodies of icosphere
+levels 2-5 on 768^3; the large membrane with two leaflet sheets on 512^3).
+bench.py replays these steps in a CUDA graph, which reproduces steps
+launched one by one bit for bit (test_gpu_graph.py).  The oracle recomputes a sample
 of well-separated bodies on the same grid and field (their supports overlap
 no other body's, so the spread force on their footprint is theirs alone):
 three drops; one body of every level; one full leaflet sheet (open, clamped,
@@ -60,17 +63,17 @@ def pick_leaflet(wl):
 
 
 CASES = {
-    "drops1000": (lambda: W.batched_drops(1000, 3, 512, seed=1), pick_drops, 0.2),
-    "uneven4096": (lambda: W.uneven_bodies(4096, 768, seed=1), pick_levels, 0.2),
-    "membranes": (lambda: W.membranes(8, 512, seed=1), pick_leaflet, 0.05),
+    "drops1000": (lambda: W.batched_drops(1000, 3, 512, seed=1), pick_drops, 0.2, 256),
+    "uneven4096": (lambda: W.uneven_bodies(4096, 768, seed=1), pick_levels, 0.2, 128),
+    "membranes": (lambda: W.membranes(8, 512, seed=1), pick_leaflet, 0.05, 128),
 }
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_full_size_step_sampled_parity(case, record_error):
-    make, pick_fn, vmax = CASES[case]
+    make, pick_fn, vmax, patch = CASES[case]
     wl = make()
-    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha, patch_size=patch)
     fields = H.fields_for(wl, DEV)
     x, v = ctx.init_state()
     rng = np.random.default_rng(0)
