@@ -278,3 +278,45 @@ def test_flow_phase_times():
     assert ph["rhs"] > 0 and ph["ibm_forcing"] > 0 and ph["body_force"] > 0
     assert sum(ph.values()) <= e0.elapsed_time(e1) * 1.05 + 0.05
     fl.close()
+
+
+def test_coupled_step_full_size_properties(record_error):
+    """The coupled benchmark's configuration (the 1000 drops on 256^3, dt at
+    CFL 0.5, nu = mu = 0.01), where the oracle cannot follow (every body
+    couples through the flow): after two coupled steps through the C ABI the
+    velocity is discretely solenoidal to float32 rounding, every node obeys
+    the symplectic update x' = x + dt v', nothing is non-finite and no marker
+    patch left shared memory."""
+    import bench
+    wl = W.batched_drops(1000, 3, 256, seed=1)
+    fields = H.fields_for(wl, DEV)
+    dt = bench.cfl_dt(fields, wl.grid.h, bench.COUPLED_CFL)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=dt, mu=bench.COUPLED_NU, alpha=wl.alpha,
+                       patch_size=256)
+    fl = _lib.Flow(wl.grid, nu=bench.COUPLED_NU, dt=dt)
+    u = tuple(t.clone() for t in fields)
+    p = torch.zeros_like(u[0])
+    f = tuple(torch.zeros_like(u[0]) for _ in range(3))
+    x, v = ctx.init_state()
+    for _ in range(2):
+        x1, v1 = torch.empty_like(x), torch.empty_like(v)
+        fl.step(u, p, ctx=ctx, x=x, v=v, x_out=x1, v_out=v1, f=f)
+        x_prev, x, v = x, x1, v1
+    ctx.check_device_error()
+    assert ctx.counters()["marker_box_fallbacks"] == 0
+    for t in (*u, p, *f, x, v):
+        assert bool(torch.isfinite(t).all())
+    h = wl.grid.h
+    ud = [t.double() for t in u]
+    div = ((torch.roll(ud[0], -1, 2) - ud[0]) / h[0] + (torch.roll(ud[1], -1, 1) - ud[1]) / h[1]
+           + (torch.roll(ud[2], -1, 0) - ud[2]) / h[2])
+    umax = max(float(t.abs().max()) for t in ud)
+    rel_div = float(div.abs().max()) * min(h) / umax
+    record_error("max|div u| h / max|u|", rel_div)
+    assert rel_div <= 1e-5
+    # x' = x + dt v' per node (float32 arithmetic on body-frame coordinates)
+    upd = (x.double() - x_prev.double() - dt * v.double()).abs().max()
+    scale = float(x_prev.abs().max())
+    record_error("update residual / |x|", float(upd) / scale)
+    assert float(upd) <= 4 * 2.0 ** -24 * scale
+    fl.close()
