@@ -76,3 +76,72 @@ def test_global_path_matches_oracle(record_error):
     record_error("dv", ev)
     record_error("f", ef)
     assert ev <= 1e-5 and ef <= 1e-5
+
+
+def sheet_body(shift):
+    """A coarse open sheet (~4 cells per face, clamped rim) inside the sphere,
+    whose one patch spans more than 1024 grid rows."""
+    rng = np.random.default_rng(7)
+    sv, st, bnd = W.elliptic_sheet(0.3, 0.28, 200, rng, jitter=0.15)
+    rot = W.random_rotation(rng)
+    c = np.array([0.5, 0.47, 0.52]) + shift
+    return W.Body(rest=c + sv @ rot.T, tri=st, origin=c, closed=False, clamped=bnd, ks=5.0,
+                  kb=0.3, ka=1.0, kA=0.0, kv=0.0, mass=1.5, radius=0.3)
+
+
+def test_global_path_open_sheet_and_pressure(record_error):
+    """The global path with two-sided probes (open sheet), the cell-centred
+    pressure and the marker-acceleration correction: traction and one step
+    against the oracle."""
+    for k in range(40):
+        wl = coarse_sphere_workload(shift=1e-3 * k)
+        wl.bodies.append(sheet_body(1e-3 * k))
+        if H.tie_free(wl, [torch.tensor(b.rest) for b in wl.bodies]):
+            break
+    else:
+        raise RuntimeError("no tie-free shift")
+    sheet = wl.bodies[1]
+    ext = (sheet.rest.max(0) - sheet.rest.min(0)) / np.array(wl.grid.h)
+    assert (ext[1] + 4) * (ext[2] + 4) > 1024      # more (y, z) rows than shared memory holds
+    ob = H.oracle_bodies(wl)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    fields = H.fields_for(wl, DEV)
+    x, _ = ctx.init_state()
+    rng = np.random.default_rng(8)
+    vb = []
+    for b in wl.bodies:
+        vv = rng.uniform(-0.2, 0.2, (len(b.rest), 3))
+        if b.clamped is not None:
+            vv[b.clamped] = 0.0
+        vb.append(vv)
+    v = H.state_tensor(wl, vb)
+    spec = W.pressure_modes(12, 3, 20.0, rng)
+    p = W.sample_pressure(spec, wl.grid, device=DEV, dtype=torch.float32)
+    p64 = W.sample_pressure(spec, wl.grid, dtype=torch.float64)
+    a = torch.tensor(rng.uniform(-20.0, 20.0, (3, ctx.V)), dtype=torch.float32, device=DEV)
+    a_b = [torch.tensor(t) for t in H.split_state(ctx, wl, a)]
+    _, _, Fe = ctx.interpolate(x, v, fields, U=False, F_marker=False, F_ext=True, p=p, accel=a)
+    n = wl.grid.n
+    f = tuple(torch.zeros((n[2], n[1], n[0]), dtype=torch.float32, device=DEV) for _ in range(3))
+    x1, v1 = torch.empty_like(x), torch.empty_like(v)
+    ctx.step(x, v, fields, x1, v1, f, p=p, accel=a)
+    ctx.check_device_error()
+    assert ctx.counters()["marker_box_fallbacks"] > 0
+    xs = H.to_abs(wl, H.split_state(ctx, wl, x))
+    vs = [torch.tensor(t) for t in H.split_state(ctx, wl, v)]
+    out = O.step(ob, xs, vs, tuple(t.double().cpu() for t in fields), H.oracle_params(wl),
+                 pressure=p64, accels=a_b)
+    e = H.rel_l2(Fe.double().cpu().numpy().T, out["F_ext_face"].numpy())
+    record_error("F_ext_face", e)
+    assert e <= 1e-5
+    vg = H.split_state(ctx, wl, v1)
+    for i in range(len(wl.bodies)):
+        vo = out["v_next"][i].numpy()
+        v0 = vs[i].numpy()
+        store = np.linalg.norm(0.5 * np.spacing(np.abs(vo).astype(np.float32)).astype(np.float64))
+        ev = max(0.0, np.linalg.norm((vg[i] - v0) - (vo - v0)) - store) / np.linalg.norm(vo - v0)
+        record_error(f"dv[{i}]", ev)
+        assert ev <= 1e-5
+    ef = H.rel_l2(torch.stack(f).cpu().numpy(), out["f"].numpy())
+    record_error("f", ef)
+    assert ef <= 1e-5
