@@ -59,13 +59,16 @@ KERNEL_SOURCES = {
 
 
 def kernel_digest(key: str) -> str:
-    """Digest of the sources and flags one profiled kernel is built from."""
+    """Digest of the sources and flags one profiled kernel is built from
+    (independent of where the repository lives: the include path is left
+    out of the flags)."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[key] + ["../../include/ibm.h"]:
         p = os.path.normpath(os.path.join(CSRC, name))
         h.update(name.encode())
         h.update(open(p, "rb").read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    flags = [f for i, f in enumerate(FLAGS) if f != "-I" and (i == 0 or FLAGS[i - 1] != "-I")]
+    h.update(" ".join(ARCH + flags).encode())
     return h.hexdigest()
 
 
