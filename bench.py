@@ -313,10 +313,13 @@ def run_reference(args, ws, rank):
         return
     make, descr = WORKLOADS[args.workload]
     wl = make(1)
-    nb = min(len(wl.bodies), 8)
     fields = W.sample_field(wl.field, wl.grid, device="cpu", dtype=torch.float64)
-    oracle_sample_rate(wl, 1, 1, fields)          # warm-up (allocator, threads)
-    rate, secs, nodes = oracle_sample_rate(wl, nb, max(1, args.steps), fields)
+    # warm-up (allocator, threads), which also sizes the sample: up to 8
+    # bodies per step, about a minute of oracle work over all the steps
+    _, t1, _ = oracle_sample_rate(wl, 1, 1, fields)
+    steps = max(1, args.steps)
+    nb = max(1, min(len(wl.bodies), 8, int(60.0 / (t1 * steps))))
+    rate, secs, nodes = oracle_sample_rate(wl, nb, steps, fields)
     cores = torch.get_num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
