@@ -544,22 +544,28 @@ def cfl_dt(fields, h, cfl):
     return cfl / rate
 
 
-def flow_bytes(n):
+def flow_bytes(n, widths):
     """Algorithmic bytes per time step of the flow solver's own kernels
     (float32 fields of N cells, spectra of NC = nz ny (nx/2+1) complex
     values), summed over the three substeps: what each kernel must read and
-    write once."""
+    write once.  `widths` are the substeps' viscous-solve widths (-1: Fourier
+    path); the u* update moves the same bytes on both paths (R or du read,
+    u read and written) and is named for the kernel that ran it."""
     N = n[0] * n[1] * n[2]
     NC = n[2] * n[1] * (n[0] // 2 + 1)
-    return {
+    n_fourier = sum(1 for w in widths if w < 0)
+    upd = {0: "cn_solve", 3: "add"}.get(n_fourier, "update")
+    out = {
         # u, v, w, p read; H and R (3 each) written; H_prev (3) read in substeps 1, 2
         "rhs": 4 * N * (3 * (4 + 6) + 2 * 3),
-        "cn_scale": 3 * 3 * NC * 8 * 2,       # three spectra read and written
-        "add": 3 * 4 * N * 9,                 # u, du read, u written (3 components)
+        upd: 3 * 4 * N * 9,                   # R or du, u read, u written (3 components)
         "div": 3 * 4 * N * 7,                 # u*, f read (3 + 3), divergence written
         "poisson_scale": 3 * NC * 8 * 2,
         "project": 3 * 4 * N * 12,            # u*, f, phi, p read; u, p written
     }
+    if n_fourier:
+        out["cn_scale"] = n_fourier * 3 * NC * 8 * 2   # three spectra read and written
+    return out
 
 
 def run_coupled(args, ws, rank, local):
@@ -656,12 +662,13 @@ def run_coupled(args, ws, rank, local):
     ctx.check_device_error()
     if rank != 0:
         return
-    fb = flow_bytes(wl.grid.n)
+    widths = flow.solve_widths()
+    fb = flow_bytes(wl.grid.n, widths)
     # the forcing launches (marker kernel, interpolate and spread), three per
     # step; their phase also holds the zeroing of the three force fields, so
     # the rate derived from it is a lower bound
     fb["forcing"] = 3 * bytes_model["forcing"]
-    ph_k = dict(ph, forcing=ph["ibm_forcing"])
+    ph_k = dict(ph, forcing=ph["ibm_forcing"], cn_solve=ph["update"], add=ph["update"])
     own = {k: ph_k[k] for k in fb}
     dom = max(own, key=own.get)
     peak, peak_kind = hbm_peak()
@@ -677,6 +684,7 @@ def run_coupled(args, ws, rank, local):
         "cell_steps_per_s": cells,
         "config": {"workload": descr + f"; flow solved: dt {dt:.3g} (CFL {COUPLED_CFL} of the "
                    "initial field), nu = mu = 0.01, p0 = 0",
+                   "viscous_solve_widths": list(widths),
                    "bodies": ctx.B, "vertices": ctx.V, "faces": ctx.F, "grid": list(wl.grid.n),
                    "max_face_area_h2": max_face_h2,
                    "l2": "flushed between timed steps (256 MiB write); fields of 64 MiB each",
@@ -688,9 +696,9 @@ def run_coupled(args, ws, rank, local):
         "fft_share": fft_ms / step_ms,
         "other_kernel": {k: {"algorithmic_bytes_per_step": fb[k],
                              "achieved_gbs": fb[k] / (ph_k[k] * 1e-3) / 1e9} for k in fb},
-        # per step: 3 x (rhs, cn_scale, add, marker, div, poisson_scale, project) + marker + force;
-        # cuFFT's own kernels and the memsets not counted
-        "gpu_launches": 23 * args.steps,
+        # per step: 3 x (rhs, [cn_scale,] add or cn_solve, marker, div, poisson_scale,
+        # project) + marker + force; cuFFT's own kernels and the memsets not counted
+        "gpu_launches": (20 + sum(1 for w in widths if w < 0)) * args.steps,
         "timing": "coupled steps launched one by one; phases from CUDA events between the "
                   "kernels of separately timed steps",
         "e2e": e2e,

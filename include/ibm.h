@@ -293,19 +293,31 @@ ibm_status ibm_gts_read(const char* path, int64_t* n_vert, int64_t* n_face, doub
  * (1 - a d_xx)(1 - a d_yy)(1 - a d_zz), a = alpha_l dt nu/2, then
  *   lap(phi) = div(u*)/(alpha_l dt),  u = u* - alpha_l dt grad(phi),
  *   p <- p + phi - a lap(phi)                                      (projection).
- * In the periodic box both implicit operators are diagonal in Fourier space
- * and are solved there exactly (cuFFT transforms, float32).  A flow object
- * owns its work arrays (about thirteen fields) and FFT plans; velocity and
- * pressure fields are caller-owned device arrays [nz][ny][nx]. */
+ * In the periodic box both implicit operators are diagonal in Fourier space.
+ * The Poisson equation is solved there (cuFFT transforms, float32).  The
+ * factorised viscous operator is inverted exactly in one of two ways, fixed
+ * per substep at creation: in real space when every direction's periodic
+ * inverse, a circulant whose entries fall off as r^|m|, has less than 2^-26
+ * of its mass beyond some |m| = W <= 8 with 2W + 1 <= n (then three
+ * separable (2W+1)-tap filters, fused with the u* update; small
+ * alpha_l dt nu / h^2), else in Fourier space.  A flow object owns its work
+ * arrays (about thirteen fields) and FFT plans; velocity and pressure fields
+ * are caller-owned device arrays [nz][ny][nx]. */
 typedef struct ibm_flow ibm_flow;
 
 /* Create a solver for grid (n >= 4 per direction; the reserved field is
  * ignored) with viscosity nu >= 0 and time step dt > 0, on the current
  * device; its calls run on the legacy default stream until
  * ibm_flow_set_stream.  Errors (message in ibm_last_error(NULL)):
- * IBM_ERR_INVALID_ARG, IBM_ERR_OOM, IBM_ERR_CUDA (no device, FFT plan). */
+ * IBM_ERR_INVALID_ARG, IBM_ERR_UNSUPPORTED (2^31 cells or more, n_z above
+ * 65535 or n_y above 524280), IBM_ERR_OOM,
+ * IBM_ERR_CUDA (no device, FFT plan). */
 ibm_status ibm_flow_create(const ibm_grid_desc* grid, double nu, double dt, ibm_flow** out);
 ibm_status ibm_flow_set_stream(ibm_flow* flow, void* stream);
+/* The viscous solve of substep `substep` (0, 1, 2): *width = W >= 0 when it
+ * runs in real space with 2W + 1 taps per direction, -1 when it runs in
+ * Fourier space.  Host only.  Errors: IBM_ERR_INVALID_ARG. */
+ibm_status ibm_flow_solve_width(const ibm_flow* flow, int32_t substep, int32_t* width);
 /* Waits for the device to finish (coupled steps may still run on a
  * context's stream), then frees everything the flow owns.  NULL is ignored. */
 void ibm_flow_destroy(ibm_flow* flow);
@@ -350,7 +362,8 @@ ibm_status ibm_flow_step(ibm_flow* flow, ibm_ctx* ctx, const float* x, const flo
  * ibm_flow_get_phase_times waits for the last recorded events and writes host
  * ms[13], each summed over substeps 0, 1, 2 of the last ones recorded:
  * (advection and right-hand side, forward FFT x3, Crank-Nicolson scaling,
- * inverse FFT x3, u* update, IBM forcing (the time between predictor and
+ * inverse FFT x3 (these three 0 in real-space substeps), u* update (with the
+ * real-space solve in it), IBM forcing (the time between predictor and
  * projection: force-field zeroing and the marker kernel), divergence,
  * forward FFT, Poisson scaling, inverse FFT, projection), then the body
  * update's marker kernel (body sums, probe traction) and force kernel

@@ -79,6 +79,7 @@ SIGNATURES = {
     "ibm_gts_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), P, P]),
     "ibm_flow_create": (C.c_int, [C.POINTER(GridDesc), C.c_double, C.c_double, C.POINTER(P)]),
     "ibm_flow_set_stream": (C.c_int, [P, P]),
+    "ibm_flow_solve_width": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32)]),
     "ibm_flow_destroy": (None, [P]),
     "ibm_flow_predict": (C.c_int, [P, C.c_int32, P, P, P, P]),
     "ibm_flow_project": (C.c_int, [P, C.c_int32, P, P, P, P, P, P, P, C.c_float]),
@@ -87,7 +88,7 @@ SIGNATURES = {
     "ibm_flow_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
 }
 
-FLOW_PHASES = ("rhs", "fft_fwd3", "cn_scale", "fft_inv3", "add", "ibm_forcing", "div",
+FLOW_PHASES = ("rhs", "fft_fwd3", "cn_scale", "fft_inv3", "update", "ibm_forcing", "div",
                "fft_fwd1", "poisson_scale", "fft_inv1", "project", "body_marker", "body_force")
 
 _lib = None
@@ -385,6 +386,16 @@ class Flow:
     def set_stream(self, stream):
         self.stream = stream
         self._check(self.lib.ibm_flow_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def solve_widths(self):
+        """Per substep, the half width W of the real-space viscous solve
+        (2W + 1 taps per direction), or -1 where it runs in Fourier space."""
+        out = []
+        for l in range(3):
+            w = C.c_int32()
+            self._check(self.lib.ibm_flow_solve_width(self.h, l, C.byref(w)))
+            out.append(int(w.value))
+        return tuple(out)
 
     def predict(self, substep, fields, p):
         u, vv, w = fields

@@ -52,6 +52,7 @@ KERNEL_SOURCES = {
     "rhs": ["ibm_flow.cu", "ibm_internal.cuh"],
     "cn_scale": ["ibm_flow.cu", "ibm_internal.cuh"],
     "add": ["ibm_flow.cu", "ibm_internal.cuh"],
+    "cn_solve": ["ibm_flow.cu", "ibm_internal.cuh"],
     "div": ["ibm_flow.cu", "ibm_internal.cuh"],
     "poisson_scale": ["ibm_flow.cu", "ibm_internal.cuh"],
     "project": ["ibm_flow.cu", "ibm_internal.cuh"],

@@ -6,10 +6,19 @@
 //                   - alpha_l grad p + alpha_l nu lap u) for the three
 //                   components, one thread per cell computing the u, v and w
 //                   nodes of that cell index
-//   R2C (batch 3) -> cn_scale_kernel -> C2R: the factorised Crank-Nicolson
-//                   operator (1 - a d_xx)(1 - a d_yy)(1 - a d_zz),
-//                   a = alpha_l dt nu / 2, is diagonal in Fourier space
-//   add_kernel      u* = u + du
+//   the factorised Crank-Nicolson solve: the operator
+//                   (1 - a d_xx)(1 - a d_yy)(1 - a d_zz), a = alpha_l dt nu / 2,
+//                   is inverted in one of two exact ways, picked per substep
+//                   at creation:
+//     cn_solve_kernel  in real space: with c = a/h_d^2 the inverse of the
+//                   periodic 1-D factor 1 - c (E - 2 + E^-1) is a circulant
+//                   whose entries fall off as r^|m|, r < 1 the smaller root
+//                   of c r^2 - (1 + 2c) r + c; when its mass beyond |m| = W
+//                   (W <= 8) is below 2^-26 in every direction, the three
+//                   inverses are applied as separable (2W+1)-tap filters and
+//                   u* = u + du is written in the same pass
+//     R2C (batch 3) -> cn_scale_kernel -> C2R, add_kernel (u* = u + du):
+//                   otherwise, the operator being diagonal in Fourier space
 //   div_kernel      div(u* + s f)
 //   R2C -> poisson_scale_kernel -> C2R: lap(phi) = div / (alpha_l dt)
 //   project_kernel  u = u* + s f - alpha_l dt grad(phi),
@@ -19,6 +28,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -42,6 +52,10 @@ struct ibm_flow {
   float* lam = nullptr;         // [n_x/2 + 1 | n_y | n_z] eigenvalues
   cufftHandle r2c3 = 0, c2r3 = 0, r2c1 = 0, c2r1 = 0;
   bool plans = false;
+  // per substep: the real-space solve's half width W (-1: Fourier path) and
+  // its taps g[d][|m|] per direction, m = 0..W
+  int solve_w[3] = {-1, -1, -1};
+  float taps[3][3][9] = {};
   // phase timing (profiling aid): events at the 12 kernel boundaries of each
   // substep and the 3 of the body update
   bool timing = false;
@@ -69,8 +83,21 @@ struct CVec3 {
   const float* c[3];
 };
 
-__device__ __forceinline__ int dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
-__device__ __forceinline__ int inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
+// offsets of the six periodic neighbours of cell (i, j, k) relative to its
+// index (grids below 2^31 cells, checked at creation): one 64-bit base per
+// thread and 32-bit offsets instead of a full index per load
+struct Nbr {
+  int xp, xm, yp, ym, zp, zm;
+  __device__ __forceinline__ Nbr(int i, int j, int k, int nx, int ny, int nz) {
+    const int sxy = nx * ny;
+    xp = i == nx - 1 ? 1 - nx : 1;
+    xm = i == 0 ? nx - 1 : -1;
+    yp = j == ny - 1 ? (1 - ny) * nx : nx;
+    ym = j == 0 ? (ny - 1) * nx : -nx;
+    zp = k == nz - 1 ? (1 - nz) * sxy : sxy;
+    zm = k == 0 ? (nz - 1) * sxy : -sxy;
+  }
+};
 
 // H(u) and the predictor's right-hand side at the u, v and w nodes of cell
 // index (i, j, k).  Products for the d-derivative of component c are formed
@@ -87,25 +114,26 @@ __global__ void __launch_bounds__(256) rhs_kernel(FGrid G, const float* __restri
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= G.nx || j >= G.ny) return;
-  const int nx = G.nx, ny = G.ny, nz = G.nz;
-  const int im = dec(i, nx), ip = inc(i, nx), jm = dec(j, ny), jp = inc(j, ny), km = dec(k, nz),
-            kp = inc(k, nz);
-  auto at = [&](int a, int b, int c) { return ((size_t)c * ny + b) * nx + a; };
-  const size_t o = at(i, j, k);
-  const float U = __ldg(u + o), Uip = __ldg(u + at(ip, j, k)), Uim = __ldg(u + at(im, j, k)),
-              Ujp = __ldg(u + at(i, jp, k)), Ujm = __ldg(u + at(i, jm, k)),
-              Ukp = __ldg(u + at(i, j, kp)), Ukm = __ldg(u + at(i, j, km)),
-              Uip_jm = __ldg(u + at(ip, jm, k)), Uip_km = __ldg(u + at(ip, j, km));
-  const float V = __ldg(v + o), Vip = __ldg(v + at(ip, j, k)), Vim = __ldg(v + at(im, j, k)),
-              Vjp = __ldg(v + at(i, jp, k)), Vjm = __ldg(v + at(i, jm, k)),
-              Vkp = __ldg(v + at(i, j, kp)), Vkm = __ldg(v + at(i, j, km)),
-              Vim_jp = __ldg(v + at(im, jp, k)), Vjp_km = __ldg(v + at(i, jp, km));
-  const float W = __ldg(w + o), Wip = __ldg(w + at(ip, j, k)), Wim = __ldg(w + at(im, j, k)),
-              Wjp = __ldg(w + at(i, jp, k)), Wjm = __ldg(w + at(i, jm, k)),
-              Wkp = __ldg(w + at(i, j, kp)), Wkm = __ldg(w + at(i, j, km)),
-              Wim_kp = __ldg(w + at(im, j, kp)), Wjm_kp = __ldg(w + at(i, jm, kp));
-  const float P = __ldg(p + o), Pim = __ldg(p + at(im, j, k)), Pjm = __ldg(p + at(i, jm, k)),
-              Pkm = __ldg(p + at(i, j, km));
+  const Nbr d(i, j, k, G.nx, G.ny, G.nz);
+  const size_t o = ((size_t)k * G.ny + j) * G.nx + i;
+  const float* up = u + o;
+  const float* vp = v + o;
+  const float* wp = w + o;
+  const float* pp = p + o;
+  const float U = __ldg(up), Uip = __ldg(up + d.xp), Uim = __ldg(up + d.xm),
+              Ujp = __ldg(up + d.yp), Ujm = __ldg(up + d.ym), Ukp = __ldg(up + d.zp),
+              Ukm = __ldg(up + d.zm), Uip_jm = __ldg(up + (d.xp + d.ym)),
+              Uip_km = __ldg(up + (d.xp + d.zm));
+  const float V = __ldg(vp), Vip = __ldg(vp + d.xp), Vim = __ldg(vp + d.xm),
+              Vjp = __ldg(vp + d.yp), Vjm = __ldg(vp + d.ym), Vkp = __ldg(vp + d.zp),
+              Vkm = __ldg(vp + d.zm), Vim_jp = __ldg(vp + (d.xm + d.yp)),
+              Vjp_km = __ldg(vp + (d.yp + d.zm));
+  const float W = __ldg(wp), Wip = __ldg(wp + d.xp), Wim = __ldg(wp + d.xm),
+              Wjp = __ldg(wp + d.yp), Wjm = __ldg(wp + d.ym), Wkp = __ldg(wp + d.zp),
+              Wkm = __ldg(wp + d.zm), Wim_kp = __ldg(wp + (d.xm + d.zp)),
+              Wjm_kp = __ldg(wp + (d.ym + d.zp));
+  const float P = __ldg(pp), Pim = __ldg(pp + d.xm), Pjm = __ldg(pp + d.ym),
+              Pkm = __ldg(pp + d.zm);
   float H[3];
   {  // u nodes
     const float cp = 0.5f * (U + Uip), cm = 0.5f * (Uim + U);
@@ -210,11 +238,9 @@ __global__ void __launch_bounds__(256) div_kernel(FGrid G, CVec3 u, CVec3 f, flo
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= G.nx || j >= G.ny) return;
-  const int nx = G.nx, ny = G.ny, nz = G.nz;
-  const size_t o = ((size_t)k * ny + j) * nx + i;
-  const size_t oi = ((size_t)k * ny + j) * nx + inc(i, nx);
-  const size_t oj = ((size_t)k * ny + inc(j, ny)) * nx + i;
-  const size_t ok = ((size_t)inc(k, nz) * ny + j) * nx + i;
+  const Nbr nb(i, j, k, G.nx, G.ny, G.nz);
+  const size_t o = ((size_t)k * G.ny + j) * G.nx + i;
+  const size_t oi = o + nb.xp, oj = o + nb.yp, ok = o + nb.zp;
   float d = (__ldg(u.c[0] + oi) - __ldg(u.c[0] + o)) * G.ih[0] +
             (__ldg(u.c[1] + oj) - __ldg(u.c[1] + o)) * G.ih[1] +
             (__ldg(u.c[2] + ok) - __ldg(u.c[2] + o)) * G.ih[2];
@@ -234,13 +260,13 @@ __global__ void __launch_bounds__(256) project_kernel(FGrid G, Vec3 u, float* __
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= G.nx || j >= G.ny) return;
-  const int nx = G.nx, ny = G.ny, nz = G.nz;
-  auto at = [&](int a_, int b, int c) { return ((size_t)c * ny + b) * nx + a_; };
-  const size_t o = at(i, j, k);
-  const float F = __ldg(phi + o);
-  const float Fim = __ldg(phi + at(dec(i, nx), j, k)), Fip = __ldg(phi + at(inc(i, nx), j, k));
-  const float Fjm = __ldg(phi + at(i, dec(j, ny), k)), Fjp = __ldg(phi + at(i, inc(j, ny), k));
-  const float Fkm = __ldg(phi + at(i, j, dec(k, nz))), Fkp = __ldg(phi + at(i, j, inc(k, nz)));
+  const Nbr nb(i, j, k, G.nx, G.ny, G.nz);
+  const size_t o = ((size_t)k * G.ny + j) * G.nx + i;
+  const float* fp = phi + o;
+  const float F = __ldg(fp);
+  const float Fim = __ldg(fp + nb.xm), Fip = __ldg(fp + nb.xp);
+  const float Fjm = __ldg(fp + nb.ym), Fjp = __ldg(fp + nb.yp);
+  const float Fkm = __ldg(fp + nb.zm), Fkp = __ldg(fp + nb.zp);
   const float g[3] = {(F - Fim) * G.ih[0], (F - Fjm) * G.ih[1], (F - Fkm) * G.ih[2]};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -251,6 +277,181 @@ __global__ void __launch_bounds__(256) project_kernel(FGrid G, Vec3 u, float* __
   const float lap = (Fip - 2.f * F + Fim) * G.ih2[0] + (Fjp - 2.f * F + Fjm) * G.ih2[1] +
                     (Fkp - 2.f * F + Fkm) * G.ih2[2];
   p[o] += F - a * lap;
+}
+
+// asynchronous 4-byte global -> shared copies
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The real-space factorised solve fused with u* = u + du.  A block owns a
+// 32 x 32 tile of (x, y) outputs of one component over kSolveZ planes; it
+// walks the kSolveZ + 2W planes that feed them (periodic wrap in every
+// direction), each staged with its x and y halo by asynchronous copies two
+// planes ahead.  Per plane: the x filter over the tile's rows and halo rows,
+// four consecutive x per thread from float4 windows; the y filter, four
+// consecutive y per thread; and a register ring of the last 2W + 1 filtered
+// planes from which the z filter gives the output plane W planes back.
+// Taps are symmetric: g[d][|m|].
+constexpr int kSolveT = 32, kSolveZ = 32, kMaxSolveW = 8;
+
+struct SolveTaps {
+  float g[3][kMaxSolveW + 1];
+};
+static_assert(sizeof(ibm_flow::taps[0]) == sizeof(SolveTaps), "tap table layout");
+
+template <int W>
+__global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* __restrict__ R,
+                                                          Vec3 u, SolveTaps T) {
+  constexpr int AY = kSolveT + 2 * W, AX = kSolveT + 2 * W;
+  constexpr int NW4 = (4 + 2 * W + 3) / 4;          // float4s in an x window
+  constexpr int AXP = kSolveT - 4 + 4 * NW4;        // row stride: windows stay in the row
+  constexpr int AN = AY * AX, SLOTS = (AN + 255) / 256, NB = 3;
+  static_assert(AXP >= AX && AXP % 4 == 0, "row stride");
+  __shared__ __align__(16) float A[NB][AY * AXP];   // raw planes with halo
+  __shared__ float Us[NB][kSolveT * kSolveT];       // u of the output plane
+  __shared__ __align__(16) float B[AY][kSolveT];    // x-filtered rows
+  const int tid = threadIdx.x;
+  const int nx = G.nx, ny = G.ny, nz = G.nz;
+  const int ntx = (nx + kSolveT - 1) / kSolveT;
+  const int x0 = (int)(blockIdx.y % ntx) * kSolveT, y0 = (int)(blockIdx.y / ntx) * kSolveT;
+  const int k0 = (int)blockIdx.x * kSolveZ;
+  const int nk = min(kSolveZ, nz - k0), nq = nk + 2 * W;
+  const size_t plane = (size_t)nx * ny;
+  const int c = blockIdx.z;
+  const float* Rc = R + (size_t)c * plane * nz;
+  float* uc = c == 0 ? u.c[0] : (c == 1 ? u.c[1] : u.c[2]);
+  // staging slots: shared index and wrapped in-plane offset (-1 past the tile)
+  int off[SLOTS];
+  short sdst[SLOTS];
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int q = tid + 256 * s;
+    off[s] = -1;
+    sdst[s] = 0;
+    if (q < AN) {
+      const int r = q / AX, cc = q - r * AX;
+      const int x = ((x0 - W + cc) % nx + nx) % nx, y = ((y0 - W + r) % ny + ny) % ny;
+      off[s] = y * nx + x;
+      sdst[s] = (short)(r * AXP + cc);
+    }
+  }
+  // outputs: column ox, rows oy .. oy + 3
+  const int lx = tid & 31, ly = (tid >> 5) * 4;
+  const int ox = x0 + lx, oy = y0 + ly;
+  auto stage = [&](int q) {
+    const int b = q % NB;
+    int k = k0 - W + q;
+    k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
+    const float* src = Rc + (size_t)k * plane;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s)
+      if (off[s] >= 0) cp_async4(&A[b][sdst[s]], src + off[s]);
+    const int ko = q - 2 * W;
+    if (ko >= 0 && ox < nx) {
+      const float* us = uc + (size_t)(k0 + ko) * plane + ox;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (oy + j < ny) cp_async4(&Us[b][(ly + j) * kSolveT + lx], us + (size_t)(oy + j) * nx);
+    }
+    cp_async_commit();
+  };
+  float ring[4][2 * W + 1];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int m = 0; m < 2 * W + 1; ++m) ring[j][m] = 0.f;
+  stage(0);
+  if (nq > 1) stage(1);
+  for (int q = 0; q < nq; ++q) {
+    if (q + 1 < nq)
+      cp_async_wait<1>();
+    else
+      cp_async_wait<0>();
+    // plane q visible; every thread is past the x filter of plane q - 1
+    // (buffer (q + 2) % NB is free) and the y filter (B is free)
+    __syncthreads();
+    if (q + 2 < nq) stage(q + 2);
+    const float* a = A[q % NB];
+    // x filter: item = (row, quad of four x), 8 quads per row
+    for (int it = tid; it < AY * 8; it += 256) {
+      const int r = it >> 3, x4 = (it & 7) * 4;
+      float win[4 * NW4];
+      const float4* src = reinterpret_cast<const float4*>(a + r * AXP + x4);
+#pragma unroll
+      for (int v = 0; v < NW4; ++v) {
+        const float4 t = src[v];
+        win[4 * v] = t.x;
+        win[4 * v + 1] = t.y;
+        win[4 * v + 2] = t.z;
+        win[4 * v + 3] = t.w;
+      }
+      float o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float acc = T.g[0][0] * win[j + W];
+#pragma unroll
+        for (int m = 1; m <= W; ++m) acc += T.g[0][m] * (win[j + W - m] + win[j + W + m]);
+        o[j] = acc;
+      }
+      *reinterpret_cast<float4*>(&B[r][x4]) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    __syncthreads();
+    // y filter: rows ly .. ly + 3 of column lx
+    float col[4 + 2 * W];
+#pragma unroll
+    for (int i = 0; i < 4 + 2 * W; ++i) col[i] = B[ly + i][lx];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float acc = T.g[1][0] * col[j + W];
+#pragma unroll
+      for (int m = 1; m <= W; ++m) acc += T.g[1][m] * (col[j + W - m] + col[j + W + m]);
+#pragma unroll
+      for (int m = 0; m < 2 * W; ++m) ring[j][m] = ring[j][m + 1];
+      ring[j][2 * W] = acc;
+    }
+    const int ko = q - 2 * W;
+    if (ko >= 0 && ox < nx) {
+      float* uo = uc + (size_t)(k0 + ko) * plane + ox;
+      const float* ub = Us[q % NB];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float d = T.g[2][0] * ring[j][W];
+#pragma unroll
+        for (int m = 1; m <= W; ++m) d += T.g[2][m] * (ring[j][W - m] + ring[j][W + m]);
+        if (oy + j < ny) uo[(size_t)(oy + j) * nx] = ub[(ly + j) * kSolveT + lx] + d;
+      }
+    }
+  }
+}
+
+FGrid fgrid(const ibm_flow* fl);
+
+cudaError_t launch_cn_solve(const ibm_flow* fl, int l, float* u, float* v, float* w,
+                            cudaStream_t s) {
+  const FGrid G = fgrid(fl);
+  SolveTaps T;
+  for (int d = 0; d < 3; ++d)
+    for (int m = 0; m <= kMaxSolveW; ++m) T.g[d][m] = fl->taps[l][d][m];
+  const unsigned tiles = (unsigned)(((fl->n[0] + kSolveT - 1) / kSolveT) *
+                                    ((fl->n[1] + kSolveT - 1) / kSolveT));
+  const dim3 grid((unsigned)((fl->n[2] + kSolveZ - 1) / kSolveZ), tiles, 3), block(256);
+  const Vec3 U{{u, v, w}};
+  switch (fl->solve_w[l]) {
+#define IBM_SOLVE_CASE(WW) \
+  case WW: cn_solve_kernel<WW><<<grid, block, 0, s>>>(G, fl->R, U, T); break;
+    IBM_SOLVE_CASE(0) IBM_SOLVE_CASE(1) IBM_SOLVE_CASE(2) IBM_SOLVE_CASE(3) IBM_SOLVE_CASE(4)
+    IBM_SOLVE_CASE(5) IBM_SOLVE_CASE(6) IBM_SOLVE_CASE(7) IBM_SOLVE_CASE(8)
+#undef IBM_SOLVE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 FGrid fgrid(const ibm_flow* fl) {
@@ -308,6 +509,55 @@ void release(ibm_flow* fl) {
     if (ev) cudaEventDestroy(ev);
 }
 
+// Entries g_m, m = 0..kMaxSolveW, of the inverse of the periodic n-point
+// operator 1 - c (E - 2 + E^-1): its eigenvalues are 1 + 4c sin^2(pi k/n), so
+// g_m = (1/n) sum_k cos(2 pi k m/n) / (1 + 4c sin^2(pi k/n))  (float64).
+// They are positive and sum to 1 over a period.
+void inverse_taps(double cc, int n, double* g) {
+  for (int m = 0; m <= kMaxSolveW; ++m) {
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double sn = std::sin(M_PI * k / n);
+      acc += std::cos(2.0 * M_PI * (double)k * m / n) / (1.0 + 4.0 * cc * sn * sn);
+    }
+    g[m] = acc / n;
+  }
+}
+
+// Picks each substep's solve: the smallest W <= kMaxSolveW, 2W + 1 <= n_d,
+// with the mass of the entries beyond |m| = W below 2^-26 in every
+// direction (real space), else the Fourier path (W = -1; also for planes of
+// more than 65535 tiles).
+void choose_solves(ibm_flow* fl) {
+  const long tiles = (long)((fl->n[0] + kSolveT - 1) / kSolveT) * ((fl->n[1] + kSolveT - 1) / kSolveT);
+  for (int l = 0; l < 3; ++l) {
+    if (tiles > 65535) {   // the launch's grid.y
+      fl->solve_w[l] = -1;
+      continue;
+    }
+    const double a = (kGamma[l] + kRho[l]) * fl->dt * fl->nu / 2.0;
+    int wl = 0;
+    double g[3][kMaxSolveW + 1];
+    for (int d = 0; d < 3 && wl >= 0; ++d) {
+      inverse_taps(a / (fl->h[d] * fl->h[d]), fl->n[d], g[d]);
+      int wd = -1;
+      double inner = g[d][0];
+      for (int w = 0; w <= kMaxSolveW && 2 * w + 1 <= fl->n[d]; ++w) {
+        if (w > 0) inner += 2.0 * g[d][w];
+        if (1.0 - inner <= std::ldexp(1.0, -26)) {
+          wd = w;
+          break;
+        }
+      }
+      wl = wd < 0 ? -1 : std::max(wl, wd);
+    }
+    fl->solve_w[l] = wl;
+    for (int d = 0; d < 3; ++d)
+      for (int m = 0; m <= kMaxSolveW; ++m)
+        fl->taps[l][d][m] = wl >= 0 && m <= wl ? (float)g[d][m] : 0.f;
+  }
+}
+
 ibm_status flow_err(ibm_status s, const std::string& m) {
   set_global_error(m);
   return s;
@@ -349,9 +599,11 @@ cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, cons
                                                      (float)kRho[l], (float)alpha, nu, dt);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = flow_mark(fl, l, 1, s);
-  if (e == cudaSuccess) e = fft_status(cufftExecR2C(fl->r2c3, fl->R, fl->S));
+  const bool fourier = fl->solve_w[l] < 0;
+  // real-space path: the three Fourier phases stay empty
+  if (e == cudaSuccess && fourier) e = fft_status(cufftExecR2C(fl->r2c3, fl->R, fl->S));
   if (e == cudaSuccess) e = flow_mark(fl, l, 2, s);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && fourier) {
     const int nxh = fl->n[0] / 2 + 1;
     cn_scale_kernel<<<dim3(row_blocks(fl), 3), dim3(kRowThreads, kRowsPerBlock), 0, s>>>(
         fl->S, nxh, fl->n[1], fl->n[2], fl->lam, (float)(alpha * fl->dt * fl->nu / 2.0),
@@ -359,11 +611,13 @@ cudaError_t flow_predict(ibm_flow* fl, int l, float* u, float* v, float* w, cons
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = flow_mark(fl, l, 3, s);
-  if (e == cudaSuccess) e = fft_status(cufftExecC2R(fl->c2r3, fl->S, fl->R));
+  if (e == cudaSuccess && fourier) e = fft_status(cufftExecC2R(fl->c2r3, fl->S, fl->R));
   if (e == cudaSuccess) e = flow_mark(fl, l, 4, s);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && fourier) {
     add_kernel<<<dim3(flat_blocks(fl->N), 3), 256, 0, s>>>(Vec3{{u, v, w}}, fl->R, fl->N);
     e = cudaGetLastError();
+  } else if (e == cudaSuccess) {
+    e = launch_cn_solve(fl, l, u, v, w, s);
   }
   if (e == cudaSuccess) e = flow_mark(fl, l, 5, s);
   if (e == cudaSuccess) {
@@ -430,6 +684,10 @@ extern "C" ibm_status ibm_flow_create(const ibm_grid_desc* grid, double nu, doub
   for (int d = 0; d < 3; ++d)
     if (grid->n[d] < 4 || !(grid->L[d] > 0.0) || !std::isfinite(grid->L[d]))
       return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_create: grid needs n >= 4 and L > 0");
+  if ((double)grid->n[0] * grid->n[1] * grid->n[2] >= 2147483648.0)
+    return flow_err(IBM_ERR_UNSUPPORTED, "ibm_flow_create: grids of 2^31 cells or more");
+  if (grid->n[2] > 65535 || (grid->n[1] + 7) / 8 > 65535)
+    return flow_err(IBM_ERR_UNSUPPORTED, "ibm_flow_create: n_z above 65535 or n_y above 524280");
   if (!(nu >= 0.0) || !std::isfinite(nu) || !(dt > 0.0) || !std::isfinite(dt))
     return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_create: needs nu >= 0 and dt > 0");
   ibm_flow* fl = new ibm_flow();
@@ -441,6 +699,7 @@ extern "C" ibm_status ibm_flow_create(const ibm_grid_desc* grid, double nu, doub
   }
   fl->nu = nu;
   fl->dt = dt;
+  ibm::choose_solves(fl);
   const int nx = fl->n[0], ny = fl->n[1], nz = fl->n[2], nxh = nx / 2 + 1;
   fl->N = (size_t)nx * ny * nz;
   fl->NC = (size_t)nxh * ny * nz;
@@ -484,6 +743,14 @@ extern "C" ibm_status ibm_flow_create(const ibm_grid_desc* grid, double nu, doub
   }
   fl->plans = true;
   *out = fl;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_flow_solve_width(const ibm_flow* fl, int32_t substep, int32_t* width) {
+  if (!fl || !width) return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_solve_width: null argument");
+  if (substep < 0 || substep > 2)
+    return flow_err(IBM_ERR_INVALID_ARG, "ibm_flow_solve_width: substep must be 0, 1 or 2");
+  *width = fl->solve_w[substep];
   return IBM_OK;
 }
 

@@ -43,3 +43,20 @@ def test_create_without_gpu_fails_loudly():
     wl = W.single_drop(level=1, n=16)
     with pytest.raises(RuntimeError):
         _lib.Context(wl.bodies, wl.grid)
+
+
+def test_flow_create_validates_before_touching_the_device():
+    """Grid and parameter checks of ibm_flow_create come before any CUDA call:
+    a grid of 2^31 cells or more (the stencils' 32-bit neighbour offsets) is
+    refused as unsupported, a grid below four cells per direction as invalid."""
+    lib = _lib.library()
+    h = ctypes.c_void_p()
+    g = _lib.GridDesc()
+    for k, n in enumerate((2048, 2048, 512)):
+        g.n[k] = n
+        g.L[k] = 1.0
+    assert lib.ibm_flow_create(ctypes.byref(g), 0.1, 1e-3, ctypes.byref(h)) == 6
+    assert b"2^31" in lib.ibm_last_error(None)
+    g.n[2] = 3
+    assert lib.ibm_flow_create(ctypes.byref(g), 0.1, 1e-3, ctypes.byref(h)) == 1
+    assert not h.value

@@ -67,14 +67,44 @@ def pressure_ok(pg, po, u_max, h_min, dt, substeps):
     return H.rel_l2(a, b), err <= 1e-5 * np.linalg.norm(b) / n + floor
 
 
-def test_substeps_match_oracle(record_error):
-    """Predictor and projection of each substep, from the same inputs."""
-    grid = W.Grid((40, 36, 20), (1.0, 0.9, 0.5))
-    flow_o = N.Flow(grid.n, grid.L, nu=0.02, dt=1e-2)
+def documented_widths(grid, nu, dt):
+    """The viscous solve's path per substep by the rule the header states:
+    the smallest W <= 8 with 2W + 1 <= n_d whose periodic inverse entries
+    (a DFT of 1/(1 + 4c sin^2(pi k/n)), c = alpha_l dt nu / (2 h_d^2)) leave
+    at most 2^-26 of their mass beyond |m| = W, the largest over the
+    directions; -1 (Fourier) when some direction has none."""
+    out = []
+    for l in range(3):
+        c_l = N.ALPHA[l] * dt * nu / 2
+        wl = 0
+        for d in range(3):
+            n = grid.n[d]
+            k = np.arange(n)
+            eig = 1 + 4 * c_l / grid.h[d] ** 2 * np.sin(np.pi * k / n) ** 2
+            g = np.real(np.fft.ifft(1 / eig))
+            wd = next((w for w in range(9) if 2 * w + 1 <= n and
+                       1 - g[0] - 2 * g[1:w + 1].sum() <= 2.0 ** -26), -1)
+            wl = -1 if wd < 0 or wl < 0 else max(wl, wd)
+        out.append(wl)
+    return tuple(out)
+
+
+@pytest.mark.parametrize("n, L, nu, widths", [
+    ((40, 36, 20), (1.0, 0.9, 0.5), 0.02, (7, 4, 6)),       # real-space solves
+    ((40, 36, 20), (1.0, 0.9, 0.5), 0.5, (-1, -1, -1)),     # Fourier solves
+    ((40, 36, 12), (1.0, 0.9, 0.3), 0.02, (-1, 4, -1)),     # 2W + 1 > n_z in substeps 0, 2
+])
+def test_substeps_match_oracle(record_error, n, L, nu, widths):
+    """Predictor and projection of each substep, from the same inputs, on
+    both paths of the viscous solve (ragged against the real-space solve's
+    32 x 16 x 32 tiles)."""
+    grid = W.Grid(n, L)
+    flow_o = N.Flow(grid.n, grid.L, nu=nu, dt=1e-2)
     u0 = curl_field(grid.n, grid.h, 1)
     g = torch.Generator().manual_seed(2)
     p0 = torch.randn((grid.n[2], grid.n[1], grid.n[0]), generator=g, dtype=DT)
     fl = _lib.Flow(grid, nu=flow_o.nu, dt=flow_o.dt)
+    assert fl.solve_widths() == widths == documented_widths(grid, nu, flow_o.dt)
     u, p = fields_dev(u0), to_dev(p0)
     uo, po, Hp = u0.clone(), p0.clone(), None
     for l in range(3):
@@ -106,6 +136,7 @@ def test_flow_steps_match_oracle(record_error):
     wl = mixed_workload()
     flow_o = N.Flow(wl.grid.n, wl.grid.L, nu=0.05, dt=5e-3)
     fl = _lib.Flow(wl.grid, nu=flow_o.nu, dt=flow_o.dt)
+    assert fl.solve_widths() == documented_widths(wl.grid, flow_o.nu, flow_o.dt) == (7, 4, 6)
     u = tuple(f.clone() for f in H.fields_for(wl, DEV))
     p = torch.zeros_like(u[0])
     uo, po = stack_cpu(u), torch.zeros(u[0].shape, dtype=DT)
@@ -143,6 +174,8 @@ def test_coupled_step_matches_oracle(record_error):
     flow_o = N.Flow(wl.grid.n, wl.grid.L, nu=wl.mu, dt=wl.dt)
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
     fl = _lib.Flow(wl.grid, nu=wl.mu, dt=wl.dt)
+    # substeps 0 and 2 on the Fourier path, substep 1 in real space
+    assert fl.solve_widths() == documented_widths(wl.grid, wl.mu, wl.dt) == (-1, 7, -1)
     x = H.state_tensor(wl, rel_x)
     v = H.state_tensor(wl, vs)
     u = tuple(f.clone() for f in H.fields_for(wl, DEV))
@@ -294,6 +327,7 @@ def test_coupled_step_full_size_properties(record_error):
     ctx = _lib.Context(wl.bodies, wl.grid, dt=dt, mu=bench.COUPLED_NU, alpha=wl.alpha,
                        patch_size=256)
     fl = _lib.Flow(wl.grid, nu=bench.COUPLED_NU, dt=dt)
+    assert fl.solve_widths() == documented_widths(wl.grid, bench.COUPLED_NU, dt) == (4, 3, 3)
     u = tuple(t.clone() for t in fields)
     p = torch.zeros_like(u[0])
     f = tuple(torch.zeros_like(u[0]) for _ in range(3))
