@@ -125,6 +125,67 @@ def test_factorised_solve_inverts_the_three_factors():
     assert torch.allclose(y, rhs, atol=1e-10 * float(rhs.abs().max()))
 
 
+def periodic_inverse_taps(c, n):
+    """Entries g_m, m = 0..n-1, of the inverse of the periodic operator
+    1 - c (E - 2 + E^-1), from its factorisation (c/r)(1 - r E)(1 - r E^-1)
+    with r < 1 the smaller root of c r^2 - (1 + 2c) r + c: on the infinite
+    line the inverse is r^(|m|+1) / (c (1 - r^2)); summing the periodic
+    images gives (r/c)(r^m + r^(n-m)) / ((1 - r^2)(1 - r^n))."""
+    r = ((1 + 2 * c) - math.sqrt(1 + 4 * c)) / (2 * c)
+    m = np.arange(n)
+    return (r / c) * (r ** m + r ** (n - m)) / ((1 - r * r) * (1 - r ** n))
+
+
+def separable_filter(x, taps, W):
+    """Apply the symmetric (2W+1)-tap periodic filter taps[d][0..W] along
+    each direction d of x [nz, ny, nx]."""
+    for d in range(3):
+        y = taps[d][0] * x
+        for m in range(1, W + 1):
+            y = y + taps[d][m] * (N.shift(x, d, m) + N.shift(x, d, -m))
+        x = y
+    return x
+
+
+def test_real_space_reading_of_the_factorised_solve():
+    """The factorised viscous solve in real space: each direction's periodic
+    inverse (closed form above, checked against the operator itself) applied
+    as a separable filter.  With every tap it is the oracle's Fourier solve;
+    truncated at the smallest W whose dropped mass is below 2^-26 per
+    direction, it stays within 3 * 2^-26 max|rhs| of it (each filter's taps
+    are positive and sum to 1)."""
+    n, h = grid((40, 36, 20), (1.0, 0.9, 0.5))
+    a = N.ALPHA[0] * 1e-2 * 0.02 / 2
+    taps = []
+    for d in range(3):
+        c = a / h[d] ** 2
+        g = periodic_inverse_taps(c, n[d])
+        op = (1 + 2 * c) * g - c * (np.roll(g, 1) + np.roll(g, -1))
+        assert np.allclose(op, np.eye(1, n[d])[0], atol=1e-14)
+        assert abs(g.sum() - 1) < 1e-12
+        taps.append(g)
+    rhs = rand_field(n, 21, 1)[0]
+    ref = N.solve_factorised(rhs, a, n, h)
+    # every tap: the full circulant along each direction
+    x = rhs
+    for d in range(3):
+        g = taps[d]
+        y = torch.zeros_like(x)
+        for m in range(n[d]):
+            y = y + g[m] * N.shift(x, d, m)
+        x = y
+    assert torch.allclose(x, ref, atol=1e-12 * float(rhs.abs().max()))
+    W = max(next(w for w in range(n[d] // 2) if 1 - g[0] - 2 * g[1:w + 1].sum() <= 2.0 ** -26)
+            for d, g in enumerate(taps))
+    assert W == 7
+    approx = separable_filter(rhs, taps, W)
+    err = float((approx - ref).abs().max())
+    assert err <= 3 * 2.0 ** -26 * float(rhs.abs().max())
+    # one tap fewer is visibly short of it
+    short = separable_filter(rhs, taps, W - 1)
+    assert float((short - ref).abs().max()) > err
+
+
 def test_projection():
     """The corrected field is solenoidal; a solenoidal field passes unchanged
     and leaves the pressure unchanged."""
