@@ -279,10 +279,14 @@ __global__ void __launch_bounds__(256) project_kernel(FGrid G, Vec3 u, float* __
   p[o] += F - a * lap;
 }
 
-// asynchronous 4-byte global -> shared copies
+// asynchronous 4- and 8-byte global -> shared copies
 __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(float* sdst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -294,17 +298,29 @@ __device__ __forceinline__ void cp_async_wait() {
 // 32 x 32 tile of (x, y) outputs of one component over kSolveZ planes; it
 // walks the kSolveZ + 2W planes that feed them (periodic wrap in every
 // direction), each staged with its x and y halo by asynchronous copies two
-// planes ahead.  Per plane: the x filter over the tile's rows and halo rows,
-// four consecutive x per thread from float4 windows; the y filter, four
-// consecutive y per thread; and a register ring of the last 2W + 1 filtered
-// planes from which the z filter gives the output plane W planes back.
-// Taps are symmetric: g[d][|m|].
+// planes ahead.  Per plane: the x filter, four consecutive x per thread from
+// float4 windows; the y filter for two x and two y per thread and the z
+// filter in packed two-lane float arithmetic (pairs of x), from a register
+// ring of the last 2W + 1 filtered planes; the z filter gives the output
+// plane W planes back.  Taps are
+// symmetric: g[d][|m|].
 constexpr int kSolveT = 32, kSolveZ = 32, kMaxSolveW = 8;
 
 struct SolveTaps {
   float g[3][kMaxSolveW + 1];
 };
 static_assert(sizeof(ibm_flow::taps[0]) == sizeof(SolveTaps), "tap table layout");
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// symmetric filter of half width W centred on win[c]: g0 w_c + sum_m g_m (w_{c-m} + w_{c+m})
+template <int W>
+__device__ __forceinline__ float2 sym_filter(const float2* win, int c, const float* g) {
+  float2 acc = __fmul2_rn(f2(g[0]), win[c]);
+#pragma unroll
+  for (int m = 1; m <= W; ++m) acc = __ffma2_rn(f2(g[m]), __fadd2_rn(win[c - m], win[c + m]), acc);
+  return acc;
+}
 
 template <int W>
 __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* __restrict__ R,
@@ -315,7 +331,7 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
   constexpr int AN = AY * AX, SLOTS = (AN + 255) / 256, NB = 3;
   static_assert(AXP >= AX && AXP % 4 == 0, "row stride");
   __shared__ __align__(16) float A[NB][AY * AXP];   // raw planes with halo
-  __shared__ float Us[NB][kSolveT * kSolveT];       // u of the output plane
+  __shared__ __align__(16) float Us[NB][kSolveT * kSolveT];   // u of the output plane
   __shared__ __align__(16) float B[AY][kSolveT];    // x-filtered rows
   const int tid = threadIdx.x;
   const int nx = G.nx, ny = G.ny, nz = G.nz;
@@ -342,9 +358,11 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
       sdst[s] = (short)(r * AXP + cc);
     }
   }
-  // outputs: column ox, rows oy .. oy + 3
-  const int lx = tid & 31, ly = (tid >> 5) * 4;
+  // outputs: columns ox, ox + 1 of rows oy, oy + 1
+  const int lx = (tid & 15) * 2, ly = (tid >> 4) * 2;
   const int ox = x0 + lx, oy = y0 + ly;
+  // 8-byte aligned column pairs: even rows and an 8-byte aligned field
+  const bool pair = (nx & 1) == 0 && (reinterpret_cast<uintptr_t>(uc) & 7) == 0;
   auto stage = [&](int q) {
     const int b = q % NB;
     int k = k0 - W + q;
@@ -354,19 +372,28 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
     for (int s = 0; s < SLOTS; ++s)
       if (off[s] >= 0) cp_async4(&A[b][sdst[s]], src + off[s]);
     const int ko = q - 2 * W;
-    if (ko >= 0 && ox < nx) {
-      const float* us = uc + (size_t)(k0 + ko) * plane + ox;
+    if (ko >= 0) {
+      const float* us = uc + (size_t)(k0 + ko) * plane;
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (oy + j < ny) cp_async4(&Us[b][(ly + j) * kSolveT + lx], us + (size_t)(oy + j) * nx);
+      for (int j = 0; j < 2; ++j) {
+        if (oy + j >= ny) continue;
+        float* d = &Us[b][(ly + j) * kSolveT + lx];
+        const float* g = us + (size_t)(oy + j) * nx + ox;
+        if (pair && ox + 1 < nx) {
+          cp_async8(d, g);
+        } else {
+          if (ox < nx) cp_async4(d, g);
+          if (ox + 1 < nx) cp_async4(d + 1, g + 1);
+        }
+      }
     }
     cp_async_commit();
   };
-  float ring[4][2 * W + 1];
+  float2 ring[2][2 * W + 1];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < 2; ++j)
 #pragma unroll
-    for (int m = 0; m < 2 * W + 1; ++m) ring[j][m] = 0.f;
+    for (int m = 0; m < 2 * W + 1; ++m) ring[j][m] = make_float2(0.f, 0.f);
   stage(0);
   if (nq > 1) stage(1);
   for (int q = 0; q < nq; ++q) {
@@ -378,8 +405,8 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
     // (buffer (q + 2) % NB is free) and the y filter (B is free)
     __syncthreads();
     if (q + 2 < nq) stage(q + 2);
-    const float* a = A[q % NB];
     // x filter: item = (row, quad of four x), 8 quads per row
+    const float* a = A[q % NB];
     for (int it = tid; it < AY * 8; it += 256) {
       const int r = it >> 3, x4 = (it & 7) * 4;
       float win[4 * NW4];
@@ -403,29 +430,36 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
       *reinterpret_cast<float4*>(&B[r][x4]) = make_float4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();
-    // y filter: rows ly .. ly + 3 of column lx
-    float col[4 + 2 * W];
+    // y filter: rows ly, ly + 1 of columns lx, lx + 1
+    {
+      float2 col[2 + 2 * W];
 #pragma unroll
-    for (int i = 0; i < 4 + 2 * W; ++i) col[i] = B[ly + i][lx];
+      for (int i = 0; i < 2 + 2 * W; ++i) col[i] = *reinterpret_cast<const float2*>(&B[ly + i][lx]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float acc = T.g[1][0] * col[j + W];
+      for (int j = 0; j < 2; ++j) {
+        const float2 v = sym_filter<W>(col, j + W, T.g[1]);
 #pragma unroll
-      for (int m = 1; m <= W; ++m) acc += T.g[1][m] * (col[j + W - m] + col[j + W + m]);
-#pragma unroll
-      for (int m = 0; m < 2 * W; ++m) ring[j][m] = ring[j][m + 1];
-      ring[j][2 * W] = acc;
+        for (int m = 0; m < 2 * W; ++m) ring[j][m] = ring[j][m + 1];
+        ring[j][2 * W] = v;
+      }
     }
     const int ko = q - 2 * W;
-    if (ko >= 0 && ox < nx) {
-      float* uo = uc + (size_t)(k0 + ko) * plane + ox;
+    if (ko >= 0) {
+      float* uo = uc + (size_t)(k0 + ko) * plane;
       const float* ub = Us[q % NB];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float d = T.g[2][0] * ring[j][W];
-#pragma unroll
-        for (int m = 1; m <= W; ++m) d += T.g[2][m] * (ring[j][W - m] + ring[j][W + m]);
-        if (oy + j < ny) uo[(size_t)(oy + j) * nx] = ub[(ly + j) * kSolveT + lx] + d;
+      for (int j = 0; j < 2; ++j) {
+        if (oy + j >= ny) continue;
+        const float2 d = sym_filter<W>(ring[j], W, T.g[2]);
+        const float2 uu = *reinterpret_cast<const float2*>(&ub[(ly + j) * kSolveT + lx]);
+        const float2 r = __fadd2_rn(uu, d);
+        float* g = uo + (size_t)(oy + j) * nx + ox;
+        if (pair && ox + 1 < nx) {
+          *reinterpret_cast<float2*>(g) = r;
+        } else {
+          if (ox < nx) g[0] = r.x;
+          if (ox + 1 < nx) g[1] = r.y;
+        }
       }
     }
   }

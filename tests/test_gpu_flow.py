@@ -93,6 +93,7 @@ def documented_widths(grid, nu, dt):
     ((40, 36, 20), (1.0, 0.9, 0.5), 0.02, (7, 4, 6)),       # real-space solves
     ((40, 36, 20), (1.0, 0.9, 0.5), 0.5, (-1, -1, -1)),     # Fourier solves
     ((40, 36, 12), (1.0, 0.9, 0.3), 0.02, (-1, 4, -1)),     # 2W + 1 > n_z in substeps 0, 2
+    ((39, 36, 20), (0.975, 0.9, 0.5), 0.02, (7, 4, 6)),     # odd n_x: unpaired columns
 ])
 def test_substeps_match_oracle(record_error, n, L, nu, widths):
     """Predictor and projection of each substep, from the same inputs, on
