@@ -323,16 +323,20 @@ __device__ __forceinline__ float2 sym_filter(const float2* win, int c, const flo
 }
 
 template <int W>
-__global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* __restrict__ R,
+__global__ void __launch_bounds__(256, W <= 4 ? 3 : 2) cn_solve_kernel(FGrid G, const float* __restrict__ R,
                                                           Vec3 u, SolveTaps T) {
   constexpr int AY = kSolveT + 2 * W, AX = kSolveT + 2 * W;
   constexpr int NW4 = (4 + 2 * W + 3) / 4;          // float4s in an x window
   constexpr int AXP = kSolveT - 4 + 4 * NW4;        // row stride: windows stay in the row
-  constexpr int AN = AY * AX, SLOTS = (AN + 255) / 256, NB = 3;
+  constexpr int AN = AY * AX, SLOTS = (AN + 255) / 256, NB = 3, NU = 4;
   static_assert(AXP >= AX && AXP % 4 == 0, "row stride");
-  __shared__ __align__(16) float A[NB][AY * AXP];   // raw planes with halo
-  __shared__ __align__(16) float Us[NB][kSolveT * kSolveT];   // u of the output plane
-  __shared__ __align__(16) float B[AY][kSolveT];    // x-filtered rows
+  // dynamic shared memory: A[NB][AY * AXP] raw planes with halo,
+  // Us[NU][32 * 32] u of the output planes, B[2][AY][32] x-filtered rows
+  extern __shared__ __align__(16) float smem[];
+  float (*A)[AY * AXP] = reinterpret_cast<float (*)[AY * AXP]>(smem);
+  float (*Us)[kSolveT * kSolveT] = reinterpret_cast<float (*)[kSolveT * kSolveT]>(smem + NB * AY * AXP);
+  float (*B)[AY][kSolveT] =
+      reinterpret_cast<float (*)[AY][kSolveT]>(smem + NB * AY * AXP + NU * kSolveT * kSolveT);
   const int tid = threadIdx.x;
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int ntx = (nx + kSolveT - 1) / kSolveT;
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
   // 8-byte aligned column pairs: even rows and an 8-byte aligned field
   const bool pair = (nx & 1) == 0 && (reinterpret_cast<uintptr_t>(uc) & 7) == 0;
   auto stage = [&](int q) {
-    const int b = q % NB;
+    const int b = q % NB, bu = q % NU;
     int k = k0 - W + q;
     k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
     const float* src = Rc + (size_t)k * plane;
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         if (oy + j >= ny) continue;
-        float* d = &Us[b][(ly + j) * kSolveT + lx];
+        float* d = &Us[bu][(ly + j) * kSolveT + lx];
         const float* g = us + (size_t)(oy + j) * nx + ox;
         if (pair && ox + 1 < nx) {
           cp_async8(d, g);
@@ -394,19 +398,10 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
   for (int j = 0; j < 2; ++j)
 #pragma unroll
     for (int m = 0; m < 2 * W + 1; ++m) ring[j][m] = make_float2(0.f, 0.f);
-  stage(0);
-  if (nq > 1) stage(1);
-  for (int q = 0; q < nq; ++q) {
-    if (q + 1 < nq)
-      cp_async_wait<1>();
-    else
-      cp_async_wait<0>();
-    // plane q visible; every thread is past the x filter of plane q - 1
-    // (buffer (q + 2) % NB is free) and the y filter (B is free)
-    __syncthreads();
-    if (q + 2 < nq) stage(q + 2);
-    // x filter: item = (row, quad of four x), 8 quads per row
+  // x filter of plane q into B[q & 1]: item = (row, quad of four x)
+  auto xfilter = [&](int q) {
     const float* a = A[q % NB];
+    float (*Bq)[kSolveT] = B[q & 1];
     for (int it = tid; it < AY * 8; it += 256) {
       const int r = it >> 3, x4 = (it & 7) * 4;
       float win[4 * NW4];
@@ -427,14 +422,37 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
         for (int m = 1; m <= W; ++m) acc += T.g[0][m] * (win[j + W - m] + win[j + W + m]);
         o[j] = acc;
       }
-      *reinterpret_cast<float4*>(&B[r][x4]) = make_float4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<float4*>(&Bq[r][x4]) = make_float4(o[0], o[1], o[2], o[3]);
     }
+  };
+  // one barrier per plane: the y and z filters of plane q and the x filter
+  // of plane q + 1 run between two barriers (B double-buffered, A three
+  // planes, Us four)
+  stage(0);
+  if (nq > 1) stage(1);
+  if (nq > 1)
+    cp_async_wait<1>();
+  else
+    cp_async_wait<0>();
+  __syncthreads();
+  if (nq > 2) stage(2);
+  xfilter(0);
+  for (int q = 0; q < nq; ++q) {
+    if (q + 2 < nq)
+      cp_async_wait<1>();
+    else
+      cp_async_wait<0>();
+    // B[q & 1] complete and plane q + 1 visible; every thread is past the x
+    // filter of plane q (A[q % NB] free) and the y filter of plane q - 1
+    // (B[(q + 1) & 1] and Us[(q - 1) % NU] free)
     __syncthreads();
+    if (q + 3 < nq) stage(q + 3);
     // y filter: rows ly, ly + 1 of columns lx, lx + 1
     {
       float2 col[2 + 2 * W];
 #pragma unroll
-      for (int i = 0; i < 2 + 2 * W; ++i) col[i] = *reinterpret_cast<const float2*>(&B[ly + i][lx]);
+      for (int i = 0; i < 2 + 2 * W; ++i)
+        col[i] = *reinterpret_cast<const float2*>(&B[q & 1][ly + i][lx]);
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const float2 v = sym_filter<W>(col, j + W, T.g[1]);
@@ -446,7 +464,7 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
     const int ko = q - 2 * W;
     if (ko >= 0) {
       float* uo = uc + (size_t)(k0 + ko) * plane;
-      const float* ub = Us[q % NB];
+      const float* ub = Us[q % NU];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         if (oy + j >= ny) continue;
@@ -462,7 +480,33 @@ __global__ void __launch_bounds__(256, 2) cn_solve_kernel(FGrid G, const float* 
         }
       }
     }
+    if (q + 1 < nq) xfilter(q + 1);
   }
+}
+
+// dynamic shared memory of cn_solve_kernel<W>
+constexpr size_t solve_smem(int W) {
+  return sizeof(float) * (3 * (size_t)(kSolveT + 2 * W) * (kSolveT - 4 + 4 * ((4 + 2 * W + 3) / 4)) +
+                          4 * (size_t)kSolveT * kSolveT + 2 * (size_t)(kSolveT + 2 * W) * kSolveT);
+}
+
+// allow each real-space substep's kernel its dynamic shared memory
+cudaError_t set_solve_smem(const ibm_flow* fl) {
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+    switch (fl->solve_w[l]) {
+#define IBM_SOLVE_ATTR(WW)                                                                 \
+  case WW:                                                                                 \
+    e = cudaFuncSetAttribute(cn_solve_kernel<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)solve_smem(WW));                                         \
+    break;
+      IBM_SOLVE_ATTR(0) IBM_SOLVE_ATTR(1) IBM_SOLVE_ATTR(2) IBM_SOLVE_ATTR(3) IBM_SOLVE_ATTR(4)
+      IBM_SOLVE_ATTR(5) IBM_SOLVE_ATTR(6) IBM_SOLVE_ATTR(7) IBM_SOLVE_ATTR(8)
+#undef IBM_SOLVE_ATTR
+      default: break;
+    }
+  }
+  return e;
 }
 
 FGrid fgrid(const ibm_flow* fl);
@@ -479,7 +523,7 @@ cudaError_t launch_cn_solve(const ibm_flow* fl, int l, float* u, float* v, float
   const Vec3 U{{u, v, w}};
   switch (fl->solve_w[l]) {
 #define IBM_SOLVE_CASE(WW) \
-  case WW: cn_solve_kernel<WW><<<grid, block, 0, s>>>(G, fl->R, U, T); break;
+  case WW: cn_solve_kernel<WW><<<grid, block, solve_smem(WW), s>>>(G, fl->R, U, T); break;
     IBM_SOLVE_CASE(0) IBM_SOLVE_CASE(1) IBM_SOLVE_CASE(2) IBM_SOLVE_CASE(3) IBM_SOLVE_CASE(4)
     IBM_SOLVE_CASE(5) IBM_SOLVE_CASE(6) IBM_SOLVE_CASE(7) IBM_SOLVE_CASE(8)
 #undef IBM_SOLVE_CASE
@@ -738,6 +782,7 @@ extern "C" ibm_status ibm_flow_create(const ibm_grid_desc* grid, double nu, doub
   fl->N = (size_t)nx * ny * nz;
   fl->NC = (size_t)nxh * ny * nz;
   cudaError_t e = cudaSuccess;
+  e = ibm::set_solve_smem(fl);
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&fl->H[b], 3 * fl->N * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&fl->R, 3 * fl->N * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&fl->rp, fl->N * sizeof(float));
