@@ -355,3 +355,29 @@ def test_coupled_step_full_size_properties(record_error):
     record_error("update residual / |x|", float(upd) / scale)
     assert float(upd) <= 4 * 2.0 ** -24 * scale
     fl.close()
+
+
+def test_flow_step_full_size_matches_oracle(record_error):
+    """One step of the flow alone at the coupled benchmark's configuration
+    (256^3, its Fourier field, dt at CFL 0.5, nu = 0.01; real-space viscous
+    solves with W = 4, 3, 3 in the benchmark's launch configuration)
+    against the oracle over the whole field."""
+    import bench
+    wl = W.batched_drops(1000, 3, 256, seed=1)
+    fields = H.fields_for(wl, DEV)
+    dt = bench.cfl_dt(fields, wl.grid.h, bench.COUPLED_CFL)
+    fl = _lib.Flow(wl.grid, nu=bench.COUPLED_NU, dt=dt)
+    assert fl.solve_widths() == (4, 3, 3)
+    flow_o = N.Flow(wl.grid.n, wl.grid.L, nu=bench.COUPLED_NU, dt=dt)
+    u = tuple(t.clone() for t in fields)
+    p = torch.zeros_like(u[0])
+    uo = stack_cpu(u)
+    fl.step(u, p)
+    uo, po = N.ns_step(flow_o, uo, torch.zeros(uo.shape[1:], dtype=DT))
+    eu = rel(stack_cpu(u), uo)
+    ep, pok = pressure_ok(p.double().cpu(), po, float(uo.abs().max()), min(wl.grid.h), dt,
+                          [0, 1, 2])
+    record_error("u", eu)
+    record_error("p", ep)
+    assert eu <= 1e-5 and pok, (eu, ep)
+    fl.close()
