@@ -393,12 +393,17 @@ ibm_status ibm_get_counters(ibm_ctx* ctx, int64_t* out);
  * allocating any memory (no counterpart in the paper: it serves callers that
  * cannot allocate device memory at the point of the call, for example code
  * that runs inside another framework's memory pool or that must not add
- * allocations while a stream is being captured).  The result equals
- * ibm_body_measures: the same float64 sums in a fixed order.
+ * allocations while a stream is being captured).  Each face's float32 area
+ * and signed volume are summed in float64 in a fixed order (deterministic);
+ * the result agrees with ibm_body_measures, which rounds each face to 2^-39
+ * of the body's rest value before an exact integer sum, to about that
+ * resolution.
  *   x         device float32 [3][n_vert], body-frame positions (SoA)
  *   tri       device int32 [F][3], GLOBAL vertex ids, faces of body b at
- *             [face_off[b], face_off[b+1])
+ *             [face_off[b], face_off[b+1]); F = face_off[n_bodies] faces
+ *             must be readable
  *   face_off  device int32 [n_bodies + 1]
+ *   max_faces_per_body  must bound face_off[b+1] - face_off[b] for every b
  *   closed    device uint8 [n_bodies] or NULL (all closed); open bodies get V = 0
  *   out       device float64 [n_bodies][2] = (A, V)
  *   stream    cudaStream_t (NULL: legacy default stream)
@@ -409,7 +414,11 @@ ibm_status ibm_get_counters(ibm_ctx* ctx, int64_t* out);
  * the array's device address (no allocation); make that first call before
  * any stream capture.  All calls share the array: calls that overlap on the
  * GPU (different streams, or different host threads) race and must be
- * serialised by the caller.  Errors: see ibm_last_error(NULL). */
+ * serialised by the caller.  Device-side checks, made before any caller
+ * index is used as an address: a body whose face range is negative or
+ * reversed, has more faces than max_faces_per_body, or holds a vertex id
+ * outside [0, n_vert) gets out = (NaN, NaN); a body with no faces gets (0, 0).
+ * Errors: see ibm_last_error(NULL). */
 ibm_status ibm_body_measures_noalloc(const float* x, int64_t n_vert, const int32_t* tri,
                                      const int32_t* face_off, int32_t n_bodies,
                                      int32_t max_faces_per_body, const uint8_t* closed,

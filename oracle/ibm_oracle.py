@@ -431,6 +431,27 @@ def distribute_to_vertices(Fface, tri, nv):
     return out
 
 
+def advance(b, x, v, F_int, F_ext_face, prm):
+    """Node update of one body (Sec. 2.3, m x'' = F_ext + F_int; Sec. 5 step
+    4): the face loads are distributed a third to each corner, then
+    symplectic Euler (reading R8: v' = v + dt a, x' = x + dt v') or forward
+    Euler (x' = x + dt v, v' = v + dt a); clamped nodes keep x and get v = 0.
+    Returns (x', v', F_ext per vertex)."""
+    dt = prm.dt
+    Fev = distribute_to_vertices(F_ext_face, b.tri, b.nv)
+    acc = (Fev + F_int) / b.mass
+    if prm.forward_euler:
+        xn = x + dt * v
+        vn = v + dt * acc
+    else:
+        vn = v + dt * acc
+        xn = x + dt * vn
+    cl = b.clamped[:, None]
+    xn = torch.where(cl, x, xn)
+    vn = torch.where(cl, torch.zeros_like(vn), vn)
+    return xn, vn, Fev
+
+
 # --------------------------------------------------------------------------
 # one loosely coupled step (Sec. 5 steps 1, 2, 3b, 4) with the flow frozen
 # --------------------------------------------------------------------------
@@ -470,18 +491,8 @@ def step(bodies, xs, vs, fields, prm: Params, create_graph=False, with_spread=Tr
         Fm = (Vb - U) / dt                                                   # F = (V^b - U)/dt
         Fe = probe_traction(fields, C, nrm, A_l, n, h, alpha, prm.mu, prm.probe_h,
                             two_sided=not b.closed, pressure=pressure, accel=acc_l)   # 4a
-        Fev = distribute_to_vertices(Fe, b.tri, b.nv)
         Fi = b.internal_forces(x, create_graph=create_graph)                # 4c
-        acc = (Fev + Fi) / b.mass
-        if prm.forward_euler:
-            xn = x + dt * v
-            vn = v + dt * acc
-        else:                                                                # 4e, reading R8
-            vn = v + dt * acc
-            xn = x + dt * vn
-        cl = b.clamped[:, None]
-        xn = torch.where(cl, x, xn)
-        vn = torch.where(cl, torch.zeros_like(vn), vn)
+        xn, vn, Fev = advance(b, x, v, Fi, Fe, prm)                         # 4d, 4e
         x_next.append(xn)
         v_next.append(vn)
         Fint_l.append(Fi)

@@ -1,9 +1,18 @@
 // Allocation-free per-body surface area and enclosed volume.
 //
-// Same fixed-order float64 reduction as the context's body measures, but it
-// needs no context and allocates nothing: its scratch (per-chunk partial sums
-// and per-body arrival counters) lives in one file-scope device array of fixed
-// size that every GPU loading the library holds until the process exits.
+// Each face's float32 area and signed tetrahedron volume are summed in
+// float64 in a fixed order (per block, then per body in chunk order), so the
+// result is deterministic; it agrees with the context's body measures (which
+// quantise each face to 2^-39 of the body's rest value and sum integers) to
+// about that resolution.  It needs no context and allocates nothing: its
+// scratch (per-chunk partial sums and per-body arrival counters) lives in one
+// file-scope device array of fixed size that every GPU loading the library
+// holds until the process exits.
+//
+// Caller data is checked on the device before it is used for addressing: a
+// body whose face range is reversed or negative, whose faces need more chunks
+// than max_faces_per_body allows, or that holds a vertex id outside [0, V)
+// gets (NaN, NaN); a body with no faces gets (0, 0).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -36,6 +45,22 @@ __global__ void __launch_bounds__(kNaThreads) measures_noalloc_kernel(
   __shared__ int s_last;
   const int b = blockIdx.y, c = blockIdx.x;
   const int f0 = face_off[b], f1 = face_off[b + 1];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  // whole-body outcomes decided by chunk 0 alone (uniform across the block)
+  if (f0 < 0 || f1 < f0 || (long long)(f1 - f0) > (long long)max_chunks * kNaThreads) {
+    if (c == 0 && threadIdx.x == 0) {
+      out[2 * b] = nan;
+      out[2 * b + 1] = nan;
+    }
+    return;
+  }
+  if (f1 == f0) {
+    if (c == 0 && threadIdx.x == 0) {
+      out[2 * b] = 0.0;
+      out[2 * b + 1] = 0.0;
+    }
+    return;
+  }
   const int n_chunk = (f1 - f0 + kNaThreads - 1) / kNaThreads;
   if (c >= n_chunk) return;                           // uniform across the block
   const bool is_closed = closed ? closed[b] != 0 : true;
@@ -43,12 +68,17 @@ __global__ void __launch_bounds__(kNaThreads) measures_noalloc_kernel(
   double a = 0.0, vol = 0.0;
   if (f < f1) {
     const int ia = tri[3 * f], ib = tri[3 * f + 1], ic = tri[3 * f + 2];
-    float xa[3], xb[3], xc[3];
+    // an out-of-range vertex id is never dereferenced: the face contributes
+    // NaN, which the sums carry to the body's output
+    const bool bad = ia < 0 || ia >= V || ib < 0 || ib >= V || ic < 0 || ic >= V;
+    float xa[3] = {0.f, 0.f, 0.f}, xb[3] = {0.f, 0.f, 0.f}, xc[3] = {0.f, 0.f, 0.f};
+    if (!bad) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      xa[d] = x[d * V + ia];
-      xb[d] = x[d * V + ib];
-      xc[d] = x[d * V + ic];
+      for (int d = 0; d < 3; ++d) {
+        xa[d] = x[d * V + ia];
+        xb[d] = x[d * V + ib];
+        xc[d] = x[d * V + ic];
+      }
     }
     const float e1[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
     const float e2[3] = {xc[0] - xa[0], xc[1] - xa[1], xc[2] - xa[2]};
@@ -58,6 +88,10 @@ __global__ void __launch_bounds__(kNaThreads) measures_noalloc_kernel(
     if (is_closed)
       vol = (double)((xa[0] * (xb[1] * xc[2] - xb[2] * xc[1]) + xa[1] * (xb[2] * xc[0] - xb[0] * xc[2]) +
                       xa[2] * (xb[0] * xc[1] - xb[1] * xc[0])) * (1.f / 6.f));
+    if (bad) {
+      a = nan;
+      vol = nan;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -91,7 +125,7 @@ __global__ void __launch_bounds__(kNaThreads) measures_noalloc_kernel(
       tv += P[2 * ((size_t)b * max_chunks + k) + 1];
     }
     out[2 * b] = ta;
-    out[2 * b + 1] = is_closed ? tv : 0.0;
+    out[2 * b + 1] = is_closed ? tv : (ta == ta ? 0.0 : nan);
     counter[b] = 0;
   }
 }

@@ -351,3 +351,52 @@ def test_scalar_row_path_two_steps_with_pressure(record_error):
     e = H.rel_l2(got, out["f"].numpy())
     record_error("f", e)
     assert e <= 1e-5
+
+
+@pytest.mark.parametrize("forward_euler", [False, True])
+@pytest.mark.parametrize("alias", [False, True])
+def test_advance_parity(mixed, forward_euler, alias, record_error):
+    """The stand-alone node update (ibm_advance; Sec. 2.3, Sec. 5 step 4):
+    given F_int [3][V] and per-face F_ext [3][F], the load distribution
+    F_ext^v = sum F_ext/3 and the symplectic or forward Euler update against
+    the oracle's, clamped nodes fixed, outputs written in place or not."""
+    wl, ob = mixed
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
+                       forward_euler=forward_euler)
+    rng = np.random.default_rng(11)
+    x = H.state_tensor(wl, deformed_state(wl, 12))
+    xs = H.to_abs(wl, H.split_state(ctx, wl, x))
+    v = torch.tensor(rng.uniform(-0.3, 0.3, (3, ctx.V)), dtype=torch.float32, device=DEV)
+    # the oracle's internal forces, and per-face loads of the same size
+    Fi = H.state_tensor(wl, [b.internal_forces(xs[i]).numpy() for i, b in enumerate(ob)])
+    scale = float(Fi.abs().max())
+    Fe = torch.tensor(rng.uniform(-scale, scale, (3, ctx.F)), dtype=torch.float32, device=DEV)
+    vs = [torch.tensor(a) for a in H.split_state(ctx, wl, v)]
+    Fis = [torch.tensor(a) for a in H.split_state(ctx, wl, Fi)]
+    Fes = [torch.tensor(a) for a in H.split_faces(ctx, wl, Fe)]
+    if alias:
+        xo, vo = x.clone(), v.clone()
+        ctx.advance(xo, vo, Fi, Fe, x_out=xo, v_out=vo)
+    else:
+        xo, vo = ctx.advance(x, v, Fi, Fe)
+    ctx.check_device_error()
+    prm = H.oracle_params(wl, forward_euler=forward_euler)
+    xg = H.split_state(ctx, wl, xo)
+    vg = H.split_state(ctx, wl, vo)
+    for i, b in enumerate(ob):
+        xn, vn, _ = O.advance(b, xs[i], vs[i], Fis[i], Fes[i], prm)
+        xref = xn.numpy() - wl.bodies[i].origin
+        err_x = H.rel_l2(xg[i], xref)
+        dv_g = vg[i] - vs[i].numpy()
+        dv_o = vn.numpy() - vs[i].numpy()
+        store = np.linalg.norm(0.5 * np.spacing(np.abs(vn.numpy()).astype(np.float32)).astype(np.float64))
+        excess = max(0.0, np.linalg.norm(dv_g - dv_o) - store) / np.linalg.norm(dv_o)
+        record_error(f"advance_x[{i}]", err_x)
+        record_error(f"advance_dv[{i}]", excess)
+        assert err_x <= 1e-6, (i, err_x)
+        assert excess <= 1e-5, (i, excess)
+        cl = wl.bodies[i].clamped
+        if cl is not None and cl.any():
+            x_in = H.split_state(ctx, wl, x)[i]
+            assert np.array_equal(xg[i][cl], x_in[cl])
+            assert np.all(vg[i][cl] == 0)

@@ -64,3 +64,68 @@ def test_noalloc_rejects_oversize_requests():
                                        ctypes.c_void_p(16), None)
     assert st == 6
     assert b"static scratch" in lib.ibm_last_error(None)
+
+
+def _call(lib, x, n_vert, tri_d, face_off, n_bodies, max_faces, closed, out, dev):
+    return lib.ibm_body_measures_noalloc(
+        ctypes.c_void_p(x.data_ptr()), n_vert, ctypes.c_void_p(tri_d.data_ptr()),
+        ctypes.c_void_p(face_off.data_ptr()), n_bodies, max_faces,
+        ctypes.c_void_p(closed.data_ptr()) if closed is not None else None,
+        ctypes.c_void_p(out.data_ptr()),
+        ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+
+
+def test_noalloc_flags_bad_caller_data_with_nan():
+    """Caller data that would address outside the arrays is caught on the
+    device before use: a body with more faces than max_faces_per_body, a body
+    with a vertex id outside [0, n_vert) and a body with a reversed face range
+    get NaN, the other bodies their exact measures; a body with no faces gets
+    (0, 0)."""
+    bs = bodies()
+    grid = W.Grid((32, 32, 32))
+    ctx = _lib.Context(bs, grid)
+    lib = _lib.library()
+    dev = torch.device("cuda", 0)
+    tri = np.concatenate([b.tri + int(ctx.v_off[i]) for i, b in enumerate(bs)]).astype(np.int32)
+    fo = np.append(ctx.f_off, ctx.F).astype(np.int32)
+    closed = torch.tensor([1 if b.closed else 0 for b in bs], dtype=torch.uint8, device=dev)
+    x, _ = ctx.init_state()
+    ref = ctx.body_measures(x).cpu().numpy()
+    nf = [len(b.tri) for b in bs]
+    assert nf[1] > max(nf[0], nf[2])
+
+    # undersized bound: body 1 does not fit, bodies 0 and 2 do
+    out = torch.full((3, 2), -1.0, dtype=torch.float64, device=dev)
+    st = _call(lib, x, ctx.V, torch.tensor(tri, device=dev), torch.tensor(fo, device=dev), 3,
+               max(nf[0], nf[2]), closed, out, dev)
+    assert st == 0, lib.ibm_last_error(None)
+    got = out.cpu().numpy()
+    assert np.isnan(got[1]).all()
+    for i in (0, 2):
+        assert np.allclose(got[i], ref[i], rtol=1e-6, atol=1e-12)
+
+    # a vertex id one past the end in body 2
+    bad = tri.copy()
+    bad[fo[2] + 5, 1] = ctx.V
+    out.fill_(-1.0)
+    st = _call(lib, x, ctx.V, torch.tensor(bad, device=dev), torch.tensor(fo, device=dev), 3,
+               max(nf), closed, out, dev)
+    assert st == 0
+    got = out.cpu().numpy()
+    assert np.isnan(got[2]).all()
+    for i in (0, 1):
+        assert np.allclose(got[i], ref[i], rtol=1e-6, atol=1e-12)
+
+    # an empty body between bodies 0 and 1, and a reversed range after them
+    fo5 = np.array([fo[0], fo[1], fo[1], fo[2], fo[1], fo[1]], dtype=np.int32)
+    closed5 = torch.tensor([1, 1, 1, 1, 1], dtype=torch.uint8, device=dev)
+    out5 = torch.full((5, 2), -1.0, dtype=torch.float64, device=dev)
+    st = _call(lib, x, ctx.V, torch.tensor(tri, device=dev), torch.tensor(fo5, device=dev), 5,
+               max(nf), closed5, out5, dev)
+    assert st == 0
+    got = out5.cpu().numpy()
+    assert np.allclose(got[0], ref[0], rtol=1e-6, atol=1e-12)
+    assert np.array_equal(got[1], [0.0, 0.0])
+    assert np.allclose(got[2], ref[1], rtol=1e-6, atol=1e-12)
+    assert np.isnan(got[3]).all()
+    assert np.array_equal(got[4], [0.0, 0.0])
