@@ -66,6 +66,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--patch", type=int, default=0)
+    ap.add_argument("--spread-variant", type=int, default=0, choices=[0, 1, 2],
+                    help="1: spread inside the marker kernel (atomic flush); 2: tile-owned "
+                         "spread kernels; 0: the library's default")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip timing the other spread variant on the headline workload")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the uneven-bodies and membrane workloads")
     ap.add_argument("--integrator", default="symplectic", choices=["symplectic", "hamming"],
                     help="hamming: the strong-coupling predictor-corrector step (ibm_step_pc), "
                          "steps launched one by one")
@@ -174,23 +181,40 @@ def touched_nodes(wl, x, ctx, device):
 
 
 def byte_model(wl, ctx, x, device):
+    """Algorithmic bytes per launch of the step's kernels, counted as the
+    byte model of the hot path states: state x, v read and written (48 B per
+    vertex), rest data (l0, theta0 per edge, A0 per face), and on the grid
+    4 B per component and unique node read by the centroid and probe
+    stencils plus 4 B per component and unique node written by the spread.
+    `marker_fused` is the marker kernel of spread variant 1 (interpolation,
+    traction and spread), `marker` that of variant 2 (interpolation and
+    traction; its per-marker outputs, about 28 B, count as written), `spread`
+    the tile-owned spread (those outputs read, the nodes written).  The
+    `_rmw` figures count the spread's nodes as read and written (8 B), what
+    float atomics into the fields move."""
     nv = sum(len(b.rest) for b in wl.bodies)
     nf = sum(len(b.tri) for b in wl.bodies)
     ne = ctx.E
     centre_nodes, all_nodes = touched_nodes(wl, x, ctx, device)
-    marker = (nv * 24            # x, v gathered (each vertex once)
-              + nf * 12          # F_ext written
-              + 4 * sum(all_nodes)          # velocity nodes read (centroid + probe stencils)
-              + 8 * sum(centre_nodes))      # force nodes read-modify-written by the spread
-    force = (nv * (12 + 12 + 24 + 1)        # x, v read; x', v' written; clamp flag
-             + ne * 12                      # l0, (cos, sin) theta0
-             + nf * (4 + 12))               # A0_f, F_ext read
-    # the coupled step's forcing launch (interpolate and spread at the
-    # centroids, no probe): x, v gathered, centroid velocity nodes read,
-    # force nodes read-modify-written
-    forcing = nv * 24 + 4 * sum(centre_nodes) + 8 * sum(centre_nodes)
-    return {"marker": marker, "force": force, "forcing": forcing, "nodes_centre": centre_nodes,
-            "nodes_all": all_nodes}
+    grid_in = 4 * sum(all_nodes)
+    grid_out = 4 * sum(centre_nodes)
+    state_in = nv * 24                      # x, v gathered (each vertex once)
+    out = {
+        "marker_fused": state_in + nf * 12 + grid_in + grid_out,
+        "marker_fused_rmw": state_in + nf * 12 + grid_in + 2 * grid_out,
+        "marker": state_in + nf * 28 + grid_in,
+        "spread": nf * 28 + grid_out,
+        "force": (nv * (12 + 12 + 24 + 1)   # x, v read; x', v' written; clamp flag
+                  + ne * 12                 # l0, (cos, sin) theta0
+                  + nf * (4 + 12)),         # A0_f, F_ext read
+        # the coupled step's forcing launch (interpolate and spread at the
+        # centroids, no probe): x, v gathered, centroid velocity nodes read,
+        # force nodes read-modify-written
+        "forcing": state_in + 4 * sum(centre_nodes) + 8 * sum(centre_nodes),
+        "step": nv * 48 + ne * 12 + nf * 4 + grid_in + grid_out,
+        "nodes_centre": centre_nodes, "nodes_all": all_nodes,
+    }
+    return out
 
 
 def hbm_peak():
@@ -241,7 +265,7 @@ class Clocks:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "50"], stdout=self.fh,
+                                          "-i", str(self.index), "-lms", "10"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
             # the timed region starts once the sampler delivers readings
             t0 = time.time()
@@ -335,6 +359,115 @@ def run_reference(args, ws, rank):
 # the GB300 arm
 # ---------------------------------------------------------------------------
 
+PHASES = ["pre", "marker", "spread", "force"]
+
+
+def time_steps(ctx, wl, fields, f, state, n_steps, flush, stream, clocks=None):
+    """Time n_steps (rounded up to even) of the whole step as replays of a
+    2-step CUDA graph, L2 flushed before every replay; CUDA events on the
+    library's stream.  Returns (total ms, steps, clock record)."""
+    xa, va, xb, vb = state
+    graph = ctx.graph(xa, va, xb, vb, fields, f, n_steps=2)
+    graph.launch()
+    torch.cuda.synchronize()
+    n_rep = (n_steps + 1) // 2
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks is not None:
+        clocks.start()
+    total = 0.0
+    for _ in range(n_rep):
+        flush.zero_()
+        ev0.record(stream)
+        graph.launch()
+        ev1.record(stream)
+        ev1.synchronize()
+        total += ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks is not None else None
+    ctx.check_device_error()
+    graph.close()
+    return total, 2 * n_rep, clk
+
+
+def phase_steps(ctx, wl, fields, f, state, n_steps, flush):
+    """The same steps launched one by one with CUDA events between the
+    kernels: mean (set-up or clear, marker, spread, force) ms and the mean
+    step ms."""
+    xa, va, xb, vb = state
+    stream = torch.cuda.current_stream(xa.device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.set_phase_timing(True)
+    phases, step_ms = [], 0.0
+    for _ in range(n_steps):
+        flush.zero_()
+        ev0.record(stream)
+        ctx.step(xa, va, fields, xb, vb, f)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms += ev0.elapsed_time(ev1)
+        phases.append(ctx.phase_times())
+        xa, va, xb, vb = xb, vb, xa, va
+    ctx.set_phase_timing(False)
+    return np.array(phases).mean(0), step_ms / n_steps, (xa, va, xb, vb)
+
+
+def kernel_roofline(variant, mean_ph, bm, peak, peak_kind):
+    """Per-kernel achieved GB/s (algorithmic bytes / mean event time) and the
+    dominant kernel's roofline record."""
+    keys = ({"marker": "marker_fused", "force": "force"} if variant == 1 else
+            {"marker": "marker", "spread": "spread", "force": "force"})
+    per = {}
+    for k, n in enumerate(PHASES):
+        if n not in keys or mean_ph[k] <= 0:
+            continue
+        b = bm[keys[n]]
+        per[n] = {"algorithmic_bytes": b, "ms": float(mean_ph[k]),
+                  "achieved_gbs": b / (mean_ph[k] * 1e-3) / 1e9,
+                  "frac": b / (mean_ph[k] * 1e-3) / 1e9 / peak}
+    dom = max(per, key=lambda n: per[n]["ms"])
+    rec = {"bound": "hbm", "kernel": dom, "achieved": per[dom]["achieved_gbs"], "peak": peak,
+           "peak_kind": peak_kind, "unit": "GB/s", "frac": per[dom]["frac"],
+           "algorithmic_bytes": per[dom]["algorithmic_bytes"]}
+    if variant == 1 and dom == "marker":
+        rmw = bm["marker_fused_rmw"] / (per[dom]["ms"] * 1e-3) / 1e9
+        rec["frac_rmw"] = rmw / peak
+    return rec, per
+
+
+def extra_workload(args, name, variant, device, flush, peak, peak_kind, patch):
+    """One of the larger configurations: whole-step throughput (graph
+    replays, L2 flushed), phases one by one, dominant kernel's roofline."""
+    from paper_1612_03399_gb300 import _lib
+    make, descr = WORKLOADS[name]
+    wl = make(1)
+    fields = W.sample_field(wl.field, wl.grid, device=device, dtype=torch.float32)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha, patch_size=patch,
+                       device=device.index, spread_variant=variant)
+    stream = torch.cuda.current_stream(device)
+    nx, ny, nz = wl.grid.n
+    f = tuple(torch.zeros((nz, ny, nx), dtype=torch.float32, device=device) for _ in range(3))
+    xa, va = ctx.init_state()
+    xb, vb = torch.empty_like(xa), torch.empty_like(va)
+    bm = byte_model(wl, ctx, xa, device)
+    for _ in range(3):
+        ctx.step(xa, va, fields, xb, vb, f)
+        xa, va, xb, vb = xb, vb, xa, va
+    mean_ph, _, st = phase_steps(ctx, wl, fields, f, (xa, va, xb, vb), 6, flush)
+    n = max(6, min(args.steps, 20))
+    total, steps, clk = time_steps(ctx, wl, fields, f, st, n, flush, stream, Clocks(device.index))
+    roof, per = kernel_roofline(ctx.spread_variant, mean_ph, bm, peak, peak_kind)
+    out = {"workload": descr, "bodies": ctx.B, "vertices": ctx.V, "faces": ctx.F,
+           "grid": list(wl.grid.n), "spread_variant": ctx.spread_variant,
+           "ms_per_step": total / steps, "value": ctx.V * steps / (total * 1e-3), "unit": UNIT,
+           "steps": steps, "phases_ms": dict(zip(PHASES, map(float, mean_ph))),
+           "roofline": roof, "kernels": per,
+           "step_algorithmic_gbs": bm["step"] / (total / steps * 1e-3) / 1e9, "clocks": clk}
+    ctx.close()
+    del fields, f, xa, va, xb, vb
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gb300(args, ws, rank, local):
     from paper_1612_03399_gb300 import _lib
     device = torch.device("cuda", local)
@@ -353,7 +486,8 @@ def run_gb300(args, ws, rank, local):
         patch, tuned = autotune_patch_size(wl.bodies, wl.grid, fields, dt=wl.dt, mu=wl.mu,
                                            alpha=wl.alpha, device=local)
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
-                       patch_size=patch, device=local)
+                       patch_size=patch, device=local, spread_variant=args.spread_variant)
+    variant = ctx.spread_variant
     stream = torch.cuda.current_stream(device)
     nx, ny, nz = wl.grid.n
     f = tuple(torch.zeros((nz, ny, nx), dtype=torch.float32, device=device) for _ in range(3))
@@ -364,56 +498,28 @@ def run_gb300(args, ws, rank, local):
         return run_hamming(args, ws, rank, ctx, wl, descr, fields, f, xa, va, xb, vb, flush,
                            device, patch)
     bytes_model = byte_model(wl, ctx, xa, device) if rank == 0 else None
-    ctx.set_phase_timing(True)
     for _ in range(max(args.warmup, 3)):
         ctx.step(xa, va, fields, xb, vb, f)
         xa, va, xb, vb = xb, vb, xa, va
     ctx.check_device_error()
     torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # per-kernel phase times (CUDA events between the step's launches) for the
     # roofline: the same steps launched one by one
-    phases = []
-    step_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        ev0.record(stream)
-        ctx.step(xa, va, fields, xb, vb, f)
-        ev1.record(stream)
-        ev1.synchronize()
-        step_ms += ev0.elapsed_time(ev1)
-        phases.append(ctx.phase_times())
-        xa, va, xb, vb = xb, vb, xa, va
-    ctx.set_phase_timing(False)
+    mean_ph, step_ms, (xa, va, xb, vb) = phase_steps(ctx, wl, fields, f, (xa, va, xb, vb),
+                                                     args.steps, flush)
     # the timed steps: the whole step captured in a CUDA graph, two steps per
     # replay (ping-pong state), L2 flushed before every replay
-    graph = ctx.graph(xa, va, xb, vb, fields, f, n_steps=2)
-    graph.launch()
-    torch.cuda.synchronize()
-    n_rep = (args.steps + 1) // 2
-    n_steps = 2 * n_rep
-    clocks = Clocks(local)
     barrier(ws)
     torch.cuda.synchronize()
-    clocks.start()
-    total_ms = 0.0
-    for _ in range(n_rep):
-        flush.zero_()
-        ev0.record(stream)
-        graph.launch()
-        ev1.record(stream)
-        ev1.synchronize()
-        total_ms += ev0.elapsed_time(ev1)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ctx.check_device_error()
-    graph.close()
+    total_ms, n_steps, clk = time_steps(ctx, wl, fields, f, (xa, va, xb, vb), args.steps, flush,
+                                        stream, Clocks(local))
     barrier(ws)
     value, t_max = job_rate(ws, ctx.V, n_steps, total_ms, device)
-    value_steps, _ = job_rate(ws, ctx.V, args.steps, step_ms, device)
+    value_steps, _ = job_rate(ws, ctx.V, 1, step_ms, device)
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if not args.no_e2e:
         xh = xa.cpu().pin_memory()
         vh = va.cpu().pin_memory()
@@ -438,49 +544,74 @@ def run_gb300(args, ws, rank, local):
         nbytes = 2 * 3 * ctx.V * 4
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    counters = ctx.counters()
+    ctx.close()
     if rank != 0:
         return
-    ph = np.array(phases)
-    mean_ph = ph.mean(0)
-    names = ["clear", "marker", "force"]
-    dom = int(np.argmax(mean_ph[1:])) + 1
     peak, peak_kind = hbm_peak()
-    algo = bytes_model[names[dom]]
-    achieved = algo / (mean_ph[dom] * 1e-3) / 1e9
-    traffic = ncu_traffic(names[dom])
+    roof, per = kernel_roofline(variant, mean_ph, bytes_model, peak, peak_kind)
+    roof["traffic"] = ncu_traffic(roof["kernel"])
+    launches = 3 if variant == 1 else 6
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": n_steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_max / n_steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": descr, "bodies": ctx.B, "vertices": ctx.V, "faces": ctx.F,
+        "config": {"workload": descr, "bodies": int(sum(1 for _ in wl.bodies)),
+                   "vertices": int(sum(len(b.rest) for b in wl.bodies)),
+                   "faces": int(sum(len(b.tri) for b in wl.bodies)),
                    "grid": list(wl.grid.n), "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"{ws} independent replica(s)", "patch_size": patch,
-                   "autotune_force_ms": tuned},
-        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_bytes": algo},
-        "phases_ms": {n: float(m) for n, m in zip(names, mean_ph)},
-        "kernel_frac": {n: float(m / mean_ph.sum()) for n, m in zip(names, mean_ph)},
-        "other_kernel": {n: {"algorithmic_bytes": bytes_model[n],
-                             "achieved_gbs": bytes_model[n] / (mean_ph[k] * 1e-3) / 1e9}
-                         for k, n in enumerate(names) if n != "clear"},
-        "gpu_launches": 3 * n_steps,
+                   "spread_variant": variant, "autotune_force_ms": tuned},
+        "roofline": roof,
+        "phases_ms": dict(zip(PHASES, map(float, mean_ph))),
+        "kernels": per,
+        "step_algorithmic_gbs": bytes_model["step"] / (t_max / n_steps * 1e-3) / 1e9,
+        "gpu_launches": launches * n_steps,
         "timing": "CUDA graph of 2 captured steps per replay; value_no_graph times the same "
                   "steps launched one by one (with phase events)",
         "value_no_graph": value_steps,
-        "counters": ctx.counters(),
+        "counters": counters,
         "e2e": e2e,
         "clocks": clk,
     }
+    if not args.no_variants and ws == 1 and args.workload == "drops1000" and not args.bodies:
+        # the other spread variant on the same workload, for the choice of default
+        other = 1 if variant == 2 else 2
+        ctx2 = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
+                            patch_size=patch, device=local, spread_variant=other)
+        xa, va = ctx2.init_state()
+        xb, vb = torch.empty_like(xa), torch.empty_like(va)
+        for t in f:
+            t.zero_()
+        for _ in range(3):
+            ctx2.step(xa, va, fields, xb, vb, f)
+            xa, va, xb, vb = xb, vb, xa, va
+        ph2, _, st = phase_steps(ctx2, wl, fields, f, (xa, va, xb, vb), 10, flush)
+        tot2, n2, _ = time_steps(ctx2, wl, fields, f, st, max(10, args.steps), flush, stream)
+        roof2, per2 = kernel_roofline(other, ph2, bytes_model, peak, peak_kind)
+        line["other_variant"] = {"spread_variant": other, "ms_per_step": tot2 / n2,
+                                 "value": ctx2.V * n2 / (tot2 * 1e-3),
+                                 "phases_ms": dict(zip(PHASES, map(float, ph2))),
+                                 "roofline": roof2}
+        ctx2.close()
+    if not args.no_extra and ws == 1 and args.workload == "drops1000" and not args.bodies:
+        del fields, f
+        torch.cuda.empty_cache()
+        line["extra_workloads"] = {
+            name: extra_workload(args, name, variant, device, flush, peak, peak_kind, patch)
+            for name in ("uneven4096", "membranes")}
+        fields = None
     if not args.no_cpu_baseline and ws == 1:
+        if fields is None:
+            fields = W.sample_field(wl.field, wl.grid, device=device, dtype=torch.float32)
         fields_cpu = tuple(t.double().cpu() for t in fields)
         oracle_sample_rate(wl, 1, 1, fields_cpu)
         nb = 16
         rate, secs, nodes = oracle_sample_rate(wl, nb, 2, fields_cpu)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": torch.get_num_threads(),
                                 "kind": "oracle",
-                                "sample": f"{nb} of the {ctx.B} bodies ({nodes} nodes) on the full "
-                                          f"grid and field, 2 steps, {secs:.1f} s"}
+                                "sample": f"{nb} of the {len(wl.bodies)} bodies ({nodes} nodes) on "
+                                          f"the full grid and field, 2 steps, {secs:.1f} s"}
     print(json.dumps(line), flush=True)
 
 

@@ -101,7 +101,18 @@ typedef struct {
   int32_t theta0_zero;     /* 1: W_b = k_b(1 - cos theta) literally; 0: rest angle */
   int32_t forward_euler;   /* 1: forward Euler node update; 0: symplectic Euler  */
   int32_t patch_size;      /* vertices per force-kernel block; 0 -> default (128) */
-  int32_t reserved;
+  int32_t spread_variant;  /* how marker forces reach the grid (Eq. mls_cl):
+                              1: inside the marker kernel, per marker patch, in
+                                 exact fixed point, merged across patches with
+                                 float atomics (order-dependent where patches
+                                 meet; ibm_step clears the previous footprint
+                                 with a separate kernel);
+                              2: tile-owned: markers listed per 16x8x8-node tile,
+                                 each tile's nodes summed in exact fixed point by
+                                 one block and stored once with plain stores
+                                 (bitwise deterministic; the previous step's
+                                 footprint is zeroed in the same pass);
+                              0: the library's default (1)                      */
 } ibm_params;
 
 /* Create a context for n_bodies bodies on CUDA device `device`: validates the
@@ -126,6 +137,10 @@ ibm_status ibm_set_stream(ibm_ctx* ctx, void* stream);
 /* host out[6]: total vertices V, faces F, edges E, bodies B, distinct
  * topologies, force-kernel work items. */
 ibm_status ibm_get_sizes(const ibm_ctx* ctx, int64_t* out);
+
+/* host *out = the context's parameters as resolved at creation (defaults
+ * filled in: patch_size, spread_variant, alpha, probe_h). */
+ibm_status ibm_get_params(const ibm_ctx* ctx, ibm_params* out);
 
 /* host out[3*B]: vertex, face, edge offset of every body. */
 ibm_status ibm_get_offsets(const ibm_ctx* ctx, int64_t* out);
@@ -173,14 +188,17 @@ ibm_status ibm_advance(ibm_ctx* ctx, const float* x, const float* v, const float
 
 /* (d) Spread marker forces F_marker [3][F] at the centroids of x onto the
  * force fields: f_i^k += c_l phi_k^l F_i^l (Eq. mls_cl).  ACCUMULATES into the
- * caller's fields (atomic adds: summation order is not fixed). */
+ * caller's fields: with spread_variant 1 by atomic adds (summation order not
+ * fixed), with 2 each touched node is read, added to and stored by one block
+ * (deterministic). */
 ibm_status ibm_spread(ibm_ctx* ctx, const float* x, const float* F_marker, float* fx, float* fy,
                       float* fz);
 
 #define IBM_STEP_CLEAR_PREV 1u  /* zero the grid nodes the previous ibm_step of this
                                    context spread to, before spreading this step   */
 
-/* One whole step (a)-(d) in three launches: x, v -> x_out, v_out (must not
+/* One whole step (a)-(d) (three launches with spread_variant 1, six with 2):
+ * x, v -> x_out, v_out (must not
  * alias x, v), spreading this step's marker forces into fx, fy, fz.  p and
  * accel as in ibm_interpolate (both may be NULL).  With
  * IBM_STEP_CLEAR_PREV the fields hold exactly this step's forces afterwards,
@@ -378,9 +396,10 @@ ibm_status ibm_check_device_error(ibm_ctx* ctx);
 
 /* Phase timing of ibm_step (profiling aid, no counterpart in the paper): when
  * on (nonzero), every ibm_step records CUDA events on the context's stream
- * around its three kernels.  ibm_get_phase_times waits for the last recorded
- * step and writes host ms[3] = (footprint clear, marker kernel, force+update
- * kernel) of that step. */
+ * between its kernels.  ibm_get_phase_times waits for the last recorded step
+ * and writes host ms[4] = (footprint clear (spread variant 1) or call set-up
+ * (variant 2), marker kernel (with the spread in variant 1), tile-owned
+ * spread (variant 2; 0 in variant 1), force+update kernel) of that step. */
 ibm_status ibm_set_phase_timing(ibm_ctx* ctx, int32_t on);
 ibm_status ibm_get_phase_times(ibm_ctx* ctx, float* ms);
 

@@ -41,7 +41,7 @@ class GridDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
                 ("probe_h", C.c_double), ("theta0_zero", C.c_int32), ("forward_euler", C.c_int32),
-                ("patch_size", C.c_int32), ("reserved", C.c_int32)]
+                ("patch_size", C.c_int32), ("spread_variant", C.c_int32)]
 
 
 # exported symbols and their signatures (ctypes types), in header order
@@ -53,6 +53,7 @@ SIGNATURES = {
     "ibm_last_error": (C.c_char_p, [P]),
     "ibm_set_stream": (C.c_int, [P, P]),
     "ibm_get_sizes": (C.c_int, [P, C.POINTER(C.c_int64)]),
+    "ibm_get_params": (C.c_int, [P, C.POINTER(Params)]),
     "ibm_get_offsets": (C.c_int, [P, C.POINTER(C.c_int64)]),
     "ibm_init_state": (C.c_int, [P, P, P]),
     "ibm_set_body_constants": (C.c_int, [P, C.POINTER(C.c_double)]),
@@ -131,7 +132,7 @@ class Context:
     """
 
     def __init__(self, bodies, grid, dt=1e-3, mu=1.0, alpha=0.3, probe_h=0.0, theta0_zero=False,
-                 forward_euler=False, patch_size=0, device=0):
+                 forward_euler=False, patch_size=0, device=0, spread_variant=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the IBM library needs a CUDA device; there is no CPU fallback")
@@ -167,7 +168,8 @@ class Context:
             g.n[k] = int(grid.n[k])
             g.L[k] = float(grid.L[k])
         p = Params(dt=dt, mu=mu, alpha=alpha, probe_h=probe_h, theta0_zero=int(theta0_zero),
-                   forward_euler=int(forward_euler), patch_size=int(patch_size))
+                   forward_euler=int(forward_euler), patch_size=int(patch_size),
+                   spread_variant=int(spread_variant))
         h = C.c_void_p()
         st = self.lib.ibm_create_bodies(C.byref(h), descs, len(bodies), C.byref(g), C.byref(p),
                                         device)
@@ -183,6 +185,10 @@ class Context:
         o = np.array(offs, dtype=np.int64).reshape(self.B, 3)
         self.v_off, self.f_off, self.e_off = o[:, 0], o[:, 1], o[:, 2]
         self.grid = grid
+        prm = Params()
+        self._check(self.lib.ibm_get_params(self.h, C.byref(prm)))
+        self.spread_variant = int(prm.spread_variant)
+        self.patch_size = int(prm.patch_size)
         self.set_stream(torch.cuda.current_stream(self.device))
 
     # -- plumbing ------------------------------------------------------------
@@ -318,8 +324,9 @@ class Context:
         return {"marker_box_fallbacks": int(out[0])}
 
     def phase_times(self):
-        """(clear, marker, force+update) milliseconds of the last timed step."""
-        ms = (C.c_float * 3)()
+        """(clear or set-up, marker, tile-owned spread, force+update)
+        milliseconds of the last timed step."""
+        ms = (C.c_float * 4)()
         self._check(self.lib.ibm_get_phase_times(self.h, ms))
         return tuple(float(m) for m in ms)
 

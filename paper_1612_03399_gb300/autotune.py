@@ -24,7 +24,8 @@ def autotune_patch_size(bodies, grid, fields, dt=1e-3, mu=1.0, alpha=0.3, device
     results = {}
     for P in candidates:
         try:
-            ctx = _lib.Context(bodies, grid, dt=dt, mu=mu, alpha=alpha, patch_size=P, device=device)
+            ctx = _lib.Context(bodies, grid, dt=dt, mu=mu, alpha=alpha, patch_size=P, device=device,
+                               spread_variant=1)
         except _lib.IBMError:
             continue           # patch tables too large for this size
         f = tuple(torch.zeros((n[2], n[1], n[0]), dtype=torch.float32, device=dev) for _ in range(3))
@@ -35,7 +36,7 @@ def autotune_patch_size(bodies, grid, fields, dt=1e-3, mu=1.0, alpha=0.3, device
         for k in range(warmup + steps):
             ctx.step(xa, va, fields, xb, vb, f)
             if k >= warmup:
-                times.append(ctx.phase_times()[2])
+                times.append(ctx.phase_times()[3])
             xa, va, xb, vb = xb, vb, xa, va
         ctx.check_device_error()
         results[P] = float(np.mean(times))

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libibm_gb300.so")
-SOURCES = ["ibm_host.cu", "k_mls.cu", "k_force.cu", "k_adjoint.cu", "k_taylor.cu",
+SOURCES = ["ibm_host.cu", "k_mls.cu", "k_tile.cu", "k_force.cu", "k_adjoint.cu", "k_taylor.cu",
            "ibm_noalloc.cu", "ibm_gts.cu", "k_pc.cu", "ibm_flow.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
@@ -44,11 +44,12 @@ def _digest() -> str:
 
 # the sources each profiled kernel is compiled from (for per-kernel digests)
 KERNEL_SOURCES = {
-    "marker": ["k_mls.cu", "ibm_internal.cuh"],
-    "clear": ["k_mls.cu", "ibm_internal.cuh"],
-    "forcing": ["k_mls.cu", "ibm_internal.cuh"],
-    "body_marker": ["k_mls.cu", "ibm_internal.cuh"],
+    "marker": ["k_mls.cu", "mls_closed_form.cuh", "ibm_internal.cuh"],
+    "clear": ["k_mls.cu", "mls_closed_form.cuh", "ibm_internal.cuh"],
+    "forcing": ["k_mls.cu", "mls_closed_form.cuh", "ibm_internal.cuh"],
+    "body_marker": ["k_mls.cu", "mls_closed_form.cuh", "ibm_internal.cuh"],
     "force": ["k_force.cu", "force_elems.cuh", "ibm_internal.cuh"],
+    "spread": ["k_tile.cu", "ibm_internal.cuh"],
     "rhs": ["ibm_flow.cu", "ibm_internal.cuh"],
     "cn_scale": ["ibm_flow.cu", "ibm_internal.cuh"],
     "add": ["ibm_flow.cu", "ibm_internal.cuh"],

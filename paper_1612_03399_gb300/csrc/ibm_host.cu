@@ -239,7 +239,7 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
 // balanced).  Writes the faces in patch order to `order` and the patch
 // boundaries to `bounds` (size parts + 1).
 void marker_patches(const int32_t* tri, int nf, const double* rest, std::vector<int32_t>& order,
-                    std::vector<int32_t>& bounds) {
+                    std::vector<int32_t>& bounds, int PT) {
   std::vector<double> c(3 * (size_t)nf);
   for (int f = 0; f < nf; ++f)
     for (int d = 0; d < 3; ++d)
@@ -251,16 +251,16 @@ void marker_patches(const int32_t* tri, int nf, const double* rest, std::vector<
   struct Part {
     int lo, hi, parts;
   };
-  std::vector<Part> stack{{0, nf, (nf + kMT - 1) / kMT}};
+  std::vector<Part> stack{{0, nf, (nf + PT - 1) / PT}};
   std::vector<std::pair<int, int>> leaves;
   while (!stack.empty()) {
     Part p = stack.back();
     stack.pop_back();
-    if (p.hi - p.lo <= kMT) {
+    if (p.hi - p.lo <= PT) {
       leaves.push_back({p.lo, p.hi});
       continue;
     }
-    p.parts = std::max(p.parts, (p.hi - p.lo + kMT - 1) / kMT);
+    p.parts = std::max(p.parts, (p.hi - p.lo + PT - 1) / PT);
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int k = p.lo; k < p.hi; ++k)
       for (int d = 0; d < 3; ++d) {
@@ -333,11 +333,12 @@ bool is_fin(double v) { return std::isfinite(v); }
 // patch's spatial order (W warps): the warp's faces are spread over the patch
 // (its simultaneous shared atomics of the spread rarely meet on a node) while
 // its loads of the face records stay contiguous.
-void interleave_full_patches(std::vector<int32_t>& mface, const std::vector<int32_t>& mbound) {
-  std::vector<int32_t> tmp(kMT);
+void interleave_full_patches(std::vector<int32_t>& mface, const std::vector<int32_t>& mbound,
+                             int PT) {
+  std::vector<int32_t> tmp(PT);
   for (size_t k = 0; k + 1 < mbound.size(); ++k) {
-    if (mbound[k + 1] - mbound[k] != kMT) continue;
-    for (int t = 0; t < kMT; ++t) tmp[t] = mface[mbound[k] + (kMT / 32) * (t & 31) + (t >> 5)];
+    if (mbound[k + 1] - mbound[k] != PT) continue;
+    for (int t = 0; t < PT; ++t) tmp[t] = mface[mbound[k] + (PT / 32) * (t & 31) + (t >> 5)];
     std::copy(tmp.begin(), tmp.end(), mface.begin() + mbound[k]);
   }
 }
@@ -388,6 +389,39 @@ ibm_status cuda_status(ibm_ctx* c, cudaError_t e, const char* what) {
   return set_err(c, IBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Bound on |phi| of the closed-form MLS shape functions over every offset
+// of the point from its nearest node: |phi| <= prod_d (max_s a_s + max_s |b_s|)
+// (phi = a_x a_y a_z - b_x a_y a_z - a_x b_y a_z - a_x a_y b_z), the factors
+// taken over a fine sweep of the fractional offset, with a margin.
+double phi_bound_of(double kappa) {
+  double best = 0.0;
+  for (int k = 0; k <= 20000; ++k) {
+    const double tp = -0.5 + k / 20000.0;
+    const double rm = std::exp(-kappa * (1 + 2 * tp)), rp = std::exp(-kappa * (1 - 2 * tp));
+    const double S = 1 + rm + rp;
+    const double a[3] = {rm / S, 1 / S, rp / S}, d[3] = {-1 - tp, -tp, 1 - tp};
+    const double mu = a[0] * d[0] + a[1] * d[1] + a[2] * d[2];
+    double s2 = 0.0;
+    for (int j = 0; j < 3; ++j) s2 += a[j] * (d[j] - mu) * (d[j] - mu);
+    double amax = 0.0, bmax = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      amax = std::max(amax, a[j]);
+      bmax = std::max(bmax, std::fabs(a[j] * mu * (d[j] - mu) / s2));
+    }
+    best = std::max(best, amax + bmax);
+  }
+  return 1.05 * best * best * best;
+}
+
+// the step's marker kernel: body sums, interpolation, traction and spread
+// with the previous footprint cleared (clear) or accumulated
+cudaError_t launch_step_marker(ibm_ctx* c, const float* x, const float* v, const float* u,
+                               const float* vv, const float* w, const float* p,
+                               const float* accel, float* fx, float* fy, float* fz, bool clear) {
+  return launch_mls(c, x, v, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz,
+                    true, true, true, true, clear);
+}
+
 void make_consts(ibm_ctx* c) {
   const ibm_params& p = c->prm;
   ibm::Grid& g = c->grid;
@@ -406,6 +440,7 @@ void make_consts(ibm_ctx* c) {
   c->sc.kappa = (float)(1.0 / ((1.5 * alpha) * (1.5 * alpha)));
   c->sc.cl_scale = (float)(((h[0] + h[1] + h[2]) / 3.0) / (h[0] * h[1] * h[2]));
   c->sc.forward_euler = p.forward_euler ? 1 : 0;
+  c->phi_bound = (float)phi_bound_of(c->sc.kappa);
 }
 
 }  // namespace
@@ -449,11 +484,15 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     if (!is_fin(p.probe_h)) fail(IBM_ERR_INVALID_ARG, "probe_h must be finite");
     const int P = p.patch_size > 0 ? p.patch_size : 128;
     if (P < 32 || P > 2048) fail(IBM_ERR_INVALID_ARG, "patch_size must be in [32, 2048]");
+    if (p.spread_variant < 0 || p.spread_variant > 2)
+      fail(IBM_ERR_INVALID_ARG, "spread_variant must be 0, 1 or 2");
 
     c = new ibm_ctx();
     c->device = device;
     c->prm = p;
     c->prm.patch_size = P;
+    c->spread_variant = p.spread_variant == 0 ? 1 : p.spread_variant;
+    c->prm.spread_variant = c->spread_variant;
     c->gdesc = *grid;
     make_consts(c);
     double h[3];
@@ -481,8 +520,9 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
         topos.emplace_back();
         try {
           build_topology(topos.back(), B.tri, B.n_vert, B.n_face, P);
-          marker_patches(B.tri, B.n_face, B.rest, topos.back().mface, topos.back().mbound);
-          interleave_full_patches(topos.back().mface, topos.back().mbound);
+          marker_patches(B.tri, B.n_face, B.rest, topos.back().mface, topos.back().mbound, kMT);
+          interleave_full_patches(topos.back().mface, topos.back().mbound, kMT);
+
         } catch (Failure& f) {
           f.msg = "body " + std::to_string(b) + ": " + f.msg;
           throw;
@@ -682,6 +722,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       mface_all.insert(mface_all.end(), T.mface.begin(), T.mface.end());
       for (const int32_t f : T.mface)
         mtri_all.push_back(make_int4(T.tri[3 * f], T.tri[3 * f + 1], T.tri[3 * f + 2], f));
+
       D.patch_off = (int32_t)patch_all.size();
       const int32_t lo = (int32_t)loc_all.size(), eo2 = (int32_t)pedge_all.size(),
                     fo2 = (int32_t)pface_all.size(), co = (int32_t)csr_all.size(),
@@ -758,6 +799,41 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.tpart = zeros<double>(c, 10 * (size_t)c->n_chunks);
     d.taylor = zeros<double>(c, 24 * (size_t)n_bodies);
     d.tgrad = zeros<double>(c, 10 * (size_t)n_bodies);
+    if (c->spread_variant == 2) {
+      // tile tables of the tile-owned spread; the marker list holds at most
+      // (tiles per direction a 4-node support can reach)^3 entries per marker:
+      // 2 per direction, 3 where a partial last tile has fewer than 3 nodes
+      TileDev& t = c->td;
+      const int TT[3] = {kTX, kTY, kTZ};
+      long long per = 1;
+      for (int k = 0; k < 3; ++k) {
+        t.nt[k] = (grid->n[k] + TT[k] - 1) / TT[k];
+        const int rem = grid->n[k] % TT[k];
+        per *= t.nt[k] == 1 ? 1 : ((rem == 1 || rem == 2) ? 3 : 2);
+      }
+      t.n_tiles = t.nt[0] * t.nt[1] * t.nt[2];
+      c->max_pairs = per * (long long)F;
+      if (c->max_pairs >= (1ll << 31))
+        fail(IBM_ERR_UNSUPPORTED, "tile-owned spread: more than 2^31 marker-tile pairs possible");
+      t.count = zeros<int32_t>(c, t.n_tiles);
+      t.off = zeros<int32_t>(c, t.n_tiles);
+      t.cur = zeros<int32_t>(c, t.n_tiles);
+      t.epoch = zeros<int32_t>(c, t.n_tiles);
+      check_cuda(cudaMemset(t.epoch, 0xff, sizeof(int32_t) * t.n_tiles), "cudaMemset");
+      t.mask = zeros<uint32_t>(c, 12 * (size_t)t.n_tiles);
+      t.tmax = zeros<uint32_t>(c, 4 * (size_t)t.n_tiles);
+      t.active[0] = zeros<int32_t>(c, t.n_tiles);
+      t.state = zeros<int32_t>(c, 8);
+      t.mlist = zeros<int32_t>(c, (size_t)std::max<long long>(c->max_pairs, 1));
+      t.rec = zeros<float4>(c, 2 * (size_t)F);
+      int per_sm = 0, n_sm = 0;
+      check_cuda(tile_spread_occupancy(&per_sm), "occupancy");
+      check_cuda(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device), "attr");
+      c->tile_grid = std::max(1, per_sm) * std::max(1, n_sm);
+      check_cuda(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreate");
+      check_cuda(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+      check_cuda(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+    }
     check_cuda(cudaDeviceSynchronize(), "create");
     *out = c;
     return IBM_OK;
@@ -786,6 +862,12 @@ extern "C" void ibm_destroy(ibm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   free_all(c);
   delete c;
 }
@@ -810,6 +892,14 @@ extern "C" ibm_status ibm_get_sizes(const ibm_ctx* c, int64_t* out) {
   out[3] = c->B;
   out[4] = c->n_topo;
   out[5] = c->n_work;
+  return IBM_OK;
+}
+
+extern "C" ibm_status ibm_get_params(const ibm_ctx* c, ibm_params* out) {
+  if (!c || !out) return IBM_ERR_INVALID_ARG;
+  *out = c->prm;
+  if (!(out->alpha > 0)) out->alpha = 0.3;
+  out->probe_h = c->sc.probe_h;
   return IBM_OK;
 }
 
@@ -911,8 +1001,17 @@ extern "C" ibm_status ibm_spread(ibm_ctx* c, const float* x, const float* Fm, fl
                                  float* fz) {
   if (!c || !x || !Fm || !fx || !fy || !fz) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   cudaSetDevice(c->device);
-  cudaError_t e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, Fm, nullptr, fx, fy, fz, false, false, false, true, false);
+  cudaError_t e = cudaSuccess;
+  if (c->spread_variant == 2) {
+    e = launch_tile_begin(c, true, false);
+    if (e == cudaSuccess)
+      e = launch_mls_records(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Fm,
+                             nullptr, false, false, true);
+    if (e == cudaSuccess) e = launch_tile_spread(c, fx, fy, fz, true);
+  } else {
+    e = launch_mls(c, x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Fm,
+                   nullptr, fx, fy, fz, false, false, false, true, false);
+  }
   return cuda_status(c, e, "ibm_spread");
 }
 
@@ -932,18 +1031,33 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[k], c->stream);
   };
   mark(0);
-  // the clear is a no-op for blocks that recorded no footprint (first step),
-  // so it is launched unconditionally: a captured step then clears whatever
-  // step ran before it.  It also zeroes the fixed-point body sums.
-  e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
-  mark(1);
-  if (e == cudaSuccess)
-    e = launch_mls(c, x, v, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz,
-                   true, true, true, true, clear);
-  mark(2);
-  if (e == cudaSuccess)
-    e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true);
-  mark(3);
+  if (c->spread_variant == 2) {
+    // set-up (epoch, lists, body sums), marker kernel (records), the
+    // tile-owned spread, then the force kernel (it needs only the marker
+    // kernel's traction and body sums)
+    e = launch_tile_begin(c, !clear, true);
+    mark(1);
+    if (e == cudaSuccess)
+      e = launch_mls_records(c, x, v, u, vv, w, p, accel, nullptr, c->d.fext, true, true, !clear);
+    mark(2);
+    if (e == cudaSuccess) e = launch_tile_spread(c, fx, fy, fz, !clear);
+    mark(3);
+    if (e == cudaSuccess)
+      e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true);
+    mark(4);
+  } else {
+    // the clear is a no-op for blocks that recorded no footprint (first step),
+    // so it is launched unconditionally: a captured step then clears whatever
+    // step ran before it.  It also zeroes the fixed-point body sums.
+    e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
+    mark(1);
+    if (e == cudaSuccess) e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, clear);
+    mark(2);
+    mark(3);
+    if (e == cudaSuccess)
+      e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true);
+    mark(4);
+  }
   if (e == cudaSuccess) {
     c->have_prev = clear;
     c->timed = c->timing;
@@ -1087,10 +1201,16 @@ extern "C" ibm_status ibm_step_pc(ibm_ctx* c, const float* x, const float* v, co
   use_parity(c, c->qpar ^ 1);
   // at y_n: footprint clear, interpolation, spreading, probe traction, body
   // sums (as ibm_step), then a_n
-  cudaError_t e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
-  if (e == cudaSuccess)
-    e = launch_mls(c, x, v, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz,
-                   true, true, true, true, clear);
+  cudaError_t e = cudaSuccess;
+  if (c->spread_variant == 2) {
+    e = launch_tile_begin(c, !clear, true);
+    if (e == cudaSuccess)
+      e = launch_mls_records(c, x, v, u, vv, w, p, accel, nullptr, c->d.fext, true, true, !clear);
+    if (e == cudaSuccess) e = launch_tile_spread(c, fx, fy, fz, !clear);
+  } else {
+    e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
+    if (e == cudaSuccess) e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, clear);
+  }
   float* an = P.a[0];
   if (e == cudaSuccess) e = launch_accel(c, x, c->d.fext, an);
   if (P.steps < 3) {
@@ -1223,16 +1343,50 @@ extern "C" ibm_status ibm_graph_create(ibm_ctx* c, float* xa, float* va, float* 
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_marker, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_clear, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && c->spread_variant == 2) {
+    // per step: set-up, marker kernel; then the force kernel on the capture
+    // stream while the tile-owned spread runs on the side stream (the two are
+    // independent: the spread reads the records, the force kernel the traction
+    // and body sums); the next step waits for both
+    for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+      const bool even = (k & 1) == 0;
+      const float* x = even ? xa : xb;
+      const float* v = even ? va : vb;
+      use_parity(c, c->qpar ^ 1);
+      e = launch_tile_begin(c, false, true);
+      if (e == cudaSuccess)
+        e = launch_mls_records(c, x, v, u, vv, w, p, accel, nullptr, c->d.fext, true, true, false);
+      if (e == cudaSuccess) e = cudaEventRecord(ev_marker, cap);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_marker, 0);
+      if (e == cudaSuccess) {
+        c->stream = side;
+        e = launch_tile_spread(c, fx, fy, fz, false);
+        c->stream = cap;
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev_clear, side);
+      if (e == cudaSuccess)
+        e = launch_force(c, x, v, c->d.fext, nullptr, even ? xb : xa, even ? vb : va, nullptr,
+                         true);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev_clear, 0);
+    }
+    if (e != cudaSuccess) st = cuda_status(c, e, "ibm_graph_create");
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (e2 == cudaSuccess && st == IBM_OK) {
+      g->graph = graph;
+      e = cudaGraphInstantiate(&g->exec, graph, 0);
+    } else {
+      if (graph) cudaGraphDestroy(graph);
+      e = e2;
+    }
+  } else if (e == cudaSuccess) {
     for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
       const bool even = (k & 1) == 0;
       const float* x = even ? xa : xb;
       const float* v = even ? va : vb;
       use_parity(c, c->qpar ^ 1);
       if (k == 0) e = launch_clear(c, fx, fy, fz);
-      if (e == cudaSuccess)
-        e = launch_mls(c, x, v, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, fx, fy,
-                       fz, true, true, true, true, true);
+      if (e == cudaSuccess) e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, true);
       const bool next = k + 1 < n_steps;
       if (next && e == cudaSuccess) {
         e = cudaEventRecord(ev_marker, cap);
@@ -1321,8 +1475,8 @@ extern "C" ibm_status ibm_get_phase_times(ibm_ctx* c, float* ms) {
   if (!c || !ms) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   if (!c->timed) return set_err(c, IBM_ERR_INVALID_ARG, "no timed ibm_step recorded");
   cudaSetDevice(c->device);
-  cudaError_t e = cudaEventSynchronize(c->ev[3]);
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(ms + k, c->ev[k], c->ev[k + 1]);
+  cudaError_t e = cudaEventSynchronize(c->ev[4]);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(ms + k, c->ev[k], c->ev[k + 1]);
   return cuda_status(c, e, "ibm_get_phase_times");
 }
 
@@ -1366,7 +1520,9 @@ extern "C" ibm_status ibm_check_device_error(ibm_ctx* c) {
     cudaMemset(c->d.err, 0, sizeof(w));
     return set_err(c, IBM_ERR_DEVICE,
                    std::string("device error word ") + std::to_string(w) +
-                       ((w & ERR_NONFINITE) ? " (non-finite or out-of-range marker position)" : ""));
+                       ((w & ERR_NONFINITE) ? " (non-finite or out-of-range marker position)" : "") +
+                       ((w & ERR_TILE_DENSE) ? " (more than 65535 markers reach one spread tile)"
+                                             : ""));
   }
   return IBM_OK;
 }

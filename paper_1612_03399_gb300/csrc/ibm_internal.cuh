@@ -83,11 +83,67 @@ struct StepConsts {
 };
 
 constexpr int kMT = 256;             // markers (faces) per block of the marker kernel (a patch)
+
+// ---------------------------------------------------------------------------
+// tile-owned spread: the grid is cut into tiles of kTX x kTY x kTZ nodes (the
+// last tile of a direction may be partial); each marker is listed under every
+// tile that the union of its three components' 3x3x3 centroid supports
+// reaches (nodes f-1 .. f+2 per direction, f = floor of the centroid in
+// cells), and one block per tile sums what its nodes receive
+// ---------------------------------------------------------------------------
+constexpr int kTX = 16, kTY = 8, kTZ = 8;
+constexpr int kTileNodes = kTX * kTY * kTZ;   // 1024 nodes, 128 x-segments of 8 nodes
+constexpr int kTileThreads = 256;
+// TileDev::state slots
+enum : int32_t { TS_EPOCH = 0, TS_LEN = 1, TS_PAIRS = 2 };
+
+struct TileDev {
+  int32_t nt[3] = {0, 0, 0};    // tiles per direction
+  int32_t n_tiles = 0;
+  int32_t* count = nullptr;     // [n_tiles] markers reaching the tile in this call (the
+                                //  spread kernel resets it to 0)
+  uint32_t* tmax = nullptr;     // [n_tiles][4] largest |c_l F| per component of those
+                                //  markers, as float bits (reset by the spread kernel)
+  int32_t* off = nullptr;       // [n_tiles] first slot of the tile's markers in mlist
+  int32_t* cur = nullptr;       // [n_tiles] fill cursor; after the fill, the end of the list
+  int32_t* epoch = nullptr;     // [n_tiles] last clear-mode call in which markers reached it
+  uint32_t* mask = nullptr;     // [n_tiles][3][4] x-segments of 8 nodes that the last
+                                //  clear-mode spread left nonzero, per component
+  int32_t* active[1] = {nullptr};  // [n_tiles] tiles listed in this call
+  int32_t* state = nullptr;     // [8] TS_* counters
+  int32_t* mlist = nullptr;     // [max_pairs] marker ids grouped by tile
+  float4* rec = nullptr;        // [F][2] per marker: (centroid in cells relative to the body's
+                                //  cell G, body id as bits, or -1 when not spread), (c_l F, 0)
+};
+
+// wrapped index of x into [0, n), any int x (one compare and add in the
+// usual case of x within one period of the box)
+__device__ __forceinline__ int wrap_any(int x, int n) {
+  if (x >= 0 && x < n) return x;
+  if (x < 0 && x >= -n) return x + n;
+  if (x >= n && x < 2 * n) return x - n;
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+
+// distinct tiles (at most 3) of direction d holding the nodes f - 1 .. f + 2
+__device__ __forceinline__ int tiles_along(int f, int n, int T, int (&out)[3]) {
+  int k = 0;
+#pragma unroll
+  for (int s = -1; s <= 2; ++s) {
+    const int t = wrap_any(f + s, n) / T;
+    bool dup = false;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dup = dup || (j < k && out[j] == t);
+    if (!dup && k < 3) out[k++] = t;
+  }
+  return k;
+}
 constexpr int kForceThreads = 256;   // threads per force-kernel block
 constexpr uint16_t kNone = 0xFFFF;
 
 // error word bits (device)
-enum : int32_t { ERR_NONFINITE = 1, ERR_BAD_INDEX = 2 };
+enum : int32_t { ERR_NONFINITE = 1, ERR_BAD_INDEX = 2, ERR_TILE_DENSE = 4, ERR_TIMEOUT = 8 };
 
 struct DeviceTables {
   BodyDev* body = nullptr;
@@ -187,6 +243,14 @@ __device__ __forceinline__ float2 body_coef(const BodyDev& B, unsigned long long
 
 struct ibm_ctx {
   int device = 0;
+  int spread_variant = 1;       // 1: spread inside the marker kernel (patch-owned, atomic
+                                //  flush); 2: tile-owned spread kernels
+  ibm::TileDev td;
+  int64_t max_pairs = 0;
+  float phi_bound = 1.f;        // bound on |phi| of the MLS shape functions (fixed-point scales)
+  int tile_grid = 0;            // blocks of the persistent tile kernels
+  cudaStream_t side = nullptr;  // second stream of ibm_step (spread beside the force kernel)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t stream = nullptr;
   std::string err;
   int64_t V = 0, F = 0, E = 0, B = 0;
@@ -220,7 +284,7 @@ struct ibm_ctx {
   } pc;
   bool timing = false;          // record phase events in ibm_step
   bool timed = false;           // a timed step has been recorded
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<ibm::BodyDev> h_body;
   std::vector<void*> allocations;
   ibm::DeviceTables d;
@@ -236,6 +300,19 @@ cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* 
                        float* fz, bool measure, bool interp, bool probe, bool spread,
                        bool record_cells);
 cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz);
+
+// marker kernel without the spread, writing the spread records and counting
+// the marker-tile pairs of the tile-owned spread (`accumulate`: into the
+// fields' existing values, outside the clear-mode bookkeeping)
+cudaError_t launch_mls_records(ibm_ctx* c, const float* x, const float* v, const float* u,
+                               const float* vv, const float* w, const float* p,
+                               const float* accel, const float* Fm_in, float* Fext, bool measure,
+                               bool probe, bool accumulate);
+// tile-owned spread (k_tile.cu): begin a call (epoch, list lengths, body
+// sums), offsets of the tiles' lists, fill, and the spread itself
+cudaError_t launch_tile_begin(ibm_ctx* c, bool accumulate, bool zero_sums);
+cudaError_t launch_tile_spread(ibm_ctx* c, float* fx, float* fy, float* fz, bool accumulate);
+cudaError_t tile_spread_occupancy(int* blocks_per_sm);
 // zero the fixed-point body sums (before a measuring marker launch that does
 // not follow a clear), and form meas / coef from them (after it)
 cudaError_t zero_body_sums(ibm_ctx* c);

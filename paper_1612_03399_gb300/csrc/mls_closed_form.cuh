@@ -1,0 +1,356 @@
+// Closed-form MLS shape functions of the factorised weight and their use on
+// 3x3x3 supports (Sec. 2.2, Eqs. mls..mls_Q), shared by the marker kernels.
+//
+// MLS with the linear basis and a weight that factorises over directions
+// (W = prod_d exp(-kappa delta_d^2), delta in cells) has an exact closed-form
+// solution of the 4x4 moment system: with per-direction normalised weights
+// a_d(s) = w_d(s)/S_d, mean mu_d and variance s2_d of the node offsets,
+//   phi(sx,sy,sz) = a_x a_y a_z (1 - beta_x - beta_y - beta_z),
+//   beta_d(s) = mu_d (delta_d(s) - mu_d) / s2_d.
+// Writing b_d = a_d beta_d, phi = a_x a_y a_z - b_x a_y a_z - a_x b_y a_z
+// - a_x a_y b_z, so value and full derivative are short tensor contractions of
+// the 27 node values.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <math.h>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+namespace {
+
+struct DirW {
+  float a[3], b[3];
+};
+struct DirWD {
+  float a[3], b[3], da[3], db[3];
+};
+
+// per-direction closed-form MLS factors for the fractional offset tp in
+// [-1/2, 1/2) of the point from its nearest node (cells).  The weights enter
+// only through their ratios to the nearest node's,
+//   w(-1)/w(0) = exp(-kappa (1 + 2 tp)),  w(+1)/w(0) = exp(-kappa (1 - 2 tp)),
+// both in (0, 1], so two exponentials suffice and nothing overflows.
+__device__ __forceinline__ void dir_weights(float tp, float kappa, DirW& o) {
+  const float rm = __expf(-kappa * fmaf(2.f, tp, 1.f)), rp = __expf(-kappa * fmaf(-2.f, tp, 1.f));
+  const float invS = __fdividef(1.f, 1.f + rm + rp);
+  const float a0 = rm * invS, a1 = invS, a2 = rp * invS;
+  const float d0 = -1.f - tp, d1 = -tp, d2 = 1.f - tp;
+  const float mu = a0 * d0 + a1 * d1 + a2 * d2;
+  const float e0 = d0 - mu, e1 = d1 - mu, e2 = d2 - mu;
+  const float s2 = a0 * e0 * e0 + a1 * e1 * e1 + a2 * e2 * e2;
+  const float r = __fdividef(mu, s2);
+  o.a[0] = a0; o.a[1] = a1; o.a[2] = a2;
+  o.b[0] = a0 * r * e0; o.b[1] = a1 * r * e1; o.b[2] = a2 * r * e2;
+}
+
+// the same factors and their derivatives with respect to the point's
+// coordinate (in cells): the node offsets move as d delta / dt = -1, the
+// weight ratios as d rm / dt = -2 kappa rm, d rp / dt = 2 kappa rp
+__device__ __forceinline__ void dir_weights_d(float tp, float kappa, DirWD& o) {
+  const float d[3] = {-1.f - tp, -tp, 1.f - tp};
+  const float rm = __expf(-kappa * fmaf(2.f, tp, 1.f)), rp = __expf(-kappa * fmaf(-2.f, tp, 1.f));
+  const float w[3] = {rm, 1.f, rp};
+  const float dw[3] = {-2.f * kappa * rm, 0.f, 2.f * kappa * rp};
+  const float invS = __fdividef(1.f, 1.f + rm + rp);
+  const float dS = dw[0] + dw[2];
+  float a[3], da[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    a[s] = w[s] * invS;
+    da[s] = (dw[s] - a[s] * dS) * invS;
+  }
+  const float mu = a[0] * d[0] + a[1] * d[1] + a[2] * d[2];
+  const float dmu = da[0] * d[0] + da[1] * d[1] + da[2] * d[2] - 1.f;
+  float e[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) e[s] = d[s] - mu;
+  const float s2 = a[0] * e[0] * e[0] + a[1] * e[1] * e[1] + a[2] * e[2] * e[2];
+  const float ds2 = da[0] * e[0] * e[0] + da[1] * e[1] * e[1] + da[2] * e[2] * e[2];
+  const float inv_s2 = __fdividef(1.f, s2);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const float beta = mu * e[s] * inv_s2;
+    const float dbeta = (dmu * e[s] + mu * (-1.f - dmu)) * inv_s2 - beta * ds2 * inv_s2;
+    o.a[s] = a[s];
+    o.b[s] = a[s] * beta;
+    o.da[s] = da[s];
+    o.db[s] = da[s] * beta + a[s] * dbeta;
+  }
+}
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  if (i >= 0 && i < n) return i;
+  if (i < 0 && i >= -n) return i + n;
+  if (i >= n && i < 2 * n) return i - n;
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// Centre node (unwrapped global lattice index) and fractional offset of a
+// point, in every direction, on the lattice of velocity component `comp`
+// (node offset 0 along the component's own direction, 1/2 across it).
+__device__ __forceinline__ void locate(const float (&tau)[3], int comp, const int (&G)[3],
+                                       int (&c)[3], float (&tp)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float u = tau[d] - (d == comp ? 0.f : 0.5f);
+    const float cc = floorf(u + 0.5f);
+    tp[d] = u - cc;
+    c[d] = G[d] + (int)cc;
+  }
+}
+
+// addressing of a 3x3x3 support: rows (sy, sz), columns sx
+struct GlobalAcc {   // wrapped indices into a full [nz][ny][nx] field
+  int ix[3], iy[3], iz[3];
+  int nx, ny;
+  __device__ void init(const int (&c)[3], const Grid& g) {
+    nx = g.n[0];
+    ny = g.n[1];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      ix[s] = wrap(c[0] - 1 + s, g.n[0]);
+      iy[s] = wrap(c[1] - 1 + s, g.n[1]);
+      iz[s] = wrap(c[2] - 1 + s, g.n[2]);
+    }
+  }
+  __device__ int row(int sy, int sz) const { return (iz[sz] * ny + iy[sy]) * nx; }
+  __device__ int col(int sx) const { return ix[sx]; }
+};
+struct RowAcc {      // indices into the rows staged in shared memory
+  const int* off;    // staged offset of row r, minus its first x
+  int ylo, zlo, sy;
+  int cx, cy, cz;    // support corner (centre - 1)
+  __device__ void init(const int (&c)[3], const int* off_minus_x0, int ylo_, int zlo_, int sy_) {
+    off = off_minus_x0;
+    ylo = ylo_;
+    zlo = zlo_;
+    sy = sy_;
+    cx = c[0] - 1;
+    cy = c[1] - 1;
+    cz = c[2] - 1;
+  }
+  __device__ int row(int a, int b) const { return off[(cy + a - ylo) + sy * (cz + b - zlo)] + cx; }
+  __device__ int col(int s) const { return s; }
+};
+
+template <class Acc>
+__device__ __forceinline__ float mls_value(const float* __restrict__ f, const Acc& A, const DirW& X,
+                                           const DirW& Y, const DirW& Z) {
+  float q = 0.f;
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      const float* r = f + A.row(sy, sz);
+      const float u0 = r[A.col(0)], u1 = r[A.col(1)], u2 = r[A.col(2)];
+      const float xa = X.a[0] * u0 + X.a[1] * u1 + X.a[2] * u2;
+      const float xb = X.b[0] * u0 + X.b[1] * u1 + X.b[2] * u2;
+      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
+      q += (xa - xb) * ay * az - xa * (by * az + ay * bz);
+    }
+  }
+  return q;
+}
+
+template <class Acc>
+__device__ __forceinline__ void mls_grad(const float* __restrict__ f, const Acc& A, const DirWD& X,
+                                         const DirWD& Y, const DirWD& Z, float (&g)[3]) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      const float* r = f + A.row(sy, sz);
+      const float u0 = r[A.col(0)], u1 = r[A.col(1)], u2 = r[A.col(2)];
+      const float xa = X.a[0] * u0 + X.a[1] * u1 + X.a[2] * u2;
+      const float xb = X.b[0] * u0 + X.b[1] * u1 + X.b[2] * u2;
+      const float xda = X.da[0] * u0 + X.da[1] * u1 + X.da[2] * u2;
+      const float xdb = X.db[0] * u0 + X.db[1] * u1 + X.db[2] * u2;
+      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
+      const float day = Y.da[sy], dby = Y.db[sy], daz = Z.da[sz], dbz = Z.db[sz];
+      gx += (xda - xdb) * ay * az - xda * (by * az + ay * bz);
+      gy += (xa - xb) * day * az - xa * (dby * az + day * bz);
+      gz += (xa - xb) * ay * daz - xa * (by * daz + ay * dbz);
+    }
+  }
+  g[0] = gx; g[1] = gy; g[2] = gz;
+}
+
+// spread coef * phi onto the 27 nodes
+template <class Acc>
+__device__ __forceinline__ void mls_spread(float* f, const Acc& A, const DirW& X, const DirW& Y,
+                                           const DirW& Z, float coef) {
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      float* r = f + A.row(sy, sz);
+      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
+      const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
+#pragma unroll
+      for (int sx = 0; sx < 3; ++sx)
+        atomicAdd(r + A.col(sx), (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1);
+    }
+  }
+}
+
+// full-derivative MLS gradient (in cells) of component `comp` at a point
+template <class Acc>
+__device__ __forceinline__ void grad_at(const float* f, const Acc& A, const float (&tp)[3],
+                                        float kappa, float (&gr)[3]) {
+  DirWD X, Y, Z;
+  dir_weights_d(tp[0], kappa, X);
+  dir_weights_d(tp[1], kappa, Y);
+  dir_weights_d(tp[2], kappa, Z);
+  mls_grad(f, A, X, Y, Z, gr);
+}
+
+// x >= 0 folded into [0, n)
+__device__ __forceinline__ int wrap_pos(int x, int n) {
+  if (x >= n) {
+    x -= n;
+    if (x >= n) x %= n;
+  }
+  return x;
+}
+
+// asynchronous global -> shared copies (cp.async: no register round trip, so
+// one thread's copies are all in flight at once)
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// the staged rows of the block, one float4 group (4 consecutive staged nodes
+// of one row) per entry of s_grow
+struct RowTable {
+  const unsigned short* grow;  // row of each group
+  const int* off;              // staged start of each row (a multiple of 4)
+  const int* base;             // global offset of the row's (y, z)
+  const int* x0w;              // first x of the row, wrapped into [0, nx)
+  int nx, vec4;
+  // global offset of node j (0..3) of group q
+  __device__ __forceinline__ size_t node(int q, int j) const {
+    const int r = grow[q];
+    return (size_t)base[r] + wrap_pos(x0w[r] + (4 * q - off[r]) + j, nx);
+  }
+};
+
+// issue the copies of one field component's staged rows into dst
+__device__ __forceinline__ void stage_async(float* dst, const float* __restrict__ src,
+                                            const RowTable& R, int ngroups) {
+  for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
+    if (R.vec4) {
+      cp_async16(dst + 4 * q, src + R.node(q, 0));   // x multiple of 4 and nx % 4 == 0
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cp_async4(dst + 4 * q + j, src + R.node(q, j));
+    }
+  }
+}
+
+// addressing factories: staged rows or the global field
+struct StagedRows {
+  const int* off_minus_x0;
+  int ylo, zlo, sy;
+  __device__ RowAcc at(const int (&c)[3]) const {
+    RowAcc A;
+    A.init(c, off_minus_x0, ylo, zlo, sy);
+    return A;
+  }
+};
+struct GlobalRows {
+  Grid g;
+  __device__ GlobalAcc at(const int (&c)[3]) const {
+    GlobalAcc A;
+    A.init(c, g);
+    return A;
+  }
+};
+
+// nearest node and derivative factors of one component at a probe point
+struct ProbeW {
+  int cc[3];
+  DirWD X, Y, Z;
+  __device__ __forceinline__ void prepare(const float (&t)[3], int comp, const int (&G)[3],
+                                          float kappa) {
+    float t3[3];
+    locate(t, comp, G, cc, t3);
+    dir_weights_d(t3[0], kappa, X);
+    dir_weights_d(t3[1], kappa, Y);
+    dir_weights_d(t3[2], kappa, Z);
+  }
+  // full-derivative gradient per unit length, times sgn, added to gr
+  template <class Rows>
+  __device__ __forceinline__ void add_gradient(const float* f, const Rows& R,
+                                               const float (&invh)[3], float sgn,
+                                               float (&gr)[3]) const {
+    float gl[3];
+    mls_grad(f, R.at(cc), X, Y, Z, gl);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gr[j] += sgn * gl[j] * invh[j];
+  }
+};
+
+// bound on |phi| over the 27 nodes: phi = a_x a_y a_z - b_x a_y a_z - a_x b_y a_z
+// - a_x a_y b_z, so |phi| <= prod_d (max|a_d| + max|b_d|)
+__device__ __forceinline__ float phi_bound(const DirW& X, const DirW& Y, const DirW& Z) {
+  auto p = [](const DirW& W) {
+    return fmaxf(fmaxf(W.a[0], W.a[1]), W.a[2]) +
+           fmaxf(fmaxf(fabsf(W.b[0]), fabsf(W.b[1])), fabsf(W.b[2]));
+  };
+  return p(X) * p(Y) * p(Z);
+}
+
+// Spread in exact fixed point: the contribution coef*phi, already scaled by
+// the block's power of two so that |value| <= 2^38, is split into
+// hi = floor(value / 2^16) (|hi| <= 2^22) and lo = value - 2^16 hi in
+// [0, 2^16], each added with a native 32-bit shared atomic.  A node receives
+// at most kMT contributions, so neither word overflows, and the node's sum
+// 2^16 * sum(hi) + sum(lo) is independent of the order of the additions.
+__device__ __forceinline__ void mls_spread_fixed(int* hi, int* lo, const RowAcc& A, const DirW& X,
+                                                 const DirW& Y, const DirW& Z, float coef) {
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      const int r = A.row(sy, sz);
+      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
+      const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
+#pragma unroll
+      for (int sx = 0; sx < 3; ++sx) {
+        const float val = (X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1;
+        const float hf = floorf(val * (1.f / 65536.f));
+        atomicAdd(hi + r + sx, (int)hf);
+        atomicAdd(lo + r + sx, __float2int_rn(fmaf(-hf, 65536.f, val)));
+      }
+    }
+  }
+}
+
+// x (|x| < 2^62) rounded to a 64-bit integer without a 64-bit conversion:
+// hi = floor(x / 2^32) is exact and the remainder x - 2^32 hi lies in [0, 2^32)
+__device__ __forceinline__ long long to_fixed(float x) {
+  const float hf = floorf(x * 0x1p-32f);
+  const unsigned lo = __float2uint_rn(fmaf(-hf, 0x1p32f, x));
+  return (long long)(int)hf * 4294967296ll + (long long)lo;
+}
+
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+}  // namespace
+}  // namespace ibm

@@ -1,6 +1,7 @@
 """The CUDA-graph replay of captured steps (ibm_graph_*) reproduces the same
 steps launched one by one: positions and velocities bitwise (fixed-order
-forces), spread fields to float32 summation order."""
+forces), spread fields bitwise with the tile-owned spread and to float32
+summation order with the atomic one."""
 import numpy as np
 import pytest
 import torch
@@ -14,7 +15,8 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda"
 
 
-def test_graph_replay_matches_step_by_step():
+@pytest.mark.parametrize("variant", [1, 2])
+def test_graph_replay_matches_step_by_step(variant):
     wl = mixed_workload()
     fields = H.fields_for(wl, DEV)
     n = wl.grid.n
@@ -22,7 +24,7 @@ def test_graph_replay_matches_step_by_step():
     x0 = H.state_tensor(wl, deformed_state(wl, 8, scale=0.02, stretch=0.02))
     v0 = torch.zeros_like(x0)
     # step by step
-    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, spread_variant=variant)
     f1 = zeros()
     xa, va = x0.clone(), v0.clone()
     for _ in range(4):
@@ -30,7 +32,7 @@ def test_graph_replay_matches_step_by_step():
         ctx.step(xa, va, fields, xb, vb, f1)
         xa, va = xb, vb
     # two replays of a 2-step graph
-    ctx2 = _lib.Context(wl.bodies, wl.grid, dt=wl.dt)
+    ctx2 = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, spread_variant=variant)
     f2 = zeros()
     ga, gva = x0.clone(), v0.clone()
     gb, gvb = torch.empty_like(ga), torch.empty_like(gva)
@@ -41,7 +43,23 @@ def test_graph_replay_matches_step_by_step():
     ctx2.check_device_error()
     assert torch.equal(ga, xa) and torch.equal(gva, va)
     for a, b in zip(f2, f1):
-        assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(b.abs().max()))
+        if variant == 2:
+            assert torch.equal(a, b)      # tile-owned spread: bitwise
+        else:
+            assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(b.abs().max()))
+    # a step launched on its own after the replays continues the sequence
+    # (the tile-owned spread keeps its bookkeeping on the device)
+    xb, vb = torch.empty_like(xa), torch.empty_like(va)
+    ctx.step(xa, va, fields, xb, vb, f1)
+    hb, hvb = torch.empty_like(ga), torch.empty_like(gva)
+    ctx2.step(ga, gva, fields, hb, hvb, f2)
+    ctx2.check_device_error()
+    assert torch.equal(hb, xb)
+    for a, b in zip(f2, f1):
+        if variant == 2:
+            assert torch.equal(a, b)
+        else:
+            assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(b.abs().max()))
     g.close()
 
 
