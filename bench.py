@@ -248,7 +248,65 @@ def ncu_traffic(kernel_key):
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 
+class _NvmlSampler:
+    """SM clock and throttle reasons read through NVML (libnvidia-ml, read-only
+    queries) every millisecond from a background thread, so that even a
+    timed region of a few milliseconds gets several samples."""
+    # clocks event reason bits (nvml.h)
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, index):
+        import ctypes
+        import threading
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        self.ctypes, self.threading = ctypes, threading
+        mx = ctypes.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx))
+        self.max_mhz = float(mx.value)
+        self.samples = []
+        self.stop_flag = False
+        self.thread = None
+
+    def read(self):
+        c = self.ctypes
+        mhz, rs = c.c_uint(), c.c_ulonglong()
+        self.lib.nvmlDeviceGetClockInfo(self.h, 1, c.byref(mhz))
+        self.reasons_fn(self.h, c.byref(rs))
+        return float(mhz.value), int(rs.value)
+
+    def start(self):
+        import time as _t
+        self.read()
+
+        def loop():
+            while not self.stop_flag:
+                self.samples.append(self.read())
+                _t.sleep(0.001)
+        self.thread = self.threading.Thread(target=loop, daemon=True)
+        self.thread.start()
+        while not self.samples:
+            _t.sleep(0.0005)
+
+    def stop(self):
+        self.stop_flag = True
+        self.thread.join(1.0)
+        sm = [m for m, _ in self.samples]
+        reasons = sorted(n for n, b in self.BITS.items() if any(r & b for _, r in self.samples))
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(sm), "source": "nvml"}
+
+
 class Clocks:
+    """Clocks and throttle reasons during a timed region: NVML when the
+    driver's library is there, else nvidia-smi sampling every 10 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -258,8 +316,15 @@ class Clocks:
         self.proc = None
         self.path = None
         self.skip = 0
+        self.nvml = None
 
     def start(self):
+        try:
+            self.nvml = _NvmlSampler(self.index)
+            self.nvml.start()
+            return
+        except Exception:
+            self.nvml = None
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -276,6 +341,11 @@ class Clocks:
             self.proc = None
 
     def stop(self):
+        if self.nvml is not None:
+            try:
+                return self.nvml.stop()
+            except Exception:
+                return None
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -303,7 +373,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi"}
 
 
 # ---------------------------------------------------------------------------

@@ -228,24 +228,31 @@ ibm_status ibm_step_pc(ibm_ctx* ctx, const float* x, const float* v, const float
 ibm_status ibm_pc_reset(ibm_ctx* ctx);
 
 /* Adjoint of one step (a vector-Jacobian product, loose coupling with the
- * flow frozen; Sec. 2.3 node update, Sec. 2.2 traction, Sec. 2.3 potentials):
- * given cotangents gx_next, gv_next [3][V] of the positions and velocities
- * an ibm_step from x produced, writes the cotangents gx, gv [3][V] of x and v
- * and gparams [B][5] float64 = cotangents of (k_s, k_b, k_a, k_A, k_v) per
- * body.  The velocity field (u, v, w) is the one the step used.  The step's
- * dependence on x through the internal forces (exact Hessian-vector products
- * of the four potentials, including the per-body global area and volume
- * terms) and through the probe traction (area, normal and the MLS velocity
- * gradient at the probe end, with its second derivatives) is included; the
- * spread force field is not differentiated (it does not feed the state).
- * p and accel are the ones the step used (NULL allowed); the pressure load's
- * dependence on x (area, normal, the MLS pressure gradient at the probe
- * ends) is included, accel is held fixed.  Outputs must not alias the
- * cotangents.  Per-body sums are in a fixed order; the result is
- * deterministic. */
-ibm_status ibm_backward(ibm_ctx* ctx, const float* x, const float* u, const float* vv,
-                        const float* w, const float* p, const float* accel, const float* gx_next,
-                        const float* gv_next, float* gx, float* gv, double* gparams);
+ * flow frozen; Sec. 2.3 node update, Sec. 2.2 traction and spreading, Sec. 2.3
+ * potentials): given cotangents gx_next, gv_next [3][V] of the positions and
+ * velocities an ibm_step from (x, v) produced, and optionally cotangents
+ * gfx, gfy, gfz of the spread force fields [nz][ny][nx] (all three or none),
+ * writes the cotangents gx, gv [3][V] of x and v and gparams [B][5] float64 =
+ * cotangents of (k_s, k_b, k_a, k_A, k_v) per body.  The velocity field
+ * (u, v, w) is the one the step used.  Included: the step's dependence on x
+ * through the internal forces (exact Hessian-vector products of the four
+ * potentials, including the per-body global area and volume terms), through
+ * the probe traction (area, normal and the MLS velocity gradient at the probe
+ * end, with its second derivatives) and, when the field cotangents are given,
+ * through the spread f_i^k = c_l phi_k(c_l) (V^b_i - U_i(c_l))/dt (centroid,
+ * area, and the vertex velocities in V^b; spreading transposed is MLS
+ * interpolation weighted by c_l).  v may be NULL when the field cotangents are
+ * (it enters only the spread).  p and accel are the ones the step used (NULL
+ * allowed); the pressure load's dependence on x (area, normal, the MLS
+ * pressure gradient at the probe ends) is included, accel is held fixed.
+ * Outputs must not alias the cotangents.  Per-body sums are in a fixed order;
+ * the result is deterministic.  Uses the context's per-face scratch (no
+ * ibm_step may run concurrently on the context). */
+ibm_status ibm_backward(ibm_ctx* ctx, const float* x, const float* v, const float* u,
+                        const float* vv, const float* w, const float* p, const float* accel,
+                        const float* gx_next, const float* gv_next, const float* gfx,
+                        const float* gfy, const float* gfz, float* gx, float* gv,
+                        double* gparams);
 
 /* Taylor deformation D = (L - B)/(L + B) of every closed body (Sec. 3.1's
  * semi-axes L, B of a deformed drop), taken from the ellipsoid with the same

@@ -281,15 +281,19 @@ class Context:
     def pc_reset(self):
         self._check(self.lib.ibm_pc_reset(self.h))
 
-    def backward(self, x, fields, gx_next, gv_next, p=None, accel=None):
-        """Cotangents (gx, gv, gparams [B, 5]) of one step from x (ibm_backward)."""
+    def backward(self, x, fields, gx_next, gv_next, p=None, accel=None, v=None, gf=None):
+        """Cotangents (gx, gv, gparams [B, 5]) of one step from (x, v)
+        (ibm_backward); gf: optional cotangents (gfx, gfy, gfz) of the spread
+        force fields, which need v."""
         import torch
         u, vv, w = fields
+        gfx, gfy, gfz = gf if gf is not None else (None, None, None)
         gx, gv = self._vec(self.V), self._vec(self.V)
         gp = torch.empty((self.B, 5), dtype=torch.float64, device=self.device)
-        self._check(self.lib.ibm_backward(self.h, _ptr(x), _ptr(u), _ptr(vv), _ptr(w), _ptr(p),
-                                          _ptr(accel), _ptr(gx_next), _ptr(gv_next), _ptr(gx),
-                                          _ptr(gv), _ptr(gp)))
+        self._check(self.lib.ibm_backward(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
+                                          _ptr(p), _ptr(accel), _ptr(gx_next), _ptr(gv_next),
+                                          _ptr(gfx), _ptr(gfy), _ptr(gfz), _ptr(gx), _ptr(gv),
+                                          _ptr(gp)))
         return gx, gv, gp
 
     def graph(self, xa, va, xb, vb, fields, f, n_steps=2, p=None, accel=None):

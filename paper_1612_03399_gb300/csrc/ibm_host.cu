@@ -1480,17 +1480,24 @@ extern "C" ibm_status ibm_get_phase_times(ibm_ctx* c, float* ms) {
   return cuda_status(c, e, "ibm_get_phase_times");
 }
 
-extern "C" ibm_status ibm_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
-                                   const float* w, const float* p, const float* accel,
-                                   const float* gx_next, const float* gv_next, float* gx,
+extern "C" ibm_status ibm_backward(ibm_ctx* c, const float* x, const float* v, const float* u,
+                                   const float* vv, const float* w, const float* p,
+                                   const float* accel, const float* gx_next, const float* gv_next,
+                                   const float* gfx, const float* gfy, const float* gfz, float* gx,
                                    float* gv, double* gparams) {
   if (!c || !x || !u || !vv || !w || !gx_next || !gv_next || !gx || !gv || !gparams)
     return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
   if (gx == gx_next || gv == gv_next || gx == gv_next || gv == gx_next)
     return set_err(c, IBM_ERR_INVALID_ARG, "ibm_backward: outputs must not alias the cotangents");
+  const int ngf = (gfx ? 1 : 0) + (gfy ? 1 : 0) + (gfz ? 1 : 0);
+  if (ngf != 0 && ngf != 3)
+    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_backward: give all three field cotangents or none");
+  if (ngf == 3 && !v)
+    return set_err(c, IBM_ERR_INVALID_ARG,
+                   "ibm_backward: the spread's cotangent needs the vertex velocities v");
   cudaSetDevice(c->device);
-  return cuda_status(c, launch_backward(c, x, u, vv, w, p, accel, gx_next, gv_next, gx, gv,
-                                       gparams),
+  return cuda_status(c, launch_backward(c, x, v, u, vv, w, p, accel, gx_next, gv_next, gfx, gfy,
+                                       gfz, gx, gv, gparams),
                      "ibm_backward");
 }
 

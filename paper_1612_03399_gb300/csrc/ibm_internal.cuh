@@ -326,9 +326,10 @@ cudaError_t launch_accel(ibm_ctx* c, const float* x, const float* Fext, float* a
 cudaError_t launch_lincomb(ibm_ctx* c, float* out, const LinComb& L);
 cudaError_t launch_ham_predict(ibm_ctx* c, const HamPredict& P);
 cudaError_t launch_ham_correct(ibm_ctx* c, const HamCorrect& C);
-cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
-                            const float* w, const float* p, const float* accel,
-                            const float* gx_next, const float* gv_next, float* gx, float* gv,
+cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* v, const float* u,
+                            const float* vv, const float* w, const float* p, const float* accel,
+                            const float* gx_next, const float* gv_next, const float* gfx,
+                            const float* gfy, const float* gfz, float* gx, float* gv,
                             double* gparams);
 cudaError_t launch_taylor(ibm_ctx* c, const float* x, double* D);
 cudaError_t launch_taylor_backward(ibm_ctx* c, const float* x, const double* gD, float* gx);

@@ -8,6 +8,10 @@
 // gF = dt (gv' + dt gx')/m (symplectic) or dt gv'/m (forward Euler), zero on
 // clamped nodes, and gx = gx' + (dF_int/dx)^T gF + (dF_ext^v/dx)^T gF.
 //
+// With cotangents g of the spread force fields (Eq. mls_cl), the spread's
+// dependence on x (centroid and area of every face) and on v (the face's
+// centroid velocity in the marker force) is added as well.
+//
 // ext_adjoint_kernel (per face): the traction F_ext = mu A (G + G^T) n at the
 // probe end p = c + h n (two probes on open sheets) depends on x through A,
 // n, c and the MLS velocity gradient G(p); its reverse sweep needs the
@@ -237,9 +241,10 @@ __device__ __forceinline__ void cross3(const float (&a)[3], const float (&b)[3],
 
 __global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
     DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
-    const float* __restrict__ u, const float* __restrict__ vv, const float* __restrict__ w,
-    const float* __restrict__ pr, const float* __restrict__ accel,
-    const float* __restrict__ gxn, const float* __restrict__ gvn) {
+    const float* __restrict__ vel, const float* __restrict__ u, const float* __restrict__ vv,
+    const float* __restrict__ w, const float* __restrict__ pr, const float* __restrict__ accel,
+    const float* __restrict__ gxn, const float* __restrict__ gvn, const float* __restrict__ gfx,
+    const float* __restrict__ gfy, const float* __restrict__ gfz, float* __restrict__ gve) {
   __shared__ double s_red[2][kMT / 32];
   __shared__ int s_last;
   const int4 ch = T.chunks[blockIdx.x];
@@ -404,6 +409,36 @@ __global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
         gc[d] -= area * gFn * dPdc[d];
       }
     }
+    if (gfx) {
+      // the spread f_i^k = c_l phi_k(c) F_i with F_i = (V^b_i - U_i(c))/dt,
+      // c_l = A cl_scale (Eq. mls_cl), against the field cotangents g_i: with
+      // G_i = sum_k phi_k(c) g_i^k (spreading transposed is interpolation),
+      // dL/dF_i = c_l G_i, so the vertex velocities get c_l G_i / (3 dt)
+      // each, the centroid c_l (F_i grad G_i - G_i grad U_i / dt) and the
+      // area cl_scale sum_i F_i G_i
+      const float* gfs[3] = {gfx, gfy, gfz};
+      float tcc[3], vb[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        tcc[d] = fmaf(c[d], g.invh[d], B.frac[d]);
+        vb[d] = (__ldg(vel + d * V + id[0]) + __ldg(vel + d * V + id[1]) +
+                 __ldg(vel + d * V + id[2])) * third;
+      }
+      const float cl = area * sc.cl_scale;
+      float gAs = 0.f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float Uv, Ug[3], Gv, Gg[3];
+        mls_val_grad(fld[i], g, tcc, i, B.G, sc.kappa, Uv, Ug);
+        mls_val_grad(gfs[i], g, tcc, i, B.G, sc.kappa, Gv, Gg);
+        const float Fi = (vb[i] - Uv) * sc.inv_dt;
+        gAs += Fi * Gv;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) gc[d] += cl * (Fi * Gg[d] - Gv * sc.inv_dt * Ug[d]) * g.invh[d];
+        gve[i * (size_t)F + gf] = cl * Gv * sc.inv_dt * third;
+      }
+      gArea += sc.cl_scale * gAs;
+    }
     // n = N/|N|, A = |N|/2
     const float gnn = gn[0] * n[0] + gn[1] * n[1] + gn[2] * n[2];
     float gN[3];
@@ -479,7 +514,7 @@ __device__ __forceinline__ float dotv(const Vec<float>& a, const Vec<Dual>& b) {
 __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
     DeviceTables T, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ gxn, const float* __restrict__ gvn, float* __restrict__ gx,
-    float* __restrict__ gvo, double* __restrict__ gparams) {
+    float* __restrict__ gvo, double* __restrict__ gparams, const float* __restrict__ gve) {
   extern __shared__ float sm[];
   __shared__ double s_red[3][kForceThreads / 32];
   __shared__ int s_last;
@@ -574,6 +609,7 @@ __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
     // traction part: the cotangents the faces left for this corner
     const int* vp = T.v2f_ptr + topo.v2f_ptr_off;
     const int q0 = __ldg(vp + lv), q1 = __ldg(vp + lv + 1);
+    float wx = 0.f, wy = 0.f, wz = 0.f;   // the spread's velocity cotangent
     for (int q = q0; q < q1; ++q) {
       const int lf = __ldg(T.v2f_idx + topo.v2f_idx_off + q);
       const int corner = (__ldg(tri + 3 * lf) == lv) ? 0 : ((__ldg(tri + 3 * lf + 1) == lv) ? 1 : 2);
@@ -581,15 +617,22 @@ __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
       jx += __ldg(T.gxe + (corner * 3 + 0) * (size_t)F + gf);
       jy += __ldg(T.gxe + (corner * 3 + 1) * (size_t)F + gf);
       jz += __ldg(T.gxe + (corner * 3 + 2) * (size_t)F + gf);
+      if (gve) {
+        wx += __ldg(gve + gf);
+        wy += __ldg(gve + (size_t)F + gf);
+        wz += __ldg(gve + 2 * (size_t)F + gf);
+      }
     }
     const bool cl = T.clamp[gvx] != 0;
     const float gx0 = __ldg(gxn + gvx), gx1 = __ldg(gxn + V + gvx), gx2 = __ldg(gxn + 2 * V + gvx);
     gx[gvx] = gx0 + jx;
     gx[V + gvx] = gx1 + jy;
     gx[2 * V + gvx] = gx2 + jz;
-    gvo[gvx] = cl ? 0.f : __ldg(gvn + gvx) + sc.dt * gx0;
-    gvo[V + gvx] = cl ? 0.f : __ldg(gvn + V + gvx) + sc.dt * gx1;
-    gvo[2 * V + gvx] = cl ? 0.f : __ldg(gvn + 2 * V + gvx) + sc.dt * gx2;
+    // a clamped node's new state does not depend on its velocity; the spread
+    // (the centroid velocity of its faces) does
+    gvo[gvx] = (cl ? 0.f : __ldg(gvn + gvx) + sc.dt * gx0) + wx;
+    gvo[V + gvx] = (cl ? 0.f : __ldg(gvn + V + gvx) + sc.dt * gx1) + wy;
+    gvo[2 * V + gvx] = (cl ? 0.f : __ldg(gvn + 2 * V + gvx) + sc.dt * gx2) + wz;
   }
   // constants' cotangents: fixed-order per-patch sums, then per body
 #pragma unroll
@@ -639,9 +682,10 @@ __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
 
 }  // namespace
 
-cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const float* vv,
-                            const float* w, const float* pr, const float* accel,
-                            const float* gx_next, const float* gv_next, float* gx, float* gv,
+cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* v, const float* u,
+                            const float* vv, const float* w, const float* pr, const float* accel,
+                            const float* gx_next, const float* gv_next, const float* gfx,
+                            const float* gfy, const float* gfz, float* gx, float* gv,
                             double* gparams) {
   if (c->n_chunks == 0) return cudaSuccess;
   // area, volume and the global-term coefficients at x
@@ -651,13 +695,16 @@ cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* u, const fl
                    nullptr, nullptr, nullptr, nullptr, nullptr, true, false, false, false, false);
   if (e == cudaSuccess) e = launch_measure_finalize(c);
   if (e != cudaSuccess) return e;
+  // per-face velocity cotangents of the spread go to the step's F_ext scratch,
+  // unused by the adjoint otherwise
+  float* gve = gfx ? c->d.fext : nullptr;
   ext_adjoint_kernel<<<c->n_chunks, kMT, 0, c->stream>>>(c->d, c->grid, c->sc, (int32_t)c->V,
-                                                         (int32_t)c->F, x, u, vv, w, pr, accel,
-                                                         gx_next, gv_next);
+                                                         (int32_t)c->F, x, v, u, vv, w, pr, accel,
+                                                         gx_next, gv_next, gfx, gfy, gfz, gve);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   force_adjoint_kernel<<<c->n_work, kForceThreads, c->adjoint_smem, c->stream>>>(
-      c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, gx_next, gv_next, gx, gv, gparams);
+      c->d, c->sc, (int32_t)c->V, (int32_t)c->F, x, gx_next, gv_next, gx, gv, gparams, gve);
   return cudaGetLastError();
 }
 
