@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     const float* __restrict__ w, const float* __restrict__ pr, const float* __restrict__ accel,
     float* __restrict__ U, float* __restrict__ Fm, const float* __restrict__ Fm_in,
     float* __restrict__ Fext, float* __restrict__ fx, float* __restrict__ fy,
-    float* __restrict__ fz, int record, int vec4, TileDev td, int tmode) {
+    float* __restrict__ fz, int record, int vec4, TileDev td, int tmode, float phi_bound_all) {
   constexpr bool FIELD = INTERP || PROBE || SPREAD;
   constexpr bool VEL = INTERP || PROBE;
   constexpr bool ROWMAP = VEL || (SPREAD && !REC);
@@ -462,80 +462,107 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     td.rec[2 * (size_t)gf + 1] = r1;
   }
 
-  // ---- spreading: one component at a time, exact fixed point in the two
-  // buffers (high and low words), flushed with float4 global atomics --------
+  // ---- spreading: exact fixed point, one 32-bit word per staged node and
+  // component; components 0 and 1 in one pass (buffers A and B), component 2
+  // in a second (A), each pass flushed with float4 global atomics ----------
   if (SPREAD && !REC) {
     const float cl = area * sc.cl_scale;
-    int* s_hiw = reinterpret_cast<int*>(bufA);
-    int* s_low = reinterpret_cast<int*>(bufB);
+    int* accA = reinterpret_cast<int*>(bufA);
+    int* accB = reinterpret_cast<int*>(bufB);
     if (fit) {
       if (VEL) __syncthreads();   // the velocity phase is done with the buffers
       for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
-        reinterpret_cast<int4*>(s_hiw)[q] = make_int4(0, 0, 0, 0);
-        reinterpret_cast<int4*>(s_low)[q] = make_int4(0, 0, 0, 0);
+        reinterpret_cast<int4*>(accA)[q] = make_int4(0, 0, 0, 0);
+        reinterpret_cast<int4*>(accB)[q] = make_int4(0, 0, 0, 0);
       }
     }
-    // the components in a loop, not unrolled: the unrolled kernel measured
-    // slower (instruction fetch stalls)
 #pragma unroll 1
-    for (int comp = 0; comp < 3; ++comp) {
-      float* fc = comp == 0 ? fx : (comp == 1 ? fy : fz);
-      float coef = 0.f;
-      int cc[3];
-      DirW X, Y, Z;
-      if (mine) {
-        float t3[3];
-        locate(tc, comp, B.G, cc, t3);
-        dir_weights(t3[0], sc.kappa, X);
-        dir_weights(t3[1], sc.kappa, Y);
-        dir_weights(t3[2], sc.kappa, Z);
-        coef = cl * (comp == 0 ? Fl[0] : (comp == 1 ? Fl[1] : Fl[2]));
+    for (int pass = 0; pass < 2; ++pass) {
+      const int c0 = 2 * pass, nc = pass == 0 ? 2 : 1;   // components c0 .. c0 + nc - 1
+      const float F0 = pass == 0 ? Fl[0] : Fl[2];
+      const float F1 = Fl[1];
+      if (fit) {
+        // per component, the block's bound on |c_l phi F| from the bound on
+        // |phi| (non-negative floats order as their bit patterns)
+        float b0 = mine ? fabsf(cl * F0) * phi_bound_all : 0.f;
+        float b1 = (mine && nc == 2) ? fabsf(cl * F1) * phi_bound_all : 0.f;
+        if (!(b0 <= 3.0e38f)) b0 = __int_as_float(0x7f800000);
+        if (!(b1 <= 3.0e38f)) b1 = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          b0 = fmaxf(b0, __shfl_xor_sync(0xffffffffu, b0, o));
+          b1 = fmaxf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+          atomicMax(&s_bmax[c0], __float_as_int(b0));
+          if (nc == 2) atomicMax(&s_bmax[1], __float_as_int(b1));
+        }
+        __syncthreads();   // also: the buffers are zero
+      }
+      float inv[2] = {0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (j >= nc) break;
+        const int comp = j == 0 ? c0 : 1;
+        const float coef = cl * (j == 0 ? F0 : F1);
+        int cc[3];
+        DirW X, Y, Z;
+        if (mine) {
+          float t3[3];
+          locate(tc, comp, B.G, cc, t3);
+          dir_weights(t3[0], sc.kappa, X);
+          dir_weights(t3[1], sc.kappa, Y);
+          dir_weights(t3[2], sc.kappa, Z);
+        }
+        if (fit) {
+          const float bm = __int_as_float(s_bmax[comp]);
+          if (!(bm <= 3.0e38f)) {
+            if (threadIdx.x == 0) atomicOr(T.err, ERR_NONFINITE);
+            continue;   // uniform over the block
+          }
+          if (bm == 0.f) continue;   // nothing to spread for this component
+          // scale 2^k with every contribution below 2^22: a node takes at most
+          // kMT of them, so the sum stays below 2^30
+          const int k = min(22 - (ilogbf(bm) + 1), 120);
+          inv[j] = pow2f(-max(k, -126));
+          if (mine && coef != 0.f)
+            mls_spread_fixed1(j == 0 ? accA : accB, SR.at(cc), X, Y, Z, coef * pow2f(max(k, -126)));
+        } else if (mine) {
+          mls_spread(comp == 0 ? fx : (comp == 1 ? fy : fz), GR.at(cc), X, Y, Z, coef);
+        }
       }
       if (fit) {
-        // block-wide bound on |coef phi| (non-negative floats order as ints)
-        float bnd = mine ? fabsf(coef) * phi_bound(X, Y, Z) : 0.f;
-        if (!(bnd <= 3.0e38f)) bnd = __int_as_float(0x7f800000);   // inf or NaN: flagged below
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bnd = fmaxf(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(&s_bmax[comp], __float_as_int(bnd));
-        __syncthreads();   // also: the buffers are zero
-        const float bm = __int_as_float(s_bmax[comp]);
-        if (!(bm <= 3.0e38f)) {
-          if (threadIdx.x == 0) atomicOr(T.err, ERR_NONFINITE);
-          continue;   // uniform over the block
-        }
-        if (bm == 0.f) continue;   // nothing to spread for this component
-        // scale 2^k with bm * 2^k < 2^38
-        const int k = min(38 - (ilogbf(bm) + 1), 120);
-        if (mine && coef != 0.f)
-          mls_spread_fixed(s_hiw, s_low, SR.at(cc), X, Y, Z, coef * pow2f(k));
         __syncthreads();
-        const float inv_scale = pow2f(-k);
+        float* fa = c0 == 0 ? fx : fz;
         for (int q = threadIdx.x; q < ngroups; q += blockDim.x) {
-          const int4 h = reinterpret_cast<const int4*>(s_hiw)[q];
-          const int4 l = reinterpret_cast<const int4*>(s_low)[q];
-          if ((h.x | h.y | h.z | h.w | l.x | l.y | l.z | l.w) == 0) continue;
-          const float4 val = make_float4(fmaf((float)h.x, 65536.f, (float)l.x) * inv_scale,
-                                         fmaf((float)h.y, 65536.f, (float)l.y) * inv_scale,
-                                         fmaf((float)h.z, 65536.f, (float)l.z) * inv_scale,
-                                         fmaf((float)h.w, 65536.f, (float)l.w) * inv_scale);
-          reinterpret_cast<int4*>(s_hiw)[q] = make_int4(0, 0, 0, 0);
-          reinterpret_cast<int4*>(s_low)[q] = make_int4(0, 0, 0, 0);
+          const int4 a = reinterpret_cast<const int4*>(accA)[q];
+          const int4 b = nc == 2 ? reinterpret_cast<const int4*>(accB)[q] : make_int4(0, 0, 0, 0);
+          const bool na = (a.x | a.y | a.z | a.w) != 0, nb = (b.x | b.y | b.z | b.w) != 0;
+          if (!na && !nb) continue;
+          if (na) reinterpret_cast<int4*>(accA)[q] = make_int4(0, 0, 0, 0);
+          if (nb) reinterpret_cast<int4*>(accB)[q] = make_int4(0, 0, 0, 0);
+          const float4 va = make_float4((float)a.x * inv[0], (float)a.y * inv[0], (float)a.z * inv[0],
+                                        (float)a.w * inv[0]);
+          const float4 vb = make_float4((float)b.x * inv[1], (float)b.y * inv[1], (float)b.z * inv[1],
+                                        (float)b.w * inv[1]);
           if (vec4) {
-            atomicAdd(reinterpret_cast<float4*>(fc + RT.node(q, 0)), val);
+            if (na) atomicAdd(reinterpret_cast<float4*>(fa + RT.node(q, 0)), va);
+            if (nb) atomicAdd(reinterpret_cast<float4*>(fy + RT.node(q, 0)), vb);
           } else {
-            if (val.x != 0.f) atomicAdd(fc + RT.node(q, 0), val.x);
-            if (val.y != 0.f) atomicAdd(fc + RT.node(q, 1), val.y);
-            if (val.z != 0.f) atomicAdd(fc + RT.node(q, 2), val.z);
-            if (val.w != 0.f) atomicAdd(fc + RT.node(q, 3), val.w);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const size_t o = RT.node(q, jj);
+              const float xa = jj == 0 ? va.x : (jj == 1 ? va.y : (jj == 2 ? va.z : va.w));
+              const float xb = jj == 0 ? vb.x : (jj == 1 ? vb.y : (jj == 2 ? vb.z : vb.w));
+              if (xa != 0.f) atomicAdd(fa + o, xa);
+              if (xb != 0.f) atomicAdd(fy + o, xb);
+            }
           }
           const int r = s_grow[q];
           atomicMin(&s_nzlo[r], q);
           atomicMax(&s_nzhi[r], q);
         }
-        __syncthreads();   // buffers zero again before the next component
-      } else if (mine) {
-        mls_spread(fc, GR.at(cc), X, Y, Z, coef);
+        __syncthreads();   // buffers zero again before the next pass
       }
     }
     if (record) {
@@ -665,7 +692,7 @@ cudaError_t launch_t(ibm_ctx* c, const float* x, const float* v, const float* u,
                    aligned16(fx) && aligned16(fy) && aligned16(fz);
   marker_kernel<M, I, P, S, R><<<c->n_chunks, kMT, smem, c->stream>>>(
       c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, pr, accel, U, Fm,
-      Fm_in, Fext, fx, fy, fz, record, vec4, c->td, tmode);
+      Fm_in, Fext, fx, fy, fz, record, vec4, c->td, tmode, c->phi_bound);
   return cudaGetLastError();
 }
 

@@ -341,6 +341,27 @@ __device__ __forceinline__ void mls_spread_fixed(int* hi, int* lo, const RowAcc&
   }
 }
 
+// Spread in exact fixed point, one 32-bit word per node: the contribution
+// coef*phi, already scaled by the block's power of two so that
+// |value| < 2^22, rounded to an integer and added with a native shared
+// atomic; a node receives at most kMT contributions, so the word does not
+// overflow, and the sum is independent of the order of the additions.
+__device__ __forceinline__ void mls_spread_fixed1(int* acc, const RowAcc& A, const DirW& X,
+                                                  const DirW& Y, const DirW& Z, float coef) {
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz) {
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      const int r = A.row(sy, sz);
+      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
+      const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
+#pragma unroll
+      for (int sx = 0; sx < 3; ++sx)
+        atomicAdd(acc + r + sx, __float2int_rn((X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1));
+    }
+  }
+}
+
 // x (|x| < 2^62) rounded to a 64-bit integer without a 64-bit conversion:
 // hi = floor(x / 2^32) is exact and the remainder x - 2^32 hi lies in [0, 2^32)
 __device__ __forceinline__ long long to_fixed(float x) {
