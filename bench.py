@@ -664,6 +664,33 @@ def run_gb300(args, ws, rank, local):
                                  "phases_ms": dict(zip(PHASES, map(float, ph2))),
                                  "roofline": roof2}
         ctx2.close()
+    if not args.no_variants and ws == 1 and args.workload == "drops1000" and not args.bodies:
+        # what the float32 closed form of the MLS moment solve saves: the
+        # interpolation and probe traction of every marker, closed form in
+        # float32 against the general 4x4 solve and geometry in float64
+        ctx3 = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
+                            patch_size=patch, device=local)
+        xa, va = ctx3.init_state()
+        va.uniform_(-0.1, 0.1)
+        times = {}
+        for name, fn in (("fp32_closed_form", ctx3.interpolate), ("fp64_general", ctx3.interpolate_fp64)):
+            fn(xa, va, fields)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(3):
+                flush.zero_()
+                ev0.record(stream)
+                fn(xa, va, fields)
+                ev1.record(stream)
+                ev1.synchronize()
+                tot += ev0.elapsed_time(ev1)
+            times[name] = tot / 3
+        ctx3.check_device_error()
+        ctx3.close()
+        line["mls_precision"] = {"interpolate_ms": times,
+                                 "fp64_over_fp32": times["fp64_general"] / times["fp32_closed_form"],
+                                 "what": "U, F_marker and the probe traction of every marker "
+                                         "(ibm_interpolate vs ibm_interpolate_fp64)"}
     if not args.no_extra and ws == 1 and args.workload == "drops1000" and not args.bodies:
         del fields, f
         torch.cuda.empty_cache()

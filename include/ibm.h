@@ -180,6 +180,16 @@ ibm_status ibm_interpolate(ibm_ctx* ctx, const float* x, const float* v, const f
                            const float* vv, const float* w, const float* p, const float* accel,
                            float* U, float* F_marker, float* F_ext);
 
+/* The same as ibm_interpolate without pressure, with the MLS shape functions
+ * of Eqs. mls_A..mls_Q from the general 4x4 moment system, factorised by LU
+ * with partial pivoting, and the face geometry, both in float64 on the GPU
+ * (the marker kernels use the exact closed form of the factorised weight in
+ * float32).  It serves to measure the accuracy and the cost of that choice;
+ * outputs are float32 [3][F], each may be NULL. */
+ibm_status ibm_interpolate_fp64(ibm_ctx* ctx, const float* x, const float* v, const float* u,
+                                const float* vv, const float* w, float* U, float* F_marker,
+                                float* F_ext);
+
 /* (c) Node update with F_ext^v = sum over faces of F_ext/3 (Sec. 2.3) and the
  * given F_int: symplectic (default) or forward Euler; clamped nodes keep x and
  * get v = 0.  x_out/v_out may alias x/v. */

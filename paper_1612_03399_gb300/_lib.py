@@ -60,6 +60,7 @@ SIGNATURES = {
     "ibm_body_measures": (C.c_int, [P, P, P]),
     "ibm_compute_forces": (C.c_int, [P, P, P, P]),
     "ibm_interpolate": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P]),
+    "ibm_interpolate_fp64": (C.c_int, [P, P, P, P, P, P, P, P, P]),
     "ibm_advance": (C.c_int, [P, P, P, P, P, P, P]),
     "ibm_spread": (C.c_int, [P, P, P, P, P, P]),
     "ibm_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
@@ -247,6 +248,17 @@ class Context:
         Fe = self._vec(self.F) if F_ext else None
         self._check(self.lib.ibm_interpolate(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
                                              _ptr(p), _ptr(accel), _ptr(Uo), _ptr(Fm), _ptr(Fe)))
+        return Uo, Fm, Fe
+
+    def interpolate_fp64(self, x, v, fields, U=True, F_marker=True, F_ext=True):
+        """(U, F_marker, F_ext) per face with the float64 general moment solve
+        (ibm_interpolate_fp64; no pressure)."""
+        u, vv, w = fields
+        Uo = self._vec(self.F) if U else None
+        Fm = self._vec(self.F) if F_marker else None
+        Fe = self._vec(self.F) if F_ext else None
+        self._check(self.lib.ibm_interpolate_fp64(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv),
+                                                  _ptr(w), _ptr(Uo), _ptr(Fm), _ptr(Fe)))
         return Uo, Fm, Fe
 
     def advance(self, x, v, F_int, F_ext, x_out=None, v_out=None):

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libibm_gb300.so")
-SOURCES = ["ibm_host.cu", "k_mls.cu", "k_tile.cu", "k_force.cu", "k_adjoint.cu", "k_taylor.cu",
+SOURCES = ["ibm_host.cu", "k_mls.cu", "k_mls64.cu", "k_tile.cu", "k_force.cu", "k_adjoint.cu", "k_taylor.cu",
            "ibm_noalloc.cu", "ibm_gts.cu", "k_pc.cu", "ibm_flow.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]

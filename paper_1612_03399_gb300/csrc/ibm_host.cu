@@ -664,6 +664,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
         const double o = Bd.origin[d] / h[d];
         const double Gd = std::floor(o);
         R.frac[d] = (float)(o - Gd);
+        R.fracd[d] = o - Gd;
         long long Gi = (long long)Gd % grid->n[d];
         if (Gi < 0) Gi += grid->n[d];
         R.G[d] = (int32_t)Gi;
@@ -987,6 +988,16 @@ extern "C" ibm_status ibm_interpolate(ibm_ctx* c, const float* x, const float* v
   cudaError_t e = launch_mls(c, x, v, u, vv, w, p, accel, U, Fm, nullptr, Fext, nullptr, nullptr,
                              nullptr, false, interp, probe, false, false);
   return cuda_status(c, e, "ibm_interpolate");
+}
+
+extern "C" ibm_status ibm_interpolate_fp64(ibm_ctx* c, const float* x, const float* v,
+                                           const float* u, const float* vv, const float* w,
+                                           float* U, float* Fm, float* Fext) {
+  if (!c || !x || !u || !vv || !w) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (Fm && !v) return set_err(c, IBM_ERR_INVALID_ARG, "F_marker needs the vertex velocities");
+  if (!U && !Fm && !Fext) return IBM_OK;
+  cudaSetDevice(c->device);
+  return cuda_status(c, launch_interp64(c, x, v, u, vv, w, U, Fm, Fext), "ibm_interpolate_fp64");
 }
 
 extern "C" ibm_status ibm_advance(ibm_ctx* c, const float* x, const float* v, const float* F_int,

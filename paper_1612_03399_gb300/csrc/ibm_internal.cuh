@@ -26,6 +26,7 @@ struct BodyDev {
   int32_t work_off;                    // first force-kernel work item (patch) of this body
   int32_t pad1;
   double A0, V0;                       // rest area and volume (float64)
+  double fracd[3];                     // frac in float64 (the float64 interpolation option)
   // Exact fixed-point body sums: a face's area (volume) contributes
   // q = rint(value * sA) (sV), a power of two chosen from A0 (V0), and the
   // q are summed with 64-bit integer atomics, independent of order.
@@ -332,6 +333,10 @@ cudaError_t launch_backward(ibm_ctx* c, const float* x, const float* v, const fl
                             const float* gfy, const float* gfz, float* gx, float* gv,
                             double* gparams);
 cudaError_t launch_taylor(ibm_ctx* c, const float* x, double* D);
+// interpolation at the centroids and probe traction with the general MLS
+// moment solve and the face geometry in float64 (k_mls64.cu)
+cudaError_t launch_interp64(ibm_ctx* c, const float* x, const float* v, const float* u,
+                            const float* vv, const float* w, float* U, float* Fm, float* Fext);
 cudaError_t launch_taylor_backward(ibm_ctx* c, const float* x, const double* gD, float* gx);
 cudaError_t set_force_smem_limit(size_t bytes);
 cudaError_t set_adjoint_smem_limit(size_t bytes);
