@@ -538,6 +538,31 @@ def extra_workload(args, name, variant, device, flush, peak, peak_kind, patch):
     return out
 
 
+def differentiation_workload(device):
+    """The differentiation configuration: 256 icosphere-L4 drops in linear
+    shear on 256^3, 50 steps with a checkpoint every 10, loss sum over drops
+    of (D - D*)^2; one calibration iteration = 50 forward, 50 recomputed and
+    50 adjoint steps and the Taylor-deformation adjoint (torch.autograd over
+    ibm_step / ibm_backward / ibm_taylor_backward).  Wall time per iteration
+    after a first one."""
+    from paper_1612_03399_gb300.autograd import Simulation
+    from paper_1612_03399_gb300.calibrate import calibrate
+    wl = W.shear_drops(256, 4, 256)
+    sim = Simulation(wl.bodies, wl.grid, wl.field, dt=1e-3, mu=1.0, device=device.index)
+    x0, v0 = sim.ctx.init_state()
+    n_steps = 50
+    _, hist = calibrate(sim, x0, v0, wl.notes["D_target"], n_steps, 10, iters=4, lr=0.1)
+    secs = [h["seconds"] for h in hist[1:]]
+    per = statistics.median(secs)
+    out = {"workload": "256 icosphere-L4 drops (2562 nodes each), r = 0.04, linear shear, 256^3 "
+                       "grid; 50 steps, checkpoint every 10; loss sum (D - D*)^2, D* ~ U[0.05, 0.3]",
+           "bodies": sim.ctx.B, "vertices": sim.ctx.V, "seconds_per_iteration": per,
+           "forward_node_steps_per_s_through_fwd_bwd": sim.ctx.V * n_steps / per,
+           "losses": [h["loss"] for h in hist]}
+    sim.ctx.close()
+    return out
+
+
 def run_gb300(args, ws, rank, local):
     from paper_1612_03399_gb300 import _lib
     device = torch.device("cuda", local)
@@ -697,6 +722,7 @@ def run_gb300(args, ws, rank, local):
         line["extra_workloads"] = {
             name: extra_workload(args, name, variant, device, flush, peak, peak_kind, patch)
             for name in ("uneven4096", "membranes")}
+        line["extra_workloads"]["differentiation"] = differentiation_workload(device)
         fields = None
     if not args.no_cpu_baseline and ws == 1:
         if fields is None:

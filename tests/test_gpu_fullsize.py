@@ -69,11 +69,14 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_full_size_step_sampled_parity(case, record_error):
+def test_full_size_step_sampled_parity(case, variant, record_error):
+    """Both spread variants: patch-owned with atomics (1), tile-owned (2)."""
     make, pick_fn, vmax, patch = CASES[case]
     wl = make()
-    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha, patch_size=patch)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha, patch_size=patch,
+                       spread_variant=variant)
     fields = H.fields_for(wl, DEV)
     x, v = ctx.init_state()
     rng = np.random.default_rng(0)
@@ -99,7 +102,7 @@ def test_full_size_step_sampled_parity(case, record_error):
     rhs = (A[None, :] * hl * Fm.double()).sum(1)
     lhs = torch.stack([fi.double().sum() for fi in f]) * dV
     cons = float((lhs - rhs).abs().max() / rhs.abs().max())
-    record_error(f"{case}:conservation", cons)
+    record_error(f"{case}:v{variant}:conservation", cons)
     assert cons <= 1e-5
     # sampled bodies, recomputed by the oracle alone
     pick = pick_fn(wl)
@@ -123,14 +126,14 @@ def test_full_size_step_sampled_parity(case, record_error):
         assert H.rel_l2(xg[i], xo) <= 1e-6
         keep = np.ones(len(xo), dtype=bool)
         keep[wl.bodies[i].tri[ties[j]["probe"]].ravel()] = False
-        record_error(f"{case}:dv_excluded_fraction[{i}]", 1.0 - keep.mean())
+        record_error(f"{case}:v{variant}:dv_excluded_fraction[{i}]", 1.0 - keep.mean())
         assert keep.mean() > 0.99
         vo = out["v_next"][j].numpy()[keep]
         v0 = vs[j].numpy()[keep]
         dv_o = vo - v0
         store = np.linalg.norm(0.5 * np.spacing(np.abs(vo).astype(np.float32)).astype(np.float64))
         excess = max(0.0, np.linalg.norm((vg[i][keep] - v0) - dv_o) - store) / np.linalg.norm(dv_o)
-        record_error(f"{case}:dv[{i}]", excess)
+        record_error(f"{case}:v{variant}:dv[{i}]", excess)
         assert excess <= 1e-5
     fo = out["f"].numpy()
     mask = np.abs(fo).sum(0) > 0
@@ -141,8 +144,8 @@ def test_full_size_step_sampled_parity(case, record_error):
             lo = np.floor(t).astype(int) - 2
             ix, iy, iz = (np.arange(lo[d], lo[d] + 5) % n[d] for d in range(3))
             mask[np.ix_(iz, iy, ix)] = False
-    record_error(f"{case}:f_nodes_compared", float(mask.sum()))
+    record_error(f"{case}:v{variant}:f_nodes_compared", float(mask.sum()))
     got = torch.stack(f).cpu().numpy()
     e = H.rel_l2(got[:, mask], fo[:, mask])
-    record_error(f"{case}:f_sampled", e)
+    record_error(f"{case}:v{variant}:f_sampled", e)
     assert e <= 1e-5
