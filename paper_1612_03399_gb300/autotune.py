@@ -13,7 +13,7 @@ import torch
 
 from . import _lib
 
-CANDIDATES = (64, 96, 128, 192, 256, 320, 384, 512)
+CANDIDATES = (96, 128, 160, 192, 224, 256, 320, 384)
 
 
 def autotune_patch_size(bodies, grid, fields, dt=1e-3, mu=1.0, alpha=0.3, device=0,

@@ -51,6 +51,10 @@ struct HostTopo {
   std::vector<PFace> pface;
   std::vector<int32_t> csr_ptr;
   std::vector<uint16_t> csr_slot;
+  std::vector<uint32_t> fblob;          // packed element records of the force kernel
+  std::vector<FPatch> fpatch;           //   (one 16-byte aligned blob per patch)
+  std::vector<int32_t> fatt;            // per face: 2 * attached edge + side (1: right face)
+  std::vector<int32_t> fface;           // per patch, its faces in the blob's order
   int max_loc = 0, max_slot = 0, max_own = 0;
   std::vector<int32_t> mface, mbound;   // faces in marker-patch order, patch boundaries
 };
@@ -134,6 +138,69 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
     v2e[fill[E.y]++] = 4 * e + 1;
     v2e[fill[E.z]++] = 4 * e + 2;
     if (E.w >= 0) v2e[fill[E.w]++] = 4 * e + 3;
+  }
+  // face -> edge attachment of the force kernel: a matching in which every
+  // face holds an edge of its own (it exists: a set of k faces touches at
+  // least 3k/2 edges, each edge having at most two faces), preferring the
+  // edges of which the face is the left face; the rest by augmenting paths.
+  {
+    std::vector<int32_t> fe(3 * (size_t)nf);
+    for (int f = 0; f < nf; ++f)
+      for (int k = 0; k < 3; ++k) {
+        const int p0 = tri[3 * f + k], p1 = tri[3 * f + (k + 1) % 3];
+        fe[3 * f + k] = und.at(key2(std::min(p0, p1), std::max(p0, p1)));
+      }
+    std::vector<int32_t> owner(T.ne, -1), fedge(nf, -1);
+    for (int e = 0; e < T.ne; ++e) {
+      const int f = T.eface[e].x;
+      if (fedge[f] < 0) { fedge[f] = e; owner[e] = f; }
+    }
+    for (int e = 0; e < T.ne; ++e) {
+      const int f = T.eface[e].y;
+      if (f >= 0 && fedge[f] < 0 && owner[e] < 0) { fedge[f] = e; owner[e] = f; }
+    }
+    std::vector<int32_t> seen(nf, -1), from(nf, -1), via(nf, -1), queue;
+    for (int f0 = 0; f0 < nf; ++f0) {
+      if (fedge[f0] >= 0) continue;
+      // breadth-first search for a free edge along alternating paths
+      queue.assign(1, f0);
+      seen[f0] = f0;
+      int end_f = -1, end_e = -1;
+      for (size_t qi = 0; qi < queue.size() && end_f < 0; ++qi) {
+        const int f = queue[qi];
+        for (int k = 0; k < 3 && end_f < 0; ++k) {
+          const int e = fe[3 * f + k];
+          if (owner[e] < 0) {
+            end_f = f;
+            end_e = e;
+          } else if (seen[owner[e]] != f0) {
+            seen[owner[e]] = f0;
+            from[owner[e]] = f;
+            via[owner[e]] = e;
+            queue.push_back(owner[e]);
+          }
+        }
+      }
+      if (end_f < 0) fail(IBM_ERR_MESH, "no face-edge matching (non-manifold mesh)");
+      // flip the path: each face on it takes the edge that led to its successor
+      int f = end_f, e = end_e;
+      while (true) {
+        const int prev_e = fedge[f];
+        fedge[f] = e;
+        owner[e] = f;
+        if (f == f0) break;
+        e = via[f];   // == prev_e: the edge f held, now passed to its predecessor
+        (void)prev_e;
+        f = from[f];
+      }
+    }
+    T.fatt.assign(nf, -1);
+    for (int f = 0; f < nf; ++f) {
+      const int e = fedge[f];
+      if (e < 0 || owner[e] != f || (fe[3 * f] != e && fe[3 * f + 1] != e && fe[3 * f + 2] != e))
+        fail(IBM_ERR_MESH, "face-edge matching failed");
+      T.fatt[f] = 2 * e + (T.eface[e].x == f ? 0 : 1);
+    }
   }
   // patches
   const int npatch = (nv + P - 1) / P;
@@ -226,6 +293,53 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
       }
     }
     T.csr_ptr.push_back((int32_t)T.csr_slot.size() - H.slot_off);
+    // The force kernel's blob of this patch.  Every face is attached to an
+    // edge of its own (as its left face (a, b, c) or its right face (b, a, d))
+    // and adds its corner forces to that edge's role slots, so an own vertex
+    // has one slot per edge role it plays, contiguous and in the order of its
+    // edge list above.  Per edge 4 words (a | b << 16, c | d << 16, slot of a |
+    // slot of b << 16, slot of c | slot of d << 16; kNone for halo vertices);
+    // per face 2 words (edge | side << 30 | owned << 31, face id); then the
+    // first slot of every own vertex (n_own + 1 16-bit entries).
+    {
+      std::vector<uint16_t> dE(4 * es.size(), kNone);
+      std::vector<int32_t> ptr(H.n_own + 1);
+      int32_t n = 0;
+      for (int v = o0; v < o1; ++v) {
+        ptr[v - o0] = n;
+        for (int k = v2e_ptr[v]; k < v2e_ptr[v + 1]; ++k)
+          dE[4 * e_loc[v2e[k] >> 2] + (v2e[k] & 3)] = (uint16_t)n++;
+      }
+      ptr[H.n_own] = n;
+      if (n >= (int)kNone)
+        fail(IBM_ERR_UNSUPPORTED, "patch too large for 16-bit local indices; lower patch_size");
+      FPatch Q{};
+      Q.blob_off = (int32_t)T.fblob.size();
+      Q.n_slot = n;
+      for (size_t i = 0; i < es.size(); ++i) {
+        const PEdge& r = T.pedge[H.edge_off + i];
+        T.fblob.push_back(r.l[0] | (uint32_t)r.l[1] << 16);
+        T.fblob.push_back(r.l[2] | (uint32_t)r.l[3] << 16);
+        T.fblob.push_back(dE[4 * i] | (uint32_t)dE[4 * i + 1] << 16);
+        T.fblob.push_back(dE[4 * i + 2] | (uint32_t)dE[4 * i + 3] << 16);
+      }
+      // faces in the patch's order; their rest data follows the same order
+      const std::vector<int32_t>& fo = fs;
+      for (const int f : fo) {
+        const int e = T.fatt[f] >> 1;
+        if (e_stamp[e] != p) fail(IBM_ERR_MESH, "face attached to an edge outside its patch");
+        const bool owned = tri[3 * f] >= o0 && tri[3 * f] < o1;
+        T.fblob.push_back((uint32_t)e_loc[e] | (uint32_t)(T.fatt[f] & 1) << 30 |
+                          (owned ? 0x80000000u : 0u));
+        T.fblob.push_back((uint32_t)f);
+      }
+      for (size_t i = 0; i < ptr.size(); i += 2)
+        T.fblob.push_back((uint32_t)ptr[i] | (i + 1 < ptr.size() ? (uint32_t)ptr[i + 1] << 16 : 0u));
+      while (T.fblob.size() % 4) T.fblob.push_back(0u);
+      Q.blob_words = (int32_t)T.fblob.size() - Q.blob_off;
+      T.fpatch.push_back(Q);
+      T.fface.insert(T.fface.end(), fo.begin(), fo.end());
+    }
     T.max_loc = std::max(T.max_loc, H.n_loc);
     T.max_slot = std::max(T.max_slot, H.n_slot);
     T.max_own = std::max(T.max_own, H.n_own);
@@ -564,6 +678,9 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     std::vector<uint8_t> clamp(V, 0);
     std::vector<int4> chunks;
     std::vector<int2> work;
+    std::vector<float> frest;        // force-kernel rest data per work item, patch order
+    std::vector<int64_t> wrest;
+    size_t force_smem = 0;
     c->h_body.resize(n_bodies);
     long long vo = 0, fo = 0, eo = 0;
     for (int b = 0; b < n_bodies; ++b) {
@@ -685,7 +802,34 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       for (int k = 0; k < nch; ++k)
         chunks.push_back(make_int4(b, T.mbound[k], T.mbound[k + 1] - T.mbound[k], k));
       R.work_off = (int32_t)work.size();
-      for (int q = 0; q < (int)T.patch.size(); ++q) work.push_back(make_int2(b, q));
+      for (int q = 0; q < (int)T.patch.size(); ++q) {
+        work.push_back(make_int2(b, q));
+        const PatchHdr& H = T.patch[q];
+        const int pe = pad4(H.n_edge), pf = pad4(H.n_face);
+        const size_t r0 = frest.size();
+        wrest.push_back((int64_t)r0);
+        frest.resize(r0 + frest_words(H.n_edge, H.n_face, varied), 0.f);
+        for (int i = 0; i < H.n_edge; ++i) {
+          const long long ge = eo + (T.pedge[H.edge_off + i].eid & 0x7fffffff);
+          frest[r0 + i] = l0[ge];
+          frest[r0 + pe + i] = cs0[ge].x;
+          frest[r0 + 2 * pe + i] = cs0[ge].y;
+          if (varied) {
+            frest[r0 + 3 * pe + pf + i] = kse[ge];
+            frest[r0 + 4 * pe + pf + i] = kbe[ge];
+          }
+        }
+        for (int i = 0; i < H.n_face; ++i) {
+          const long long gf = fo + T.fface[H.face_off + i];
+          frest[r0 + 3 * pe + i] = A0f[gf];
+          if (varied) frest[r0 + 5 * pe + pf + i] = kaf[gf];
+        }
+        // shared memory of the block: blob, rest data, positions, slots
+        const FPatch& Q = T.fpatch[q];
+        force_smem = std::max(force_smem,
+                              sizeof(float) * ((size_t)Q.blob_words + frest_words(H.n_edge, H.n_face, varied) +
+                                               3 * (size_t)pad4(H.n_loc) + 3 * (size_t)pad4(Q.n_slot)));
+      }
       vo += Bd.n_vert;
       fo += Bd.n_face;
       eo += T.ne;
@@ -702,6 +846,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     std::vector<PEdge> pedge_all;
     std::vector<PFace> pface_all;
     std::vector<uint16_t> slot_all;
+    std::vector<uint32_t> fblob_all;
+    std::vector<FPatch> fpatch_all;
     int max_loc = 0, max_slot = 0, max_own = 0;
     for (size_t t = 0; t < topos.size(); ++t) {
       const HostTopo& T = topos[t];
@@ -741,11 +887,20 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
       pface_all.insert(pface_all.end(), T.pface.begin(), T.pface.end());
       csr_all.insert(csr_all.end(), T.csr_ptr.begin(), T.csr_ptr.end());
       slot_all.insert(slot_all.end(), T.csr_slot.begin(), T.csr_slot.end());
+      const int32_t bo = (int32_t)fblob_all.size();
+      for (FPatch Q : T.fpatch) {
+        Q.blob_off += bo;
+        fpatch_all.push_back(Q);
+      }
+      fblob_all.insert(fblob_all.end(), T.fblob.begin(), T.fblob.end());
       max_loc = std::max(max_loc, T.max_loc);
       max_slot = std::max(max_slot, T.max_slot);
       max_own = std::max(max_own, T.max_own);
     }
-    c->force_smem = sizeof(float) * 3 * ((size_t)max_loc + (size_t)max_slot);
+    (void)max_slot;
+    c->force_smem = force_smem;
+    if (c->force_smem > 227 * 1024)
+      fail(IBM_ERR_UNSUPPORTED, "force-kernel shared memory above 227 KB; lower patch_size");
     c->adjoint_smem = sizeof(float) * (6 * (size_t)max_loc + 3 * (size_t)max_slot);
     c->max_own = max_own;
     if (c->adjoint_smem > 227 * 1024)
@@ -768,6 +923,10 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     d.pface = upload(c, pface_all);
     d.csr_ptr = upload(c, csr_all);
     d.csr_slot = upload(c, slot_all);
+    d.fblob = upload(c, fblob_all);
+    d.fpatch = upload(c, fpatch_all);
+    d.frest = upload(c, frest);
+    d.wrest = upload(c, wrest);
     d.l0 = upload(c, l0);
     d.cs0 = upload(c, cs0);
     d.A0f = upload(c, A0f);

@@ -69,6 +69,26 @@ struct PFace {
   int32_t fid;         // body-local face id
 };
 
+// The force kernel's own packed copy of a patch's element records, moved into
+// shared memory with one bulk copy (16-byte aligned, whole 16-byte units):
+// 4 words per edge, 2 per face (each face attached to an edge of its own),
+// then the first contribution slot of every own vertex (16 bits); its rest data
+// (per work item: rest lengths, cos and sin of the rest angles, rest face
+// areas, and the element multipliers of a varied body, in the patch's edge and
+// face order) with a second one.
+struct FPatch {
+  int32_t blob_off;      // word offset in fblob (a multiple of 4)
+  int32_t blob_words;    // 4 n_edge + 2 n_face + (n_own + 2) / 2, rounded up to a multiple of 4
+  int32_t n_slot;        // contributions to the own vertices (one per edge role)
+  int32_t pad;
+};
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
+// rest words of a work item: l0, cos0, sin0 (pad4(n_edge) each), A0f
+// (pad4(n_face)); a varied body adds kse, kbe and kaf
+__host__ __device__ constexpr int frest_words(int n_edge, int n_face, bool varied) {
+  return (varied ? 5 : 3) * pad4(n_edge) + (varied ? 2 : 1) * pad4(n_face);
+}
+
 struct Grid {
   int32_t n[3];
   float h[3], invh[3];
@@ -159,6 +179,10 @@ struct DeviceTables {
   PFace* pface = nullptr;
   int32_t* csr_ptr = nullptr;
   uint16_t* csr_slot = nullptr;
+  uint32_t* fblob = nullptr;    // force-kernel element blobs (FPatch)
+  FPatch* fpatch = nullptr;     // per topology patch, indexed like `patch`
+  float* frest = nullptr;       // rest data of every work item, in patch order
+  int64_t* wrest = nullptr;     // [n_work] word offset of the work item's rest data
   float* l0 = nullptr;          // [E] rest edge lengths
   float2* cs0 = nullptr;        // [E] (cos theta0, sin theta0) per hinge edge
   float* A0f = nullptr;         // [F] rest face areas

@@ -4,24 +4,18 @@
 // One block per patch (a contiguous range of a topology's vertices).  The
 // block stages the positions of its own and halo vertices in shared memory,
 // evaluates every element touching an own vertex exactly once into
-// shared-memory contribution slots (4 per edge: a, b and the wings c, d; 3 per
-// face), and each own vertex then sums its slots through a CSR list fixed at
-// build time.  The summation order never changes, so F_int is bitwise
-// deterministic; nothing is written to global memory but the result.
+// shared-memory contribution slots, and each own vertex then sums its slots,
+// which are contiguous and in an order fixed at build time.  The summation
+// order never changes, so F_int is bitwise deterministic; nothing is written
+// to global memory but the result.
 //
-// Edge e = (a, b) with wings c (face (a, b, c)) and d (face (b, a, d)):
-//   spring   W = k_s/2 (l - l0)^2      F_a = k_s (l - l0) e/l, F_b = -F_a
-//   bending  W = k_b (1 - cos(theta - theta0)),  F = -k_b sin(theta - theta0) grad theta,
-//            cos theta = n1.n2, sin theta = (n1 x n2).e/|e|, and with
-//            N1 = e x (c - a), N2 = (d - b) x e, s_c = (c - a).e/|e|^2, s_d likewise,
-//            grad_c theta = -|e| N1/|N1|^2, grad_d theta = -|e| N2/|N2|^2,
-//            grad_a theta = -(1 - s_c) grad_c - (1 - s_d) grad_d,
-//            grad_b theta = -s_c grad_c - s_d grad_d
-//            (the unique gradient that is invariant under translations and
-//            rotations and moves the wings about the hinge).
-// Face (a, b, c), A_f = |N|/2, n = N/|N|:
-//   grad_a A_f = n x (c - b)/2 (cyclic), grad_a V = b x c / 6 (cyclic, body frame),
-//   F = -(k_A (A - A0)/A0 + k_a (A_f - A0_f)/A0_f) grad A_f - k_v (V - V0)/V0 grad V.
+// The patch's element records (with the slot each role writes) and its rest
+// data arrive in shared memory with two bulk copies completing on an
+// mbarrier, issued first; the position gather runs meanwhile.  After that the
+// element loops read shared memory only, so a block waits on global memory
+// about three times (positions, the marker kernel's traction, the velocities),
+// not once per element.
+//
 #include <cuda_runtime.h>
 
 #include "force_elems.cuh"
@@ -34,9 +28,16 @@ struct Smem {
   float *px, *py, *pz, *cx, *cy, *cz;
   __device__ Vec<float> pos(int i) const { return {px[i], py[i], pz[i]}; }
   __device__ void put(int s, const Vec<float>& f) const {
+    if (s == kNone) return;
     cx[s] = f.x;
     cy[s] = f.y;
     cz[s] = f.z;
+  }
+  __device__ void add(int s, const Vec<float>& f) const {
+    if (s == kNone) return;
+    cx[s] += f.x;
+    cy[s] += f.y;
+    cz[s] += f.z;
   }
 };
 
@@ -46,6 +47,50 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// mbarrier and bulk-copy primitives (PTX, sm_90 and later)
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  // the initialisation is visible to the bulk-copy unit before its first use
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(r)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return r != 0;
+}
+// wait for phase 0 of the barrier, at most about `limit` SM clocks
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, 0)) {
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+constexpr long long kCopyWaitClocks = 1ll << 31;   // about a second
+
 // MODE 0: F_int only; 1: F_int + F_ext^v and the node update; 2: the
 // acceleration (F_int + F_ext^v)/m, zero on clamped nodes, into Fint
 template <int MODE>
@@ -53,53 +98,96 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
     DeviceTables T, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ v, const float* __restrict__ Fext, float* __restrict__ Fint,
     float* __restrict__ x_out, float* __restrict__ v_out, double* __restrict__ energy) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
+  __shared__ __align__(8) unsigned long long bar;
   const int2 wk = T.work[blockIdx.x];
   const BodyDev B = T.body[wk.x];
   const TopoDev topo = T.topo[B.topo];
   const PatchHdr P = T.patch[topo.patch_off + wk.y];
+  const FPatch Q = T.fpatch[topo.patch_off + wk.y];
+  const int pe = pad4(P.n_edge), pf = pad4(P.n_face);
+  const int rest_words = frest_words(P.n_edge, P.n_face, B.varied != 0);
+  const uint4* rec = reinterpret_cast<const uint4*>(sm);                   // edges
+  const uint2* frec = reinterpret_cast<const uint2*>(sm + 4 * P.n_edge);   // faces
+  const uint16_t* ptr = reinterpret_cast<const uint16_t*>(sm + 4 * P.n_edge + 2 * P.n_face);
+  const float* rest = sm + Q.blob_words;
   Smem S;
-  S.px = sm;
-  S.py = S.px + P.n_loc;
-  S.pz = S.py + P.n_loc;
-  S.cx = S.pz + P.n_loc;
-  S.cy = S.cx + P.n_slot;
-  S.cz = S.cy + P.n_slot;
+  S.px = sm + Q.blob_words + rest_words;
+  S.py = S.px + pad4(P.n_loc);
+  S.pz = S.py + pad4(P.n_loc);
+  S.cx = S.pz + pad4(P.n_loc);
+  S.cy = S.cx + pad4(Q.n_slot);
+  S.cz = S.cy + pad4(Q.n_slot);
 
-  for (int i = threadIdx.x; i < P.n_loc; i += blockDim.x) {
-    const int gv = B.v_off + __ldg(T.loc_vert + P.loc_off + i);
-    S.px[i] = __ldg(x + gv);
-    S.py[i] = __ldg(x + V + gv);
-    S.pz[i] = __ldg(x + 2 * V + gv);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    const unsigned nb = 4u * (unsigned)Q.blob_words, nr = 4u * (unsigned)rest_words;
+    mbar_arrive_tx(&bar, nb + nr);
+    if (nb) bulk_load(sm, T.fblob + Q.blob_off, nb, &bar);
+    if (nr) bulk_load(sm + Q.blob_words, T.frest + T.wrest[blockIdx.x], nr, &bar);
+  }
+  // meanwhile: positions of the own and halo vertices, two per thread in flight
+  for (int i = threadIdx.x; i < P.n_loc; i += 2 * blockDim.x) {
+    const int j = i + blockDim.x;
+    const int gi = B.v_off + __ldg(T.loc_vert + P.loc_off + i);
+    const int gj = j < P.n_loc ? B.v_off + __ldg(T.loc_vert + P.loc_off + j) : gi;
+    const float xi = __ldg(x + gi), yi = __ldg(x + V + gi), zi = __ldg(x + 2 * V + gi);
+    const float xj = __ldg(x + gj), yj = __ldg(x + V + gj), zj = __ldg(x + 2 * V + gj);
+    S.px[i] = xi;
+    S.py[i] = yi;
+    S.pz[i] = zi;
+    if (j < P.n_loc) {
+      S.px[j] = xj;
+      S.py[j] = yj;
+      S.pz[j] = zj;
+    }
+  }
+  // and the velocity and clamp flag of the thread's first own vertex
+  float pv[3] = {0.f, 0.f, 0.f};
+  bool pcl = false;
+  if (MODE == 1 && (int)threadIdx.x < P.n_own) {
+    const int gv = B.v_off + P.own0 + threadIdx.x;
+    pv[0] = __ldg(v + gv);
+    pv[1] = __ldg(v + V + gv);
+    pv[2] = __ldg(v + 2 * V + gv);
+    pcl = T.clamp[gv] != 0;
   }
   const bool want_e = energy != nullptr;
   double eS = 0.0, eB = 0.0, eA = 0.0;
-  __syncthreads();
+  __syncthreads();   // positions staged, barrier initialised
+  if (!__syncthreads_and(mbar_wait(&bar, kCopyWaitClocks))) {
+    // the copies did not land: flag it, give them one more bounded wait
+    // (they write this block's shared memory) and leave
+    if (threadIdx.x == 0) {
+      atomicOr(T.err, ERR_TIMEOUT);
+      mbar_wait(&bar, kCopyWaitClocks);
+    }
+    __syncthreads();
+    return;
+  }
 
-  // edges: spring + bending
+  // edges: spring + bending, from shared memory only
   for (int k = threadIdx.x; k < P.n_edge; k += blockDim.x) {
-    const PEdge r = T.pedge[P.edge_off + k];
-    const int ge = B.e_off + (r.eid & 0x7fffffff);
-    const bool hinge = r.l[3] != kNone;
-    const Vec<float> pa = S.pos(r.l[0]), pb = S.pos(r.l[1]);
-    const Vec<float> pc = hinge ? S.pos(r.l[2]) : pa, pd = hinge ? S.pos(r.l[3]) : pb;
-    const float2 cs0 = hinge ? __ldg(T.cs0 + ge) : make_float2(1.f, 0.f);
+    const uint4 r = rec[k];
+    const int la = r.x & 0xFFFF, lb = r.x >> 16, lc = r.y & 0xFFFF, ld = r.y >> 16;
+    const bool hinge = ld != kNone;
+    const Vec<float> pa = S.pos(la), pb = S.pos(lb);
+    const Vec<float> pc = hinge ? S.pos(lc) : pa, pd = hinge ? S.pos(ld) : pb;
+    const float c0 = hinge ? rest[pe + k] : 1.f, s0 = hinge ? rest[2 * pe + k] : 0.f;
     Vec<float> fa, fb, fc, fd, us[2], ub[4];
     float es, eb;
     // per-edge constants (van Gelder springs, materials) where the body has them
-    const float ks = B.varied ? B.ks * __ldg(T.kse + ge) : B.ks;
-    const float kb = B.varied ? B.kb * __ldg(T.kbe + ge) : B.kb;
-    edge_forces(pa, pb, pc, pd, hinge, __ldg(T.l0 + ge), cs0.x, cs0.y, ks, kb, fa, fb, fc, fd, us,
-                ub, es, eb);
-    if (want_e && (r.eid < 0)) {
+    const float ks = B.varied ? B.ks * rest[3 * pe + pf + k] : B.ks;
+    const float kb = B.varied ? B.kb * rest[4 * pe + pf + k] : B.kb;
+    edge_forces(pa, pb, pc, pd, hinge, rest[k], c0, s0, ks, kb, fa, fb, fc, fd, us, ub, es, eb);
+    if (want_e && (r.z & 0xFFFF) != kNone) {   // the patch of vertex a owns the edge
       eS += (double)es;
       eB += (double)eb;
     }
-    // slot layout [role][element]: consecutive threads hit consecutive banks
-    S.put(k, fa);
-    S.put(P.n_edge + k, fb);
-    S.put(2 * P.n_edge + k, fc);
-    S.put(3 * P.n_edge + k, fd);
+    S.put(r.z & 0xFFFF, fa);
+    S.put(r.z >> 16, fb);
+    S.put(r.w & 0xFFFF, fc);
+    S.put(r.w >> 16, fd);
   }
   // Everything above reads only static tables and positions written two
   // launches back; the marker kernel launched just before (it lets this grid
@@ -110,38 +198,59 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
   // fixed-point area / volume sums
   const float2 cf = body_coef(B, __ldg(T.qsum + 2 * wk.x), __ldg(T.qsum + 2 * wk.x + 1));
   const float cA = cf.x, cV = cf.y;
-  // faces: local area, global area, volume
-  const int fbase = 4 * P.n_edge;
-  for (int k = threadIdx.x; k < P.n_face; k += blockDim.x) {
-    const PFace r = T.pface[P.face_off + k];
-    Vec<float> f[3], gA[3], gV[3], ua[3];
-    float ea;
-    const float ka = B.varied ? B.ka * __ldg(T.kaf + B.f_off + r.fid) : B.ka;
-    face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid), ka,
-                cA, cV, f, gA, gV, ua, ea);
+  __syncthreads();   // every edge slot written
+  // faces: local area, global area, volume, added to the slots of the edge
+  // each face is attached to (an edge per face: no two threads touch the same
+  // slot); two faces per thread with their tractions in flight
+  const float third = 1.f / 3.f;
+  for (int k0 = threadIdx.x; k0 < P.n_face; k0 += 2 * blockDim.x) {
+    const int k1 = k0 + blockDim.x;
+    const bool two = k1 < P.n_face;
+    const uint2 r0 = frec[k0];
+    const uint2 r1 = two ? frec[k1] : r0;
+    Vec<float> fe0 = {0.f, 0.f, 0.f}, fe1 = {0.f, 0.f, 0.f};
     if (MODE != 0) {
       // F_ext^v = sum over the vertex's faces of F_ext / 3: each face adds a
-      // third of its load to its corner slots, gathered with the forces
-      const int gf = B.f_off + r.fid;
-      const float third = 1.f / 3.f;
-      const Vec<float> fe = {__ldg(Fext + gf) * third, __ldg(Fext + F + gf) * third,
-                             __ldg(Fext + 2 * F + gf) * third};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) f[c] = vadd(f[c], fe);
+      // third of its load to its corners, gathered with the forces
+      const int g0 = B.f_off + (int)r0.y, g1 = B.f_off + (int)r1.y;
+      fe0 = {__ldg(Fext + g0), __ldg(Fext + F + g0), __ldg(Fext + 2 * F + g0)};
+      fe1 = {__ldg(Fext + g1), __ldg(Fext + F + g1), __ldg(Fext + 2 * F + g1)};
     }
-    S.put(fbase + k, f[0]);
-    S.put(fbase + P.n_face + k, f[1]);
-    S.put(fbase + 2 * P.n_face + k, f[2]);
-    if (want_e && r.owned) eA += (double)ea;
+#pragma unroll 1
+    for (int h = 0; h < (two ? 2 : 1); ++h) {
+      const uint2 fr = h ? r1 : r0;
+      const int k = h ? k1 : k0;
+      const uint4 r = rec[fr.x & 0x3FFFFFFFu];
+      const bool right = (fr.x >> 30) & 1u;
+      const int la = r.x & 0xFFFF, lb = r.x >> 16;
+      const int v0 = right ? lb : la, v1 = right ? la : lb;
+      const int v2 = right ? (int)(r.y >> 16) : (int)(r.y & 0xFFFF);
+      const int d0 = right ? (int)(r.z >> 16) : (int)(r.z & 0xFFFF);
+      const int d1 = right ? (int)(r.z & 0xFFFF) : (int)(r.z >> 16);
+      const int d2 = right ? (int)(r.w >> 16) : (int)(r.w & 0xFFFF);
+      Vec<float> f[3], gA[3], gV[3], ua[3];
+      float ea;
+      const float ka = B.varied ? B.ka * rest[5 * pe + pf + k] : B.ka;
+      face_forces(S.pos(v0), S.pos(v1), S.pos(v2), rest[3 * pe + k], ka, cA, cV, f, gA, gV, ua,
+                  ea);
+      if (MODE != 0) {
+        const Vec<float> fe = vscale(h ? fe1 : fe0, third);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] = vadd(f[c], fe);
+      }
+      S.add(d0, f[0]);
+      S.add(d1, f[1]);
+      S.add(d2, f[2]);
+      if (want_e && (fr.x >> 31)) eA += (double)ea;
+    }
   }
   __syncthreads();
 
-  // own vertices: fixed-order gather of the slots
+  // own vertices: fixed-order sum of their contiguous slots
   for (int i = threadIdx.x; i < P.n_own; i += blockDim.x) {
-    const int s0 = __ldg(T.csr_ptr + P.csr_off + i), s1 = __ldg(T.csr_ptr + P.csr_off + i + 1);
+    const int s0 = ptr[i], s1 = ptr[i + 1];
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int k = s0; k < s1; ++k) {
-      const int s = T.csr_slot[P.slot_off + k];
+    for (int s = s0; s < s1; ++s) {
       fx += S.cx[s];
       fy += S.cy[s];
       fz += S.cz[s];
@@ -161,7 +270,10 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
       // the gathered slots hold F_int + F_ext^v
       const float ax = fx * B.inv_mass, ay = fy * B.inv_mass, az = fz * B.inv_mass;
       const float x0 = S.px[i], y0 = S.py[i], z0 = S.pz[i];
-      float vx = __ldg(v + gv), vy = __ldg(v + V + gv), vz = __ldg(v + 2 * V + gv);
+      const bool first = i == (int)threadIdx.x;
+      float vx = first ? pv[0] : __ldg(v + gv), vy = first ? pv[1] : __ldg(v + V + gv),
+            vz = first ? pv[2] : __ldg(v + 2 * V + gv);
+      const bool clamped = first ? pcl : T.clamp[gv] != 0;
       float nx, ny, nz;
       if (sc.forward_euler) {
         nx = x0 + sc.dt * vx; ny = y0 + sc.dt * vy; nz = z0 + sc.dt * vz;
@@ -170,7 +282,7 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
         vx += sc.dt * ax; vy += sc.dt * ay; vz += sc.dt * az;
         nx = x0 + sc.dt * vx; ny = y0 + sc.dt * vy; nz = z0 + sc.dt * vz;
       }
-      if (T.clamp[gv]) {
+      if (clamped) {
         nx = x0; ny = y0; nz = z0;
         vx = vy = vz = 0.f;
       }
