@@ -253,9 +253,8 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
       }
       __syncthreads();
       // row lengths in whole groups of 4 nodes (aligned to float4 in global
-      // memory when the grid allows vector access), their exclusive scan, and
-      // per row: group -> row ids, global row offset, wrapped first x and
-      // staged offset - x0.  Thread t owns rows 4t .. 4t + 3.
+      // memory when the grid allows vector access) and their exclusive scan;
+      // thread t owns rows 4t .. 4t + 3 here
       int len[4], st[4], run = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -265,8 +264,8 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
           a = s_xmin[r];
           int b = s_xmax[r] + 1;
           if (vec4) {
-            a = a - (((a % 4) + 4) % 4);
-            b = b + ((4 - ((b % 4) + 4) % 4) % 4);
+            a &= ~3;             // floor to a multiple of 4 (two's complement)
+            b = (b + 3) & ~3;
           } else {
             b = a + ((b - a + 3) & ~3);
           }
@@ -294,15 +293,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
         if (r < kMaxRows) {
           s_off[r] = pos;
           s_xmax[r] = len[q];
-          if (len[q] > 0) {
-            // groups past kMaxNodes / 4 only occur when the block does not fit
-            const int q1 = min((pos + len[q]) / 4, kMaxNodes / 4);
-            for (int k = pos / 4; k < q1; ++k) s_grow[k] = (unsigned short)r;
-            const int yy = wrap(ylo + r % sy, g.n[1]), zz = wrap(zlo + r / sy, g.n[2]);
-            s_base[r] = (zz * g.n[1] + yy) * g.n[0];
-            s_x0w[r] = wrap(st[q], g.n[0]);
-            s_xmin[r] = pos - st[q];
-          }
+          s_xmin[r] = st[q];
         }
         pos += len[q];
       }
@@ -313,6 +304,31 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
       __syncthreads();
       N = s_N;
       fit = N <= kMaxNodes;
+      // per row, strided over the whole block: group -> row ids, global row
+      // offset, wrapped first x and staged offset - x0 (row r is (y, z) =
+      // (r % sy, r / sy), followed incrementally)
+      {
+        int yy = (int)threadIdx.x % sy, zz = (int)threadIdx.x / sy;
+        const int dy = (int)blockDim.x % sy, dz = (int)blockDim.x / sy;
+        for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
+          const int L = s_xmax[r];
+          if (L > 0) {
+            const int p0 = s_off[r], a = s_xmin[r];
+            // groups past kMaxNodes / 4 only occur when the block does not fit
+            const int q1 = min((p0 + L) / 4, kMaxNodes / 4);
+            for (int k = p0 / 4; k < q1; ++k) s_grow[k] = (unsigned short)r;
+            s_base[r] = (wrap(zlo + zz, g.n[2]) * g.n[1] + wrap(ylo + yy, g.n[1])) * g.n[0];
+            s_x0w[r] = wrap(a, g.n[0]);
+            s_xmin[r] = p0 - a;
+          }
+          yy += dy;
+          zz += dz;
+          if (yy >= sy) {
+            yy -= sy;
+            ++zz;
+          }
+        }
+      }
     }
     if (!fit && threadIdx.x == 0) atomicAdd(T.stats, 1);
     __syncthreads();

@@ -137,21 +137,33 @@ struct RowAcc {      // indices into the rows staged in shared memory
   __device__ int col(int s) const { return s; }
 };
 
+// The contractions below run x first (per row, the a- and b-weighted sums as
+// one pair in packed two-lane float arithmetic), then y within each z-plane,
+// then z:  U = sum_z [a_z (P1 - P2 - P3) - b_z P1],  P1 = sum_y a_y xa,
+// P2 = sum_y a_y xb, P3 = sum_y b_y xa.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
 template <class Acc>
 __device__ __forceinline__ float mls_value(const float* __restrict__ f, const Acc& A, const DirW& X,
                                            const DirW& Y, const DirW& Z) {
+  const float2 ab0 = make_float2(X.a[0], X.b[0]), ab1 = make_float2(X.a[1], X.b[1]),
+               ab2 = make_float2(X.a[2], X.b[2]);
   float q = 0.f;
 #pragma unroll
   for (int sz = 0; sz < 3; ++sz) {
+    float2 P = make_float2(0.f, 0.f);
+    float P3 = 0.f;
 #pragma unroll
     for (int sy = 0; sy < 3; ++sy) {
       const float* r = f + A.row(sy, sz);
       const float u0 = r[A.col(0)], u1 = r[A.col(1)], u2 = r[A.col(2)];
-      const float xa = X.a[0] * u0 + X.a[1] * u1 + X.a[2] * u2;
-      const float xb = X.b[0] * u0 + X.b[1] * u1 + X.b[2] * u2;
-      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
-      q += (xa - xb) * ay * az - xa * (by * az + ay * bz);
+      float2 x2 = __ffma2_rn(ab0, f2(u0), make_float2(0.f, 0.f));
+      x2 = __ffma2_rn(ab1, f2(u1), x2);
+      x2 = __ffma2_rn(ab2, f2(u2), x2);
+      P = __ffma2_rn(f2(Y.a[sy]), x2, P);
+      P3 = fmaf(Y.b[sy], x2.x, P3);
     }
+    q = fmaf(Z.a[sz], P.x - P.y - P3, fmaf(-Z.b[sz], P.x, q));
   }
   return q;
 }
@@ -159,23 +171,37 @@ __device__ __forceinline__ float mls_value(const float* __restrict__ f, const Ac
 template <class Acc>
 __device__ __forceinline__ void mls_grad(const float* __restrict__ f, const Acc& A, const DirWD& X,
                                          const DirWD& Y, const DirWD& Z, float (&g)[3]) {
+  const float2 ab0 = make_float2(X.a[0], X.b[0]), ab1 = make_float2(X.a[1], X.b[1]),
+               ab2 = make_float2(X.a[2], X.b[2]);
+  const float2 db0 = make_float2(X.da[0], X.db[0]), db1 = make_float2(X.da[1], X.db[1]),
+               db2 = make_float2(X.da[2], X.db[2]);
   float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
   for (int sz = 0; sz < 3; ++sz) {
+    // per plane: P = sum_y a_y (xa, xb), P3 = sum_y b_y xa; the same with the
+    // x-derivative sums (Pd, Pd3) and with the y-derivative factors (Q, Q3)
+    float2 P = make_float2(0.f, 0.f), Pd = P, Q = P;
+    float P3 = 0.f, Pd3 = 0.f, Q3 = 0.f;
 #pragma unroll
     for (int sy = 0; sy < 3; ++sy) {
       const float* r = f + A.row(sy, sz);
       const float u0 = r[A.col(0)], u1 = r[A.col(1)], u2 = r[A.col(2)];
-      const float xa = X.a[0] * u0 + X.a[1] * u1 + X.a[2] * u2;
-      const float xb = X.b[0] * u0 + X.b[1] * u1 + X.b[2] * u2;
-      const float xda = X.da[0] * u0 + X.da[1] * u1 + X.da[2] * u2;
-      const float xdb = X.db[0] * u0 + X.db[1] * u1 + X.db[2] * u2;
-      const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
-      const float day = Y.da[sy], dby = Y.db[sy], daz = Z.da[sz], dbz = Z.db[sz];
-      gx += (xda - xdb) * ay * az - xda * (by * az + ay * bz);
-      gy += (xa - xb) * day * az - xa * (dby * az + day * bz);
-      gz += (xa - xb) * ay * daz - xa * (by * daz + ay * dbz);
+      float2 x2 = __ffma2_rn(ab0, f2(u0), make_float2(0.f, 0.f));
+      x2 = __ffma2_rn(ab1, f2(u1), x2);
+      x2 = __ffma2_rn(ab2, f2(u2), x2);
+      float2 d2 = __ffma2_rn(db0, f2(u0), make_float2(0.f, 0.f));
+      d2 = __ffma2_rn(db1, f2(u1), d2);
+      d2 = __ffma2_rn(db2, f2(u2), d2);
+      P = __ffma2_rn(f2(Y.a[sy]), x2, P);
+      P3 = fmaf(Y.b[sy], x2.x, P3);
+      Pd = __ffma2_rn(f2(Y.a[sy]), d2, Pd);
+      Pd3 = fmaf(Y.b[sy], d2.x, Pd3);
+      Q = __ffma2_rn(f2(Y.da[sy]), x2, Q);
+      Q3 = fmaf(Y.db[sy], x2.x, Q3);
     }
+    gx = fmaf(Z.a[sz], Pd.x - Pd.y - Pd3, fmaf(-Z.b[sz], Pd.x, gx));
+    gy = fmaf(Z.a[sz], Q.x - Q.y - Q3, fmaf(-Z.b[sz], Q.x, gy));
+    gz = fmaf(Z.da[sz], P.x - P.y - P3, fmaf(-Z.db[sz], P.x, gz));
   }
   g[0] = gx; g[1] = gy; g[2] = gz;
 }
@@ -348,6 +374,9 @@ __device__ __forceinline__ void mls_spread_fixed(int* hi, int* lo, const RowAcc&
 // overflow, and the sum is independent of the order of the additions.
 __device__ __forceinline__ void mls_spread_fixed1(int* acc, const RowAcc& A, const DirW& X,
                                                   const DirW& Y, const DirW& Z, float coef) {
+  // nodes 0 and 1 of each row in packed two-lane arithmetic
+  const float2 d01 = make_float2(X.a[0] - X.b[0], X.a[1] - X.b[1]), a01 = make_float2(X.a[0], X.a[1]);
+  const float d2 = X.a[2] - X.b[2];
 #pragma unroll
   for (int sz = 0; sz < 3; ++sz) {
 #pragma unroll
@@ -355,9 +384,10 @@ __device__ __forceinline__ void mls_spread_fixed1(int* acc, const RowAcc& A, con
       const int r = A.row(sy, sz);
       const float ay = Y.a[sy], by = Y.b[sy], az = Z.a[sz], bz = Z.b[sz];
       const float t0 = ay * az * coef, t1 = (by * az + ay * bz) * coef;
-#pragma unroll
-      for (int sx = 0; sx < 3; ++sx)
-        atomicAdd(acc + r + sx, __float2int_rn((X.a[sx] - X.b[sx]) * t0 - X.a[sx] * t1));
+      const float2 v01 = __ffma2_rn(d01, f2(t0), __fmul2_rn(a01, f2(-t1)));
+      atomicAdd(acc + r, __float2int_rn(v01.x));
+      atomicAdd(acc + r + 1, __float2int_rn(v01.y));
+      atomicAdd(acc + r + 2, __float2int_rn(fmaf(d2, t0, -X.a[2] * t1)));
     }
   }
 }
