@@ -244,6 +244,39 @@ def ncu_traffic(kernel_key):
         return None
 
 
+def ncu_instructions(kernel_key):
+    """Warp instructions per marker of `kernel_key` from the committed ncu
+    summary (the drop workload's count), or None when the kernel's sources
+    changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        from paper_1612_03399_gb300 import build as B
+        d = json.load(open(p))
+        if d.get("digests", {}).get(kernel_key) != B.kernel_digest(kernel_key):
+            return None
+        return d.get("instructions", {}).get(kernel_key)
+    except Exception:
+        return None
+
+
+def issue_roofline(kernel_key, faces, ms, clk, device_index):
+    """The kernel against its compute-side bound, instruction issue: warp
+    instructions per launch (ncu's per-marker count x markers) / its mean
+    duration, against 4 schedulers per SM issuing one warp instruction per
+    clock each, at the SM clock sampled during the timed region."""
+    ipf = ncu_instructions(kernel_key)
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+    if not ipf or not mhz:
+        return None
+    n_sm = torch.cuda.get_device_properties(device_index).multi_processor_count
+    peak = n_sm * 4 * mhz * 1e6
+    achieved = ipf * faces / (ms * 1e-3)
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp-instr/s",
+            "frac": achieved / peak, "inst_per_marker": ipf, "sm_mhz": mhz, "sms": n_sm}
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -646,6 +679,10 @@ def run_gb300(args, ws, rank, local):
     peak, peak_kind = hbm_peak()
     roof, per = kernel_roofline(variant, mean_ph, bytes_model, peak, peak_kind)
     roof["traffic"] = ncu_traffic(roof["kernel"])
+    if variant == 1 and args.workload == "drops1000" and roof["kernel"] == "marker":
+        # per-marker instruction count measured on this workload's drops
+        roof["issue"] = issue_roofline("marker", int(sum(len(b.tri) for b in wl.bodies)),
+                                       per["marker"]["ms"], clk, local)
     launches = 3 if variant == 1 else 6
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": n_steps,
