@@ -44,11 +44,11 @@ def _digest() -> str:
 
 # the sources each profiled kernel is compiled from (for per-kernel digests)
 KERNEL_SOURCES = {
-    "marker": ["k_mls.cu", "mls_closed_form.cuh", "ibm_internal.cuh"],
-    "clear": ["k_mls.cu", "mls_closed_form.cuh", "ibm_internal.cuh"],
-    "forcing": ["k_mls.cu", "mls_closed_form.cuh", "ibm_internal.cuh"],
-    "body_marker": ["k_mls.cu", "mls_closed_form.cuh", "ibm_internal.cuh"],
-    "force": ["k_force.cu", "force_elems.cuh", "ibm_internal.cuh"],
+    "marker": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
+    "clear": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
+    "forcing": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
+    "body_marker": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
+    "force": ["k_force.cu", "force_elems.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
     "spread": ["k_tile.cu", "ibm_internal.cuh"],
     "rhs": ["ibm_flow.cu", "ibm_internal.cuh"],
     "cn_scale": ["ibm_flow.cu", "ibm_internal.cuh"],

@@ -1260,14 +1260,31 @@ extern "C" ibm_status ibm_flow_step(ibm_flow* fl, ibm_ctx* c, const float* x, co
   const cudaStream_t s = c ? c->stream : flow_stream(fl);
   const size_t cells = flow_cells(fl);
   cudaError_t e = cudaSuccess;
+  if (c && !c->fc_tab) {
+    // the forcing's cache and footprint record, allocated once
+    try {
+      const size_t nc = (size_t)std::max(c->n_chunks, 1);
+      int2* rm = zeros<int2>(c, (size_t)kMaxRows * nc);
+      int4* bx = zeros<int4>(c, 2 * nc);
+      float4* fa = zeros<float4>(c, (size_t)2 * kMT * nc);
+      c->fc_tab = zeros<int32_t>(c, (size_t)kCacheWords * nc);   // set last: marks all four
+      c->fc_face = fa;
+      c->fc_boxes = bx;
+      c->fc_rowmap = rm;
+    } catch (Failure& f) {
+      set_global_error(f.msg);
+      return set_err(c, f.s, f.msg);
+    }
+  }
   for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
     e = flow_predict(fl, l, u, vv, w, p, s);
     if (c && e == cudaSuccess) {
-      for (float* f : {fx, fy, fz})
-        if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, cells * sizeof(float), s);
-      if (e == cudaSuccess)
-        e = launch_mls(c, x, xv, u, vv, w, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, fx,
-                       fy, fz, false, true, false, true, false);
+      // substep 0 zeroes the fields; later substeps clear the previous
+      // substep's footprint (inside launch_forcing)
+      if (l == 0)
+        for (float* f : {fx, fy, fz})
+          if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, cells * sizeof(float), s);
+      if (e == cudaSuccess) e = launch_forcing(c, l, x, xv, u, vv, w, fx, fy, fz);
     }
     if (e == cudaSuccess)
       e = flow_project(fl, l, u, vv, w, p, c ? fx : nullptr, c ? fy : nullptr, c ? fz : nullptr,

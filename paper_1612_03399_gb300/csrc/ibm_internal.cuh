@@ -227,7 +227,15 @@ struct DeviceTables {
 // accumulators of one force component)
 constexpr int kMaxRows = 4 * kMT;                                  // (y, z) rows per patch
 constexpr int kMaxNodes = 35 * kMT;                                // staged nodes per buffer
-constexpr int kRowTableBytes = ((4 * (7 * kMaxRows + 1) + 2 * (kMaxNodes / 4)) + 15) / 16 * 16;
+// (the staged-row-start array has kMaxRows + 4 entries, so every array
+// starts on a 16-byte boundary)
+constexpr int kRowTableBytes = ((4 * (7 * kMaxRows + 4) + 2 * (kMaxNodes / 4)) + 15) / 16 * 16;
+// Per-chunk cache of the coupled forcing launch (the markers stay at x^n for
+// the three substeps of a coupled step): a 16-word header (x, y, z lo, x, y,
+// z size, staged nodes, fits), then the five row arrays (kMaxRows words
+// each: staged offset - x0, row length, staged start, global row offset,
+// wrapped first x) and the group -> row table (kMaxNodes / 4 16-bit ids)
+constexpr int kCacheWords = 16 + 5 * kMaxRows + kMaxNodes / 8;
 constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes;
 
 // elementwise combinations of [3][V] arrays for the strong-coupling integrator
@@ -268,6 +276,13 @@ __device__ __forceinline__ float2 body_coef(const BodyDev& B, unsigned long long
 
 struct ibm_ctx {
   int device = 0;
+  // coupled forcing (allocated by the first ibm_flow_step with this context):
+  // the per-chunk tables and per-face geometry of substep 0, and the forcing's
+  // own footprint record for the clears between substeps
+  int32_t* fc_tab = nullptr;        // [n_chunks][kCacheWords]
+  float4* fc_face = nullptr;        // [n_chunks][kMT][2] (centroid in cells, area), (V^b, ok)
+  int4* fc_boxes = nullptr;         // [n_chunks][2]
+  int2* fc_rowmap = nullptr;        // [n_chunks][kMaxRows]
   int spread_variant = 1;       // 1: spread inside the marker kernel (patch-owned, atomic
                                 //  flush); 2: tile-owned spread kernels
   ibm::TileDev td;
@@ -325,6 +340,9 @@ cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* 
                        float* fz, bool measure, bool interp, bool probe, bool spread,
                        bool record_cells);
 cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz);
+cudaError_t launch_forcing(ibm_ctx* c, int substep, const float* x, const float* xv,
+                           const float* u, const float* vv, const float* w, float* fx, float* fy,
+                           float* fz);
 
 // marker kernel without the spread, writing the spread records and counting
 // the marker-tile pairs of the tile-owned spread (`accumulate`: into the

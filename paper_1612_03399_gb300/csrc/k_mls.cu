@@ -31,6 +31,7 @@
 #include <limits.h>
 #include <math.h>
 
+#include "bulk_copy.cuh"
 #include "ibm_internal.cuh"
 #include "mls_closed_form.cuh"
 
@@ -48,15 +49,22 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     const float* __restrict__ w, const float* __restrict__ pr, const float* __restrict__ accel,
     float* __restrict__ U, float* __restrict__ Fm, const float* __restrict__ Fm_in,
     float* __restrict__ Fext, float* __restrict__ fx, float* __restrict__ fy,
-    float* __restrict__ fz, int record, int vec4, TileDev td, int tmode, float phi_bound_all) {
+    float* __restrict__ fz, int record, int vec4, TileDev td, int tmode, float phi_bound_all,
+    int cache, int* __restrict__ cache_tab, float4* __restrict__ cache_face) {
   constexpr bool FIELD = INTERP || PROBE || SPREAD;
+  // the coupled forcing launch (interpolation and spread at the centroids)
+  // may save its face geometry and row tables (cache 1) and, in the later
+  // substeps of the same step, load them instead of recomputing (cache 2)
+  constexpr bool CACHEABLE = !MEASURE && INTERP && !PROBE && SPREAD && !REC;
+  const bool load = CACHEABLE && cache == 2;
+  const bool save = CACHEABLE && cache == 1;
   constexpr bool VEL = INTERP || PROBE;
   constexpr bool ROWMAP = VEL || (SPREAD && !REC);
   extern __shared__ __align__(16) unsigned char dyn[];
   int* s_xmin = reinterpret_cast<int*>(dyn);   // [kMaxRows]  then: staged offset - x0
   int* s_xmax = s_xmin + kMaxRows;             // [kMaxRows]  then: row length
-  int* s_off = s_xmax + kMaxRows;              // [kMaxRows + 1] staged row start
-  int* s_base = s_off + kMaxRows + 1;          // [kMaxRows] global offset of row (y, z)
+  int* s_off = s_xmax + kMaxRows;              // [kMaxRows + 4] staged row start
+  int* s_base = s_off + kMaxRows + 4;          // [kMaxRows] global offset of row (y, z)
   int* s_x0w = s_base + kMaxRows;              // [kMaxRows] first x, wrapped
   int* s_nzlo = s_x0w + kMaxRows;              // [kMaxRows] first / last group of the row
   int* s_nzhi = s_nzlo + kMaxRows;             //   that received a nonzero spread
@@ -67,6 +75,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   __shared__ int s_N;
   __shared__ int s_warp[kMT / 32];
   __shared__ int s_bmax[3];
+  __shared__ __align__(8) unsigned long long s_bar;
 
   // a force kernel launched after this one may start once every block of
   // this grid runs (it waits for this grid's results before using them)
@@ -87,7 +96,15 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   float am[3] = {0.f, 0.f, 0.f};     // marker acceleration
   bool ok = false;
   int gf = 0;
-  if (active) {
+  if (load && active) {
+    const float4 c0 = cache_face[2 * ((size_t)blockIdx.x * kMT + threadIdx.x)];
+    const float4 c1 = cache_face[2 * ((size_t)blockIdx.x * kMT + threadIdx.x) + 1];
+    tc[0] = c0.x; tc[1] = c0.y; tc[2] = c0.z;
+    area = c0.w;
+    vb[0] = c1.x; vb[1] = c1.y; vb[2] = c1.z;
+    ok = c1.w != 0.f;
+  }
+  if (active && !load) {
     // full patches are stored so that a warp's faces are spread over the patch
     // (its shared atomics of the spread rarely meet on a node) while thread t
     // reads record t
@@ -148,6 +165,11 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
       }
       if (!ok) atomicOr(T.err, ERR_NONFINITE);
     }
+    if (save) {
+      cache_face[2 * ((size_t)blockIdx.x * kMT + threadIdx.x)] = make_float4(tc[0], tc[1], tc[2], area);
+      cache_face[2 * ((size_t)blockIdx.x * kMT + threadIdx.x) + 1] =
+          make_float4(vb[0], vb[1], vb[2], ok ? 1.f : 0.f);
+    }
   }
 
   // ---- per-body area and volume: exact fixed-point sums -------------------
@@ -183,7 +205,51 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   int ylo = 0, zlo = 0, sy = 0, sz = 0, xlo = 0, sx = 0;
   bool fit = false;
   int N = 0;
-  if (ROWMAP) {
+  if (ROWMAP && load) {
+    // the tables of substep 0 of this coupled step: header, then one bulk
+    // copy per row array and one for the group -> row table
+    const int* hd = cache_tab + (size_t)blockIdx.x * kCacheWords;
+    xlo = hd[0];
+    ylo = hd[1];
+    zlo = hd[2];
+    sx = hd[3];
+    sy = hd[4];
+    sz = hd[5];
+    N = hd[6];
+    fit = hd[7] != 0;
+    const int nrows = fit ? sy * sz : 0;
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar, 1);
+      const unsigned rb = 4u * (unsigned)pad4(nrows), gb = fit ? 2u * (unsigned)((N / 4 + 7) & ~7) : 0u;
+      mbar_arrive_tx(&s_bar, 5u * rb + gb);
+      if (fit) {
+        const int* src = hd + 16;
+        bulk_load(s_xmin, src, rb, &s_bar);
+        bulk_load(s_xmax, src + kMaxRows, rb, &s_bar);
+        bulk_load(s_off, src + 2 * kMaxRows, rb, &s_bar);
+        bulk_load(s_base, src + 3 * kMaxRows, rb, &s_bar);
+        bulk_load(s_x0w, src + 4 * kMaxRows, rb, &s_bar);
+        bulk_load(s_grow, src + 5 * kMaxRows, gb, &s_bar);
+      }
+      s_off[kMaxRows] = N;
+    }
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      s_nzlo[r] = INT_MAX;
+      s_nzhi[r] = INT_MIN;
+    }
+    __syncthreads();   // barrier initialised
+    if (!__syncthreads_and(mbar_wait(&s_bar, kCopyWaitClocks))) {
+      // the copies did not land: flag it, give them one more bounded wait
+      // (they write this block's shared memory) and leave
+      if (threadIdx.x == 0) {
+        atomicOr(T.err, ERR_TIMEOUT);
+        mbar_wait(&s_bar, kCopyWaitClocks);
+      }
+      __syncthreads();
+      return;
+    }
+    if (!fit && threadIdx.x == 0) atomicAdd(T.stats, 1);
+  } else if (ROWMAP) {
     int mlo[3] = {INT_MAX, INT_MAX, INT_MAX}, mhi[3] = {INT_MIN, INT_MIN, INT_MIN};
     if (mine) {
 #pragma unroll
@@ -332,6 +398,31 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     }
     if (!fit && threadIdx.x == 0) atomicAdd(T.stats, 1);
     __syncthreads();
+    if (save) {
+      int* hd = cache_tab + (size_t)blockIdx.x * kCacheWords;
+      if (threadIdx.x == 0) {
+        hd[0] = xlo;
+        hd[1] = ylo;
+        hd[2] = zlo;
+        hd[3] = sx;
+        hd[4] = sy;
+        hd[5] = sz;
+        hd[6] = N;
+        hd[7] = fit ? 1 : 0;
+      }
+      if (fit) {
+        int* dst = hd + 16;
+        for (int r = threadIdx.x; r < sy * sz; r += blockDim.x) {
+          dst[r] = s_xmin[r];
+          dst[kMaxRows + r] = s_xmax[r];
+          dst[2 * kMaxRows + r] = s_off[r];
+          dst[3 * kMaxRows + r] = s_base[r];
+          dst[4 * kMaxRows + r] = s_x0w[r];
+        }
+        unsigned short* gg = reinterpret_cast<unsigned short*>(dst + 5 * kMaxRows);
+        for (int q = threadIdx.x; q < N / 4; q += blockDim.x) gg[q] = s_grow[q];
+      }
+    }
   }
   const RowTable RT{s_grow, s_off, s_base, s_x0w, g.n[0], vec4};
   const StagedRows SR{s_xmin, ylo, zlo, sy};
@@ -701,14 +792,15 @@ template <bool M, bool I, bool P, bool S, bool R = false>
 cudaError_t launch_t(ibm_ctx* c, const float* x, const float* v, const float* u, const float* vv,
                      const float* w, const float* pr, const float* accel, float* U, float* Fm,
                      const float* Fm_in, float* Fext, float* fx, float* fy, float* fz,
-                     int record, int tmode = 0) {
+                     int record, int tmode = 0, const DeviceTables* tab = nullptr, int cache = 0) {
   if (c->n_chunks == 0) return cudaSuccess;
   const size_t smem = (I || P || (S && !R)) ? kMarkerSmemBytes : 0;
   const int vec4 = c->vec4 && aligned16(u) && aligned16(vv) && aligned16(w) && aligned16(pr) &&
                    aligned16(fx) && aligned16(fy) && aligned16(fz);
   marker_kernel<M, I, P, S, R><<<c->n_chunks, kMT, smem, c->stream>>>(
-      c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, pr, accel, U, Fm,
-      Fm_in, Fext, fx, fy, fz, record, vec4, c->td, tmode, c->phi_bound);
+      tab ? *tab : c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, pr, accel,
+      U, Fm, Fm_in, Fext, fx, fy, fz, record, vec4, c->td, tmode, c->phi_bound, cache,
+      c->fc_tab, c->fc_face);
   return cudaGetLastError();
 }
 
@@ -790,6 +882,30 @@ cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz) {
   clear_kernel<<<c->n_chunks, 256, 0, c->stream>>>(c->d, c->grid, fx, fy, fz, vec4, c->d.chunks,
                                                   c->d.boxes, c->d.rowmap, kMaxRows);
   return cudaGetLastError();
+}
+
+// The coupled forcing of substep `substep` (interpolation of u* and spread
+// at the centroids of x): footprints recorded in the flow's own record (the
+// step's record is left alone), the previous substep's footprint cleared
+// first (substep 0: the caller zeroes the fields), and the face geometry and
+// row tables saved in substep 0 and loaded in substeps 1 and 2.
+cudaError_t launch_forcing(ibm_ctx* c, int substep, const float* x, const float* xv,
+                           const float* u, const float* vv, const float* w, float* fx, float* fy,
+                           float* fz) {
+  if (c->n_chunks == 0) return cudaSuccess;
+  DeviceTables t = c->d;
+  t.boxes = c->fc_boxes;
+  t.rowmap = c->fc_rowmap;
+  if (substep > 0) {
+    const int vec4 = c->vec4 && aligned16(fx) && aligned16(fy) && aligned16(fz);
+    clear_kernel<<<c->n_chunks, 256, 0, c->stream>>>(t, c->grid, fx, fy, fz, vec4, c->d.chunks,
+                                                    t.boxes, t.rowmap, kMaxRows);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_t<false, true, false, true>(c, x, xv, u, vv, w, nullptr, nullptr, nullptr, nullptr,
+                                            nullptr, nullptr, fx, fy, fz, 1, 0, &t,
+                                            substep == 0 ? 1 : 2);
 }
 
 }  // namespace ibm
