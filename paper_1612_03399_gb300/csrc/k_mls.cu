@@ -89,6 +89,17 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     s_hi[threadIdx.x] = INT_MIN;
     s_bmax[threadIdx.x] = 0;
   }
+  if (ROWMAP && !load) {
+    // every row's x-range and nonzero range start empty; done first, so that
+    // the stores overlap the geometry loads (the barriers of the bounding-box
+    // reduction make them visible)
+    for (int r = threadIdx.x; r < kMaxRows; r += blockDim.x) {
+      s_xmin[r] = INT_MAX;
+      s_xmax[r] = INT_MIN;
+      s_nzlo[r] = INT_MAX;
+      s_nzhi[r] = INT_MIN;
+    }
+  }
   float Af = 0.f, Vf = 0.f;
   float nrm[3] = {0.f, 0.f, 0.f}, area = 0.f;
   float tc[3] = {0.f, 0.f, 0.f}, tp[3] = {0.f, 0.f, 0.f}, tm[3] = {0.f, 0.f, 0.f};
@@ -290,13 +301,6 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     const long long nrows = (long long)sy * sz;
     const bool rows_ok = nrows > 0 && nrows <= kMaxRows && sx <= 30000;
     if (rows_ok) {
-      for (int r = threadIdx.x; r < (int)nrows; r += blockDim.x) {
-        s_xmin[r] = INT_MAX;
-        s_xmax[r] = INT_MIN;
-        s_nzlo[r] = INT_MAX;
-        s_nzhi[r] = INT_MIN;
-      }
-      __syncthreads();
       if (mine) {
         // every component's support at a point with f = floor(tau) lies in
         // the 4x4x4 window f - 1 .. f + 2 (the nearest-node choice is exact
