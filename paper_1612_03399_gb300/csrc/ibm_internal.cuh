@@ -221,21 +221,22 @@ struct DeviceTables {
   int32_t* err = nullptr;       // device error word
 };
 
-// marker-kernel dynamic shared memory: row tables (7 int arrays of kMaxRows,
-// one row id per staged float4 group), then two staging buffers of kMaxNodes
-// words (velocity components, double-buffered; then the fixed-point spread
-// accumulators of one force component)
+// marker-kernel dynamic shared memory: row tables (5 int arrays of kMaxRows;
+// per staged float4 group its global offset and its row id), then two
+// staging buffers of kMaxNodes words (velocity components, double-buffered;
+// then the fixed-point spread accumulators of two force components)
 constexpr int kMaxRows = 4 * kMT;                                  // (y, z) rows per patch
 constexpr int kMaxNodes = 35 * kMT;                                // staged nodes per buffer
 // (the staged-row-start array has kMaxRows + 4 entries, so every array
 // starts on a 16-byte boundary)
-constexpr int kRowTableBytes = ((4 * (7 * kMaxRows + 4) + 2 * (kMaxNodes / 4)) + 15) / 16 * 16;
+constexpr int kRowTableBytes =
+    ((4 * (5 * kMaxRows + 4) + 4 * (kMaxNodes / 4) + 2 * (kMaxNodes / 4)) + 15) / 16 * 16;
 // Per-chunk cache of the coupled forcing launch (the markers stay at x^n for
 // the three substeps of a coupled step): a 16-word header (x, y, z lo, x, y,
-// z size, staged nodes, fits), then the five row arrays (kMaxRows words
-// each: staged offset - x0, row length, staged start, global row offset,
-// wrapped first x) and the group -> row table (kMaxNodes / 4 16-bit ids)
-constexpr int kCacheWords = 16 + 5 * kMaxRows + kMaxNodes / 8;
+// z size, staged nodes, fits), then three row arrays (kMaxRows words each:
+// staged offset - x0, row length, staged start), the groups' global offsets
+// (kMaxNodes / 4 words) and their row ids (kMaxNodes / 4 16-bit ids)
+constexpr int kCacheWords = 16 + 3 * kMaxRows + kMaxNodes / 4 + kMaxNodes / 8;
 constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes;
 
 // elementwise combinations of [3][V] arrays for the strong-coupling integrator

@@ -64,11 +64,10 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   int* s_xmin = reinterpret_cast<int*>(dyn);   // [kMaxRows]  then: staged offset - x0
   int* s_xmax = s_xmin + kMaxRows;             // [kMaxRows]  then: row length
   int* s_off = s_xmax + kMaxRows;              // [kMaxRows + 4] staged row start
-  int* s_base = s_off + kMaxRows + 4;          // [kMaxRows] global offset of row (y, z)
-  int* s_x0w = s_base + kMaxRows;              // [kMaxRows] first x, wrapped
-  int* s_nzlo = s_x0w + kMaxRows;              // [kMaxRows] first / last group of the row
+  int* s_nzlo = s_off + kMaxRows + 4;          // [kMaxRows] first / last group of the row
   int* s_nzhi = s_nzlo + kMaxRows;             //   that received a nonzero spread
-  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_nzhi + kMaxRows);  // [kMaxNodes/4]
+  int* s_gofs = s_nzhi + kMaxRows;             // [kMaxNodes/4] global offset of each group
+  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_gofs + kMaxNodes / 4);  // row ids
   float* bufA = reinterpret_cast<float*>(dyn + kRowTableBytes);
   float* bufB = bufA + kMaxNodes;
   __shared__ int s_lo[3], s_hi[3];
@@ -231,16 +230,17 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     const int nrows = fit ? sy * sz : 0;
     if (threadIdx.x == 0) {
       mbar_init(&s_bar, 1);
-      const unsigned rb = 4u * (unsigned)pad4(nrows), gb = fit ? 2u * (unsigned)((N / 4 + 7) & ~7) : 0u;
-      mbar_arrive_tx(&s_bar, 5u * rb + gb);
+      const unsigned rb = 4u * (unsigned)pad4(nrows);
+      const unsigned ob = fit ? 4u * (unsigned)pad4(N / 4) : 0u;
+      const unsigned gb = fit ? 2u * (unsigned)((N / 4 + 7) & ~7) : 0u;
+      mbar_arrive_tx(&s_bar, 3u * rb + ob + gb);
       if (fit) {
         const int* src = hd + 16;
         bulk_load(s_xmin, src, rb, &s_bar);
         bulk_load(s_xmax, src + kMaxRows, rb, &s_bar);
         bulk_load(s_off, src + 2 * kMaxRows, rb, &s_bar);
-        bulk_load(s_base, src + 3 * kMaxRows, rb, &s_bar);
-        bulk_load(s_x0w, src + 4 * kMaxRows, rb, &s_bar);
-        bulk_load(s_grow, src + 5 * kMaxRows, gb, &s_bar);
+        bulk_load(s_gofs, src + 3 * kMaxRows, ob, &s_bar);
+        bulk_load(s_grow, src + 3 * kMaxRows + kMaxNodes / 4, gb, &s_bar);
       }
       s_off[kMaxRows] = N;
     }
@@ -384,11 +384,14 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
           const int L = s_xmax[r];
           if (L > 0) {
             const int p0 = s_off[r], a = s_xmin[r];
+            const int base = (wrap(zlo + zz, g.n[2]) * g.n[1] + wrap(ylo + yy, g.n[1])) * g.n[0];
+            const int x0w = wrap(a, g.n[0]);
             // groups past kMaxNodes / 4 only occur when the block does not fit
             const int q1 = min((p0 + L) / 4, kMaxNodes / 4);
-            for (int k = p0 / 4; k < q1; ++k) s_grow[k] = (unsigned short)r;
-            s_base[r] = (wrap(zlo + zz, g.n[2]) * g.n[1] + wrap(ylo + yy, g.n[1])) * g.n[0];
-            s_x0w[r] = wrap(a, g.n[0]);
+            for (int k = p0 / 4; k < q1; ++k) {
+              s_grow[k] = (unsigned short)r;
+              s_gofs[k] = base + wrap_pos(x0w + 4 * (k - p0 / 4), g.n[0]);
+            }
             s_xmin[r] = p0 - a;
           }
           yy += dy;
@@ -420,15 +423,16 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
           dst[r] = s_xmin[r];
           dst[kMaxRows + r] = s_xmax[r];
           dst[2 * kMaxRows + r] = s_off[r];
-          dst[3 * kMaxRows + r] = s_base[r];
-          dst[4 * kMaxRows + r] = s_x0w[r];
         }
-        unsigned short* gg = reinterpret_cast<unsigned short*>(dst + 5 * kMaxRows);
-        for (int q = threadIdx.x; q < N / 4; q += blockDim.x) gg[q] = s_grow[q];
+        unsigned short* gg = reinterpret_cast<unsigned short*>(dst + 3 * kMaxRows + kMaxNodes / 4);
+        for (int q = threadIdx.x; q < N / 4; q += blockDim.x) {
+          dst[3 * kMaxRows + q] = s_gofs[q];
+          gg[q] = s_grow[q];
+        }
       }
     }
   }
-  const RowTable RT{s_grow, s_off, s_base, s_x0w, g.n[0], vec4};
+  const RowTable RT{s_gofs, g.n[0], vec4};
   const StagedRows SR{s_xmin, ylo, zlo, sy};
   const GlobalRows GR{g};
   const int ngroups = fit ? N / 4 : 0;
@@ -686,8 +690,8 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
           int2 e = make_int2(0, 0);
           if (s_xmax[r] > 0 && s_nzlo[r] <= s_nzhi[r]) {
             const int L = min(4 * (s_nzhi[r] - s_nzlo[r] + 1), g.n[0]);
-            const int x0 = wrap_pos(s_x0w[r] + (4 * s_nzlo[r] - s_off[r]), g.n[0]);
-            e = make_int2(s_base[r], x0 | (L << 16));
+            const int go = s_gofs[s_nzlo[r]], x0 = go % g.n[0];
+            e = make_int2(go - x0, x0 | (L << 16));
           }
           T.rowmap[(size_t)gc * kMaxRows + r] = e;
         }

@@ -261,17 +261,17 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // the staged rows of the block, one float4 group (4 consecutive staged nodes
-// of one row) per entry of s_grow
+// of one row) per entry: the global offset of the group's first node
 struct RowTable {
-  const unsigned short* grow;  // row of each group
-  const int* off;              // staged start of each row (a multiple of 4)
-  const int* base;             // global offset of the row's (y, z)
-  const int* x0w;              // first x of the row, wrapped into [0, nx)
+  const int* gofs;             // global offset of each group's first node
   int nx, vec4;
-  // global offset of node j (0..3) of group q
+  // global offset of node j (0..3) of group q (without vector access a group
+  // may cross the periodic x boundary: its nodes are wrapped one by one)
   __device__ __forceinline__ size_t node(int q, int j) const {
-    const int r = grow[q];
-    return (size_t)base[r] + wrap_pos(x0w[r] + (4 * q - off[r]) + j, nx);
+    const int g = gofs[q];
+    if (vec4 || j == 0) return (size_t)g + j;
+    const int x = g % nx;
+    return (size_t)(g - x) + (x + j < nx ? x + j : x + j - nx);
   }
 };
 
