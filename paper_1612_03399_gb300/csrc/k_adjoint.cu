@@ -239,7 +239,7 @@ __device__ __forceinline__ void cross3(const float (&a)[3], const float (&b)[3],
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-__global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
+__global__ void __launch_bounds__(kMT, 2) ext_adjoint_kernel(
     DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ vel, const float* __restrict__ u, const float* __restrict__ vv,
     const float* __restrict__ w, const float* __restrict__ pr, const float* __restrict__ accel,
@@ -311,17 +311,33 @@ __global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
     }
     const bool two = !B.closed;
     const float* fld[3] = {u, vv, w};
+    // one gradient-and-Hessian evaluation per component and probe end: the
+    // gradient forms G, the Hessian the position cotangent of the probe ends,
+    // gp_k = sum_ij gG_ij H_ijk with gG_ij = mu A (gF_i n_j + gF_j n_i), which
+    // does not depend on G
     float G[3][3];
-#pragma unroll
+    float gpp[3] = {0.f, 0.f, 0.f}, gpm[3] = {0.f, 0.f, 0.f};
+    const float s = sc.mu * area;
+#pragma unroll 1
     for (int i = 0; i < 3; ++i) {
       float gr[3], hs[6];
       mls_grad_hess(fld[i], g, tpp, i, B.G, sc.kappa, gr, hs);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) G[i][j] = gr[j] * g.invh[j];
+      for (int j = 0; j < 3; ++j) {
+        G[i][j] = gr[j] * g.invh[j];
+        const float gG = s * (gF[i] * n[j] + gF[j] * n[i]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gpp[k] += gG * hess_at(hs, j, k) * g.invh[j] * g.invh[k];
+      }
       if (two) {
         mls_grad_hess(fld[i], g, tpm, i, B.G, sc.kappa, gr, hs);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) G[i][j] -= gr[j] * g.invh[j];
+        for (int j = 0; j < 3; ++j) {
+          G[i][j] -= gr[j] * g.invh[j];
+          const float gG = s * (gF[i] * n[j] + gF[j] * n[i]);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) gpm[k] -= gG * hess_at(hs, j, k) * g.invh[j] * g.invh[k];
+        }
       }
     }
     // F = mu A (G + G^T) n
@@ -339,30 +355,6 @@ __global__ void __launch_bounds__(kMT) ext_adjoint_kernel(
     }
     float gArea = sc.mu * (gF[0] * Tn[0] + gF[1] * Tn[1] + gF[2] * Tn[2]);
     float gn[3] = {sc.mu * area * TgF[0], sc.mu * area * TgF[1], sc.mu * area * TgF[2]};
-    // d/dp of G through the MLS Hessian: gp_k = sum_ij gG_ij H_ijk,
-    // gG_ij = mu A (gF_i n_j + gF_j n_i)
-    float gpp[3] = {0.f, 0.f, 0.f}, gpm[3] = {0.f, 0.f, 0.f};
-    const float s = sc.mu * area;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      float gr[3], hs[6];
-      mls_grad_hess(fld[i], g, tpp, i, B.G, sc.kappa, gr, hs);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const float gG = s * (gF[i] * n[j] + gF[j] * n[i]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) gpp[k] += gG * hess_at(hs, j, k) * g.invh[j] * g.invh[k];
-      }
-      if (two) {
-        mls_grad_hess(fld[i], g, tpm, i, B.G, sc.kappa, gr, hs);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const float gG = s * (gF[i] * n[j] + gF[j] * n[i]);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) gpm[k] -= gG * hess_at(hs, j, k) * g.invh[j] * g.invh[k];
-        }
-      }
-    }
     // p+- = c +- h n
     float gc[3];
 #pragma unroll
