@@ -337,6 +337,22 @@ void build_topology(HostTopo& T, const int32_t* tri, int nv, int nf, int P) {
         T.fblob.push_back((uint32_t)ptr[i] | (i + 1 < ptr.size() ? (uint32_t)ptr[i + 1] << 16 : 0u));
       while (T.fblob.size() % 4) T.fblob.push_back(0u);
       Q.blob_words = (int32_t)T.fblob.size() - Q.blob_off;
+      // adjoint-only tail: the faces of each own vertex with its corner
+      std::vector<int32_t> vptr(H.n_own + 1);
+      std::vector<uint32_t> vent;
+      for (int v = o0; v < o1; ++v) {
+        vptr[v - o0] = (int32_t)vent.size();
+        for (int k = T.v2f_ptr[v]; k < T.v2f_ptr[v + 1]; ++k)
+          vent.push_back((uint32_t)(v2fc[k] / 3) | (uint32_t)(v2fc[k] % 3) << 30);
+      }
+      vptr[H.n_own] = (int32_t)vent.size();
+      if (vent.size() >= (size_t)kNone || nf >= (1 << 30))
+        fail(IBM_ERR_UNSUPPORTED, "patch too large for 16-bit local indices; lower patch_size");
+      for (size_t i = 0; i < vptr.size(); i += 2)
+        T.fblob.push_back((uint32_t)vptr[i] | (i + 1 < vptr.size() ? (uint32_t)vptr[i + 1] << 16 : 0u));
+      T.fblob.insert(T.fblob.end(), vent.begin(), vent.end());
+      while (T.fblob.size() % 4) T.fblob.push_back(0u);
+      Q.vf_words = (int32_t)T.fblob.size() - Q.blob_off - Q.blob_words;
       T.fpatch.push_back(Q);
       T.fface.insert(T.fface.end(), fo.begin(), fo.end());
     }
@@ -680,7 +696,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     std::vector<int2> work;
     std::vector<float> frest;        // force-kernel rest data per work item, patch order
     std::vector<int64_t> wrest;
-    size_t force_smem = 0;
+    size_t force_smem = 0, adjoint_smem = 0;
     c->h_body.resize(n_bodies);
     long long vo = 0, fo = 0, eo = 0;
     for (int b = 0; b < n_bodies; ++b) {
@@ -829,6 +845,12 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
         force_smem = std::max(force_smem,
                               sizeof(float) * ((size_t)Q.blob_words + frest_words(H.n_edge, H.n_face, varied) +
                                                3 * (size_t)pad4(H.n_loc) + 3 * (size_t)pad4(Q.n_slot)));
+        // the adjoint: blob with its tail, rest data, positions and
+        // tangents, slots
+        adjoint_smem = std::max(
+            adjoint_smem, sizeof(float) * ((size_t)Q.blob_words + Q.vf_words +
+                                           frest_words(H.n_edge, H.n_face, varied) +
+                                           6 * (size_t)pad4(H.n_loc) + 3 * (size_t)pad4(Q.n_slot)));
       }
       vo += Bd.n_vert;
       fo += Bd.n_face;
@@ -901,7 +923,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     c->force_smem = force_smem;
     if (c->force_smem > 227 * 1024)
       fail(IBM_ERR_UNSUPPORTED, "force-kernel shared memory above 227 KB; lower patch_size");
-    c->adjoint_smem = sizeof(float) * (6 * (size_t)max_loc + 3 * (size_t)max_slot);
+    c->adjoint_smem = adjoint_smem;
     c->max_own = max_own;
     if (c->adjoint_smem > 227 * 1024)
       fail(IBM_ERR_UNSUPPORTED, "force-kernel shared memory above 227 KB; lower patch_size");

@@ -80,7 +80,9 @@ struct FPatch {
   int32_t blob_off;      // word offset in fblob (a multiple of 4)
   int32_t blob_words;    // 4 n_edge + 2 n_face + (n_own + 2) / 2, rounded up to a multiple of 4
   int32_t n_slot;        // contributions to the own vertices (one per edge role)
-  int32_t pad;
+  int32_t vf_words;      // words after the blob read by the adjoint only: every own
+                         //  vertex's first entry (n_own + 1 16-bit values), then its
+                         //  faces as face | corner << 30, rounded up to a multiple of 4
 };
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
 // rest words of a work item: l0, cos0, sin0 (pad4(n_edge) each), A0f

@@ -25,6 +25,7 @@
 // constants' cotangents are gF . dF/dk, summed per body in a fixed order.
 #include <cuda_runtime.h>
 
+#include "bulk_copy.cuh"
 #include "force_elems.cuh"
 #include "ibm_internal.cuh"
 
@@ -493,9 +494,16 @@ struct DSmem {
   }
   __device__ Vec<float> cot(int i) const { return {tx[i], ty[i], tz[i]}; }
   __device__ void put(int s, const Vec<Dual>& f) const {
+    if (s == kNone) return;
     cx[s] = f.x.d;
     cy[s] = f.y.d;
     cz[s] = f.z.d;
+  }
+  __device__ void add(int s, const Vec<Dual>& f) const {
+    if (s == kNone) return;
+    cx[s] += f.x.d;
+    cy[s] += f.y.d;
+    cz[s] += f.z.d;
   }
 };
 
@@ -507,23 +515,43 @@ __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
     DeviceTables T, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ gxn, const float* __restrict__ gvn, float* __restrict__ gx,
     float* __restrict__ gvo, double* __restrict__ gparams, const float* __restrict__ gve) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ double s_red[3][kForceThreads / 32];
   __shared__ int s_last;
+  __shared__ __align__(8) unsigned long long bar;
   const int2 wk = T.work[blockIdx.x];
   const BodyDev B = T.body[wk.x];
   const TopoDev topo = T.topo[B.topo];
   const PatchHdr P = T.patch[topo.patch_off + wk.y];
+  const FPatch Q = T.fpatch[topo.patch_off + wk.y];
+  // the forward kernel's blob (edge and face records, slot starts) with the
+  // adjoint's tail (each own vertex's faces and corners), the rest data,
+  // positions and tangents of the local vertices, contribution slots
+  const int pe = pad4(P.n_edge), pf = pad4(P.n_face);
+  const int rest_words = frest_words(P.n_edge, P.n_face, B.varied != 0);
+  const uint4* rec = reinterpret_cast<const uint4*>(sm);
+  const uint2* frec = reinterpret_cast<const uint2*>(sm + 4 * P.n_edge);
+  const uint16_t* ptr = reinterpret_cast<const uint16_t*>(sm + 4 * P.n_edge + 2 * P.n_face);
+  const uint16_t* vptr = reinterpret_cast<const uint16_t*>(sm + Q.blob_words);
+  const uint32_t* vent = reinterpret_cast<const uint32_t*>(sm + Q.blob_words) + (P.n_own + 2) / 2;
+  const float* rest = sm + Q.blob_words + Q.vf_words;
   DSmem S;
-  S.px = sm;
-  S.py = S.px + P.n_loc;
-  S.pz = S.py + P.n_loc;
-  S.tx = S.pz + P.n_loc;
-  S.ty = S.tx + P.n_loc;
-  S.tz = S.ty + P.n_loc;
-  S.cx = S.tz + P.n_loc;
-  S.cy = S.cx + P.n_slot;
-  S.cz = S.cy + P.n_slot;
+  S.px = sm + Q.blob_words + Q.vf_words + rest_words;
+  S.py = S.px + pad4(P.n_loc);
+  S.pz = S.py + pad4(P.n_loc);
+  S.tx = S.pz + pad4(P.n_loc);
+  S.ty = S.tx + pad4(P.n_loc);
+  S.tz = S.ty + pad4(P.n_loc);
+  S.cx = S.tz + pad4(P.n_loc);
+  S.cy = S.cx + pad4(Q.n_slot);
+  S.cz = S.cy + pad4(Q.n_slot);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    const unsigned nb = 4u * (unsigned)(Q.blob_words + Q.vf_words), nr = 4u * (unsigned)rest_words;
+    mbar_arrive_tx(&bar, nb + nr);
+    if (nb) bulk_load(sm, T.fblob + Q.blob_off, nb, &bar);
+    if (nr) bulk_load(sm + Q.blob_words + Q.vf_words, T.frest + T.wrest[blockIdx.x], nr, &bar);
+  }
   for (int i = threadIdx.x; i < P.n_loc; i += blockDim.x) {
     const int gvx = B.v_off + __ldg(T.loc_vert + P.loc_off + i);
     S.px[i] = __ldg(x + gvx);
@@ -541,71 +569,85 @@ __global__ void __launch_bounds__(kForceThreads) force_adjoint_kernel(
   const Dual cA(cf.x, (float)(B.kA / B.A0 * dA));
   const Dual cV(cf.y, B.closed ? (float)(B.kv / B.V0 * dV) : 0.f);
   double gks = 0.0, gkb = 0.0, gka = 0.0;
-  __syncthreads();
+  __syncthreads();   // positions and tangents staged, barrier initialised
+  if (!__syncthreads_and(mbar_wait(&bar, kCopyWaitClocks))) {
+    // the copies did not land: flag it, give them one more bounded wait
+    // (they write this block's shared memory) and leave
+    if (threadIdx.x == 0) {
+      atomicOr(T.err, ERR_TIMEOUT);
+      mbar_wait(&bar, kCopyWaitClocks);
+    }
+    __syncthreads();
+    return;
+  }
   for (int k = threadIdx.x; k < P.n_edge; k += blockDim.x) {
-    const PEdge r = T.pedge[P.edge_off + k];
-    const int ge = B.e_off + (r.eid & 0x7fffffff);
-    const bool hinge = r.l[3] != kNone;
-    const Vec<Dual> pa = S.pos(r.l[0]), pb = S.pos(r.l[1]);
-    const Vec<Dual> pc = hinge ? S.pos(r.l[2]) : pa, pd = hinge ? S.pos(r.l[3]) : pb;
-    const float2 cs0 = hinge ? __ldg(T.cs0 + ge) : make_float2(1.f, 0.f);
+    const uint4 r = rec[k];
+    const int la = r.x & 0xFFFF, lb = r.x >> 16, lc = r.y & 0xFFFF, ld = r.y >> 16;
+    const bool hinge = ld != kNone;
+    const Vec<Dual> pa = S.pos(la), pb = S.pos(lb);
+    const Vec<Dual> pc = hinge ? S.pos(lc) : pa, pd = hinge ? S.pos(ld) : pb;
+    const float c0 = hinge ? rest[pe + k] : 1.f, s0 = hinge ? rest[2 * pe + k] : 0.f;
     Vec<Dual> fa, fb, fc, fd, us[2], ub[4];
     float es, eb;
     // per-edge multipliers m: the forces use m k, the constants' cotangents
     // scale the per-unit-k forces by m
-    const float ms = B.varied ? __ldg(T.kse + ge) : 1.f;
-    const float mb = B.varied ? __ldg(T.kbe + ge) : 1.f;
-    edge_forces(pa, pb, pc, pd, hinge, __ldg(T.l0 + ge), cs0.x, cs0.y, B.ks * ms, B.kb * mb, fa, fb,
-                fc, fd, us, ub, es, eb);
-    S.put(k, fa);
-    S.put(P.n_edge + k, fb);
-    S.put(2 * P.n_edge + k, fc);
-    S.put(3 * P.n_edge + k, fd);
-    if (r.eid < 0) {   // owned edge: constants' cotangents
-      const Vec<float> ca = S.cot(r.l[0]), cb = S.cot(r.l[1]);
+    const float ms = B.varied ? rest[3 * pe + pf + k] : 1.f;
+    const float mb = B.varied ? rest[4 * pe + pf + k] : 1.f;
+    edge_forces(pa, pb, pc, pd, hinge, rest[k], c0, s0, B.ks * ms, B.kb * mb, fa, fb, fc, fd, us,
+                ub, es, eb);
+    S.put(r.z & 0xFFFF, fa);
+    S.put(r.z >> 16, fb);
+    S.put(r.w & 0xFFFF, fc);
+    S.put(r.w >> 16, fd);
+    if ((r.z & 0xFFFF) != kNone) {   // owned edge: constants' cotangents
+      const Vec<float> ca = S.cot(la), cb = S.cot(lb);
       gks += ms * (dotv(ca, us[0]) + dotv(cb, us[1]));
       if (hinge) {
-        const Vec<float> cc = S.cot(r.l[2]), cd = S.cot(r.l[3]);
+        const Vec<float> cc = S.cot(lc), cd = S.cot(ld);
         gkb += mb * (dotv(ca, ub[0]) + dotv(cb, ub[1]) + dotv(cc, ub[2]) + dotv(cd, ub[3]));
       }
     }
   }
-  const int fbase = 4 * P.n_edge;
+  __syncthreads();   // every edge slot written
+  // faces, added to the slots of the edge each is attached to (an edge per
+  // face: no two threads touch the same slot)
   for (int k = threadIdx.x; k < P.n_face; k += blockDim.x) {
-    const PFace r = T.pface[P.face_off + k];
+    const uint2 fr = frec[k];
+    const uint4 r = rec[fr.x & 0x3FFFFFFFu];
+    const bool right = (fr.x >> 30) & 1u;
+    const int la = r.x & 0xFFFF, lb = r.x >> 16;
+    const int v0 = right ? lb : la, v1 = right ? la : lb;
+    const int v2 = right ? (int)(r.y >> 16) : (int)(r.y & 0xFFFF);
+    const int d0 = right ? (int)(r.z >> 16) : (int)(r.z & 0xFFFF);
+    const int d1 = right ? (int)(r.z & 0xFFFF) : (int)(r.z >> 16);
+    const int d2 = right ? (int)(r.w >> 16) : (int)(r.w & 0xFFFF);
     Vec<Dual> f[3], gA[3], gV[3], ua[3];
     float ea;
-    const float ma = B.varied ? __ldg(T.kaf + B.f_off + r.fid) : 1.f;
-    face_forces(S.pos(r.l[0]), S.pos(r.l[1]), S.pos(r.l[2]), __ldg(T.A0f + B.f_off + r.fid),
-                B.ka * ma, cA, cV, f, gA, gV, ua, ea);
-    S.put(fbase + k, f[0]);
-    S.put(fbase + P.n_face + k, f[1]);
-    S.put(fbase + 2 * P.n_face + k, f[2]);
-    if (r.owned)
-      gka += ma * (dotv(S.cot(r.l[0]), ua[0]) + dotv(S.cot(r.l[1]), ua[1]) +
-                   dotv(S.cot(r.l[2]), ua[2]));
+    const float ma = B.varied ? rest[5 * pe + pf + k] : 1.f;
+    face_forces(S.pos(v0), S.pos(v1), S.pos(v2), rest[3 * pe + k], B.ka * ma, cA, cV, f, gA, gV,
+                ua, ea);
+    S.add(d0, f[0]);
+    S.add(d1, f[1]);
+    S.add(d2, f[2]);
+    if (fr.x >> 31)
+      gka += ma * (dotv(S.cot(v0), ua[0]) + dotv(S.cot(v1), ua[1]) + dotv(S.cot(v2), ua[2]));
   }
   __syncthreads();
-  const int* tri = T.tri + topo.tri_off;
   for (int i = threadIdx.x; i < P.n_own; i += blockDim.x) {
-    const int s0 = __ldg(T.csr_ptr + P.csr_off + i), s1 = __ldg(T.csr_ptr + P.csr_off + i + 1);
+    const int s0 = ptr[i], s1 = ptr[i + 1];
     float jx = 0.f, jy = 0.f, jz = 0.f;
-    for (int k = s0; k < s1; ++k) {
-      const int s = T.csr_slot[P.slot_off + k];
+    for (int s = s0; s < s1; ++s) {
       jx += S.cx[s];
       jy += S.cy[s];
       jz += S.cz[s];
     }
-    const int lv = P.own0 + i;
-    const int gvx = B.v_off + lv;
+    const int gvx = B.v_off + P.own0 + i;
     // traction part: the cotangents the faces left for this corner
-    const int* vp = T.v2f_ptr + topo.v2f_ptr_off;
-    const int q0 = __ldg(vp + lv), q1 = __ldg(vp + lv + 1);
     float wx = 0.f, wy = 0.f, wz = 0.f;   // the spread's velocity cotangent
-    for (int q = q0; q < q1; ++q) {
-      const int lf = __ldg(T.v2f_idx + topo.v2f_idx_off + q);
-      const int corner = (__ldg(tri + 3 * lf) == lv) ? 0 : ((__ldg(tri + 3 * lf + 1) == lv) ? 1 : 2);
-      const size_t gf = (size_t)B.f_off + lf;
+    for (int q = vptr[i]; q < vptr[i + 1]; ++q) {
+      const uint32_t e = vent[q];
+      const int corner = (int)(e >> 30);
+      const size_t gf = (size_t)B.f_off + (e & 0x3FFFFFFFu);
       jx += __ldg(T.gxe + (corner * 3 + 0) * (size_t)F + gf);
       jy += __ldg(T.gxe + (corner * 3 + 1) * (size_t)F + gf);
       jz += __ldg(T.gxe + (corner * 3 + 2) * (size_t)F + gf);
