@@ -408,7 +408,12 @@ ibm_status ibm_flow_set_phase_timing(ibm_flow* flow, int32_t on);
 ibm_status ibm_flow_get_phase_times(ibm_flow* flow, float* ms);
 
 /* Synchronise the stream and report the device error word (IBM_ERR_DEVICE if
- * a kernel flagged an out-of-range or non-finite value). */
+ * a kernel flagged an out-of-range or non-finite value, too many markers in
+ * one spread tile, or a wait for a bulk copy into shared memory that ran out:
+ * every such wait is bounded (about a second), after which the block sets the
+ * flag and returns; the word is reset by this call).  For testing that path,
+ * the environment variable IBM_TEST_STARVE_TX (bytes, at most 1024), when set
+ * at context creation, makes those waits expect more bytes than arrive. */
 ibm_status ibm_check_device_error(ibm_ctx* ctx);
 
 /* Phase timing of ibm_step (profiling aid, no counterpart in the paper): when

@@ -3,6 +3,7 @@
 // incidence), per-patch tables of the force kernel, the rest state in float64,
 // device upload and the entry points declared in include/ibm.h.
 #include <cuda_runtime.h>
+#include <cstdlib>
 
 #include <algorithm>
 #include <cmath>
@@ -570,6 +571,8 @@ void make_consts(ibm_ctx* c) {
   c->sc.kappa = (float)(1.0 / ((1.5 * alpha) * (1.5 * alpha)));
   c->sc.cl_scale = (float)(((h[0] + h[1] + h[2]) / 3.0) / (h[0] * h[1] * h[2]));
   c->sc.forward_euler = p.forward_euler ? 1 : 0;
+  const char* st = std::getenv("IBM_TEST_STARVE_TX");
+  c->sc.starve_tx = st ? std::max(0, std::min(std::atoi(st), 1024)) : 0;
   c->phi_bound = (float)phi_bound_of(c->sc.kappa);
 }
 
@@ -1738,7 +1741,9 @@ extern "C" ibm_status ibm_check_device_error(ibm_ctx* c) {
                    std::string("device error word ") + std::to_string(w) +
                        ((w & ERR_NONFINITE) ? " (non-finite or out-of-range marker position)" : "") +
                        ((w & ERR_TILE_DENSE) ? " (more than 65535 markers reach one spread tile)"
-                                             : ""));
+                                             : "") +
+                       ((w & ERR_TIMEOUT) ? " (a wait for a bulk copy into shared memory ran out)"
+                                          : ""));
   }
   return IBM_OK;
 }

@@ -102,7 +102,10 @@ struct StepConsts {
   float kappa;           // 1 / (1.5 alpha)^2: W = exp(-kappa * (delta in cells)^2) per direction
   float cl_scale;        // (hx + hy + hz) / 3 / (hx hy hz): c_l = A_l * cl_scale
   int32_t forward_euler;
-  int32_t pad;
+  int32_t starve_tx;     // bytes announced to the bulk-copy barriers beyond the copies: 0 in
+                         //  use; the environment variable IBM_TEST_STARVE_TX sets it at
+                         //  context creation, to test that every such wait runs out and
+                         //  reports ERR_TIMEOUT
 };
 
 constexpr int kMT = 256;             // markers (faces) per block of the marker kernel (a patch)

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     const unsigned nb = 4u * (unsigned)Q.blob_words, nr = 4u * (unsigned)rest_words;
-    mbar_arrive_tx(&bar, nb + nr);
+    mbar_arrive_tx(&bar, nb + nr + (unsigned)sc.starve_tx);
     if (nb) bulk_load(sm, T.fblob + Q.blob_off, nb, &bar);
     if (nr) bulk_load(sm + Q.blob_words, T.frest + T.wrest[blockIdx.x], nr, &bar);
   }

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
       const unsigned rb = 4u * (unsigned)pad4(nrows);
       const unsigned ob = fit ? 4u * (unsigned)pad4(N / 4) : 0u;
       const unsigned gb = fit ? 2u * (unsigned)((N / 4 + 7) & ~7) : 0u;
-      mbar_arrive_tx(&s_bar, 3u * rb + ob + gb);
+      mbar_arrive_tx(&s_bar, 3u * rb + ob + gb + (unsigned)sc.starve_tx);
       if (fit) {
         const int* src = hd + 16;
         bulk_load(s_xmin, src, rb, &s_bar);
