@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--patch", type=int, default=0)
+    ap.add_argument("--marker-patch", type=int, default=0, choices=[0, 128, 256],
+                    help="faces per marker-kernel block; 0: picked by measurement")
     ap.add_argument("--spread-variant", type=int, default=0, choices=[0, 1, 2],
                     help="1: spread inside the marker kernel (atomic flush); 2: tile-owned "
                          "spread kernels; 0: the library's default")
@@ -545,7 +547,8 @@ def extra_workload(args, name, variant, device, flush, peak, peak_kind, patch):
     wl = make(1)
     fields = W.sample_field(wl.field, wl.grid, device=device, dtype=torch.float32)
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha, patch_size=patch,
-                       device=device.index, spread_variant=variant)
+                       device=device.index, spread_variant=variant,
+                       marker_patch=getattr(args, "marker_patch_used", 0))
     stream = torch.cuda.current_stream(device)
     nx, ny, nz = wl.grid.n
     f = tuple(torch.zeros((nz, ny, nx), dtype=torch.float32, device=device) for _ in range(3))
@@ -613,8 +616,17 @@ def run_gb300(args, ws, rank, local):
         from paper_1612_03399_gb300.autotune import autotune_patch_size
         patch, tuned = autotune_patch_size(wl.bodies, wl.grid, fields, dt=wl.dt, mu=wl.mu,
                                            alpha=wl.alpha, device=local)
+    mtuned = None
+    mpatch = args.marker_patch
+    if mpatch == 0:
+        # marker-kernel patch size (faces per block) picked by measurement too
+        from paper_1612_03399_gb300.autotune import autotune_marker_patch
+        mpatch, mtuned = autotune_marker_patch(wl.bodies, wl.grid, fields, dt=wl.dt, mu=wl.mu,
+                                               alpha=wl.alpha, device=local, patch_size=patch)
+    args.marker_patch_used = mpatch
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
-                       patch_size=patch, device=local, spread_variant=args.spread_variant)
+                       patch_size=patch, device=local, spread_variant=args.spread_variant,
+                       marker_patch=mpatch)
     variant = ctx.spread_variant
     stream = torch.cuda.current_stream(device)
     nx, ny, nz = wl.grid.n
@@ -678,8 +690,10 @@ def run_gb300(args, ws, rank, local):
         return
     peak, peak_kind = hbm_peak()
     roof, per = kernel_roofline(variant, mean_ph, bytes_model, peak, peak_kind)
-    roof["traffic"] = ncu_traffic(roof["kernel"])
-    if variant == 1 and args.workload == "drops1000" and roof["kernel"] == "marker":
+    # the recorded counters were taken with 256-face marker patches
+    roof["traffic"] = ncu_traffic(roof["kernel"]) if mpatch == 256 or roof["kernel"] != "marker" \
+        else None
+    if variant == 1 and args.workload == "drops1000" and roof["kernel"] == "marker" and mpatch == 256:
         # per-marker instruction count measured on this workload's drops
         roof["issue"] = issue_roofline("marker", int(sum(len(b.tri) for b in wl.bodies)),
                                        per["marker"]["ms"], clk, local)
@@ -693,6 +707,7 @@ def run_gb300(args, ws, rank, local):
                    "faces": int(sum(len(b.tri) for b in wl.bodies)),
                    "grid": list(wl.grid.n), "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"{ws} independent replica(s)", "patch_size": patch,
+                   "marker_patch": mpatch, "autotune_marker_ms": mtuned,
                    "spread_variant": variant, "autotune_force_ms": tuned},
         "roofline": roof,
         "phases_ms": dict(zip(PHASES, map(float, mean_ph))),
@@ -710,7 +725,8 @@ def run_gb300(args, ws, rank, local):
         # the other spread variant on the same workload, for the choice of default
         other = 1 if variant == 2 else 2
         ctx2 = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
-                            patch_size=patch, device=local, spread_variant=other)
+                            patch_size=patch, device=local, spread_variant=other,
+                            marker_patch=mpatch)
         xa, va = ctx2.init_state()
         xb, vb = torch.empty_like(xa), torch.empty_like(va)
         for t in f:
@@ -731,7 +747,7 @@ def run_gb300(args, ws, rank, local):
         # interpolation and probe traction of every marker, closed form in
         # float32 against the general 4x4 solve and geometry in float64
         ctx3 = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
-                            patch_size=patch, device=local)
+                            patch_size=patch, device=local, marker_patch=mpatch)
         xa, va = ctx3.init_state()
         va.uniform_(-0.1, 0.1)
         times = {}

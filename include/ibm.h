@@ -113,6 +113,8 @@ typedef struct {
                                  (bitwise deterministic; the previous step's
                                  footprint is zeroed in the same pass);
                               0: the library's default (1)                      */
+  int32_t marker_patch;    /* faces per marker-kernel block (a surface patch of
+                              one body): 128 or 256; 0 -> 256                   */
 } ibm_params;
 
 /* Create a context for n_bodies bodies on CUDA device `device`: validates the

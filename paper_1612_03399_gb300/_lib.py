@@ -41,7 +41,8 @@ class GridDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
                 ("probe_h", C.c_double), ("theta0_zero", C.c_int32), ("forward_euler", C.c_int32),
-                ("patch_size", C.c_int32), ("spread_variant", C.c_int32)]
+                ("patch_size", C.c_int32), ("spread_variant", C.c_int32),
+                ("marker_patch", C.c_int32)]
 
 
 # exported symbols and their signatures (ctypes types), in header order
@@ -133,7 +134,7 @@ class Context:
     """
 
     def __init__(self, bodies, grid, dt=1e-3, mu=1.0, alpha=0.3, probe_h=0.0, theta0_zero=False,
-                 forward_euler=False, patch_size=0, device=0, spread_variant=0):
+                 forward_euler=False, patch_size=0, device=0, spread_variant=0, marker_patch=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the IBM library needs a CUDA device; there is no CPU fallback")
@@ -170,7 +171,7 @@ class Context:
             g.L[k] = float(grid.L[k])
         p = Params(dt=dt, mu=mu, alpha=alpha, probe_h=probe_h, theta0_zero=int(theta0_zero),
                    forward_euler=int(forward_euler), patch_size=int(patch_size),
-                   spread_variant=int(spread_variant))
+                   spread_variant=int(spread_variant), marker_patch=int(marker_patch))
         h = C.c_void_p()
         st = self.lib.ibm_create_bodies(C.byref(h), descs, len(bodies), C.byref(g), C.byref(p),
                                         device)
@@ -190,6 +191,7 @@ class Context:
         self._check(self.lib.ibm_get_params(self.h, C.byref(prm)))
         self.spread_variant = int(prm.spread_variant)
         self.patch_size = int(prm.patch_size)
+        self.marker_patch = int(prm.marker_patch)
         self.set_stream(torch.cuda.current_stream(self.device))
 
     # -- plumbing ------------------------------------------------------------

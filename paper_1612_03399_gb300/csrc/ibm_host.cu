@@ -619,6 +619,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     if (P < 32 || P > 2048) fail(IBM_ERR_INVALID_ARG, "patch_size must be in [32, 2048]");
     if (p.spread_variant < 0 || p.spread_variant > 2)
       fail(IBM_ERR_INVALID_ARG, "spread_variant must be 0, 1 or 2");
+    if (p.marker_patch != 0 && p.marker_patch != 128 && p.marker_patch != 256)
+      fail(IBM_ERR_INVALID_ARG, "marker_patch must be 0, 128 or 256");
 
     c = new ibm_ctx();
     c->device = device;
@@ -626,6 +628,8 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     c->prm.patch_size = P;
     c->spread_variant = p.spread_variant == 0 ? 1 : p.spread_variant;
     c->prm.spread_variant = c->spread_variant;
+    c->marker_patch = p.marker_patch == 0 ? kMT : p.marker_patch;
+    c->prm.marker_patch = c->marker_patch;
     c->gdesc = *grid;
     make_consts(c);
     double h[3];
@@ -653,8 +657,9 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
         topos.emplace_back();
         try {
           build_topology(topos.back(), B.tri, B.n_vert, B.n_face, P);
-          marker_patches(B.tri, B.n_face, B.rest, topos.back().mface, topos.back().mbound, kMT);
-          interleave_full_patches(topos.back().mface, topos.back().mbound, kMT);
+          marker_patches(B.tri, B.n_face, B.rest, topos.back().mface, topos.back().mbound,
+                         c->marker_patch);
+          interleave_full_patches(topos.back().mface, topos.back().mbound, c->marker_patch);
 
         } catch (Failure& f) {
           f.msg = "body " + std::to_string(b) + ": " + f.msg;

@@ -108,7 +108,8 @@ struct StepConsts {
                          //  reports ERR_TIMEOUT
 };
 
-constexpr int kMT = 256;             // markers (faces) per block of the marker kernel (a patch)
+constexpr int kMT = 256;             // most markers (faces) per block of the marker kernel (a
+                                     //  patch); the context picks 128 or 256 (marker_patch)
 
 // ---------------------------------------------------------------------------
 // tile-owned spread: the grid is cut into tiles of kTX x kTY x kTZ nodes (the
@@ -243,6 +244,17 @@ constexpr int kRowTableBytes =
 // (kMaxNodes / 4 words) and their row ids (kMaxNodes / 4 16-bit ids)
 constexpr int kCacheWords = 16 + 3 * kMaxRows + kMaxNodes / 4 + kMaxNodes / 8;
 constexpr int kMarkerSmemBytes = kRowTableBytes + 8 * kMaxNodes;
+// the same sizes for a marker patch of MT faces (kMaxRows, kMaxNodes and the
+// cache layout are those of the largest patch, kMT)
+__host__ __device__ constexpr int marker_rows(int MT) { return 4 * MT; }
+__host__ __device__ constexpr int marker_nodes(int MT) { return 35 * MT; }
+__host__ __device__ constexpr int marker_row_table_bytes(int MT) {
+  return ((4 * (5 * marker_rows(MT) + 4) + 6 * (marker_nodes(MT) / 4)) + 15) / 16 * 16;
+}
+__host__ __device__ constexpr int marker_smem_bytes(int MT) {
+  return marker_row_table_bytes(MT) + 8 * marker_nodes(MT);
+}
+static_assert(marker_smem_bytes(kMT) == kMarkerSmemBytes, "marker layout");
 
 // elementwise combinations of [3][V] arrays for the strong-coupling integrator
 constexpr int kLinCombMax = 6;
@@ -282,6 +294,7 @@ __device__ __forceinline__ float2 body_coef(const BodyDev& B, unsigned long long
 
 struct ibm_ctx {
   int device = 0;
+  int marker_patch = ibm::kMT;      // faces per marker-kernel block: 128 or 256
   // coupled forcing (allocated by the first ibm_flow_step with this context):
   // the per-chunk tables and per-face geometry of substep 0, and the forcing's
   // own footprint record for the clears between substeps

@@ -2,7 +2,7 @@
 // interpolation at the centroid, direct-forcing marker force, probe gradient
 // and traction, and spreading (Sec. 2.2, Eqs. mls..mls_cl; Sec. 5 steps 1-3).
 //
-// One block = one surface patch of ONE body (up to kMT faces, built by
+// One block = one surface patch of ONE body (up to 128 or 256 faces, built by
 // recursive coordinate bisection of the rest mesh), one thread per face.
 // The block builds a ROW MAP of its grid footprint: for every (y, z) row of
 // the nodes its 3x3x3 supports (centroids and probe ends) touch, the x-range
@@ -42,8 +42,8 @@ namespace {
 // REC (record mode): instead of spreading, write each marker's spread record
 // (centroid in cells, c_l F) and count it under the tiles of the tile-owned
 // spread, with the tile's largest |c_l F| per component
-template <bool MEASURE, bool INTERP, bool PROBE, bool SPREAD, bool REC>
-__global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
+template <int MT, bool MEASURE, bool INTERP, bool PROBE, bool SPREAD, bool REC>
+__global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
     DeviceTables T, Grid g, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ v, const float* __restrict__ u, const float* __restrict__ vv,
     const float* __restrict__ w, const float* __restrict__ pr, const float* __restrict__ accel,
@@ -61,18 +61,19 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
   constexpr bool VEL = INTERP || PROBE;
   constexpr bool ROWMAP = VEL || (SPREAD && !REC);
   extern __shared__ __align__(16) unsigned char dyn[];
-  int* s_xmin = reinterpret_cast<int*>(dyn);   // [kMaxRows]  then: staged offset - x0
-  int* s_xmax = s_xmin + kMaxRows;             // [kMaxRows]  then: row length
-  int* s_off = s_xmax + kMaxRows;              // [kMaxRows + 4] staged row start
-  int* s_nzlo = s_off + kMaxRows + 4;          // [kMaxRows] first / last group of the row
-  int* s_nzhi = s_nzlo + kMaxRows;             //   that received a nonzero spread
-  int* s_gofs = s_nzhi + kMaxRows;             // [kMaxNodes/4] global offset of each group
-  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_gofs + kMaxNodes / 4);  // row ids
-  float* bufA = reinterpret_cast<float*>(dyn + kRowTableBytes);
-  float* bufB = bufA + kMaxNodes;
+  constexpr int MR = marker_rows(MT), MN = marker_nodes(MT);   // (y, z) rows, staged nodes
+  int* s_xmin = reinterpret_cast<int*>(dyn);   // [MR]  then: staged offset - x0
+  int* s_xmax = s_xmin + MR;                   // [MR]  then: row length
+  int* s_off = s_xmax + MR;                    // [MR + 4] staged row start
+  int* s_nzlo = s_off + MR + 4;                // [MR] first / last group of the row
+  int* s_nzhi = s_nzlo + MR;                   //   that received a nonzero spread
+  int* s_gofs = s_nzhi + MR;                   // [MN/4] global offset of each group
+  unsigned short* s_grow = reinterpret_cast<unsigned short*>(s_gofs + MN / 4);  // row ids
+  float* bufA = reinterpret_cast<float*>(dyn + marker_row_table_bytes(MT));
+  float* bufB = bufA + MN;
   __shared__ int s_lo[3], s_hi[3];
   __shared__ int s_N;
-  __shared__ int s_warp[kMT / 32];
+  __shared__ int s_warp[MT / 32];
   __shared__ int s_bmax[3];
   __shared__ __align__(8) unsigned long long s_bar;
 
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     // every row's x-range and nonzero range start empty; done first, so that
     // the stores overlap the geometry loads (the barriers of the bounding-box
     // reduction make them visible)
-    for (int r = threadIdx.x; r < kMaxRows; r += blockDim.x) {
+    for (int r = threadIdx.x; r < MR; r += blockDim.x) {
       s_xmin[r] = INT_MAX;
       s_xmax[r] = INT_MIN;
       s_nzlo[r] = INT_MAX;
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
         bulk_load(s_gofs, src + 3 * kMaxRows, ob, &s_bar);
         bulk_load(s_grow, src + 3 * kMaxRows + kMaxNodes / 4, gb, &s_bar);
       }
-      s_off[kMaxRows] = N;
+      s_off[MR] = N;
     }
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
       s_nzlo[r] = INT_MAX;
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
     sy = s_hi[1] >= s_lo[1] ? s_hi[1] - s_lo[1] + 1 : 0;
     sz = s_hi[2] >= s_lo[2] ? s_hi[2] - s_lo[2] + 1 : 0;
     const long long nrows = (long long)sy * sz;
-    const bool rows_ok = nrows > 0 && nrows <= kMaxRows && sx <= 30000;
+    const bool rows_ok = nrows > 0 && nrows <= MR && sx <= 30000;
     if (rows_ok) {
       if (mine) {
         // every component's support at a point with f = floor(tau) lies in
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int r = 4 * threadIdx.x + q;
-        if (r < kMaxRows) {
+        if (r < MR) {
           s_off[r] = pos;
           s_xmax[r] = len[q];
           s_xmin[r] = st[q];
@@ -369,11 +370,11 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
       }
       if (threadIdx.x == blockDim.x - 1) {
         s_N = pos;
-        s_off[kMaxRows] = pos;
+        s_off[MR] = pos;
       }
       __syncthreads();
       N = s_N;
-      fit = N <= kMaxNodes;
+      fit = N <= MN;
       // per row, strided over the whole block: group -> row ids, global row
       // offset, wrapped first x and staged offset - x0 (row r is (y, z) =
       // (r % sy, r / sy), followed incrementally)
@@ -386,8 +387,8 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
             const int p0 = s_off[r], a = s_xmin[r];
             const int base = (wrap(zlo + zz, g.n[2]) * g.n[1] + wrap(ylo + yy, g.n[1])) * g.n[0];
             const int x0w = wrap(a, g.n[0]);
-            // groups past kMaxNodes / 4 only occur when the block does not fit
-            const int q1 = min((p0 + L) / 4, kMaxNodes / 4);
+            // groups past MN / 4 only occur when the block does not fit
+            const int q1 = min((p0 + L) / 4, MN / 4);
             for (int k = p0 / 4; k < q1; ++k) {
               s_grow[k] = (unsigned short)r;
               s_gofs[k] = base + wrap_pos(x0w + 4 * (k - p0 / 4), g.n[0]);
@@ -637,7 +638,7 @@ __global__ void __launch_bounds__(kMT, 512 / kMT) marker_kernel(
           }
           if (bm == 0.f) continue;   // nothing to spread for this component
           // scale 2^k with every contribution below 2^22: a node takes at most
-          // kMT of them, so the sum stays below 2^30
+          // MT <= 256 of them, so the sum stays below 2^30
           const int k = min(22 - (ilogbf(bm) + 1), 120);
           inv[j] = pow2f(-max(k, -126));
           if (mine && coef != 0.f)
@@ -796,20 +797,33 @@ __global__ void measure_finalize_kernel(DeviceTables T, int32_t nb) {
 // null (unused) pointers count as aligned
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+template <int MT, bool M, bool I, bool P, bool S, bool R>
+cudaError_t launch_mt(ibm_ctx* c, const float* x, const float* v, const float* u, const float* vv,
+                      const float* w, const float* pr, const float* accel, float* U, float* Fm,
+                      const float* Fm_in, float* Fext, float* fx, float* fy, float* fz,
+                      int record, int tmode, const DeviceTables* tab, int cache) {
+  const size_t smem = (I || P || (S && !R)) ? marker_smem_bytes(MT) : 0;
+  const int vec4 = c->vec4 && aligned16(u) && aligned16(vv) && aligned16(w) && aligned16(pr) &&
+                   aligned16(fx) && aligned16(fy) && aligned16(fz);
+  marker_kernel<MT, M, I, P, S, R><<<c->n_chunks, MT, smem, c->stream>>>(
+      tab ? *tab : c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, pr, accel,
+      U, Fm, Fm_in, Fext, fx, fy, fz, record, vec4, c->td, tmode, c->phi_bound, cache,
+      c->fc_tab, c->fc_face);
+  return cudaGetLastError();
+}
+
+// the marker kernel for the context's patch size (128 or 256 faces per block)
 template <bool M, bool I, bool P, bool S, bool R = false>
 cudaError_t launch_t(ibm_ctx* c, const float* x, const float* v, const float* u, const float* vv,
                      const float* w, const float* pr, const float* accel, float* U, float* Fm,
                      const float* Fm_in, float* Fext, float* fx, float* fy, float* fz,
                      int record, int tmode = 0, const DeviceTables* tab = nullptr, int cache = 0) {
   if (c->n_chunks == 0) return cudaSuccess;
-  const size_t smem = (I || P || (S && !R)) ? kMarkerSmemBytes : 0;
-  const int vec4 = c->vec4 && aligned16(u) && aligned16(vv) && aligned16(w) && aligned16(pr) &&
-                   aligned16(fx) && aligned16(fy) && aligned16(fz);
-  marker_kernel<M, I, P, S, R><<<c->n_chunks, kMT, smem, c->stream>>>(
-      tab ? *tab : c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, pr, accel,
-      U, Fm, Fm_in, Fext, fx, fy, fz, record, vec4, c->td, tmode, c->phi_bound, cache,
-      c->fc_tab, c->fc_face);
-  return cudaGetLastError();
+  if (c->marker_patch == 128)
+    return launch_mt<128, M, I, P, S, R>(c, x, v, u, vv, w, pr, accel, U, Fm, Fm_in, Fext, fx, fy,
+                                         fz, record, tmode, tab, cache);
+  return launch_mt<kMT, M, I, P, S, R>(c, x, v, u, vv, w, pr, accel, U, Fm, Fm_in, Fext, fx, fy,
+                                       fz, record, tmode, tab, cache);
 }
 
 }  // namespace
@@ -818,8 +832,12 @@ cudaError_t set_marker_smem_limit() {
   cudaError_t e = cudaSuccess;
 #define SET(M, I, P, S, R)                                                                   \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(marker_kernel<M, I, P, S, R>,                                   \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMarkerSmemBytes);
+    e = cudaFuncSetAttribute(marker_kernel<kMT, M, I, P, S, R>,                              \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMarkerSmemBytes);  \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(marker_kernel<128, M, I, P, S, R>,                              \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,                    \
+                             marker_smem_bytes(128));
   SET(true, true, true, true, false)
   SET(true, false, true, false, false)
   SET(false, true, true, false, false)

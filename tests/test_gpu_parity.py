@@ -177,11 +177,15 @@ def tie_free_state(wl, seed0, **kw):
     raise RuntimeError("no tie-free state found")
 
 
-@pytest.mark.parametrize("forward_euler,variant", [(False, 1), (False, 2), (True, 2)])
-def test_step_parity(mixed, forward_euler, variant, record_error):
+@pytest.mark.parametrize("forward_euler,variant,marker_patch",
+                         [(False, 1, 0), (False, 2, 0), (True, 2, 0), (False, 1, 128),
+                          (False, 2, 128)])
+def test_step_parity(mixed, forward_euler, variant, marker_patch, record_error):
     wl, ob = mixed
     ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha,
-                       forward_euler=forward_euler, spread_variant=variant)
+                       forward_euler=forward_euler, spread_variant=variant,
+                       marker_patch=marker_patch)
+    assert ctx.marker_patch == (marker_patch or 256)
     rng = np.random.default_rng(5)
     rel = tie_free_state(wl, 10, scale=0.05, stretch=0.05)
     x = H.state_tensor(wl, rel)
