@@ -124,30 +124,48 @@ __device__ void mls_grad_hess(const float* __restrict__ f, const Grid& g, const 
     iy[s] = wrap(c[1] - 1 + s, g.n[1]);
     iz[s] = wrap(c[2] - 1 + s, g.n[2]);
   }
-  // derivative orders of the nine needed patterns (x, y, z)
-  constexpr int OX[9] = {1, 0, 0, 2, 0, 0, 1, 1, 0};
-  constexpr int OY[9] = {0, 1, 0, 0, 2, 0, 1, 0, 1};
-  constexpr int OZ[9] = {0, 0, 1, 0, 0, 2, 0, 1, 1};
+  // nine derivative patterns (x, y, z orders): 100 010 001 200 020 002 110
+  // 101 011.  Separable contraction: per row the (a, b) sums of the three x
+  // orders as packed pairs; per z-plane, for the six (x, y) order pairs the
+  // patterns use, P = sum_y a_y (xa, xb) and P3 = sum_y b_y xa; then per
+  // pattern acc += a_z (P.x - P.y - P3) - b_z P.x
+  constexpr int GX[6] = {1, 0, 0, 2, 0, 1}, GY[6] = {0, 1, 0, 0, 2, 1};
   float acc[9];
 #pragma unroll
   for (int p = 0; p < 9; ++p) acc[p] = 0.f;
 #pragma unroll
   for (int sz = 0; sz < 3; ++sz) {
+    float2 P[6];
+    float P3[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      P[q] = make_float2(0.f, 0.f);
+      P3[q] = 0.f;
+    }
 #pragma unroll
     for (int sy = 0; sy < 3; ++sy) {
       const float* r = f + ((size_t)iz[sz] * g.n[1] + iy[sy]) * g.n[0];
       const float u0 = __ldg(r + ix[0]), u1 = __ldg(r + ix[1]), u2 = __ldg(r + ix[2]);
-      float XA[3], XB[3];
+      float2 xo[3];
 #pragma unroll
       for (int o = 0; o < 3; ++o) {
-        XA[o] = X.a[o][0] * u0 + X.a[o][1] * u1 + X.a[o][2] * u2;
-        XB[o] = X.b[o][0] * u0 + X.b[o][1] * u1 + X.b[o][2] * u2;
+        xo[o] = __fmul2_rn(make_float2(X.a[o][0], X.b[o][0]), make_float2(u0, u0));
+        xo[o] = __ffma2_rn(make_float2(X.a[o][1], X.b[o][1]), make_float2(u1, u1), xo[o]);
+        xo[o] = __ffma2_rn(make_float2(X.a[o][2], X.b[o][2]), make_float2(u2, u2), xo[o]);
       }
 #pragma unroll
-      for (int p = 0; p < 9; ++p) {
-        const float ay = Y.a[OY[p]][sy], by = Y.b[OY[p]][sy], az = Z.a[OZ[p]][sz], bz = Z.b[OZ[p]][sz];
-        acc[p] += (XA[OX[p]] - XB[OX[p]]) * ay * az - XA[OX[p]] * (by * az + ay * bz);
+      for (int q = 0; q < 6; ++q) {
+        const float ay = Y.a[GY[q]][sy];
+        P[q] = __ffma2_rn(make_float2(ay, ay), xo[GX[q]], P[q]);
+        P3[q] = fmaf(Y.b[GY[q]][sy], xo[GX[q]].x, P3[q]);
       }
+    }
+    // pattern p: (x, y) pair and z order
+    constexpr int PQ[9] = {0, 1, 2, 3, 4, 2, 5, 0, 1}, PZ[9] = {0, 0, 1, 0, 0, 2, 0, 1, 1};
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      const int q = PQ[p];
+      acc[p] = fmaf(Z.a[PZ[p]][sz], P[q].x - P[q].y - P3[q], fmaf(-Z.b[PZ[p]][sz], P[q].x, acc[p]));
     }
   }
   gr[0] = acc[0];
@@ -182,28 +200,42 @@ __device__ void mls_val_grad(const float* __restrict__ f, const Grid& g, const f
     iy[s] = wrap(c[1] - 1 + s, g.n[1]);
     iz[s] = wrap(c[2] - 1 + s, g.n[2]);
   }
-  // derivative orders of the value and the three first derivatives
-  constexpr int OX[4] = {0, 1, 0, 0};
-  constexpr int OY[4] = {0, 0, 1, 0};
-  constexpr int OZ[4] = {0, 0, 0, 1};
+  // value and the three first derivatives (patterns 000 100 010 001), with
+  // the separable contraction of mls_grad_hess: (x, y) order pairs 00, 10, 01
+  constexpr int GX[3] = {0, 1, 0}, GY[3] = {0, 0, 1};
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int sz = 0; sz < 3; ++sz) {
+    float2 P[3];
+    float P3[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      P[q] = make_float2(0.f, 0.f);
+      P3[q] = 0.f;
+    }
 #pragma unroll
     for (int sy = 0; sy < 3; ++sy) {
       const float* r = f + ((size_t)iz[sz] * g.n[1] + iy[sy]) * g.n[0];
       const float u0 = __ldg(r + ix[0]), u1 = __ldg(r + ix[1]), u2 = __ldg(r + ix[2]);
-      float XA[2], XB[2];
+      float2 xo[2];
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
-        XA[o] = X.a[o][0] * u0 + X.a[o][1] * u1 + X.a[o][2] * u2;
-        XB[o] = X.b[o][0] * u0 + X.b[o][1] * u1 + X.b[o][2] * u2;
+        xo[o] = __fmul2_rn(make_float2(X.a[o][0], X.b[o][0]), make_float2(u0, u0));
+        xo[o] = __ffma2_rn(make_float2(X.a[o][1], X.b[o][1]), make_float2(u1, u1), xo[o]);
+        xo[o] = __ffma2_rn(make_float2(X.a[o][2], X.b[o][2]), make_float2(u2, u2), xo[o]);
       }
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const float ay = Y.a[OY[p]][sy], by = Y.b[OY[p]][sy], az = Z.a[OZ[p]][sz], bz = Z.b[OZ[p]][sz];
-        acc[p] += (XA[OX[p]] - XB[OX[p]]) * ay * az - XA[OX[p]] * (by * az + ay * bz);
+      for (int q = 0; q < 3; ++q) {
+        const float ay = Y.a[GY[q]][sy];
+        P[q] = __ffma2_rn(make_float2(ay, ay), xo[GX[q]], P[q]);
+        P3[q] = fmaf(Y.b[GY[q]][sy], xo[GX[q]].x, P3[q]);
       }
+    }
+    constexpr int PQ[4] = {0, 1, 2, 0}, PZ[4] = {0, 0, 0, 1};
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int q = PQ[p];
+      acc[p] = fmaf(Z.a[PZ[p]][sz], P[q].x - P[q].y - P3[q], fmaf(-Z.b[PZ[p]][sz], P[q].x, acc[p]));
     }
   }
   val = acc[0];
