@@ -381,3 +381,56 @@ def test_flow_step_full_size_matches_oracle(record_error):
     record_error("p", ep)
     assert eu <= 1e-5 and pok, (eu, ep)
     fl.close()
+
+
+def test_step_and_coupled_step_keep_separate_footprints():
+    """ibm_step clears the footprint of its own previous spread, the coupled
+    forcing its own (it keeps a record of its own): interleaving the two on
+    one context leaves each call's fields as a fresh context making only that
+    call would (up to the float order of the atomic merge), with nothing
+    left outside the footprint."""
+    wl, rel_x, vs = coupled_case(20)
+
+    def state():
+        return H.state_tensor(wl, rel_x), H.state_tensor(wl, vs)
+
+    def zeros3(like):
+        return tuple(torch.zeros_like(like) for _ in range(3))
+
+    fields = H.fields_for(wl, DEV)
+    ctx = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    fl = _lib.Flow(wl.grid, nu=wl.mu, dt=wl.dt)
+    x, v = state()
+    x1, v1 = torch.empty_like(x), torch.empty_like(v)
+    f1 = zeros3(fields[0])
+    ctx.step(x, v, fields, x1, v1, f1)
+    # a coupled step from x1 into fields of its own
+    u = tuple(t.clone() for t in fields)
+    p = torch.zeros_like(u[0])
+    f2 = zeros3(fields[0])
+    x2, v2 = torch.empty_like(x), torch.empty_like(v)
+    fl.step(u, p, ctx=ctx, x=x1, v=v1, x_out=x2, v_out=v2, f=f2)
+    # the step again, from x1, into f1 (its previous footprint is cleared)
+    x3, v3 = torch.empty_like(x), torch.empty_like(v)
+    ctx.step(x1, v1, fields, x3, v3, f1)
+    ctx.check_device_error()
+    # references: fresh contexts, each making one of the calls
+    ref = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    g1 = zeros3(fields[0])
+    ref.step(x1, v1, fields, torch.empty_like(x), torch.empty_like(v), g1)
+    ref2 = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha)
+    fl2 = _lib.Flow(wl.grid, nu=wl.mu, dt=wl.dt)
+    u2 = tuple(t.clone() for t in fields)
+    g2 = zeros3(fields[0])
+    fl2.step(u2, torch.zeros_like(u2[0]), ctx=ref2, x=x1, v=v1, x_out=torch.empty_like(x),
+             v_out=torch.empty_like(v), f=g2)
+    ref2.check_device_error()
+    for got, want in ((f1, g1), (f2, g2)):
+        a, b = stack_cpu(got), stack_cpu(want)
+        assert rel(a, b) <= 1e-6
+        assert torch.count_nonzero(a[b == 0]) == 0
+    assert rel(stack_cpu(u), stack_cpu(u2)) <= 1e-6
+    for c in (ctx, ref, ref2):
+        c.close()
+    fl.close()
+    fl2.close()
