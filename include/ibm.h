@@ -386,9 +386,14 @@ ibm_status ibm_flow_project(ibm_flow* flow, int32_t substep, float* u, float* v,
  * the narrow MLS kernel a marker corrects its nearest node with a gain of
  * about A_l/h^2, so faces must stay below about two grid cells in area (the
  * paper's meshes keep triangles near the grid size); coarser meshes make the
- * slip, and then the flow, grow from substep to substep.  Errors:
+ * slip, and then the flow, grow from substep to substep.  The first call with
+ * a context allocates that context's forcing cache (per marker patch its
+ * geometry and row tables, kept across the three substeps, and a footprint
+ * record of its own, so ibm_step's clear is not disturbed): make it outside
+ * a stream capture.  Errors:
  * IBM_ERR_INVALID_ARG on a mismatch or a null argument (message in
- * ibm_last_error(NULL) and, with a context, ibm_last_error(ctx)). */
+ * ibm_last_error(NULL) and, with a context, ibm_last_error(ctx));
+ * IBM_ERR_OOM when the forcing cache cannot be allocated. */
 ibm_status ibm_flow_step(ibm_flow* flow, ibm_ctx* ctx, const float* x, const float* xv,
                          float* x_out, float* v_out, float* u, float* v, float* w, float* p,
                          float* fx, float* fy, float* fz);
