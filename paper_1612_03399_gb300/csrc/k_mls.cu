@@ -747,34 +747,41 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
     const int nrows = sz.w;
     const int2* rm = rowmap + (size_t)blockIdx.x * max_rows;
     const int al = nx % 8 == 0 ? 8 : 4;   // widening, in floats
-    // eight lanes per row: each store instruction of a warp covers four rows
-    // with one contiguous 128-byte span each (a thread per row would scatter
-    // 32 rows over one instruction)
-    const int sub = threadIdx.x & 7;
-    for (int r = threadIdx.x >> 3; r < nrows; r += blockDim.x >> 3) {
-      const int2 e = rm[r];                  // (row base, first x wrapped | length << 16)
-      int L = e.y >> 16, x0 = e.y & 0xFFFF;  // L <= nx, x0 < nx
-      if (L <= 0) continue;
-      if (vec4) {
-        L = min((L + (x0 & (al - 1)) + al - 1) & ~(al - 1), nx);
-        x0 &= ~(al - 1);
-        for (int q = 4 * sub; q < L; q += 32) {
-          int xg = x0 + q;
-          if (xg >= nx) xg -= nx;
-          const size_t o = (size_t)e.x + xg;
-          const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-          *reinterpret_cast<float4*>(fx + o) = z4;
-          *reinterpret_cast<float4*>(fy + o) = z4;
-          *reinterpret_cast<float4*>(fz + o) = z4;
-        }
-      } else {
-        for (int q = sub; q < L; q += 8) {
-          int xg = x0 + q;
-          if (xg >= nx) xg -= nx;
-          const size_t o = (size_t)e.x + xg;
-          fx[o] = 0.f;
-          fy[o] = 0.f;
-          fz[o] = 0.f;
+    // each warp takes 32 rows at a time: one coalesced load of their records,
+    // then its four 8-lane groups clear 8 rows each, the records passed by
+    // shuffles (eight lanes per row: each store instruction of a warp covers
+    // four rows with one contiguous 128-byte span each)
+    const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+    for (int r0 = (threadIdx.x >> 5) * 32; r0 < nrows; r0 += blockDim.x) {
+      const int2 mine = r0 + lane < nrows ? rm[r0 + lane] : make_int2(0, 0);
+#pragma unroll 1
+      for (int j = 0; j < 8; ++j) {
+        const int src = 8 * grp + j;
+        const int ex = __shfl_sync(0xffffffffu, mine.x, src);
+        const int ey = __shfl_sync(0xffffffffu, mine.y, src);
+        int L = ey >> 16, x0 = ey & 0xFFFF;  // (row base, first x wrapped | length << 16)
+        if (L <= 0) continue;
+        if (vec4) {
+          L = min((L + (x0 & (al - 1)) + al - 1) & ~(al - 1), nx);
+          x0 &= ~(al - 1);
+          for (int q = 4 * sub; q < L; q += 32) {
+            int xg = x0 + q;
+            if (xg >= nx) xg -= nx;
+            const size_t o = (size_t)ex + xg;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(fx + o) = z4;
+            *reinterpret_cast<float4*>(fy + o) = z4;
+            *reinterpret_cast<float4*>(fz + o) = z4;
+          }
+        } else {
+          for (int q = sub; q < L; q += 8) {
+            int xg = x0 + q;
+            if (xg >= nx) xg -= nx;
+            const size_t o = (size_t)ex + xg;
+            fx[o] = 0.f;
+            fy[o] = 0.f;
+            fz[o] = 0.f;
+          }
         }
       }
     }
