@@ -690,12 +690,12 @@ def run_gb300(args, ws, rank, local):
         return
     peak, peak_kind = hbm_peak()
     roof, per = kernel_roofline(variant, mean_ph, bytes_model, peak, peak_kind)
-    # the recorded counters were taken with 256-face marker patches
-    roof["traffic"] = ncu_traffic(roof["kernel"]) if mpatch == 256 or roof["kernel"] != "marker" \
-        else None
-    if variant == 1 and args.workload == "drops1000" and roof["kernel"] == "marker" and mpatch == 256:
+    # counters are recorded per marker patch size (256: "marker", 128: "marker_p128")
+    rkey = roof["kernel"] if roof["kernel"] != "marker" or mpatch == 256 else f"marker_p{mpatch}"
+    roof["traffic"] = ncu_traffic(rkey)
+    if variant == 1 and args.workload == "drops1000" and roof["kernel"] == "marker":
         # per-marker instruction count measured on this workload's drops
-        roof["issue"] = issue_roofline("marker", int(sum(len(b.tri) for b in wl.bodies)),
+        roof["issue"] = issue_roofline(rkey, int(sum(len(b.tri) for b in wl.bodies)),
                                        per["marker"]["ms"], clk, local)
     launches = 3 if variant == 1 else 6
     line = {

@@ -45,6 +45,7 @@ def _digest() -> str:
 # the sources each profiled kernel is compiled from (for per-kernel digests)
 KERNEL_SOURCES = {
     "marker": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
+    "marker_p128": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
     "clear": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
     "forcing": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
     "body_marker": ["k_mls.cu", "mls_closed_form.cuh", "bulk_copy.cuh", "ibm_internal.cuh"],
