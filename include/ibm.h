@@ -239,6 +239,34 @@ ibm_status ibm_step_pc(ibm_ctx* ctx, const float* x, const float* v, const float
  * trajectory with Runge-Kutta steps. */
 ibm_status ibm_pc_reset(ibm_ctx* ctx);
 
+/* Checkpoint and resume.  The context's own mutable state: the
+ * strong-coupling history of ibm_step_pc (steps since ibm_pc_reset, the three
+ * previous states, the two previous accelerations and the last
+ * predictor-corrector difference; Sec. 2.3) and the record of the grid nodes
+ * the last clear-mode step left nonzero in the caller's force fields (spread
+ * variant 1: each marker patch's box and rows; variant 2: each tile's
+ * clear-mode epoch and nonzero 8-node segments).  Positions, velocities,
+ * fields and body constants belong to the caller and are not part of it.  A
+ * context given the state of another context of the same bodies, grid, step
+ * size and spread variant, with the caller's arrays as they were when it was
+ * taken, continues exactly as the other would have: ibm_step_pc takes the same
+ * predictor-corrector steps and a clear-mode step zeroes the same nodes.
+ *
+ * ibm_get_state: *size = the state's size in bytes; with buf != NULL the
+ * state is also written to buf (HOST memory of `capacity` bytes; a smaller
+ * capacity: IBM_ERR_INVALID_ARG, nothing written).  Synchronises the
+ * context's stream and reports a device error word first (as
+ * ibm_check_device_error), so no state is taken after a device error.
+ *
+ * ibm_set_state: reads `size` bytes of such a state from HOST memory buf;
+ * IBM_ERR_INVALID_ARG (context unchanged) when it is truncated, was not
+ * written by ibm_get_state of this format, belongs to a context of other
+ * sizes, step size or spread variant, or holds a footprint record that names
+ * nodes outside the grid.  Allocates the strong-coupling history if the state
+ * holds one (so not inside a stream capture); synchronous. */
+ibm_status ibm_get_state(ibm_ctx* ctx, void* buf, int64_t capacity, int64_t* size);
+ibm_status ibm_set_state(ibm_ctx* ctx, const void* buf, int64_t size);
+
 /* Adjoint of one step (a vector-Jacobian product, loose coupling with the
  * flow frozen; Sec. 2.3 node update, Sec. 2.2 traction and spreading, Sec. 2.3
  * potentials): given cotangents gx_next, gv_next [3][V] of the positions and

@@ -67,6 +67,8 @@ SIGNATURES = {
     "ibm_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
     "ibm_step_pc": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
     "ibm_pc_reset": (C.c_int, [P]),
+    "ibm_get_state": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64)]),
+    "ibm_set_state": (C.c_int, [P, P, C.c_int64]),
     "ibm_check_device_error": (C.c_int, [P]),
     "ibm_set_phase_timing": (C.c_int, [P, C.c_int32]),
     "ibm_get_phase_times": (C.c_int, [P, C.POINTER(C.c_float)]),
@@ -294,6 +296,20 @@ class Context:
 
     def pc_reset(self):
         self._check(self.lib.ibm_pc_reset(self.h))
+
+    def get_state(self):
+        """The context's own mutable state (ibm_get_state) as bytes: the
+        strong-coupling history and the last clear-mode step's footprint."""
+        n = C.c_int64(0)
+        self._check(self.lib.ibm_get_state(self.h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.ibm_get_state(self.h, C.cast(buf, C.c_void_p), n.value, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def set_state(self, state):
+        """Restore a state taken by get_state (ibm_set_state)."""
+        state = bytes(state)
+        self._check(self.lib.ibm_set_state(self.h, state, len(state)))
 
     def backward(self, x, fields, gx_next, gv_next, p=None, accel=None, v=None, gf=None):
         """Cotangents (gx, gv, gparams [B, 5]) of one step from (x, v)

@@ -1398,6 +1398,223 @@ extern "C" ibm_status ibm_pc_reset(ibm_ctx* c) {
   return IBM_OK;
 }
 
+namespace {
+
+// Checkpoint of the context's own mutable state (ibm_get_state/ibm_set_state):
+// a fixed header, then the strong-coupling history (when steps > 0: ten
+// [3][V] float arrays), then the footprint record of the spread variant in
+// use (1: every marker patch's two box words and its rows, compacted to the
+// rows the box declares; 2: every tile's clear-mode epoch and nonzero-segment
+// mask).  Host byte order.
+struct StateHeader {
+  char magic[8];          // "IBMSTATE"
+  uint32_t version;       // 1
+  int32_t spread_variant;
+  int64_t V, F, n_chunks, n_tiles;
+  int32_t grid_n[3];      // grid nodes per direction
+  uint32_t dt_bits;       // the step size the history belongs to
+  int32_t pc_steps;       // ibm_step_pc calls since ibm_pc_reset
+  int32_t pc_have;        // the last step's predictor-corrector difference is held
+  int32_t tile_epoch;     // clear-mode epoch of the tile-owned spread
+  int32_t reserved;       // 0
+  int64_t n_rows;         // row records of the variant-1 footprint
+};
+static_assert(sizeof(StateHeader) == 88, "state header layout");
+constexpr char kStateMagic[8] = {'I', 'B', 'M', 'S', 'T', 'A', 'T', 'E'};
+constexpr int kStateArrays = 10;
+
+// the history arrays in their logical order: y_{n-1..n-3} (x, then v), a_n,
+// a_{n-1} as the next step sees them, and p - c of the last step
+void state_arrays(ibm_ctx* c, float* (&out)[kStateArrays]) {
+  auto& P = c->pc;
+  float* a[kStateArrays] = {P.yx[0], P.yx[1], P.yx[2], P.yv[0], P.yv[1],
+                            P.yv[2], P.a[1],  P.a[2],  P.pcx,   P.pcv};
+  for (int k = 0; k < kStateArrays; ++k) out[k] = a[k];
+}
+
+// rows a variant-1 box declares (what the clear kernel reads of its rows)
+int64_t box_rows(const int4& lo, const int4& sz) {
+  if (sz.x <= 0 || sz.y <= 0 || sz.z <= 0 || lo.w == 1) return 0;
+  return std::max(sz.w, 0);
+}
+
+// a footprint record from a checkpoint may only name nodes of this grid
+bool box_valid(const ibm_ctx* c, const int4& lo, const int4& sz) {
+  if (lo.w < 0 || lo.w > 2) return false;
+  // corners well inside int range (the clear wraps lo + offset into the grid)
+  const int lim = 1 << 28;
+  if (std::abs(lo.x) > lim || std::abs(lo.y) > lim || std::abs(lo.z) > lim) return false;
+  if (sz.x > c->grid.n[0] || sz.y > c->grid.n[1] || sz.z > c->grid.n[2]) return false;
+  return sz.w >= 0 && sz.w <= kMaxRows;
+}
+
+bool row_valid(const ibm_ctx* c, const int2& e) {
+  const int L = e.y >> 16, x0 = e.y & 0xFFFF;
+  if (L <= 0) return true;   // skipped by the clear
+  const int64_t nx = c->grid.n[0];
+  const int64_t total = nx * c->grid.n[1] * c->grid.n[2];
+  return L <= nx && x0 < nx && e.x >= 0 && e.x % nx == 0 && (int64_t)e.x < total;
+}
+
+}  // namespace
+
+extern "C" ibm_status ibm_get_state(ibm_ctx* c, void* buf, int64_t capacity, int64_t* size) {
+  if (!c || !size) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  const ibm_status st = ibm_check_device_error(c);
+  if (st != IBM_OK) return st;
+  cudaSetDevice(c->device);
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, sizeof(h.magic));
+  h.version = 1;
+  h.spread_variant = c->spread_variant;
+  h.V = c->V;
+  h.F = c->F;
+  h.n_chunks = c->n_chunks;
+  h.n_tiles = c->spread_variant == 2 ? c->td.n_tiles : 0;
+  for (int k = 0; k < 3; ++k) h.grid_n[k] = c->grid.n[k];
+  std::memcpy(&h.dt_bits, &c->sc.dt, sizeof(h.dt_bits));
+  h.pc_steps = c->pc.pcx ? c->pc.steps : 0;
+  h.pc_have = h.pc_steps > 0 && c->pc.have_pc ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  std::vector<int4> boxes;
+  std::vector<int2> rows;
+  if (c->spread_variant == 2) {
+    e = cudaMemcpy(&h.tile_epoch, c->td.state + TS_EPOCH, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  } else if (c->n_chunks > 0) {
+    boxes.resize(2 * (size_t)c->n_chunks);
+    rows.resize((size_t)kMaxRows * c->n_chunks);
+    e = cudaMemcpy(boxes.data(), c->d.boxes, sizeof(int4) * boxes.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(rows.data(), c->d.rowmap, sizeof(int2) * rows.size(), cudaMemcpyDeviceToHost);
+    // compact: each patch's declared rows, in patch order
+    size_t n = 0;
+    for (int64_t q = 0; q < c->n_chunks && e == cudaSuccess; ++q) {
+      const int64_t r = box_rows(boxes[2 * q], boxes[2 * q + 1]);
+      std::memmove(rows.data() + n, rows.data() + (size_t)q * kMaxRows, sizeof(int2) * r);
+      n += (size_t)r;
+    }
+    rows.resize(n);
+    h.n_rows = (int64_t)n;
+  }
+  if (e != cudaSuccess) return cuda_status(c, e, "ibm_get_state");
+  const int64_t hist = h.pc_steps > 0 ? (int64_t)kStateArrays * 3 * c->V * 4 : 0;
+  const int64_t total = (int64_t)sizeof(h) + hist +
+                        (c->spread_variant == 2
+                             ? 13 * 4 * h.n_tiles
+                             : (int64_t)sizeof(int4) * (int64_t)boxes.size() + 8 * h.n_rows);
+  *size = total;
+  if (!buf) return IBM_OK;
+  if (capacity < total)
+    return set_err(c, IBM_ERR_INVALID_ARG,
+                   "ibm_get_state: the buffer holds " + std::to_string(capacity) +
+                       " bytes, the state needs " + std::to_string(total));
+  char* o = static_cast<char*>(buf);
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  if (hist) {
+    float* a[kStateArrays];
+    state_arrays(c, a);
+    const size_t bytes = sizeof(float) * 3 * (size_t)c->V;
+    for (int k = 0; k < kStateArrays && e == cudaSuccess; ++k, o += bytes)
+      e = cudaMemcpy(o, a[k], bytes, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess && c->spread_variant == 2 && h.n_tiles > 0) {
+    e = cudaMemcpy(o, c->td.epoch, 4 * (size_t)h.n_tiles, cudaMemcpyDeviceToHost);
+    o += 4 * (size_t)h.n_tiles;
+    if (e == cudaSuccess)
+      e = cudaMemcpy(o, c->td.mask, 48 * (size_t)h.n_tiles, cudaMemcpyDeviceToHost);
+  } else if (c->spread_variant != 2) {
+    std::memcpy(o, boxes.data(), sizeof(int4) * boxes.size());
+    o += sizeof(int4) * boxes.size();
+    std::memcpy(o, rows.data(), sizeof(int2) * rows.size());
+  }
+  return cuda_status(c, e, "ibm_get_state");
+}
+
+extern "C" ibm_status ibm_set_state(ibm_ctx* c, const void* buf, int64_t size) {
+  if (!c || !buf) return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  auto bad = [c](const std::string& m) {
+    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_set_state: " + m);
+  };
+  if (size < (int64_t)sizeof(StateHeader)) return bad("truncated state");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kStateMagic, sizeof(h.magic)) != 0 || h.version != 1)
+    return bad("not a state of this library");
+  uint32_t dt_bits;
+  std::memcpy(&dt_bits, &c->sc.dt, sizeof(dt_bits));
+  const int64_t n_tiles = c->spread_variant == 2 ? c->td.n_tiles : 0;
+  if (h.spread_variant != c->spread_variant || h.V != c->V || h.F != c->F ||
+      h.n_chunks != c->n_chunks || h.n_tiles != n_tiles || h.dt_bits != dt_bits ||
+      h.grid_n[0] != c->grid.n[0] || h.grid_n[1] != c->grid.n[1] || h.grid_n[2] != c->grid.n[2])
+    return bad("the state belongs to a context of other bodies, grid, parameters or spread "
+               "variant");
+  if (h.pc_steps < 0 || (h.pc_have != 0 && h.pc_have != 1) || h.reserved != 0 || h.n_rows < 0 ||
+      h.n_rows > (int64_t)kMaxRows * c->n_chunks || (c->spread_variant == 2 && h.n_rows != 0))
+    return bad("corrupt header");
+  const int64_t hist = h.pc_steps > 0 ? (int64_t)kStateArrays * 3 * c->V * 4 : 0;
+  const int64_t total = (int64_t)sizeof(h) + hist +
+                        (c->spread_variant == 2 ? 13 * 4 * n_tiles
+                                                : 32 * (int64_t)c->n_chunks + 8 * h.n_rows);
+  if (size != total) return bad("size does not match the header");
+  const char* in = static_cast<const char*>(buf) + sizeof(h);
+  const char* rec = in + hist;
+  // check the footprint record before anything reaches the device: the next
+  // clear-mode step writes zeros where it points
+  std::vector<int2> rowmap;
+  if (c->spread_variant != 2 && c->n_chunks > 0) {
+    std::vector<int4> boxes(2 * (size_t)c->n_chunks);
+    std::memcpy(boxes.data(), rec, sizeof(int4) * boxes.size());
+    const char* rp = rec + sizeof(int4) * boxes.size();
+    rowmap.assign((size_t)kMaxRows * c->n_chunks, make_int2(0, 0));
+    int64_t n = 0;
+    for (int64_t q = 0; q < c->n_chunks; ++q) {
+      if (!box_valid(c, boxes[2 * q], boxes[2 * q + 1])) return bad("corrupt footprint box");
+      const int64_t r = box_rows(boxes[2 * q], boxes[2 * q + 1]);
+      if (n + r > h.n_rows) return bad("footprint rows do not match the header");
+      std::memcpy(rowmap.data() + (size_t)q * kMaxRows, rp + 8 * n, 8 * (size_t)r);
+      for (int64_t k = 0; k < r; ++k)
+        if (!row_valid(c, rowmap[(size_t)q * kMaxRows + k])) return bad("corrupt footprint row");
+      n += r;
+    }
+    if (n != h.n_rows) return bad("footprint rows do not match the header");
+  }
+  cudaSetDevice(c->device);
+  if (h.pc_steps > 0) {
+    try {
+      pc_allocate(c);
+    } catch (Failure& f) {
+      return set_err(c, f.s, f.msg);
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (hist && e == cudaSuccess) {
+    float* a[kStateArrays];
+    state_arrays(c, a);
+    const size_t bytes = sizeof(float) * 3 * (size_t)c->V;
+    for (int k = 0; k < kStateArrays && e == cudaSuccess; ++k)
+      e = cudaMemcpy(a[k], in + k * bytes, bytes, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && c->spread_variant == 2 && n_tiles > 0) {
+    e = cudaMemcpy(c->td.state + TS_EPOCH, &h.tile_epoch, sizeof(int32_t),
+                   cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->td.epoch, rec, 4 * (size_t)n_tiles, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->td.mask, rec + 4 * (size_t)n_tiles, 48 * (size_t)n_tiles,
+                     cudaMemcpyHostToDevice);
+  } else if (e == cudaSuccess && c->spread_variant != 2 && c->n_chunks > 0) {
+    e = cudaMemcpy(c->d.boxes, rec, 32 * (size_t)c->n_chunks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d.rowmap, rowmap.data(), sizeof(int2) * rowmap.size(),
+                     cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return cuda_status(c, e, "ibm_set_state");
+  c->pc.steps = h.pc_steps;
+  c->pc.have_pc = h.pc_have != 0;
+  return IBM_OK;
+}
+
 extern "C" ibm_status ibm_step_pc(ibm_ctx* c, const float* x, const float* v, const float* u,
                                   const float* vv, const float* w, const float* p,
                                   const float* accel, float* x_out, float* v_out, float* fx,
