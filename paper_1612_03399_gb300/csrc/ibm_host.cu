@@ -548,9 +548,12 @@ double phi_bound_of(double kappa) {
 // with the previous footprint cleared (clear) or accumulated
 cudaError_t launch_step_marker(ibm_ctx* c, const float* x, const float* v, const float* u,
                                const float* vv, const float* w, const float* p,
-                               const float* accel, float* fx, float* fy, float* fz, bool clear) {
+                               const float* accel, float* fx, float* fy, float* fz, bool clear,
+                               bool after_clear) {
+  // after_clear: the footprint clear is the launch just before this one on
+  // the same stream (nothing between them), so the marker kernel may overlap it
   return launch_mls(c, x, v, u, vv, w, p, accel, nullptr, nullptr, nullptr, c->d.fext, fx, fy, fz,
-                    true, true, true, true, clear);
+                    true, true, true, true, clear, after_clear && !c->timing);
 }
 
 void make_consts(ibm_ctx* c) {
@@ -1251,7 +1254,8 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     // step ran before it.  It also zeroes the fixed-point body sums.
     e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
     mark(1);
-    if (e == cudaSuccess) e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, clear);
+    if (e == cudaSuccess)
+      e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, clear, clear);
     mark(2);
     mark(3);
     if (e == cudaSuccess)
@@ -1643,7 +1647,8 @@ extern "C" ibm_status ibm_step_pc(ibm_ctx* c, const float* x, const float* v, co
     if (e == cudaSuccess) e = launch_tile_spread(c, fx, fy, fz, !clear);
   } else {
     e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
-    if (e == cudaSuccess) e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, clear);
+    if (e == cudaSuccess)
+      e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, clear, clear);
   }
   float* an = P.a[0];
   if (e == cudaSuccess) e = launch_accel(c, x, c->d.fext, an);
@@ -1819,8 +1824,11 @@ extern "C" ibm_status ibm_graph_create(ibm_ctx* c, float* xa, float* va, float* 
       const float* x = even ? xa : xb;
       const float* v = even ? va : vb;
       use_parity(c, c->qpar ^ 1);
+      // step 0's marker kernel overlaps the clear just before it; the later
+      // steps' follow the previous force kernel, with their clear on the side
       if (k == 0) e = launch_clear(c, fx, fy, fz);
-      if (e == cudaSuccess) e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, true);
+      if (e == cudaSuccess)
+        e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, true, k == 0);
       const bool next = k + 1 < n_steps;
       if (next && e == cudaSuccess) {
         e = cudaEventRecord(ev_marker, cap);

@@ -352,12 +352,13 @@ struct ibm_ctx {
 namespace ibm {
 // kernel launchers (defined in the kernel translation units)
 // p, accel: optional cell-centred pressure and vertex accelerations (probe
-// pressure with the marker-acceleration correction)
+// pressure with the marker-acceleration correction); after_clear: the launch
+// directly follows launch_clear on the stream and may overlap it
 cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* u,
                        const float* vv, const float* w, const float* p, const float* accel,
                        float* U, float* Fm, const float* Fm_in, float* Fext, float* fx, float* fy,
                        float* fz, bool measure, bool interp, bool probe, bool spread,
-                       bool record_cells);
+                       bool record_cells, bool after_clear = false);
 cudaError_t launch_clear(ibm_ctx* c, float* fx, float* fy, float* fz);
 cudaError_t launch_forcing(ibm_ctx* c, int substep, const float* x, const float* xv,
                            const float* u, const float* vv, const float* w, float* fx, float* fy,

@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
   __shared__ int s_warp[MT / 32];
   __shared__ int s_bmax[3];
   __shared__ __align__(8) unsigned long long s_bar;
+  __shared__ unsigned long long s_q[2][MT / 32];   // per-warp fixed-point body sums
 
   // a force kernel launched after this one may start once every block of
   // this grid runs (it waits for this grid's results before using them)
@@ -203,9 +204,11 @@ __global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
       qa += __shfl_xor_sync(0xffffffffu, qa, o);
       qv += __shfl_xor_sync(0xffffffffu, qv, o);
     }
-    if ((threadIdx.x & 31) == 0 && (threadIdx.x >> 5) * 32 < ch.z) {
-      atomicAdd(T.qsum + 2 * ch.x, (unsigned long long)qa);
-      if (B.closed) atomicAdd(T.qsum + 2 * ch.x + 1, (unsigned long long)qv);
+    // added to the body's sums after the wait below (a footprint clear
+    // launched before this kernel zeroes them)
+    if ((threadIdx.x & 31) == 0) {
+      s_q[0][threadIdx.x >> 5] = (unsigned long long)qa;
+      s_q[1][threadIdx.x >> 5] = (unsigned long long)qv;
     }
   }
 
@@ -578,6 +581,17 @@ __global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
     td.rec[2 * (size_t)gf + 1] = r1;
   }
 
+  // Everything above reads only inputs.  What follows meets the footprint
+  // clear of the step, which may be the grid launched just before this one
+  // (this kernel may then start while the clear still runs): the body sums
+  // it zeroes, the fields and the footprint record.  Wait for that grid to
+  // complete (immediate when nothing precedes programmatically).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (MEASURE && (threadIdx.x & 31) == 0 && (threadIdx.x >> 5) * 32 < ch.z) {
+    atomicAdd(T.qsum + 2 * ch.x, s_q[0][threadIdx.x >> 5]);
+    if (B.closed) atomicAdd(T.qsum + 2 * ch.x + 1, s_q[1][threadIdx.x >> 5]);
+  }
+
   // ---- spreading: exact fixed point, one 32-bit word per staged node and
   // component; components 0 and 1 in one pass (buffers A and B), component 2
   // in a second (A), each pass flushed with float4 global atomics ----------
@@ -717,6 +731,9 @@ __global__ void __launch_bounds__(256) clear_kernel(DeviceTables T, Grid g, floa
                                                     int vec4, const int4* __restrict__ chunks,
                                                     int4* __restrict__ boxes,
                                                     const int2* __restrict__ rowmap, int max_rows) {
+  // the marker kernel launched after this one may start at once: it waits
+  // for this grid's completion before it touches what this grid writes
+  asm volatile("griddepcontrol.launch_dependents;");
   // the first chunk of each body also zeroes the body's fixed-point sums
   if (threadIdx.x == 0) {
     const int4 ch = chunks[blockIdx.x];
@@ -808,15 +825,26 @@ template <int MT, bool M, bool I, bool P, bool S, bool R>
 cudaError_t launch_mt(ibm_ctx* c, const float* x, const float* v, const float* u, const float* vv,
                       const float* w, const float* pr, const float* accel, float* U, float* Fm,
                       const float* Fm_in, float* Fext, float* fx, float* fy, float* fz,
-                      int record, int tmode, const DeviceTables* tab, int cache) {
+                      int record, int tmode, const DeviceTables* tab, int cache, bool pdl) {
   const size_t smem = (I || P || (S && !R)) ? marker_smem_bytes(MT) : 0;
   const int vec4 = c->vec4 && aligned16(u) && aligned16(vv) && aligned16(w) && aligned16(pr) &&
                    aligned16(fx) && aligned16(fy) && aligned16(fz);
-  marker_kernel<MT, M, I, P, S, R><<<c->n_chunks, MT, smem, c->stream>>>(
-      tab ? *tab : c->d, c->grid, c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, pr, accel,
-      U, Fm, Fm_in, Fext, fx, fy, fz, record, vec4, c->td, tmode, c->phi_bound, cache,
-      c->fc_tab, c->fc_face);
-  return cudaGetLastError();
+  // pdl: launched as the programmatic dependent of the footprint clear just
+  // before it on the stream (it may start once every clear block runs)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)c->n_chunks);
+  cfg.blockDim = dim3(MT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, marker_kernel<MT, M, I, P, S, R>, tab ? *tab : c->d, c->grid,
+                            c->sc, (int32_t)c->V, (int32_t)c->F, x, v, u, vv, w, pr, accel, U,
+                            Fm, Fm_in, Fext, fx, fy, fz, record, vec4, c->td, tmode,
+                            c->phi_bound, cache, c->fc_tab, c->fc_face);
 }
 
 // the marker kernel for the context's patch size (128 or 256 faces per block)
@@ -824,13 +852,14 @@ template <bool M, bool I, bool P, bool S, bool R = false>
 cudaError_t launch_t(ibm_ctx* c, const float* x, const float* v, const float* u, const float* vv,
                      const float* w, const float* pr, const float* accel, float* U, float* Fm,
                      const float* Fm_in, float* Fext, float* fx, float* fy, float* fz,
-                     int record, int tmode = 0, const DeviceTables* tab = nullptr, int cache = 0) {
+                     int record, int tmode = 0, const DeviceTables* tab = nullptr, int cache = 0,
+                     bool pdl = false) {
   if (c->n_chunks == 0) return cudaSuccess;
   if (c->marker_patch == 128)
     return launch_mt<128, M, I, P, S, R>(c, x, v, u, vv, w, pr, accel, U, Fm, Fm_in, Fext, fx, fy,
-                                         fz, record, tmode, tab, cache);
+                                         fz, record, tmode, tab, cache, pdl);
   return launch_mt<kMT, M, I, P, S, R>(c, x, v, u, vv, w, pr, accel, U, Fm, Fm_in, Fext, fx, fy,
-                                       fz, record, tmode, tab, cache);
+                                       fz, record, tmode, tab, cache, pdl);
 }
 
 }  // namespace
@@ -862,11 +891,13 @@ cudaError_t launch_mls(ibm_ctx* c, const float* x, const float* v, const float* 
                        const float* vv, const float* w, const float* pr, const float* accel,
                        float* U, float* Fm, const float* Fm_in, float* Fext, float* fx, float* fy,
                        float* fz, bool measure, bool interp, bool probe, bool spread,
-                       bool record_box) {
+                       bool record_box, bool after_clear) {
   const int rb = record_box ? 1 : 0;
 #define L(M, I, P, S) \
   launch_t<M, I, P, S>(c, x, v, u, vv, w, pr, accel, U, Fm, Fm_in, Fext, fx, fy, fz, rb)
-  if (measure && interp && probe && spread) return L(true, true, true, true);
+  if (measure && interp && probe && spread)
+    return launch_t<true, true, true, true>(c, x, v, u, vv, w, pr, accel, U, Fm, Fm_in, Fext, fx,
+                                            fy, fz, rb, 0, nullptr, 0, after_clear);
   if (measure && !interp && !probe && !spread) return L(true, false, false, false);
   if (measure && !interp && probe && !spread) return L(true, false, true, false);
   if (!measure && interp && probe && !spread) return L(false, true, true, false);
