@@ -219,6 +219,22 @@ ibm_status ibm_step(ibm_ctx* ctx, const float* x, const float* v, const float* u
                     const float* vv, const float* w, const float* p, const float* accel,
                     float* x_out, float* v_out, float* fx, float* fy, float* fz, uint32_t flags);
 
+/* ibm_step with the body state in host memory: the same step, the same
+ * results, but x, v, x_out, v_out ([3][V] float32) may be HOST arrays
+ * (page-locked or ordinary) as well as device arrays; u, vv, w, p, accel and
+ * the fields are device arrays as in ibm_step.  Host inputs are copied into
+ * device arrays the context owns, on a second stream while the footprint
+ * clear runs; outputs in device or page-locked host memory are written by
+ * the force kernel directly (host memory over the host link), other host
+ * outputs through the context's device arrays and a copy.  Synchronous:
+ * returns when x_out, v_out hold the new state.  The first call allocates
+ * the context's copies of the state (4 [3][V] float arrays), a stream and two
+ * events.  Errors as ibm_step. */
+ibm_status ibm_step_host(ibm_ctx* ctx, const float* x, const float* v, const float* u,
+                         const float* vv, const float* w, const float* p, const float* accel,
+                         float* x_out, float* v_out, float* fx, float* fy, float* fz,
+                         uint32_t flags);
+
 /* Strong coupling (Sec. 2.3; the flow frozen, so the fluid-structure
  * iteration reduces to the structural integrator): one step of Hamming's
  * fourth-order predictor-corrector for y = (x, v), y' = (v, (F_int +

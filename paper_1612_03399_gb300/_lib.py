@@ -66,6 +66,7 @@ SIGNATURES = {
     "ibm_spread": (C.c_int, [P, P, P, P, P, P]),
     "ibm_step": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
     "ibm_step_pc": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
+    "ibm_step_host": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_uint32]),
     "ibm_pc_reset": (C.c_int, [P]),
     "ibm_get_state": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64)]),
     "ibm_set_state": (C.c_int, [P, P, C.c_int64]),
@@ -124,6 +125,14 @@ def _ptr(t):
     import torch
     if not (t.is_cuda and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _any_ptr(t):
+    """Address of a contiguous float32 tensor on the device or the host."""
+    import torch
+    if not (t.is_contiguous() and t.dtype == torch.float32):
+        raise ValueError("expected a contiguous float32 tensor")
     return C.c_void_p(t.data_ptr())
 
 
@@ -283,6 +292,20 @@ class Context:
         self._check(self.lib.ibm_step(self.h, _ptr(x), _ptr(v), _ptr(u), _ptr(vv), _ptr(w),
                                       _ptr(p), _ptr(accel), _ptr(x_out), _ptr(v_out), _ptr(fx),
                                       _ptr(fy), _ptr(fz), IBM_STEP_CLEAR_PREV if clear else 0))
+
+    def step_host(self, x, v, fields, x_out, v_out, f, clear=True, p=None, accel=None):
+        """One step with the state (x, v in; x_out, v_out out) in host or
+        device tensors (ibm_step_host): the copies between host and device
+        are part of the call, which returns when x_out, v_out are written."""
+        u, vv, w = fields
+        fx, fy, fz = f
+        for t in (x, v, x_out, v_out):
+            if t.numel() != 3 * self.V:
+                raise ValueError("state arrays are [3, V] float32")
+        self._check(self.lib.ibm_step_host(self.h, _any_ptr(x), _any_ptr(v), _ptr(u), _ptr(vv),
+                                           _ptr(w), _ptr(p), _ptr(accel), _any_ptr(x_out),
+                                           _any_ptr(v_out), _ptr(fx), _ptr(fy), _ptr(fz),
+                                           IBM_STEP_CLEAR_PREV if clear else 0))
 
     def step_pc(self, x, v, fields, x_out, v_out, f, clear=True, p=None, accel=None):
         """One Hamming predictor-corrector step (ibm_step_pc); the context

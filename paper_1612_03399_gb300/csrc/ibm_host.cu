@@ -1061,6 +1061,12 @@ extern "C" void ibm_destroy(ibm_ctx* c) {
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->hcopy) {
+    cudaStreamSynchronize(c->hcopy);
+    cudaStreamDestroy(c->hcopy);
+  }
+  if (c->ev_hfork) cudaEventDestroy(c->ev_hfork);
+  if (c->ev_hcopy) cudaEventDestroy(c->ev_hcopy);
   free_all(c);
   delete c;
 }
@@ -1218,15 +1224,15 @@ extern "C" ibm_status ibm_spread(ibm_ctx* c, const float* x, const float* Fm, fl
   return cuda_status(c, e, "ibm_spread");
 }
 
-extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const float* u,
-                               const float* vv, const float* w, const float* p,
-                               const float* accel, float* x_out, float* v_out, float* fx,
-                               float* fy, float* fz, uint32_t flags) {
-  if (!c || !x || !v || !u || !vv || !w || !x_out || !v_out || !fx || !fy || !fz)
-    return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
-  if (x_out == x || v_out == v || x_out == v || v_out == x)
-    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_step: outputs must not alias the inputs");
-  cudaSetDevice(c->device);
+namespace {
+
+// The launches of one ibm_step on the context's stream.  before_marker
+// (optional): an event the marker kernel must wait for (inputs copied in on
+// another stream); the footprint clear or set-up runs before that wait.
+cudaError_t step_launches(ibm_ctx* c, const float* x, const float* v, const float* u,
+                          const float* vv, const float* w, const float* p, const float* accel,
+                          float* x_out, float* v_out, float* fx, float* fy, float* fz,
+                          uint32_t flags, cudaEvent_t before_marker) {
   const bool clear = (flags & IBM_STEP_CLEAR_PREV) != 0;
   use_parity(c, c->qpar ^ 1);
   cudaError_t e = cudaSuccess;
@@ -1240,6 +1246,7 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     // kernel's traction and body sums)
     e = launch_tile_begin(c, !clear, true);
     mark(1);
+    if (e == cudaSuccess && before_marker) e = cudaStreamWaitEvent(c->stream, before_marker, 0);
     if (e == cudaSuccess)
       e = launch_mls_records(c, x, v, u, vv, w, p, accel, nullptr, c->d.fext, true, true, !clear);
     mark(2);
@@ -1254,8 +1261,10 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     // step ran before it.  It also zeroes the fixed-point body sums.
     e = clear ? launch_clear(c, fx, fy, fz) : zero_body_sums(c);
     mark(1);
+    if (e == cudaSuccess && before_marker) e = cudaStreamWaitEvent(c->stream, before_marker, 0);
     if (e == cudaSuccess)
-      e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, clear, clear);
+      e = launch_step_marker(c, x, v, u, vv, w, p, accel, fx, fy, fz, clear,
+                             clear && !before_marker);
     mark(2);
     mark(3);
     if (e == cudaSuccess)
@@ -1266,7 +1275,101 @@ extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const
     c->have_prev = clear;
     c->timed = c->timing;
   }
-  return cuda_status(c, e, "ibm_step");
+  return e;
+}
+
+// where the kernels can reach a caller's array: device (or registered host)
+// memory by its device address, anything else only through a copy
+const float* device_view(const void* ptr, bool host_ok) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || (host_ok && at.type == cudaMemoryTypeHost))
+    return static_cast<const float*>(at.devicePointer);
+  return nullptr;
+}
+
+}  // namespace
+
+extern "C" ibm_status ibm_step(ibm_ctx* c, const float* x, const float* v, const float* u,
+                               const float* vv, const float* w, const float* p,
+                               const float* accel, float* x_out, float* v_out, float* fx,
+                               float* fy, float* fz, uint32_t flags) {
+  if (!c || !x || !v || !u || !vv || !w || !x_out || !v_out || !fx || !fy || !fz)
+    return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (x_out == x || v_out == v || x_out == v || v_out == x)
+    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_step: outputs must not alias the inputs");
+  cudaSetDevice(c->device);
+  return cuda_status(c, step_launches(c, x, v, u, vv, w, p, accel, x_out, v_out, fx, fy, fz,
+                                      flags, nullptr),
+                     "ibm_step");
+}
+
+extern "C" ibm_status ibm_step_host(ibm_ctx* c, const float* x, const float* v, const float* u,
+                                    const float* vv, const float* w, const float* p,
+                                    const float* accel, float* x_out, float* v_out, float* fx,
+                                    float* fy, float* fz, uint32_t flags) {
+  if (!c || !x || !v || !u || !vv || !w || !x_out || !v_out || !fx || !fy || !fz)
+    return set_err(c, IBM_ERR_INVALID_ARG, "null argument");
+  if (x_out == x || v_out == v || x_out == v || v_out == x)
+    return set_err(c, IBM_ERR_INVALID_ARG, "ibm_step_host: outputs must not alias the inputs");
+  cudaSetDevice(c->device);
+  const size_t bytes = sizeof(float) * 3 * (size_t)c->V;
+  if (!c->hcopy) {
+    // all or nothing: the staging arrays, the copy stream and its events
+    try {
+      float* b[4];
+      for (int k = 0; k < 4; ++k) b[k] = zeros<float>(c, 3 * (size_t)c->V);
+      cudaStream_t st = nullptr;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        if (st) cudaStreamDestroy(st);
+        if (e0) cudaEventDestroy(e0);
+        return cuda_status(c, e, "ibm_step_host");
+      }
+      for (int k = 0; k < 4; ++k) c->hs_buf[k] = b[k];
+      c->hcopy = st;
+      c->ev_hfork = e0;
+      c->ev_hcopy = e1;
+    } catch (Failure& f) {
+      return set_err(c, f.s, f.msg);
+    }
+  }
+  // inputs: device arrays are used in place; host arrays are copied into the
+  // staging arrays by the copy stream while the footprint clear runs (the
+  // kernels gather positions by vertex id, which host memory serves poorly)
+  const float* xd = device_view(x, false);
+  const float* vd = device_view(v, false);
+  // outputs: written by the force kernel wherever it can reach them
+  // (device or page-locked host memory); staged and copied back otherwise
+  float* xo = const_cast<float*>(device_view(x_out, true));
+  float* vo = const_cast<float*>(device_view(v_out, true));
+  cudaError_t e = cudaSuccess;
+  cudaEvent_t join = nullptr;
+  if (!xd || !vd) {
+    e = cudaEventRecord(c->ev_hfork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->hcopy, c->ev_hfork, 0);
+    if (e == cudaSuccess && !xd)
+      e = cudaMemcpyAsync(c->hs_buf[0], x, bytes, cudaMemcpyDefault, c->hcopy);
+    if (e == cudaSuccess && !vd)
+      e = cudaMemcpyAsync(c->hs_buf[1], v, bytes, cudaMemcpyDefault, c->hcopy);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_hcopy, c->hcopy);
+    join = c->ev_hcopy;
+  }
+  if (e == cudaSuccess)
+    e = step_launches(c, xd ? xd : c->hs_buf[0], vd ? vd : c->hs_buf[1], u, vv, w, p, accel,
+                      xo ? xo : c->hs_buf[2], vo ? vo : c->hs_buf[3], fx, fy, fz, flags, join);
+  if (e == cudaSuccess && !xo)
+    e = cudaMemcpyAsync(x_out, c->hs_buf[2], bytes, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess && !vo)
+    e = cudaMemcpyAsync(v_out, c->hs_buf[3], bytes, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(c, e, "ibm_step_host");
 }
 
 // One loosely coupled time step (Sec. 5 steps 1-4): per RK3 substep the flow's

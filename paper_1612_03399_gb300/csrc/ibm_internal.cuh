@@ -309,6 +309,13 @@ struct ibm_ctx {
   float phi_bound = 1.f;        // bound on |phi| of the MLS shape functions (fixed-point scales)
   int tile_grid = 0;            // blocks of the persistent tile kernels
   cudaStream_t side = nullptr;  // second stream of ibm_step (spread beside the force kernel)
+  // ibm_step_host: device copies of host-resident state (x, v in; x', v' out
+  // when the caller's memory is not device-accessible), the stream that
+  // copies the inputs in beside the footprint clear, and its events; made by
+  // the first call
+  float* hs_buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t hcopy = nullptr;
+  cudaEvent_t ev_hfork = nullptr, ev_hcopy = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t stream = nullptr;
   std::string err;
