@@ -247,9 +247,10 @@ def ncu_traffic(kernel_key):
 
 
 def ncu_instructions(kernel_key):
-    """Warp instructions per marker of `kernel_key` from the committed ncu
-    summary (the drop workload's count), or None when the kernel's sources
-    changed since it was taken."""
+    """Warp instructions per unit (marker, or own vertex for the force
+    kernel) of `kernel_key` from the committed ncu summary (the drop
+    workload's count), or None when the kernel's sources changed since it
+    was taken."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -263,20 +264,21 @@ def ncu_instructions(kernel_key):
         return None
 
 
-def issue_roofline(kernel_key, faces, ms, clk, device_index):
+def issue_roofline(kernel_key, units, ms, clk, device_index):
     """The kernel against its compute-side bound, instruction issue: warp
-    instructions per launch (ncu's per-marker count x markers) / its mean
-    duration, against 4 schedulers per SM issuing one warp instruction per
-    clock each, at the SM clock sampled during the timed region."""
+    instructions per launch (ncu's count per unit -- marker, or own vertex
+    for the force kernel -- x the units of a launch) / its mean duration,
+    against 4 schedulers per SM issuing one warp instruction per clock each,
+    at the SM clock sampled during the timed region."""
     ipf = ncu_instructions(kernel_key)
     mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
     if not ipf or not mhz:
         return None
     n_sm = torch.cuda.get_device_properties(device_index).multi_processor_count
     peak = n_sm * 4 * mhz * 1e6
-    achieved = ipf * faces / (ms * 1e-3)
+    achieved = ipf * units / (ms * 1e-3)
     return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp-instr/s",
-            "frac": achieved / peak, "inst_per_marker": ipf, "sm_mhz": mhz, "sms": n_sm}
+            "frac": achieved / peak, "inst_per_unit": ipf, "sm_mhz": mhz, "sms": n_sm}
 
 
 # ---------------------------------------------------------------------------
@@ -698,6 +700,10 @@ def run_gb300(args, ws, rank, local):
         # per-marker instruction count measured on this workload's drops
         roof["issue"] = issue_roofline(rkey, int(sum(len(b.tri) for b in wl.bodies)),
                                        per["marker"]["ms"], clk, local)
+        # the force kernel against the same bound (instructions per own vertex)
+        if "force" in per:
+            per["force"]["issue"] = issue_roofline("force", int(ctx.V), per["force"]["ms"], clk,
+                                                   local)
     launches = 3 if variant == 1 else 6
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": n_steps,
