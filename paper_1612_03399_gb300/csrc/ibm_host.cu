@@ -619,6 +619,7 @@ extern "C" ibm_status ibm_create_bodies(ibm_ctx** out, const ibm_body_desc* bodi
     if (!is_fin(p.alpha) || p.alpha < 0) fail(IBM_ERR_INVALID_ARG, "alpha must be >= 0");
     if (!is_fin(p.probe_h)) fail(IBM_ERR_INVALID_ARG, "probe_h must be finite");
     const int P = p.patch_size > 0 ? p.patch_size : 128;
+    static_assert(kMirrorChunk >= 2048, "a patch's own run meets at most two mirror chunks");
     if (P < 32 || P > 2048) fail(IBM_ERR_INVALID_ARG, "patch_size must be in [32, 2048]");
     if (p.spread_variant < 0 || p.spread_variant > 2)
       fail(IBM_ERR_INVALID_ARG, "spread_variant must be 0, 1 or 2");
@@ -1232,7 +1233,8 @@ namespace {
 cudaError_t step_launches(ibm_ctx* c, const float* x, const float* v, const float* u,
                           const float* vv, const float* w, const float* p, const float* accel,
                           float* x_out, float* v_out, float* fx, float* fy, float* fz,
-                          uint32_t flags, cudaEvent_t before_marker) {
+                          uint32_t flags, cudaEvent_t before_marker,
+                          const Mirror* mirror = nullptr) {
   const bool clear = (flags & IBM_STEP_CLEAR_PREV) != 0;
   use_parity(c, c->qpar ^ 1);
   cudaError_t e = cudaSuccess;
@@ -1253,7 +1255,7 @@ cudaError_t step_launches(ibm_ctx* c, const float* x, const float* v, const floa
     if (e == cudaSuccess) e = launch_tile_spread(c, fx, fy, fz, !clear);
     mark(3);
     if (e == cudaSuccess)
-      e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true);
+      e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true, mirror);
     mark(4);
   } else {
     // the clear is a no-op for blocks that recorded no footprint (first step),
@@ -1268,7 +1270,7 @@ cudaError_t step_launches(ibm_ctx* c, const float* x, const float* v, const floa
     mark(2);
     mark(3);
     if (e == cudaSuccess)
-      e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true);
+      e = launch_force(c, x, v, c->d.fext, nullptr, x_out, v_out, nullptr, true, mirror);
     mark(4);
   }
   if (e == cudaSuccess) {
@@ -1278,17 +1280,20 @@ cudaError_t step_launches(ibm_ctx* c, const float* x, const float* v, const floa
   return e;
 }
 
-// where the kernels can reach a caller's array: device (or registered host)
-// memory by its device address, anything else only through a copy
-const float* device_view(const void* ptr, bool host_ok) {
+// where a caller's array lives: device memory, page-locked host memory
+// (reachable by the kernels at its device address) or other host memory
+enum class Place { kDevice, kPinned, kOther };
+Place place_of(const void* ptr, float** dev) {
   cudaPointerAttributes at{};
+  *dev = nullptr;
   if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    return Place::kOther;
   }
-  if (at.type == cudaMemoryTypeDevice || (host_ok && at.type == cudaMemoryTypeHost))
-    return static_cast<const float*>(at.devicePointer);
-  return nullptr;
+  *dev = static_cast<float*>(at.devicePointer);
+  if (at.type == cudaMemoryTypeDevice) return Place::kDevice;
+  if (at.type == cudaMemoryTypeHost && *dev) return Place::kPinned;
+  return Place::kOther;
 }
 
 }  // namespace
@@ -1332,7 +1337,9 @@ extern "C" ibm_status ibm_step_host(ibm_ctx* c, const float* x, const float* v, 
         if (e0) cudaEventDestroy(e0);
         return cuda_status(c, e, "ibm_step_host");
       }
+      int* cnt = zeros<int>(c, (3 * (size_t)c->V + kMirrorChunk - 1) / kMirrorChunk);
       for (int k = 0; k < 4; ++k) c->hs_buf[k] = b[k];
+      c->hs_count = cnt;
       c->hcopy = st;
       c->ev_hfork = e0;
       c->ev_hcopy = e1;
@@ -1343,15 +1350,31 @@ extern "C" ibm_status ibm_step_host(ibm_ctx* c, const float* x, const float* v, 
   // inputs: device arrays are used in place; host arrays are copied into the
   // staging arrays by the copy stream while the footprint clear runs (the
   // kernels gather positions by vertex id, which host memory serves poorly)
-  const float* xd = device_view(x, false);
-  const float* vd = device_view(v, false);
-  // outputs: written by the force kernel wherever it can reach them
-  // (device or page-locked host memory); staged and copied back otherwise
-  float* xo = const_cast<float*>(device_view(x_out, true));
-  float* vo = const_cast<float*>(device_view(v_out, true));
+  float *xdv, *vdv, *xodv, *vodv;
+  const Place px = place_of(x, &xdv), pv = place_of(v, &vdv);
+  const Place pxo = place_of(x_out, &xodv), pvo = place_of(v_out, &vodv);
+  const float* xd = px == Place::kDevice ? xdv : nullptr;
+  const float* vd = pv == Place::kDevice ? vdv : nullptr;
+  // outputs: device arrays written in place; page-locked host arrays (both)
+  // mirrored chunk by chunk from the staging arrays by the force kernel,
+  // whole 64-byte lines at a time, while it runs; otherwise staged and copied
+  // back after the step
+  Mirror mirror;
+  float* xo = pxo == Place::kDevice ? xodv : nullptr;
+  float* vo = pvo == Place::kDevice ? vodv : nullptr;
+  if (pxo == Place::kPinned && pvo == Place::kPinned) {
+    mirror.hx = xodv;
+    mirror.hv = vodv;
+    mirror.count = c->hs_count;
+    mirror.vec = ((reinterpret_cast<uintptr_t>(xodv) | reinterpret_cast<uintptr_t>(vodv)) & 15u) == 0;
+  }
   cudaError_t e = cudaSuccess;
+  if (mirror.hx)
+    e = cudaMemsetAsync(c->hs_count, 0,
+                        sizeof(int) * ((3 * (size_t)c->V + kMirrorChunk - 1) / kMirrorChunk),
+                        c->stream);
   cudaEvent_t join = nullptr;
-  if (!xd || !vd) {
+  if (e == cudaSuccess && (!xd || !vd)) {
     e = cudaEventRecord(c->ev_hfork, c->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->hcopy, c->ev_hfork, 0);
     if (e == cudaSuccess && !xd)
@@ -1363,10 +1386,11 @@ extern "C" ibm_status ibm_step_host(ibm_ctx* c, const float* x, const float* v, 
   }
   if (e == cudaSuccess)
     e = step_launches(c, xd ? xd : c->hs_buf[0], vd ? vd : c->hs_buf[1], u, vv, w, p, accel,
-                      xo ? xo : c->hs_buf[2], vo ? vo : c->hs_buf[3], fx, fy, fz, flags, join);
-  if (e == cudaSuccess && !xo)
+                      xo ? xo : c->hs_buf[2], vo ? vo : c->hs_buf[3], fx, fy, fz, flags, join,
+                      mirror.hx ? &mirror : nullptr);
+  if (e == cudaSuccess && !xo && !mirror.hx)
     e = cudaMemcpyAsync(x_out, c->hs_buf[2], bytes, cudaMemcpyDefault, c->stream);
-  if (e == cudaSuccess && !vo)
+  if (e == cudaSuccess && !vo && !mirror.hx)
     e = cudaMemcpyAsync(v_out, c->hs_buf[3], bytes, cudaMemcpyDefault, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return cuda_status(c, e, "ibm_step_host");

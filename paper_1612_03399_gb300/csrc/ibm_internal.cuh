@@ -167,6 +167,17 @@ __device__ __forceinline__ int tiles_along(int f, int n, int T, int (&out)[3]) {
   return k;
 }
 constexpr int kForceThreads = 256;   // threads per force-kernel block
+// host mirror of the node update's outputs (ibm_step_host): the force kernel
+// writes x', v' to device arrays and the last block to complete each chunk of
+// kMirrorChunk entries of the flat [3][V] arrays copies that chunk into host
+// memory in whole lines
+constexpr int kMirrorChunk = 2048;
+struct Mirror {
+  float* hx = nullptr;   // host x' and v' ([3][V]); null: no mirror
+  float* hv = nullptr;
+  int* count = nullptr;  // [ceil(3V / kMirrorChunk)] entries written per chunk (zeroed before)
+  int vec = 0;           // both host arrays 16-byte aligned
+};
 constexpr uint16_t kNone = 0xFFFF;
 
 // error word bits (device)
@@ -316,6 +327,7 @@ struct ibm_ctx {
   float* hs_buf[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t hcopy = nullptr;
   cudaEvent_t ev_hfork = nullptr, ev_hcopy = nullptr;
+  int* hs_count = nullptr;      // the host mirror's per-chunk counters
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t stream = nullptr;
   std::string err;
@@ -388,7 +400,8 @@ cudaError_t tile_spread_occupancy(int* blocks_per_sm);
 cudaError_t zero_body_sums(ibm_ctx* c);
 cudaError_t launch_measure_finalize(ibm_ctx* c);
 cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float* Fext,
-                         float* Fint, float* x_out, float* v_out, double* energy, bool advance);
+                         float* Fint, float* x_out, float* v_out, double* energy, bool advance,
+                         const Mirror* mirror = nullptr);
 cudaError_t launch_advance(ibm_ctx* c, const float* x, const float* v, const float* Fint,
                            const float* Fext, float* x_out, float* v_out);
 // a = (F_int + F_ext^v)/m at x (zero on clamped nodes), from per-face F_ext

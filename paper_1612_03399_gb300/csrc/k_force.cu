@@ -49,13 +49,67 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 
+// Host mirror of x', v' (one block, after its own vertices' writes): count
+// this block's entries into the chunks of the flat [3][V] arrays they fall in;
+// the block whose entries complete a chunk copies the whole chunk, written by
+// whichever blocks, into host memory with contiguous (vector) stores.  Each
+// block fences its writes before it counts, and the copying block reads
+// through L2, so it sees every block's writes to the chunk.  No block waits.
+__device__ __noinline__ void mirror_chunks(Mirror m, const float* x_out, const float* v_out,
+                                           int32_t V, int gv0, int n_own) {
+  // a run of at most 2048 own vertices (the patch-size limit, which is
+  // kMirrorChunk) meets at most two chunks per component
+  __shared__ int s_done[6];
+  __threadfence();
+  __syncthreads();
+  const long long total = 3ll * V;
+  if (threadIdx.x < 6) {
+    // thread 2 d + j: component d, the j-th chunk its run of own vertices meets
+    const int d = threadIdx.x >> 1, j = threadIdx.x & 1;
+    const long long f0 = (long long)d * V + gv0, f1 = f0 + n_own;   // [f0, f1)
+    const long long k = f0 / kMirrorChunk + j;
+    int done = -1;
+    if (n_own > 0 && k * kMirrorChunk < f1) {
+      const long long lo = max(f0, k * kMirrorChunk), hi = min(f1, (k + 1) * kMirrorChunk);
+      const int n = (int)(hi - lo);
+      const int len = (int)min((long long)kMirrorChunk, total - k * kMirrorChunk);
+      if (atomicAdd(m.count + k, n) + n == len) done = (int)k;
+    }
+    s_done[threadIdx.x] = done;
+  }
+  __syncthreads();
+  for (int t = 0; t < 6; ++t) {
+    const int k = s_done[t];
+    if (k < 0) continue;   // uniform over the block
+    __threadfence();
+    const long long b0 = (long long)k * kMirrorChunk;
+    const int len = (int)min((long long)kMirrorChunk, total - b0);
+    if (m.vec && (len & 3) == 0) {
+      const float4* sx = reinterpret_cast<const float4*>(x_out + b0);
+      const float4* sv = reinterpret_cast<const float4*>(v_out + b0);
+      float4* dx = reinterpret_cast<float4*>(m.hx + b0);
+      float4* dv = reinterpret_cast<float4*>(m.hv + b0);
+      for (int q = threadIdx.x; q < len / 4; q += blockDim.x) {
+        dx[q] = __ldcg(sx + q);
+        dv[q] = __ldcg(sv + q);
+      }
+    } else {
+      for (int q = threadIdx.x; q < len; q += blockDim.x) {
+        m.hx[b0 + q] = __ldcg(x_out + b0 + q);
+        m.hv[b0 + q] = __ldcg(v_out + b0 + q);
+      }
+    }
+  }
+}
+
 // MODE 0: F_int only; 1: F_int + F_ext^v and the node update; 2: the
 // acceleration (F_int + F_ext^v)/m, zero on clamped nodes, into Fint
 template <int MODE>
 __global__ void __launch_bounds__(kForceThreads) force_kernel(
     DeviceTables T, StepConsts sc, int32_t V, int32_t F, const float* __restrict__ x,
     const float* __restrict__ v, const float* __restrict__ Fext, float* __restrict__ Fint,
-    float* __restrict__ x_out, float* __restrict__ v_out, double* __restrict__ energy) {
+    float* __restrict__ x_out, float* __restrict__ v_out, double* __restrict__ energy,
+    Mirror mirror) {
   extern __shared__ __align__(16) float sm[];
   __shared__ __align__(8) unsigned long long bar;
   const int2 wk = T.work[blockIdx.x];
@@ -248,6 +302,7 @@ __global__ void __launch_bounds__(kForceThreads) force_kernel(
       v_out[gv] = vx; v_out[V + gv] = vy; v_out[2 * V + gv] = vz;
     }
   }
+  if (MODE == 1 && mirror.hx) mirror_chunks(mirror, x_out, v_out, V, B.v_off + P.own0, P.n_own);
 
   if (want_e) {
     __shared__ double red[3][kForceThreads / 32];
@@ -333,7 +388,8 @@ __global__ void __launch_bounds__(kForceThreads) advance_kernel(
 // as usual, when it has completed.
 template <int MODE>
 cudaError_t launch_force_mode(ibm_ctx* c, const float* x, const float* v, const float* Fext,
-                              float* Fint, float* x_out, float* v_out, double* energy) {
+                              float* Fint, float* x_out, float* v_out, double* energy,
+                              const Mirror& mirror = Mirror()) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)c->n_work);
   cfg.blockDim = dim3(kForceThreads);
@@ -345,13 +401,15 @@ cudaError_t launch_force_mode(ibm_ctx* c, const float* x, const float* v, const 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, force_kernel<MODE>, c->d, c->sc, (int32_t)c->V, (int32_t)c->F,
-                            x, v, Fext, Fint, x_out, v_out, energy);
+                            x, v, Fext, Fint, x_out, v_out, energy, mirror);
 }
 
 cudaError_t launch_force(ibm_ctx* c, const float* x, const float* v, const float* Fext,
-                         float* Fint, float* x_out, float* v_out, double* energy, bool advance) {
+                         float* Fint, float* x_out, float* v_out, double* energy, bool advance,
+                         const Mirror* mirror) {
   if (c->n_work == 0) return cudaSuccess;
-  return advance ? launch_force_mode<1>(c, x, v, Fext, Fint, x_out, v_out, energy)
+  return advance ? launch_force_mode<1>(c, x, v, Fext, Fint, x_out, v_out, energy,
+                                        mirror ? *mirror : Mirror())
                  : launch_force_mode<0>(c, x, v, Fext, Fint, x_out, v_out, energy);
 }
 

@@ -7,6 +7,7 @@ import pytest
 import torch
 
 from paper_1612_03399_gb300 import _lib
+from paper_1612_03399_gb300 import workloads as W
 
 import helpers as H
 from test_gpu_parity import mixed_workload
@@ -63,6 +64,28 @@ def test_host_step_matches_device_step(variant, where_in, where_out):
     a.check_device_error()
     b.check_device_error()
     assert_fields(fa, fb, variant)
+
+
+@pytest.mark.parametrize("patch", [96, 224])
+def test_host_step_many_mirror_chunks(patch):
+    """40 drops: the outputs span 38 chunks of the host mirror, and the runs
+    of own vertices of the force patches straddle chunk boundaries."""
+    wl = W.batched_drops(40, 3, 128, seed=3)
+    fields = W.sample_field(wl.field, wl.grid, device=DEV, dtype=torch.float32)
+    a = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha, patch_size=patch)
+    b = _lib.Context(wl.bodies, wl.grid, dt=wl.dt, mu=wl.mu, alpha=wl.alpha, patch_size=patch)
+    x, v = a.init_state()
+    fa, fb = zero_fields(wl), zero_fields(wl)
+    xh, vh = x.cpu().pin_memory(), v.cpu().pin_memory()
+    for _ in range(STEPS):
+        x1, v1 = torch.empty_like(x), torch.empty_like(v)
+        a.step(x, v, fields, x1, v1, fa)
+        xo, vo = torch.empty_like(xh).pin_memory(), torch.empty_like(vh).pin_memory()
+        b.step_host(xh, vh, fields, xo, vo, fb)
+        assert torch.equal(xo.to(DEV), x1) and torch.equal(vo.to(DEV), v1)
+        x, v, xh, vh = x1, v1, xo, vo
+    b.check_device_error()
+    assert_fields(fa, fb, 1)
 
 
 def test_host_step_refuses_aliased_outputs():
