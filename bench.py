@@ -901,7 +901,8 @@ def run_coupled(args, ws, rank, local):
                                                      b.rest[b.tri[:, 2]] - b.rest[b.tri[:, 0]]),
                                             axis=1).max()) / 2 for b in wl.bodies) / hm ** 2
     ctx = _lib.Context(wl.bodies, wl.grid, dt=dt, mu=COUPLED_NU, alpha=wl.alpha,
-                       patch_size=args.patch if args.patch else 256, device=local)
+                       patch_size=args.patch if args.patch else 256, device=local,
+                       marker_patch=args.marker_patch)
     flow = _lib.Flow(wl.grid, nu=COUPLED_NU, dt=dt, device=local)
     stream = torch.cuda.current_stream(device)
     u = tuple(t.clone() for t in fields)
@@ -998,7 +999,7 @@ def run_coupled(args, ws, rank, local):
         "cell_steps_per_s": cells,
         "config": {"workload": descr + f"; flow solved: dt {dt:.3g} (CFL {COUPLED_CFL} of the "
                    "initial field), nu = mu = 0.01, p0 = 0",
-                   "viscous_solve_widths": list(widths),
+                   "viscous_solve_widths": list(widths), "marker_patch": ctx.marker_patch,
                    "bodies": ctx.B, "vertices": ctx.V, "faces": ctx.F, "grid": list(wl.grid.n),
                    "max_face_area_h2": max_face_h2,
                    "l2": "flushed between timed steps (256 MiB write); fields of 64 MiB each",
