@@ -38,6 +38,25 @@
 namespace ibm {
 namespace {
 
+// The global-memory path of a marker block whose footprint does not fit its
+// shared memory (rare): out of line, so that it does not crowd the
+// instruction cache of the staged path it sits beside.
+__device__ __noinline__ float value_global(const float* f, Grid g, int c0, int c1, int c2, DirW X,
+                                          DirW Y, DirW Z) {
+  const int c[3] = {c0, c1, c2};
+  return mls_value(f, GlobalRows{g}.at(c), X, Y, Z);
+}
+__device__ __noinline__ float3 gradient_global(const float* f, Grid g, ProbeW P, float sgn) {
+  float gr[3] = {0.f, 0.f, 0.f};
+  P.add_gradient(f, GlobalRows{g}, g.invh, sgn, gr);
+  return make_float3(gr[0], gr[1], gr[2]);
+}
+__device__ __noinline__ void spread_global(float* f, Grid g, int c0, int c1, int c2, DirW X,
+                                           DirW Y, DirW Z, float coef) {
+  const int c[3] = {c0, c1, c2};
+  mls_spread(f, GlobalRows{g}.at(c), X, Y, Z, coef);
+}
+
 
 // REC (record mode): instead of spreading, write each marker's spread record
 // (centroid in cells, c_l F) and count it under the tiles of the tile-owned
@@ -438,7 +457,6 @@ __global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
   }
   const RowTable RT{s_gofs, g.n[0], vec4};
   const StagedRows SR{s_xmin, ylo, zlo, sy};
-  const GlobalRows GR{g};
   const int ngroups = fit ? N / 4 : 0;
 
   // ---- velocity: interpolation at the centroid, gradient at the probes -----
@@ -494,7 +512,8 @@ __global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
           dir_weights(t3[0], sc.kappa, X);
           dir_weights(t3[1], sc.kappa, Y);
           dir_weights(t3[2], sc.kappa, Z);
-          const float ps = fit ? mls_value(buf, SR.at(cc), X, Y, Z) : mls_value(pr, GR.at(cc), X, Y, Z);
+          const float ps = fit ? mls_value(buf, SR.at(cc), X, Y, Z)
+                               : value_global(pr, g, cc[0], cc[1], cc[2], X, Y, Z);
           Pj += (l == 0 ? 1.f : -1.f) * ps + sc.probe_h * an;
         }
       } else if (mine) {
@@ -503,13 +522,25 @@ __global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
           float gr[3] = {0.f, 0.f, 0.f};
           ProbeW P0;
           P0.prepare(tp, comp, B.G, sc.kappa);
-          if (fit) P0.add_gradient(buf, SR, g.invh, 1.f, gr);
-          else P0.add_gradient(velc, GR, g.invh, 1.f, gr);
+          if (fit) {
+            P0.add_gradient(buf, SR, g.invh, 1.f, gr);
+          } else {
+            const float3 q = gradient_global(velc, g, P0, 1.f);
+            gr[0] += q.x;
+            gr[1] += q.y;
+            gr[2] += q.z;
+          }
           if (two) {
             ProbeW P1;
             P1.prepare(tm, comp, B.G, sc.kappa);
-            if (fit) P1.add_gradient(buf, SR, g.invh, -1.f, gr);
-            else P1.add_gradient(velc, GR, g.invh, -1.f, gr);
+            if (fit) {
+              P1.add_gradient(buf, SR, g.invh, -1.f, gr);
+            } else {
+              const float3 q = gradient_global(velc, g, P1, -1.f);
+              gr[0] += q.x;
+              gr[1] += q.y;
+              gr[2] += q.z;
+            }
           }
           const float gn = gr[0] * nrm[0] + gr[1] * nrm[1] + gr[2] * nrm[2];
           const float ni = comp == 0 ? nrm[0] : (comp == 1 ? nrm[1] : nrm[2]);
@@ -521,7 +552,7 @@ __global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
         }
         if (INTERP) {
           const float Ul = fit ? mls_value(buf, SR.at(ccC), CX, CY, CZ)
-                               : mls_value(velc, GR.at(ccC), CX, CY, CZ);
+                               : value_global(velc, g, ccC[0], ccC[1], ccC[2], CX, CY, CZ);
           const float Fc = ((comp == 0 ? vb[0] : (comp == 1 ? vb[1] : vb[2])) - Ul) * sc.inv_dt;
           if (comp == 0) Fl[0] = Fc;
           if (comp == 1) Fl[1] = Fc;
@@ -658,7 +689,8 @@ __global__ void __launch_bounds__(MT, 512 / MT) marker_kernel(
           if (mine && coef != 0.f)
             mls_spread_fixed1(j == 0 ? accA : accB, SR.at(cc), X, Y, Z, coef * pow2f(max(k, -126)));
         } else if (mine) {
-          mls_spread(comp == 0 ? fx : (comp == 1 ? fy : fz), GR.at(cc), X, Y, Z, coef);
+          spread_global(comp == 0 ? fx : (comp == 1 ? fy : fz), g, cc[0], cc[1], cc[2], X, Y, Z,
+                        coef);
         }
       }
       if (fit) {
