@@ -229,7 +229,9 @@ ibm_status ibm_step(ibm_ctx* ctx, const float* x, const float* v, const float* u
  * outputs through the context's device arrays and a copy.  Synchronous:
  * returns when x_out, v_out hold the new state.  The first call allocates
  * the context's copies of the state (4 [3][V] float arrays), a stream and two
- * events.  Errors as ibm_step. */
+ * events.  Errors as ibm_step; like ibm_step it leaves the device error word
+ * to ibm_check_device_error (after a kernel has flagged an error, x_out and
+ * v_out may be incomplete). */
 ibm_status ibm_step_host(ibm_ctx* ctx, const float* x, const float* v, const float* u,
                          const float* vv, const float* w, const float* p, const float* accel,
                          float* x_out, float* v_out, float* fx, float* fy, float* fz,
