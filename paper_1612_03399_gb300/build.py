@@ -61,15 +61,41 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments and with runs of white space
+    collapsed (string literals kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_digest(key: str) -> str:
-    """Digest of the sources and flags one profiled kernel is built from
-    (independent of where the repository lives: the include path is left
-    out of the flags)."""
+    """Digest of the code and flags one profiled kernel is built from:
+    comments and layout do not count, and neither does where the repository
+    lives (the include path is left out of the flags)."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[key] + ["../../include/ibm.h"]:
         p = os.path.normpath(os.path.join(CSRC, name))
         h.update(name.encode())
-        h.update(open(p, "rb").read())
+        with open(p, encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     flags = [f for i, f in enumerate(FLAGS) if f != "-I" and (i == 0 or FLAGS[i - 1] != "-I")]
     h.update(" ".join(ARCH + flags).encode())
     return h.hexdigest()
